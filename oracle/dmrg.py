@@ -1,0 +1,227 @@
+"""Two-site DMRG for the GBS parent Hamiltonian -- oracle (test infrastructure only).
+
+The paper solves min <H> over matrix product states (Eq. MPSAnsatz, open boundaries)
+with DMRG (Sec. "Matrix Product States"; single-site DMRG via quimb in Sec. "Results").
+This restatement is the two-site variant, step by step in plain numpy:
+
+* MPS tensors A[s] with shape (chi_s, d, chi_{s+1}); chi_0 = chi_N = 1.
+* environments L[s] (sites 0..s-1) with index order (channel, bra, ket) and
+  R[s] (sites s..N-1) with index order (channel, ket, bra); L[0] = R[N] = 1.
+* two-site effective Hamiltonian product (the contraction
+  Y = sum L W_i W_{i+1} Theta R written out as one einsum),
+* Lanczos with full re-orthogonalisation (classical Gram-Schmidt, two passes) and
+  explicit restarts; the Ritz pair of the tridiagonal matrix by scipy's
+  ``eigh_tridiagonal`` (library primitive),
+* truncation by the eigendecomposition of the reduced density matrix (library
+  ``eigh``), keeping k = min(chi, chi_l d, d chi_r) largest eigenpairs -- the squared
+  Schmidt values of Eq. SurrogateEpsChi -- and reporting the discarded weight,
+* energy <psi|H|psi>/<psi|psi> (Eq. MagOfSimError) by a full left-to-right contraction.
+
+Readings where the paper is silent (recorded in the design notes): Lanczos tolerance,
+restart rule, initial state (Philox Gaussian entries, rows orthonormalised in order so
+the initial MPS is right-canonical), sweep order (all N-1 bonds left-to-right, then all
+N-1 bonds right-to-left), and chi schedule (Discussion: chi grown from O(1)).
+
+Parity: pinned at the plain workload by the dense exact ground state (chi = d^2 makes
+the MPS exact), by the product-state special case U = I, and by E >= 0.
+"""
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.linalg as sla
+
+from . import philox
+
+
+def bond_dims(N, d, chi):
+    """chi_s = min(chi, d^s, d^(N-s)) for the cuts s = 0..N (Python integers, no overflow)."""
+    return [int(min(chi, d ** s, d ** (N - s))) for s in range(N + 1)]
+
+
+def orthonormal_rows(M):
+    """Gram-Schmidt of the rows of M in order (equivalently the Q factor of the LQ
+    decomposition with a positive diagonal)."""
+    Q, R = np.linalg.qr(M.conj().T)
+    ph = np.diag(R).copy()
+    ph = np.where(np.abs(ph) > 0, ph / np.abs(ph), 1.0)
+    Q = Q * ph[None, :]
+    return Q.conj().T
+
+
+def initial_mps(N, d, chi0, seed):
+    dims = bond_dims(N, d, chi0)
+    mps = []
+    for s in range(N):
+        cl, cr = dims[s], dims[s + 1]
+        z = philox.complex_normals(seed, s, cl * d * cr).reshape(cl, d * cr)
+        mps.append(orthonormal_rows(z).reshape(cl, d, cr))
+    return mps
+
+
+# ---------------------------------------------------------------- contractions
+def env_left(L, A, W):
+    """L'[b, l, k] = sum conj(A[i,t,l]) L[a,i,j] W[a,b,t,s] A[j,s,k]."""
+    return np.einsum("itl,aij,abts,jsk->blk", A.conj(), L, W, A, optimize=True)
+
+
+def env_right(R, A, W):
+    """R'[b, j, i] = sum W[b,c,t,s] A[j,s,g] conj(A[i,t,p]) R[c,g,p]."""
+    return np.einsum("bcts,jsg,itp,cgp->bji", W, A, A.conj(), R, optimize=True)
+
+
+def heff_apply(L, W1, W2, R, theta):
+    """Y[i,t,u,l] = sum L[a,i,j] W1[a,b,t,s] W2[b,c,u,v] theta[j,s,v,k] R[c,k,l]."""
+    return np.einsum("aij,abts,bcuv,jsvk,ckl->itul", L, W1, W2, theta, R, optimize=True)
+
+
+# ---------------------------------------------------------------- Lanczos
+@dataclass
+class LanczosParams:
+    krylov_max: int = 32
+    max_restarts: int = 4
+    tol: float = 1e-10          # absolute residual ||H x - theta x||
+    breakdown: float = 1e-14
+
+
+def lanczos_lowest(matvec, x0, p: LanczosParams):
+    """Lowest eigenpair of a Hermitian operator.  Returns (theta, x, n_matvec, converged)."""
+    v = x0 / np.linalg.norm(x0)
+    n_mv = 0
+    theta, x, converged = None, v, False
+    for _ in range(p.max_restarts + 1):
+        V = [v]
+        alpha, beta = [], []
+        resid = np.inf
+        for j in range(p.krylov_max):
+            w = matvec(V[j])
+            n_mv += 1
+            Vm = np.array(V)
+            c = Vm.conj() @ w
+            alpha.append(float(c[j].real))
+            w = w - Vm.T @ c
+            c2 = Vm.conj() @ w
+            w = w - Vm.T @ c2
+            b = float(np.linalg.norm(w))
+            if j == 0:
+                th, y = np.array([alpha[0]]), np.ones((1, 1))
+            else:
+                th, y = sla.eigh_tridiagonal(np.array(alpha), np.array(beta),
+                                             select="i", select_range=(0, 0))
+            theta, ycol = float(th[0]), y[:, 0]
+            resid = b * abs(ycol[-1])
+            if resid <= p.tol or b <= p.breakdown or j == p.krylov_max - 1:
+                break
+            beta.append(b)
+            V.append(w / b)
+        Vm = np.array(V)
+        x = Vm.T @ ycol
+        x = x / np.linalg.norm(x)
+        v = x
+        if resid <= p.tol or b <= p.breakdown:
+            converged = True
+            break
+    return theta, x, n_mv, converged
+
+
+# ---------------------------------------------------------------- truncation
+def truncate(theta, direction, chi_max):
+    """Split a two-site tensor (chi_l, d, d, chi_r).  direction 'right': returns
+    (A_left_canonical, centre, kept_eigs, discarded); 'left': (centre, B_right_canonical,
+    kept_eigs, discarded)."""
+    cl, d1, d2, cr = theta.shape
+    Tm = theta.reshape(cl * d1, d2 * cr)
+    nL, nR = Tm.shape
+    k = min(chi_max, nL, nR)
+    if direction == "right":
+        rho = Tm @ Tm.conj().T
+        w, U = np.linalg.eigh(rho)
+        total = float(np.real(np.trace(rho)))
+        w, U = w[::-1][:k], U[:, ::-1][:, :k]
+        A = U.reshape(cl, d1, k)
+        C = (U.conj().T @ Tm).reshape(k, d2, cr)
+        return A, C, w, 1.0 - float(np.sum(w)) / total
+    rho = Tm.conj().T @ Tm
+    w, V = np.linalg.eigh(rho)
+    total = float(np.real(np.trace(rho)))
+    w, V = w[::-1][:k], V[:, ::-1][:, :k]
+    B = V.conj().T.reshape(k, d2, cr)
+    C = (Tm @ V).reshape(cl, d1, k)
+    return C, B, w, 1.0 - float(np.sum(w)) / total
+
+
+# ---------------------------------------------------------------- energy
+def norm2(mps):
+    E = np.ones((1, 1), dtype=np.complex128)
+    for A in mps:
+        E = np.einsum("ij,isk,jsl->kl", E, A.conj(), A, optimize=True)
+    return float(E[0, 0].real)
+
+
+def energy(mps, cores):
+    """<psi|H|psi>/<psi|psi> by a full left-to-right environment contraction."""
+    L = np.ones((1, 1, 1), dtype=np.complex128)
+    for A, W in zip(mps, cores):
+        L = env_left(L, A, W)
+    return float(L[0, 0, 0].real) / norm2(mps)
+
+
+# ---------------------------------------------------------------- sweeps
+@dataclass
+class SweepReport:
+    energies: list = field(default_factory=list)
+    max_discarded: list = field(default_factory=list)
+    matvecs: int = 0
+    not_converged: int = 0
+
+
+def dmrg(cores, d, chi_max, n_sweeps, seed, chi_schedule=(), lanczos=None,
+         e_tol=0.0, e_target=None, mps=None, max_bonds=None):
+    """Two-site DMRG sweeps.  Returns (mps, report).  ``max_bonds`` stops after that
+    many bond optimisations (used only to time a bounded sample)."""
+    N = len(cores)
+    p = lanczos or LanczosParams()
+    sched = list(chi_schedule) if chi_schedule else [chi_max]
+    if mps is None:
+        mps = initial_mps(N, d, sched[0], seed)
+    mps = [A.copy() for A in mps]
+    Lenv = [None] * (N + 1)
+    Renv = [None] * (N + 1)
+    Lenv[0] = np.ones((1, 1, 1), dtype=np.complex128)
+    Renv[N] = np.ones((1, 1, 1), dtype=np.complex128)
+    for s in range(N - 1, 0, -1):
+        Renv[s] = env_right(Renv[s + 1], mps[s], cores[s])
+    rep = SweepReport()
+    bonds_done = 0
+    prev = None
+    for sweep in range(n_sweeps):
+        chi_s = sched[min(sweep, len(sched) - 1)]
+        disc_max = 0.0
+        for direction, bonds in (("right", range(0, N - 1)), ("left", range(N - 2, -1, -1))):
+            for i in bonds:
+                theta = np.einsum("asb,btc->astc", mps[i], mps[i + 1])
+                shape = theta.shape
+                L, R, W1, W2 = Lenv[i], Renv[i + 2], cores[i], cores[i + 1]
+                mv = lambda x: heff_apply(L, W1, W2, R, x.reshape(shape)).reshape(-1)
+                _, x, nmv, conv = lanczos_lowest(mv, theta.reshape(-1), p)
+                rep.matvecs += nmv
+                rep.not_converged += 0 if conv else 1
+                theta = x.reshape(shape)
+                left, right, _, disc = truncate(theta, direction, chi_s)
+                disc_max = max(disc_max, disc)
+                mps[i], mps[i + 1] = left, right
+                if direction == "right":
+                    Lenv[i + 1] = env_left(Lenv[i], mps[i], cores[i])
+                else:
+                    Renv[i + 1] = env_right(Renv[i + 2], mps[i + 1], cores[i + 1])
+                bonds_done += 1
+                if max_bonds is not None and bonds_done >= max_bonds:
+                    return mps, rep
+        E = energy(mps, cores)
+        rep.energies.append(E)
+        rep.max_discarded.append(disc_max)
+        if e_target is not None and E <= e_target:
+            break
+        if prev is not None and e_tol > 0 and abs(E - prev) <= e_tol:
+            break
+        prev = E
+    return mps, rep

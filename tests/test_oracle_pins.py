@@ -1,0 +1,376 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Every test here runs on the CPU (no GPU marker).  Each pin is chosen so that a
+plausible mistake in the oracle (a dropped term, a wrong sign or index, a transposed
+operand) fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.stats
+
+from oracle import dense, dmrg, gbs, mpo, observables, philox
+from paper_2410_18740_gb300 import inputs
+from tests.conftest import GOLDEN
+
+
+# ------------------------------------------------------------------ Philox
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = philox.philox4x32_10(np.array(v[0:4], dtype=np.uint64), np.array(v[4:6], dtype=np.uint64))
+        assert [int(x) for x in out] == v[6:10]
+
+
+def test_philox_uniform_range_and_moments():
+    u = philox.sample_uniforms(7, np.arange(200000, dtype=np.uint64), 3)
+    assert u.min() >= 0.0 and u.max() < 1.0
+    assert abs(u.mean() - 0.5) < 3e-3 and abs(u.var() - 1 / 12) < 3e-3
+
+
+# ------------------------------------------------------------------ covariance, G
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_covariance_invariants(seed):
+    w = inputs.workload("plain", seed, M=5)
+    V = gbs.covariance(w.r, w.U)
+    G = gbs.hamiltonian_coefficients(w.r, w.U)
+    N = w.M
+    # trace: tr V = sum cosh 2r (invariant under the passive interferometer)
+    assert abs(np.trace(V) - np.sum(np.cosh(2 * w.r))) < 1e-12
+    # Fock-basis mean photon number sum <n_i> = tr V / 2 - N/2 = sum sinh^2 r
+    assert abs(0.5 * np.trace(V) - N / 2 - np.sum(np.sinh(w.r) ** 2)) < 1e-12
+    # pure state: 2V is symplectic
+    Om = np.block([[np.zeros((N, N)), np.eye(N)], [-np.eye(N), np.zeros((N, N))]])
+    assert np.abs((2 * V) @ Om @ (2 * V).T - Om).max() < 1e-12
+    # G = V^{-1}/4 equals the closed form 1/2 O diag(e^{2r}, e^{-2r}) O^T (different route)
+    O = gbs.quadrature_orthogonal(w.U)
+    Gc = 0.5 * O @ np.diag(np.concatenate([np.exp(2 * w.r), np.exp(-2 * w.r)])) @ O.T
+    assert np.abs(G - Gc).max() < 1e-12
+    assert abs(np.max(np.linalg.eigvalsh(G)) - 0.5 * np.exp(2 * np.max(w.r))) < 1e-12
+
+
+# ------------------------------------------------------------------ local operators
+@pytest.mark.parametrize("d", [2, 3, 4, 6, 9])
+def test_local_ops_exact_projection(d):
+    ops = gbs.local_ops(d)
+    n = np.arange(d)
+    assert np.abs(ops["X2"] + ops["P2"] - np.diag(2 * n + 1.0)).max() < 1e-13
+    # exactly projected X^2 differs from (P X P)^2 only at (d-1, d-1) (SM Sec. 5)
+    diff = ops["X2"] - ops["X"] @ ops["X"]
+    mask = np.ones((d, d), bool)
+    mask[d - 1, d - 1] = False
+    assert np.abs(diff[mask]).max() < 1e-13
+    assert abs(diff[d - 1, d - 1] - d / 2.0) < 1e-13
+    # XP + PX = i (a^dag^2 - a^2): entries -+ i sqrt((n+1)(n+2))
+    for m in range(d - 2):
+        v = math.sqrt((m + 1) * (m + 2))
+        assert abs(ops["XPPX"][m, m + 2] + 1j * v) < 1e-13
+        assert abs(ops["XPPX"][m + 2, m] - 1j * v) < 1e-13
+    assert np.abs(ops["XPPX"] - ops["XPPX"].conj().T).max() < 1e-14
+
+
+def test_commutator_defect_golden():
+    for line in open(os.path.join(GOLDEN, "commutator_defect.txt")):
+        if not line.strip() or line.startswith("#"):
+            continue
+        vals = [int(x) for x in line.split()]
+        d, diag = vals[0], np.array(vals[1:], dtype=float)
+        ops = gbs.local_ops(d)
+        C = ops["X"] @ ops["P"] - ops["P"] @ ops["X"]
+        assert np.abs(C - 1j * np.diag(diag)).max() < 1e-13
+
+
+# ------------------------------------------------------------------ optimal local basis
+@pytest.mark.parametrize("seed", [3, 4])
+def test_williamson_and_rotated_blocks(seed):
+    w = inputs.workload("large", seed, M=6)
+    S_list, nu, Grot = gbs.lbo_transform(w.r, w.U)
+    V = gbs.covariance(w.r, w.U)
+    N = w.M
+    for i, S in enumerate(S_list):
+        Vi = gbs.reduced_covariance(V, i)
+        assert abs(np.linalg.det(S) - 1.0) < 1e-12
+        assert np.abs(S @ (nu[i] * np.eye(2)) @ S.T - Vi).max() < 1e-12
+    # (4 G')^{-1} is the rotated covariance with nu_i I diagonal blocks (text after Eq. WilliamsonDecomposition)
+    Vrot = np.linalg.inv(4 * Grot)
+    for i in range(N):
+        blk = gbs.reduced_covariance(Vrot, i)
+        assert np.abs(blk - nu[i] * np.eye(2)).max() < 1e-11
+    # nu_i >= 1/2, and the thermal occupation is at most the Fock occupation
+    nfock = 0.5 * (np.diag(V)[:N] + np.diag(V)[N:]) - 0.5
+    assert np.all(nu >= 0.5 - 1e-12) and np.all(nu - 0.5 <= nfock + 1e-12)
+
+
+@pytest.mark.parametrize("seed", [5, 6])
+def test_lbo_isometry(seed):
+    """Eq. Effectivecutoff: V^dagger V -> I_d as the Fock cutoff D grows; at D = 100 it
+    holds to 1e-10 for the squeezing of the large workload (at D = 24 it need not: the
+    cutoff can lie below the effective cutoff, and the lost tail is what marginals miss)."""
+    w = inputs.workload("large", seed, M=3)
+    S_list, nu, _ = gbs.lbo_transform(w.r, w.U)
+    d = 6
+    for S in S_list:
+        errs = []
+        for D in (24, 40, 100):
+            Viso = gbs.lbo_isometry(S, D, d)
+            G = Viso.conj().T @ Viso
+            errs.append(np.abs(G - np.eye(d)).max())
+            # the deficit is a loss of norm only: the Gram matrix stays <= I
+            assert np.max(np.linalg.eigvalsh(G)) <= 1 + 1e-12
+        assert errs[2] < 1e-10
+        assert errs[0] + 1e-15 >= errs[1] >= errs[2] - 1e-15
+
+
+def test_lbo_isometry_squeezed_vacuum_statistics():
+    w = inputs.workload("large", 11, M=3)
+    S_list, _, _ = gbs.lbo_transform(w.r, w.U)
+    D = 40
+    for S in S_list:
+        Viso = gbs.lbo_isometry(S, D, 4)
+        r_loc = math.log(np.max(np.linalg.eigvalsh(S)))
+        t = math.tanh(r_loc)
+        p = np.abs(Viso[:, 0]) ** 2
+        for k in range(D):
+            if k % 2:
+                assert p[k] < 1e-24
+            else:
+                m = k // 2
+                exact = math.factorial(2 * m) / (4 ** m * math.factorial(m) ** 2) * t ** (2 * m) / math.cosh(r_loc)
+                assert abs(p[k] - exact) < 1e-12
+        # covariance of S^dagger|0> equals S S^T / 2
+        Db = 120
+        ops = gbs.local_ops(Db)
+        c = gbs.lbo_isometry(S, Db, 1)[:, 0]
+        cov = np.array([[np.vdot(c, ops["X2"] @ c).real, 0.5 * np.vdot(c, ops["XPPX"] @ c).real],
+                        [0.0, np.vdot(c, ops["P2"] @ c).real]])
+        cov[1, 0] = cov[0, 1]
+        assert np.abs(cov - 0.5 * S @ S.T).max() < 1e-10
+
+
+def test_truncation_bound_eps_le_epsD_le_Neps():
+    """Eq. SpecWfromSDsums: eps <= eps_D <= N eps, eps_D from the (large-cutoff) ground
+    state in the optimal local basis."""
+    for seed in (20, 21):
+        w = inputs.workload("plain", seed, M=3, r_lo=0.4, r_hi=0.9)
+        _, nu, Grot = gbs.lbo_transform(w.r, w.U)
+        dbig = 12
+        e0, v0 = dense.ground_state(Grot, dbig)
+        assert e0[0] < 1e-5          # cutoff 12 leaves ~1e-6 of the state out; tolerances below
+        psi = v0[:, 0].reshape((dbig,) * 3)
+        for d in (2, 3, 4):
+            epsD = 1.0 - np.sum(np.abs(psi[:d, :d, :d]) ** 2)
+            eps = gbs.truncation_epsilon(nu, d)
+            assert eps <= epsD + 1e-5
+            assert epsD <= 3 * eps + 1e-5
+            assert epsD > 1.5 * eps     # neither bound is trivially saturated here
+
+
+def test_lbo_reduced_density_is_thermal():
+    """In the optimal local basis the single-mode reduced density matrix is diagonal with
+    weights nbar^k/(nbar+1)^(k+1) (Eq. diagReducedGaussianDM)."""
+    w = inputs.workload("plain", 30, M=2, r_lo=0.3, r_hi=0.6)
+    _, nu, Grot = gbs.lbo_transform(w.r, w.U)
+    dbig = 24
+    _, v0 = dense.ground_state(Grot, dbig)
+    psi = v0[:, 0].reshape(dbig, dbig)
+    rho0 = psi @ psi.conj().T
+    nbar = nu[0] - 0.5
+    k = np.arange(8)
+    thermal = nbar ** k / (nbar + 1) ** (k + 1)
+    assert np.abs(np.diag(rho0)[:8].real - thermal).max() < 1e-8
+    off = rho0[:8, :8] - np.diag(np.diag(rho0[:8, :8]))
+    assert np.abs(off).max() < 1e-8
+
+
+# ------------------------------------------------------------------ MPO vs dense
+@pytest.mark.parametrize("seed,M,d", [(0, 3, 3), (1, 4, 3), (2, 3, 4)])
+def test_mpo_contracts_to_dense_hamiltonian(seed, M, d):
+    w = inputs.workload("plain", seed, M=M)
+    G = gbs.hamiltonian_coefficients(w.r, w.U)
+    H1 = mpo.contract_dense(mpo.build_mpo(G, d))
+    H2 = dense.dense_hamiltonian(G, d).toarray()
+    assert np.abs(H1 - H2).max() < 1e-12
+    assert np.abs(H1 - H1.conj().T).max() < 1e-12
+
+
+# ------------------------------------------------------------------ hafnian amplitudes
+def test_hafnian_closed_forms():
+    for m in range(1, 6):
+        assert abs(dense.hafnian(np.ones((2 * m, 2 * m))) - math.prod(range(1, 2 * m, 2))) < 1e-9
+    A = np.array([[0, 2.0], [2.0, 0]])
+    assert abs(dense.hafnian(A) - 2.0) < 1e-15
+    rng = np.random.default_rng(0)
+    B = rng.standard_normal((4, 4)); B = B + B.T
+    expect = B[0, 1] * B[2, 3] + B[0, 2] * B[1, 3] + B[0, 3] * B[1, 2]
+    assert abs(dense.hafnian(B) - expect) < 1e-12
+
+
+def test_single_mode_amplitudes_textbook():
+    r = np.array([0.7])
+    U = np.eye(1, dtype=complex)
+    t = math.tanh(0.7)
+    for m in range(6):
+        a = dense.gbs_amplitude(r, U, (2 * m,))
+        exact = (-t) ** m * math.sqrt(math.factorial(2 * m)) / (2 ** m * math.factorial(m)) / math.sqrt(math.cosh(0.7))
+        assert abs(a - exact) < 1e-13
+        assert abs(dense.gbs_amplitude(r, U, (2 * m + 1,))) == 0.0
+
+
+def test_vacuum_probability_and_normalisation():
+    w = inputs.workload("plain", 4, M=3)
+    amp = dense.gbs_amplitudes(w.r, w.U, 9)
+    assert abs(abs(amp[0, 0, 0]) ** 2 - 1.0 / np.prod(np.cosh(w.r))) < 1e-13
+    assert 0.99 < np.sum(np.abs(amp) ** 2) <= 1.0 + 1e-12
+
+
+# ------------------------------------------------------------------ dense spectrum
+def test_dense_ground_state_matches_hafnian_state():
+    """The ground state of P H P approaches the GBS state as d grows; this fixes the
+    U -> O map and the sign of B together."""
+    w = inputs.workload("plain", 2, M=2, r_lo=0.3, r_hi=0.5)
+    G = gbs.hamiltonian_coefficients(w.r, w.U)
+    prev = None
+    for d in (6, 10, 14):
+        e0, v0 = dense.ground_state(G, d)
+        amp = dense.gbs_amplitudes(w.r, w.U, d).reshape(-1)
+        F = abs(np.vdot(amp, v0[:, 0])) ** 2 / np.vdot(amp, amp).real
+        assert e0[0] >= -1e-12
+        if prev is not None:
+            assert 1 - F <= prev + 1e-12
+        prev = 1 - F
+    assert prev < 1e-6
+
+
+def test_interlacing_monotone_and_spectrum_near_integers():
+    w = inputs.workload("plain", 8, M=2, r_lo=0.2, r_hi=0.4)
+    G = gbs.hamiltonian_coefficients(w.r, w.U)
+    energies = []
+    for d in range(2, 13):
+        energies.append(dense.ground_state(G, d)[0][0])
+    assert all(e >= -1e-12 for e in energies)
+    assert all(energies[k + 1] <= energies[k] + 1e-12 for k in range(len(energies) - 1))
+    wl = np.linalg.eigvalsh(dense.dense_hamiltonian(G, 16).toarray())[:4]
+    assert np.abs(wl - np.array([0, 1, 1, 2])).max() < 1e-3
+
+
+def test_fidelity_bound_F_ge_1_minus_E():
+    """|<psi|phi>|^2 >= 1 - <phi|PHP|phi> for any normalised phi in the truncated space
+    (text after Eq. MagOfSimError), with psi the exact (untruncated) GBS state."""
+    w = inputs.workload("plain", 9, M=3, r_lo=0.3, r_hi=0.6)
+    G = gbs.hamiltonian_coefficients(w.r, w.U)
+    d = 4
+    H = dense.dense_hamiltonian(G, d).toarray()
+    amp = dense.gbs_amplitudes(w.r, w.U, d).reshape(-1)
+    rng = np.random.default_rng(1)
+    _, v0 = dense.ground_state(G, d)
+    cands = [v0[:, 0]] + [v0[:, 0] + 0.3 * inputs.random_complex(d ** 3, rng) for _ in range(5)]
+    for phi in cands:
+        phi = phi / np.linalg.norm(phi)
+        E = np.vdot(phi, H @ phi).real
+        F = abs(np.vdot(amp, phi)) ** 2
+        assert F >= 1 - E - 1e-12
+
+
+def test_product_state_U_identity():
+    """U = I: H decouples, the ground state is a product and each mode's energy is the
+    lowest eigenvalue of its d x d single-mode problem; marginals tend to the squeezed
+    vacuum (2n)!/(4^n n!^2) tanh^{2n} r / cosh r."""
+    w = inputs.workload("plain", 12, M=3, identity_U=True, r_lo=0.3, r_hi=0.5)
+    G = gbs.hamiltonian_coefficients(w.r, w.U)
+    d = 10
+    ops = gbs.local_ops(d)
+    e_single = []
+    for i in range(3):
+        h = G[i, i] * ops["X2"] + G[3 + i, 3 + i] * ops["P2"] + G[i, 3 + i] * ops["XPPX"] - 0.5 * ops["I"]
+        e_single.append(np.linalg.eigvalsh(h)[0])
+    cores = mpo.build_mpo(G, d)
+    mps, rep = dmrg.dmrg(cores, d, 1, 3, seed=3, lanczos=dmrg.LanczosParams(tol=1e-12))
+    assert abs(rep.energies[-1] - sum(e_single)) < 1e-10
+    marg = observables.marginal(mps, None, [1])
+    t = math.tanh(w.r[1])
+    for m in range(3):
+        exact = math.factorial(2 * m) / (4 ** m * math.factorial(m) ** 2) * t ** (2 * m) / math.cosh(w.r[1])
+        assert abs(marg[2 * m] - exact) < 1e-4
+        assert marg[2 * m + 1] < 1e-12
+
+
+# ------------------------------------------------------------------ DMRG
+@pytest.mark.parametrize("seed", [0, 1])
+def test_dmrg_plain_is_exact(seed):
+    """Plain workload (M=4, d=4, chi=16 = d^2): the MPS is exact, so two-site DMRG must
+    reach the dense ground energy to 1e-12 ||H||."""
+    w = inputs.workload("plain", seed)
+    G = gbs.hamiltonian_coefficients(w.r, w.U)
+    Hn = gbs.norm_bound(G, w.M, w.d)
+    e0, v0 = dense.ground_state(G, w.d)
+    cores = mpo.build_mpo(G, w.d)
+    mps, rep = dmrg.dmrg(cores, w.d, w.chi, 4, seed=seed + 100, lanczos=dmrg.LanczosParams(tol=1e-12))
+    assert abs(rep.energies[-1] - e0[0]) <= 1e-12 * Hn
+    assert rep.energies[-1] >= -1e-12
+    for i in range(w.M):
+        m = observables.marginal(mps, None, [i])
+        md = dense.marginals_from_vector(v0[:, 0], w.M, w.d, [i])
+        assert np.abs(m - md).max() < 1e-10
+    m2 = observables.marginal(mps, None, [3, 1])
+    md2 = dense.marginals_from_vector(v0[:, 0], w.M, w.d, [3, 1])
+    assert np.abs(m2 - md2).max() < 1e-10
+
+
+def test_truncation_weights_and_reconstruction():
+    rng = np.random.default_rng(5)
+    th = inputs.random_complex((3, 4, 4, 5), rng)
+    th /= np.linalg.norm(th)
+    A, C, w, disc = dmrg.truncate(th, "right", 100)
+    assert abs(disc) < 1e-14 and abs(w.sum() - 1) < 1e-13
+    assert np.abs(np.einsum("asb,btc->astc", A, C) - th).max() < 1e-13
+    Al = A.reshape(12, -1)
+    assert np.abs(Al.conj().T @ Al - np.eye(Al.shape[1])).max() < 1e-13
+    C2, B, w2, disc2 = dmrg.truncate(th, "left", 5)
+    assert abs(disc2 - (1 - w2.sum())) < 1e-14 and disc2 > 0
+    Bm = B.reshape(5, -1)
+    assert np.abs(Bm @ Bm.conj().T - np.eye(5)).max() < 1e-13
+    # kept weight of the best rank-5 approximation equals the reconstruction overlap
+    approx = np.einsum("asb,btc->astc", C2, B)
+    assert abs(np.linalg.norm(th - approx) ** 2 - disc2) < 1e-12
+
+
+def test_lanczos_against_dense_eigh():
+    rng = np.random.default_rng(7)
+    A = inputs.random_complex((60, 60), rng)
+    H = A + A.conj().T
+    lam, vec = np.linalg.eigh(H)
+    th, x, nmv, conv = dmrg.lanczos_lowest(lambda v: H @ v, inputs.random_complex(60, rng),
+                                           dmrg.LanczosParams(krylov_max=30, max_restarts=10, tol=1e-11))
+    assert conv and abs(th - lam[0]) < 1e-10
+    assert abs(abs(np.vdot(vec[:, 0], x)) - 1) < 1e-10
+
+
+def test_initial_mps_right_canonical():
+    mps = dmrg.initial_mps(5, 3, 7, seed=11)
+    assert [A.shape for A in mps][2] == (7, 3, 7)
+    for A in mps:
+        Am = A.reshape(A.shape[0], -1)
+        assert np.abs(Am @ Am.conj().T - np.eye(A.shape[0])).max() < 1e-13
+    assert abs(dmrg.norm2(mps) - 1) < 1e-12
+
+
+# ------------------------------------------------------------------ sampler
+def test_sampler_goodness_of_fit():
+    w = inputs.workload("plain", 1, M=3)
+    G = gbs.hamiltonian_coefficients(w.r, w.U)
+    cores = mpo.build_mpo(G, 3)
+    mps, _ = dmrg.dmrg(cores, 3, 9, 3, seed=2, lanczos=dmrg.LanczosParams(tol=1e-12))
+    joint = observables.marginal(mps, None, [0, 1, 2]).reshape(-1)
+    smp = observables.sample(mps, None, seed=99, n_samples=4000)
+    idx = smp[:, 0] * 9 + smp[:, 1] * 3 + smp[:, 2]
+    counts = np.bincount(idx, minlength=27)
+    keep = joint * 4000 > 5
+    exp = joint[keep] * 4000
+    obs = counts[keep]
+    stat = np.sum((obs - exp) ** 2 / exp)
+    pval = scipy.stats.chi2.sf(stat, df=keep.sum() - 1)
+    assert pval > 1e-4
