@@ -1,0 +1,277 @@
+/*
+ * vtn.h -- C ABI of the GB300 (sm_103a) implementation of the variational tensor-network
+ * simulation of Gaussian Boson Sampling (Vinther & Kastoryano, arXiv 2410.18740).
+ *
+ * The method: the GBS output state |psi> = U V|0> is the unique zero-energy ground state
+ * of the parent Hamiltonian H = sum_n A_n^dag A_n (Eq. CentralEquation), which for
+ * single-mode squeezers r_k followed by an interferometer U is the quadratic form
+ * H = R^T (V^{-1}/4) R - N/2 in the quadratures R = (X_1..X_N, P_1..P_N) with V the
+ * covariance matrix (Eq. GBSHamiltonian).  H is written in a truncated Fock basis
+ * (Eq. ProjectionOperator: the projected P H P) or in the Gaussian optimal local basis
+ * (Eqs. WilliamsonDecomposition, OLB), as a matrix product operator, and its ground
+ * state is found as a matrix product state (Eq. MPSAnsatz) by two-site DMRG.  The
+ * variational energy <H> >= 0 measures the simulation error (Eq. MagOfSimError).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - hbar = 1, vacuum quadrature variance 1/2, a = (X + iP)/sqrt(2); output modes
+ *    a_out = U a_in; squeezer k squeezes X: Var X_k = exp(-2 r_k)/2.
+ *  - Complex numbers are stored as interleaved (re, im) pairs of IEEE doubles.
+ *    "complex[n]" below means 2n doubles.
+ *  - Tensors are row-major.  MPS site tensor A[a][s][b] (left bond, physical, right
+ *    bond).  Left environment L[w][bra][ket], right environment R[w][ket][bra].  MPO
+ *    core W[a][b][s'][s] = <s'|op_ab|s>.
+ *  - Ownership: the caller owns every array it passes; the library copies what it
+ *    keeps.  The library owns vtn_ctx / vtn_mpo / vtn_mps handles; they are released
+ *    only by the matching *_free / vtn_destroy call.  Output arrays are allocated by
+ *    the caller.  Pointers documented as "device" must be device memory of the
+ *    context's GPU; all others are host memory.
+ *  - Streams: all device work of a context runs on the stream given to vtn_create
+ *    (NULL = the legacy default stream).  Calls that write host outputs synchronise
+ *    that stream before returning; calls whose outputs are device arrays are
+ *    asynchronous with respect to the host and ordered on the stream.
+ *  - Errors: every call returns a vtn_status and never aborts or exits.  On failure
+ *    the out-parameters are left untouched (vtn_sweep keeps the last valid MPS) and
+ *    vtn_last_error(ctx) holds a one-line message.
+ *  - Threads: one context per host thread.
+ */
+#ifndef VTN_H
+#define VTN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vtn_ctx_s* vtn_ctx;
+typedef struct vtn_mpo_s* vtn_mpo;
+typedef struct vtn_mps_s* vtn_mps;
+
+typedef enum {
+    VTN_OK = 0,
+    VTN_EINVAL = 1,        /* invalid argument (sizes, non-unitary U, d > D, ...)        */
+    VTN_ENOMEM = 2,        /* device or host allocation failed                           */
+    VTN_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed                */
+    VTN_ENOCONV = 4,       /* Lanczos missed its tolerance after all restarts; the best
+                              Ritz vector was still used                                 */
+    VTN_ETIMEOUT = 5,      /* a bounded device-side wait gave up                         */
+    VTN_EUNSUPPORTED = 6   /* a valid request outside what this build implements         */
+} vtn_status;
+
+typedef enum {
+    VTN_FP64 = 0,          /* every contraction in IEEE double                           */
+    VTN_TF32X3 = 1,        /* reserved: three-term TF32 split products, FP32 accumulate  */
+    VTN_BF16X3 = 2         /* reserved: three-term BF16 split products, FP32 accumulate  */
+} vtn_precision;
+
+/* Optional device-memory provider.  alloc returns device memory of at least `bytes`
+ * bytes aligned to 256 B on the context's device, or NULL on failure; free releases
+ * it.  With no provider the library calls cudaMalloc / cudaFree. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* user);
+    void (*free)(void* ptr, void* user);
+    void* user;
+} vtn_allocator;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device` whose work runs on `cuda_stream`
+ * (a cudaStream_t, NULL = legacy default stream).  `allocator` may be NULL. */
+vtn_status vtn_create(vtn_ctx* out, int device, void* cuda_stream, const vtn_allocator* allocator);
+vtn_status vtn_destroy(vtn_ctx ctx);
+/* Last error message of the context ("" if none).  Valid until the next call on ctx.
+ * vtn_last_error(NULL) returns the message of the last failed vtn_create. */
+const char* vtn_last_error(vtn_ctx ctx);
+/* Number of kernels this context has launched since creation (all entry points). */
+vtn_status vtn_launch_count(vtn_ctx ctx, long long* out);
+
+/* ---------------------------------------------------------------- problem -> MPO */
+
+#define VTN_FLAG_LBO 1u    /* force the Gaussian optimal local basis even when d == D */
+
+/* Build the MPO of the GBS parent Hamiltonian (Eq. GBSHamiltonian) and upload it.
+ *   M  >= 1 modes; r: double[M] squeezing parameters; U: complex[M*M] row-major
+ *      interferometer with a_out = U a_in (validated: max |U^dag U - I| <= 1e-10).
+ *   D  >= 2 physical Fock cutoff (Eq. ProjectionOperator).
+ *   d  local dimension of the solver, 1 <= d <= D, d <= 16.  d == D (and no
+ *      VTN_FLAG_LBO): Fock basis.  Otherwise each mode is rotated to its optimal local
+ *      basis S_i^dag|m> from the Williamson decomposition of its reduced covariance
+ *      (Eqs. WilliamsonDecomposition, OLB) and the D x d isometry
+ *      V_nm = <n|S_i^dag|m> (Eq. InverseBasisTransformation) is kept for read-out.
+ * Same-mode operator products are exactly projected (P H P; SM Sec. 5).
+ * The MPO is the centre-collapsed state machine of SM Sec. 8 (Gaussian part):
+ * bond dimension w_s = 2 min(s, M - s) + 2 inside, 1 at the ends. */
+vtn_status vtn_build_mpo(vtn_ctx ctx, int M, const double* r, const double* U,
+                         int D, int d, unsigned flags, vtn_mpo* out);
+vtn_status vtn_mpo_free(vtn_mpo mpo);
+/* Shape queries: M, d, D and the bond dimensions w[0..M] (w may be NULL). */
+vtn_status vtn_mpo_info(vtn_mpo mpo, int* M, int* d, int* D, int* w);
+/* Coefficient matrix of the quadratic form actually used, G = V^{-1}/4 (xxpp order),
+ * or G' = S^T G S in the optimal local basis: double[2M*2M]. */
+vtn_status vtn_mpo_coefficients(vtn_mpo mpo, double* G);
+/* Covariance matrix V (xxpp order): double[2M*2M]. */
+vtn_status vtn_mpo_covariance(vtn_mpo mpo, double* V);
+/* Isometry of mode `site` (complex[D*d], row n, column m); identity block in the Fock
+ * basis.  Its global phase is a convention: probabilities do not depend on it. */
+vtn_status vtn_mpo_isometry(vtn_mpo mpo, int site, double* V);
+/* Sparse entries of core `site`: *nnz on input is the capacity of rows/cols/ops, on
+ * output the count.  ops: complex[nnz*d*d], ops[k][s'][s].  Passing rows == NULL
+ * returns only the count. */
+vtn_status vtn_mpo_core(vtn_mpo mpo, int site, int* nnz, int* rows, int* cols, double* ops);
+/* Deterministic bound ||P H P|| <= lambda_max(G) M (2d - 1), used to scale tolerances. */
+vtn_status vtn_mpo_norm_bound(vtn_mpo mpo, double* out);
+
+/* ---------------------------------------------------------------- MPS */
+
+/* Seeded random right-canonical MPS with bond dimensions min(chi, d^s, d^(M-s)):
+ * entry j of site s is the complex normal (g1 + i g2)/sqrt(2) drawn by Box-Muller from
+ * Philox4x32-10 (key = seed, counter = (j, site, 1)); the rows of every site matrix
+ * (left bond) x (physical, right bond) are then orthonormalised in order. */
+vtn_status vtn_mps_random(vtn_ctx ctx, vtn_mpo mpo, int chi, uint64_t seed, vtn_mps* out);
+/* MPS from host tensors: dims[0..M] bond dimensions (dims[0] = dims[M] = 1), sites[s]
+ * complex[dims[s]*d*dims[s+1]].  No canonical form is assumed. */
+vtn_status vtn_mps_from_host(vtn_ctx ctx, vtn_mpo mpo, const int* dims, const double* const* sites,
+                             vtn_mps* out);
+vtn_status vtn_mps_free(vtn_mps mps);
+vtn_status vtn_mps_info(vtn_mps mps, int* M, int* d, int* dims);
+/* Copy site s to host: complex[dims[s]*d*dims[s+1]]. */
+vtn_status vtn_mps_get_site(vtn_ctx ctx, vtn_mps mps, int site, double* out);
+/* Flat binary checkpoint: magic, M, d, dims, tensors. */
+vtn_status vtn_mps_save(vtn_ctx ctx, vtn_mps mps, const char* path);
+vtn_status vtn_mps_load(vtn_ctx ctx, vtn_mpo mpo, const char* path, vtn_mps* out);
+
+/* ---------------------------------------------------------------- solver */
+
+typedef struct {
+    int chi_max;               /* maximum bond dimension                                 */
+    const int* chi_schedule;   /* per-sweep chi (growth from O(1), Discussion); NULL = chi_max */
+    int n_schedule;
+    int n_sweeps;              /* maximum number of sweeps (<= 64)                       */
+    vtn_precision prec;        /* contraction precision of H_eff psi and environments    */
+    double lanczos_tol;        /* absolute residual ||H x - theta x|| to stop Lanczos     */
+    int krylov_max;            /* Krylov dimension before an explicit restart (<= 64)    */
+    int lanczos_max_restarts;
+    double e_tol;              /* stop when |E_k - E_{k-1}| <= e_tol (0 = off)            */
+    double e_target;           /* stop when E_k <= e_target (used when use_e_target != 0) */
+    int use_e_target;
+    uint64_t seed;             /* seed of the random initial MPS when *state == NULL      */
+} vtn_sweep_opts;
+
+typedef struct {
+    int sweeps_done;
+    double energy[64];         /* FP64 <H> of the normalised MPS after each sweep         */
+    double max_discarded[64];  /* largest discarded weight of the sweep (Eq. SurrogateEpsChi) */
+    double seconds[64];        /* wall time of each sweep                                */
+    long long matvecs;         /* H_eff psi products                                      */
+    long long lanczos_not_converged;
+    double heff_flops;         /* algorithmic real flops of all H_eff psi products        */
+    double heff_seconds;       /* device time of the H_eff psi GEMM launches (timing on)  */
+    double gemm_flops;         /* algorithmic real flops of every complex GEMM launch     */
+    double gemm_seconds;       /* their device time (timing on)                           */
+    double eig_seconds;        /* device time of the truncation eigensolver (timing on)   */
+} vtn_sweep_report;
+
+/* Fill opts with the defaults: chi_max 16, 8 sweeps, FP64, lanczos_tol 1e-10,
+ * krylov_max 32, 4 restarts, e_tol 0, seed 0. */
+vtn_status vtn_sweep_opts_default(vtn_sweep_opts* opts);
+
+/* Two-site DMRG sweeps.  *state == NULL: start from vtn_mps_random(opts->chi_schedule[0]
+ * or chi_max, opts->seed).  A sweep optimises bonds (0,1) .. (M-2,M-1) left to right,
+ * then (M-2,M-1) .. (0,1) right to left; it ends right-canonical with the centre at
+ * site 0.  Each bond: Lanczos on H_eff (full re-orthogonalisation, restarts), FP64
+ * eigendecomposition of the reduced density matrix, keep min(chi, chi_l d, d chi_r)
+ * largest eigenpairs, environment update.  Returns VTN_ENOCONV (after finishing) if
+ * some Lanczos solve missed its tolerance.  report may be NULL. */
+vtn_status vtn_sweep(vtn_ctx ctx, vtn_mpo mpo, vtn_mps* state, const vtn_sweep_opts* opts,
+                     vtn_sweep_report* report);
+
+/* <psi|H|psi> / <psi|psi> in FP64 by a full environment contraction (Eq. MagOfSimError). */
+vtn_status vtn_energy(vtn_ctx ctx, vtn_mpo mpo, vtn_mps mps, double* E);
+
+/* Joint photon-number distribution of the k distinct modes `modes` in the Fock basis
+ * (after the inverse basis transformation, Eq. InverseBasisTransformation):
+ * out: double[D^k], index sum_j n_j D^(k-1-j) in the order of `modes`.  Normalised by
+ * <psi|psi> of the solver basis, so with a local basis the D^k values sum to <= 1.
+ * VTN_EINVAL if k < 1, a mode repeats or is out of range, or D^k > 2^26. */
+vtn_status vtn_marginals(vtn_ctx ctx, vtn_mpo mpo, vtn_mps mps, const int* modes, int k, double* out);
+/* Every single-mode marginal: out double[M*D], row i = P_i(n), n < D. */
+vtn_status vtn_marginals_all(vtn_ctx ctx, vtn_mpo mpo, vtn_mps mps, double* out);
+
+/* n_samples photon-number patterns by sequential conditional sampling in the Fock
+ * basis: p(n_i | n_<i) from the chain rule on the MPS; mode i of sample t takes the
+ * smallest n with CDF(n) > u * CDF(D-1), u the 53-bit uniform of Philox4x32-10
+ * (key = seed, counter = (t, i, 2)).  out: int32[n_samples*M]. */
+vtn_status vtn_sample(vtn_ctx ctx, vtn_mpo mpo, vtn_mps mps, uint64_t seed, int n_samples, int32_t* out);
+
+/* ---------------------------------------------------------------- kernel-level calls
+ * These expose single steps of the solver on caller-provided device buffers.  They
+ * are what the solver runs internally and serve parity tests and kernel timing. */
+
+/* Host description of one sparse MPO core: nnz entries (rows[k], cols[k]) with
+ * operators ops[k] = complex[d*d] (ops[k][s'][s]), w_left x w_right channels. */
+typedef struct {
+    int w_left, w_right, d, nnz;
+    const int* rows;
+    const int* cols;
+    const double* ops;
+} vtn_core;
+
+/* Two-site effective-Hamiltonian product (the hot path):
+ *   y[i,t,u,l] = sum L[a,i,j] Wi[a,b,t,s] Wj[b,c,u,v] theta[j,s,v,k] R[c,k,l]
+ * L: device complex[Wi.w_left*chi_l*chi_l]; R: device complex[Wj.w_right*chi_r*chi_r];
+ * theta, y: device complex[chi_l*d*d*chi_r].  y must not alias theta. */
+vtn_status vtn_heff_apply(vtn_ctx ctx, const vtn_core* Wi, const vtn_core* Wj, int chi_l, int chi_r,
+                          const double* L, const double* R, const double* theta, double* y,
+                          vtn_precision prec);
+
+/* Environment update across one site with tensor A (device complex[chi_l*d*chi_r]):
+ *  side 0 (left):  out[b,l,k] = sum conj(A[i,t,l]) env[a,i,j] W[a,b,t,s] A[j,s,k]
+ *                  env: complex[W.w_left*chi_l*chi_l] -> out: complex[W.w_right*chi_r*chi_r]
+ *  side 1 (right): out[b,j,i] = sum W[b,c,t,s] A[j,s,g] conj(A[i,t,p]) env[c,g,p]
+ *                  env: complex[W.w_right*chi_r*chi_r] -> out: complex[W.w_left*chi_l*chi_l] */
+vtn_status vtn_env_update(vtn_ctx ctx, const vtn_core* W, int side, int chi_l, int chi_r,
+                          const double* env, const double* A, double* out, vtn_precision prec);
+
+/* Lowest eigenpair of the two-site H_eff by the solver's Lanczos (full
+ * re-orthogonalisation, restarts).  theta: device complex[chi_l*d*d*chi_r], start vector
+ * on input, normalised Ritz vector on output.  E: host double.  n_matvec: host, may be
+ * NULL.  Returns VTN_ENOCONV if the tolerance was missed. */
+vtn_status vtn_heff_ground(vtn_ctx ctx, const vtn_core* Wi, const vtn_core* Wj, int chi_l, int chi_r,
+                           const double* L, const double* R, double* theta, double tol,
+                           int krylov_max, int max_restarts, double* E, int* n_matvec);
+
+/* Truncation of a two-site tensor theta (device complex[chi_l*d1*d2*chi_r]) viewed as
+ * the (chi_l d1) x (d2 chi_r) matrix T, by the FP64 eigendecomposition of the reduced
+ * density matrix, keeping k = min(k_max, chi_l d1, d2 chi_r) eigenpairs of largest
+ * eigenvalue (squared Schmidt values, Eq. SurrogateEpsChi):
+ *  direction 0: rho = T T^dag = U diag(lam) U^dag; left = U_k (chi_l,d1,k, left-canonical),
+ *               right = U_k^dag T (k,d2,chi_r).
+ *  direction 1: rho = T^dag T = V diag(lam) V^dag; left = T V_k (chi_l,d1,k),
+ *               right = V_k^dag (k,d2,chi_r, right-canonical).
+ * left/right: device buffers of chi_l*d1*k and k*d2*chi_r complex.  lam: host double[k]
+ * (descending), discarded: host double = 1 - sum(kept)/tr(rho).  *k_out = k. */
+vtn_status vtn_truncate(vtn_ctx ctx, int chi_l, int d1, int d2, int chi_r, int direction, int k_max,
+                        const double* theta, double* left, double* right, double* lam,
+                        double* discarded, int* k_out);
+
+/* Inverse basis transformation on one site (Eq. InverseBasisTransformation):
+ * out[a][n][b] = sum_m V[n][m] A[a][m][b], V device complex[D*d], A device
+ * complex[chi_l*d*chi_r], out device complex[chi_l*D*chi_r]. */
+vtn_status vtn_lbo_rotate(vtn_ctx ctx, int chi_l, int d, int D, int chi_r, const double* V,
+                          const double* A, double* out);
+
+/* Turn per-kernel device timing (CUDA events on the context stream) on or off and read
+ * the accumulated figures: launches, algorithmic flops and seconds per kernel class.
+ * classes: 0 = complex GEMM (all), 1 = GEMMs inside H_eff psi, 2 = truncation eigensolver,
+ * 3 = Lanczos vector kernels, 4 = W mixing. */
+vtn_status vtn_timing(vtn_ctx ctx, int enable);
+vtn_status vtn_timing_read(vtn_ctx ctx, int cls, long long* launches, double* flops, double* seconds);
+vtn_status vtn_timing_reset(vtn_ctx ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VTN_H */

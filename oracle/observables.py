@@ -3,9 +3,11 @@
 * ``fock_tensors``: the inverse basis transformation of Eq. InverseBasisTransformation
   applied to every physical leg, A^F[a, n, b] = sum_m V_nm A[a, m, b] (n < D).
 * ``marginal``: joint photon-number distribution P(n_{i1}, ..., n_{ik}) of the listed
-  modes (the P(n) of Sec. "Main Methodology"), normalised by <psi|psi> computed in the
-  solver basis, so with a local basis the probabilities of n < D sum to at most one.
-  Computed by brute-force transfer contractions carrying the open photon numbers.
+  modes (the P(n) of Sec. "Main Methodology"): the partial trace over every other mode
+  (taken in the solver basis, which is complete for the variational state), then the
+  inverse basis transformation on the listed modes only.  Normalised by <psi|psi>, so
+  with a local basis the probabilities of n < D sum to at most one.  Computed by
+  brute-force transfer contractions carrying the open photon numbers.
 * ``sample``: sequential conditional sampling in the Fock basis,
   p(n_i | n_<i) proportional to || l_{i-1} A^F_i[n_i] ||^2 weighted by the right
   environment, inverse-CDF pick with a Philox uniform per (sample, mode).  The paper
@@ -23,12 +25,13 @@ def fock_tensors(mps, isometries):
     return [np.einsum("nm,amb->anb", V, A) for A, V in zip(mps, isometries)]
 
 
-def _right_envs(mpsF):
-    N = len(mpsF)
+def _right_envs(mps):
+    """Right transfer environments (ket, bra) of <psi|psi> in the solver basis."""
+    N = len(mps)
     E = [None] * (N + 1)
     E[N] = np.ones((1, 1), dtype=np.complex128)
     for s in range(N - 1, -1, -1):
-        A = mpsF[s]
+        A = mps[s]
         E[s] = np.einsum("asb,csd,bd->ac", A, A.conj(), E[s + 1], optimize=True)
     return E
 
@@ -58,7 +61,8 @@ def marginal(mps, isometries, modes):
                     An = A[:, n, :]
                     new[key + (n,)] = An.conj().T @ E @ An
             else:
-                new[key] = np.einsum("ij,isk,jsl->kl", E, A.conj(), A, optimize=True)
+                As = mps[s]   # traced mode: solver basis
+                new[key] = np.einsum("ij,isk,jsl->kl", E, As.conj(), As, optimize=True)
         envs = new
     D = mpsF[0].shape[1]
     out = np.zeros((D,) * len(modes))
@@ -77,7 +81,7 @@ def sample(mps, isometries, seed, n_samples):
     """int32 array [n_samples, N] of photon numbers."""
     mpsF = fock_tensors(mps, isometries)
     N = len(mpsF)
-    Er = _right_envs(mpsF)
+    Er = _right_envs(mps)
     out = np.zeros((n_samples, N), dtype=np.int32)
     for t in range(n_samples):
         l = np.ones((1,), dtype=np.complex128)

@@ -1,0 +1,1039 @@
+// extern "C" entry points of libvtn (declared in include/vtn.h).
+//
+// The host code here only orchestrates: every arithmetic step of the solver (effective
+// Hamiltonian products, Lanczos, eigendecomposition, environments, energy, marginals,
+// sampling) is a kernel launched on the context's stream.  The host builds the MPO
+// once (host_mpo.cpp) and reads back per-iteration status words and final scalars.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "vtn_internal.cuh"
+
+using namespace vtn;
+
+namespace {
+
+std::string g_create_error;
+
+template <class F>
+vtn_status guard(vtn_ctx ctx, F&& f) {
+    try {
+        vtn_status s = f();
+        if (ctx) {
+            if (s == VTN_OK) ctx->c.err.clear();
+        }
+        return s;
+    } catch (const Error& e) {
+        if (ctx) ctx->c.err = e.msg;
+        else g_create_error = e.msg;
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        if (ctx) ctx->c.err = "host allocation failed";
+        return VTN_ENOMEM;
+    } catch (const std::exception& e) {
+        if (ctx) ctx->c.err = e.what();
+        return VTN_EINVAL;
+    }
+}
+
+void use_device(Ctx& c) { VTN_CUDA_TRY(cudaSetDevice(c.device)); }
+
+void ensure_mpo_device(vtn_ctx ctx, vtn_mpo mpo) {
+    VTN_REQUIRE(mpo != nullptr, "null MPO");
+    if (!mpo->dcores.empty()) {
+        VTN_REQUIRE(mpo->owner == ctx, "MPO is resident on another context");
+        return;
+    }
+    Ctx& c = ctx->c;
+    mpo->dcores.resize(mpo->hp.M);
+    for (int s = 0; s < mpo->hp.M; ++s) upload_core(c, mpo->hp.cores[s], mpo->dcores[s]);
+    const size_t iso_bytes = sizeof(double2) * mpo->hp.iso.size();
+    mpo->iso_dev = (double2*)c.dalloc(iso_bytes);
+    VTN_CUDA_TRY(cudaMemcpyAsync(mpo->iso_dev, mpo->hp.iso.data(), iso_bytes, cudaMemcpyHostToDevice, c.stream));
+    c.sync();
+    mpo->owner = ctx;
+    mpo->device = c.device;
+}
+
+long long safe_pow_min(int d, int e, long long cap) {
+    long long v = 1;
+    for (int i = 0; i < e; ++i) {
+        v *= d;
+        if (v >= cap) return cap;
+    }
+    return v;
+}
+
+std::vector<int> bond_dims(int M, int d, int chi) {
+    std::vector<int> dims(M + 1);
+    for (int s = 0; s <= M; ++s) {
+        long long a = safe_pow_min(d, s, chi), b = safe_pow_min(d, M - s, chi);
+        dims[s] = (int)std::min<long long>(chi, std::min(a, b));
+    }
+    return dims;
+}
+
+// capacity per cut: chi_cap inside the chain, 1 at the two ends
+std::vector<int> cap_dims(int M, int chi_cap) {
+    std::vector<int> v(M + 1, chi_cap);
+    v[0] = 1;
+    v[M] = 1;
+    return v;
+}
+
+// site buffers able to hold chi_cap x d x chi_cap (content preserved)
+void mps_reserve(Ctx& c, vtn_mps mps, int chi_cap) {
+    for (int x : mps->dims) chi_cap = std::max(chi_cap, x);
+    if (chi_cap <= mps->chi_cap && (int)mps->sites.size() == mps->M) return;
+    std::vector<int> cd = cap_dims(mps->M, chi_cap);
+    mps->sites.resize(mps->M, nullptr);
+    mps->cap.resize(mps->M, 0);
+    for (int s = 0; s < mps->M; ++s) {
+        size_t need = (size_t)cd[s] * mps->d * cd[s + 1];
+        if (need <= mps->cap[s]) continue;
+        double2* nb = (double2*)c.dalloc(sizeof(double2) * need);
+        if (mps->sites[s]) {
+            VTN_CUDA_TRY(cudaMemcpyAsync(nb, mps->sites[s],
+                                         sizeof(double2) * (size_t)mps->dims[s] * mps->d * mps->dims[s + 1],
+                                         cudaMemcpyDeviceToDevice, c.stream));
+            c.sync();
+            c.dfree(mps->sites[s]);
+        }
+        mps->sites[s] = nb;
+        mps->cap[s] = need;
+    }
+    mps->chi_cap = chi_cap;
+}
+
+vtn_mps new_mps(vtn_ctx ctx, int M, int d, const std::vector<int>& dims) {
+    vtn_mps m = new vtn_mps_s();
+    m->M = M;
+    m->d = d;
+    m->dims = dims;
+    m->owner = ctx;
+    m->chi_cap = 0;
+    int chi = 1;
+    for (int x : dims) chi = std::max(chi, x);
+    try {
+        mps_reserve(ctx->c, m, chi);
+    } catch (...) {
+        for (auto p : m->sites) ctx->c.dfree(p);
+        delete m;
+        throw;
+    }
+    return m;
+}
+
+void destroy_mps(vtn_mps m) {
+    if (!m) return;
+    if (m->owner) {
+        for (auto p : m->sites) m->owner->c.dfree(p);
+    }
+    delete m;
+}
+
+// A DevCore with w channels, each passing through with op (d x d) -- used for norms.
+struct TempCore {
+    Ctx* c;
+    DevCore dc;
+    TempCore(Ctx& ctx, const HostCore& h) : c(&ctx) { upload_core(ctx, h, dc); }
+    ~TempCore() {
+        if (c) {
+            cudaStreamSynchronize(c->stream);
+            free_core(*c, dc);
+        }
+    }
+};
+
+HostCore identity_core(int d) {
+    HostCore h;
+    h.wl = 1; h.wr = 1; h.d = d;
+    h.rows.push_back(0);
+    h.cols.push_back(0);
+    h.ops.assign((size_t)d * d, cplx(0, 0));
+    for (int i = 0; i < d; ++i) h.ops[(size_t)i * d + i] = 1.0;
+    h.ident.push_back(1);
+    return h;
+}
+
+// batched left transfer: Eout[t] = sum_s A[:,s,:]^dag E[t] A[:,s,:], t < count
+void transfer_left_batch(Ctx& c, int count, int chi_l, int d, int chi_r, const double2* E, const double2* A,
+                         double2* Eout, double2* tmp) {
+    GemmArgs g1;
+    g1.M = chi_l; g1.N = d * chi_r; g1.K = chi_l; g1.batch = count;
+    g1.A = E; g1.lda = chi_l; g1.sA_batch = (long long)chi_l * chi_l;
+    g1.B = A; g1.ldb = (long long)d * chi_r; g1.sB_batch = 0;
+    g1.C = tmp; g1.ldc = (long long)d * chi_r; g1.sC_batch = (long long)chi_l * d * chi_r;
+    gemm_c64(c, g1);
+    GemmArgs g2;
+    g2.M = chi_r; g2.N = chi_r; g2.K = chi_l * d; g2.batch = count;
+    g2.opA = OP_C; g2.A = A; g2.lda = chi_r; g2.sA_batch = 0;
+    g2.B = tmp; g2.ldb = chi_r; g2.sB_batch = (long long)chi_l * d * chi_r;
+    g2.C = Eout; g2.ldc = chi_r; g2.sC_batch = (long long)chi_r * chi_r;
+    gemm_c64(c, g2);
+}
+
+// right transfer: Eout[b][b'] = sum A[b s g] E[g][g'] conj(A[b' s g'])
+void transfer_right(Ctx& c, int chi_l, int d, int chi_r, const double2* E, const double2* A, double2* Eout,
+                    double2* tmp) {
+    GemmArgs g1;
+    g1.M = chi_l * d; g1.N = chi_r; g1.K = chi_r;
+    g1.A = A; g1.lda = chi_r;
+    g1.B = E; g1.ldb = chi_r;
+    g1.C = tmp; g1.ldc = chi_r;
+    gemm_c64(c, g1);
+    GemmArgs g2;
+    g2.M = chi_l; g2.N = chi_l; g2.K = d * chi_r;
+    g2.A = tmp; g2.lda = (long long)d * chi_r;
+    g2.opB = OP_C; g2.B = A; g2.ldb = (long long)d * chi_r;
+    g2.C = Eout; g2.ldc = chi_l;
+    gemm_c64(c, g2);
+}
+
+int max_dim(const std::vector<int>& v) {
+    int m = 1;
+    for (int x : v) m = std::max(m, x);
+    return m;
+}
+
+double read_scalar_re(Ctx& c, const double2* p) {
+    VTN_CUDA_TRY(cudaMemcpyAsync(c.pinned, p, sizeof(double2), cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+    return c.pinned[0];
+}
+
+double mps_norm2(Ctx& c, vtn_mps mps) {
+    const int chi = max_dim(mps->dims);
+    const size_t env = (size_t)chi * chi;
+    double2* E0 = (double2*)c.workspace(WS_Z, sizeof(double2) * env * 2);
+    double2* E1 = E0 + env;
+    double2* tmp = (double2*)c.workspace(WS_ENV_TMP, sizeof(double2) * (size_t)chi * mps->d * chi);
+    set_scalar_one(c, E0);
+    for (int s = 0; s < mps->M; ++s) {
+        transfer_left_batch(c, 1, mps->dims[s], mps->d, mps->dims[s + 1], E0, mps->sites[s], E1, tmp);
+        std::swap(E0, E1);
+    }
+    return read_scalar_re(c, E0);
+}
+
+double energy_dev(Ctx& c, vtn_mpo mpo, vtn_mps mps) {
+    int wmax = 1;
+    for (int w : mpo->hp.w) wmax = std::max(wmax, w);
+    const int chi = max_dim(mps->dims);
+    const size_t env = (size_t)wmax * chi * chi;
+    double2* L0 = (double2*)c.workspace(WS_Z, sizeof(double2) * env * 2);
+    double2* L1 = L0 + env;
+    set_scalar_one(c, L0);
+    for (int s = 0; s < mps->M; ++s) {
+        env_left_dev(c, mpo->dcores[s], mps->dims[s], mps->dims[s + 1], L0, mps->sites[s], L1);
+        std::swap(L0, L1);
+    }
+    const double e = read_scalar_re(c, L0);
+    const double n2 = mps_norm2(c, mps);
+    return e / n2;
+}
+
+struct Envs {
+    Ctx* c = nullptr;
+    std::vector<double2*> L, R;
+    ~Envs() {
+        if (!c) return;
+        cudaStreamSynchronize(c->stream);
+        for (auto p : L) c->dfree(p);
+        for (auto p : R) c->dfree(p);
+    }
+};
+
+void check_mps_matches(vtn_mpo mpo, vtn_mps mps) {
+    VTN_REQUIRE(mps != nullptr, "null MPS");
+    VTN_REQUIRE(mps->M == mpo->hp.M && mps->d == mpo->hp.d, "MPS does not match the MPO (M or d)");
+}
+
+}  // namespace
+
+// =====================================================================================
+extern "C" {
+
+vtn_status vtn_create(vtn_ctx* out, int device, void* cuda_stream, const vtn_allocator* allocator) {
+    if (!out) return VTN_EINVAL;
+    vtn_ctx ctx = nullptr;
+    vtn_status st = guard(nullptr, [&]() -> vtn_status {
+        int n = 0;
+        VTN_CUDA_TRY(cudaGetDeviceCount(&n));
+        VTN_REQUIRE(device >= 0 && device < n, "device index out of range");
+        VTN_CUDA_TRY(cudaSetDevice(device));
+        ctx = new vtn_ctx_s();
+        Ctx& c = ctx->c;
+        c.device = device;
+        c.stream = (cudaStream_t)cuda_stream;
+        if (allocator && allocator->alloc && allocator->free) {
+            c.alloc = *allocator;
+            c.has_alloc = true;
+        }
+        VTN_CUDA_TRY(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, device));
+        VTN_CUDA_TRY(cudaMallocHost((void**)&c.pinned, sizeof(double) * 4096));
+        c.ws.resize(WS_COUNT);
+        return VTN_OK;
+    });
+    if (st != VTN_OK) {
+        if (ctx) {
+            if (ctx->c.pinned) cudaFreeHost(ctx->c.pinned);
+            delete ctx;
+        }
+        return st;
+    }
+    *out = ctx;
+    return VTN_OK;
+}
+
+vtn_status vtn_destroy(vtn_ctx ctx) {
+    if (!ctx) return VTN_EINVAL;
+    Ctx& c = ctx->c;
+    cudaSetDevice(c.device);
+    cudaStreamSynchronize(c.stream);
+    for (auto& b : c.ws) c.dfree(b.p);
+    for (auto& p : c.pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : c.event_pool) cudaEventDestroy(e);
+    if (c.pinned) cudaFreeHost(c.pinned);
+    delete ctx;
+    return VTN_OK;
+}
+
+const char* vtn_last_error(vtn_ctx ctx) {
+    if (!ctx) return g_create_error.c_str();
+    return ctx->c.err.c_str();
+}
+
+vtn_status vtn_launch_count(vtn_ctx ctx, long long* out) {
+    if (!ctx || !out) return VTN_EINVAL;
+    *out = ctx->c.launches;
+    return VTN_OK;
+}
+
+// ------------------------------------------------------------------ MPO
+vtn_status vtn_build_mpo(vtn_ctx ctx, int M, const double* r, const double* U, int D, int d, unsigned flags,
+                         vtn_mpo* out) {
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(out && r && U, "null argument");
+        vtn_mpo mpo = new vtn_mpo_s();
+        std::string err = build_problem(M, r, U, D, d, (flags & VTN_FLAG_LBO) != 0, mpo->hp);
+        if (!err.empty()) {
+            delete mpo;
+            throw Error{VTN_EINVAL, err};
+        }
+        if (ctx) {
+            try {
+                use_device(ctx->c);
+                ensure_mpo_device(ctx, mpo);
+            } catch (...) {
+                for (auto& dc : mpo->dcores) free_core(ctx->c, dc);
+                delete mpo;
+                throw;
+            }
+        }
+        *out = mpo;
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_mpo_free(vtn_mpo mpo) {
+    if (!mpo) return VTN_EINVAL;
+    if (mpo->owner) {
+        Ctx& c = mpo->owner->c;
+        cudaStreamSynchronize(c.stream);
+        for (auto& dc : mpo->dcores) free_core(c, dc);
+        c.dfree(mpo->iso_dev);
+    }
+    delete mpo;
+    return VTN_OK;
+}
+
+vtn_status vtn_mpo_info(vtn_mpo mpo, int* M, int* d, int* D, int* w) {
+    if (!mpo) return VTN_EINVAL;
+    if (M) *M = mpo->hp.M;
+    if (d) *d = mpo->hp.d;
+    if (D) *D = mpo->hp.D;
+    if (w) std::copy(mpo->hp.w.begin(), mpo->hp.w.end(), w);
+    return VTN_OK;
+}
+
+vtn_status vtn_mpo_coefficients(vtn_mpo mpo, double* G) {
+    if (!mpo || !G) return VTN_EINVAL;
+    std::copy(mpo->hp.G.begin(), mpo->hp.G.end(), G);
+    return VTN_OK;
+}
+
+vtn_status vtn_mpo_covariance(vtn_mpo mpo, double* V) {
+    if (!mpo || !V) return VTN_EINVAL;
+    std::copy(mpo->hp.V.begin(), mpo->hp.V.end(), V);
+    return VTN_OK;
+}
+
+vtn_status vtn_mpo_isometry(vtn_mpo mpo, int site, double* V) {
+    if (!mpo || !V || site < 0 || site >= mpo->hp.M) return VTN_EINVAL;
+    const size_t n = (size_t)mpo->hp.D * mpo->hp.d;
+    std::memcpy(V, mpo->hp.iso.data() + (size_t)site * n, sizeof(double) * 2 * n);
+    return VTN_OK;
+}
+
+vtn_status vtn_mpo_core(vtn_mpo mpo, int site, int* nnz, int* rows, int* cols, double* ops) {
+    if (!mpo || !nnz || site < 0 || site >= mpo->hp.M) return VTN_EINVAL;
+    const HostCore& h = mpo->hp.cores[site];
+    const int n = h.nnz();
+    if (!rows) {
+        *nnz = n;
+        return VTN_OK;
+    }
+    if (*nnz < n || !cols || !ops) return VTN_EINVAL;
+    std::copy(h.rows.begin(), h.rows.end(), rows);
+    std::copy(h.cols.begin(), h.cols.end(), cols);
+    std::memcpy(ops, h.ops.data(), sizeof(double) * 2 * h.ops.size());
+    *nnz = n;
+    return VTN_OK;
+}
+
+vtn_status vtn_mpo_norm_bound(vtn_mpo mpo, double* out) {
+    if (!mpo || !out) return VTN_EINVAL;
+    *out = mpo->hp.norm_bound;
+    return VTN_OK;
+}
+
+// ------------------------------------------------------------------ MPS
+vtn_status vtn_mps_random(vtn_ctx ctx, vtn_mpo mpo, int chi, uint64_t seed, vtn_mps* out) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(out && mpo, "null argument");
+        VTN_REQUIRE(chi >= 1, "chi must be >= 1");
+        Ctx& c = ctx->c;
+        use_device(c);
+        const int M = mpo->hp.M, d = mpo->hp.d;
+        vtn_mps m = new_mps(ctx, M, d, bond_dims(M, d, chi));
+        try {
+            for (int s = 0; s < M; ++s) {
+                const int cl = m->dims[s], cr = m->dims[s + 1];
+                fill_random_normal(c, m->sites[s], (long long)cl * d * cr, seed, s);
+                orthonormalize_rows(c, m->sites[s], cl, d * cr);
+            }
+            c.sync();
+        } catch (...) {
+            destroy_mps(m);
+            throw;
+        }
+        m->center = 0;
+        *out = m;
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_mps_from_host(vtn_ctx ctx, vtn_mpo mpo, const int* dims, const double* const* sites, vtn_mps* out) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(out && mpo && dims && sites, "null argument");
+        Ctx& c = ctx->c;
+        use_device(c);
+        const int M = mpo->hp.M, d = mpo->hp.d;
+        std::vector<int> dv(dims, dims + M + 1);
+        VTN_REQUIRE(dv[0] == 1 && dv[M] == 1, "dims[0] and dims[M] must be 1");
+        for (int s = 0; s <= M; ++s) VTN_REQUIRE(dv[s] >= 1 && dv[s] <= 65536, "bond dimension out of range");
+        vtn_mps m = new_mps(ctx, M, d, dv);
+        try {
+            for (int s = 0; s < M; ++s) {
+                VTN_REQUIRE(sites[s] != nullptr, "null site tensor");
+                VTN_CUDA_TRY(cudaMemcpyAsync(m->sites[s], sites[s], sizeof(double2) * (size_t)dv[s] * d * dv[s + 1],
+                                             cudaMemcpyHostToDevice, c.stream));
+            }
+            c.sync();
+        } catch (...) {
+            destroy_mps(m);
+            throw;
+        }
+        m->center = -1;
+        *out = m;
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_mps_free(vtn_mps mps) {
+    if (!mps) return VTN_EINVAL;
+    if (mps->owner) {
+        cudaStreamSynchronize(mps->owner->c.stream);
+    }
+    destroy_mps(mps);
+    return VTN_OK;
+}
+
+vtn_status vtn_mps_info(vtn_mps mps, int* M, int* d, int* dims) {
+    if (!mps) return VTN_EINVAL;
+    if (M) *M = mps->M;
+    if (d) *d = mps->d;
+    if (dims) std::copy(mps->dims.begin(), mps->dims.end(), dims);
+    return VTN_OK;
+}
+
+vtn_status vtn_mps_get_site(vtn_ctx ctx, vtn_mps mps, int site, double* out) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(mps && out && site >= 0 && site < mps->M, "bad argument");
+        Ctx& c = ctx->c;
+        use_device(c);
+        const size_t n = (size_t)mps->dims[site] * mps->d * mps->dims[site + 1];
+        VTN_CUDA_TRY(cudaMemcpyAsync(out, mps->sites[site], sizeof(double2) * n, cudaMemcpyDeviceToHost, c.stream));
+        c.sync();
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_mps_save(vtn_ctx ctx, vtn_mps mps, const char* path) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(mps && path, "null argument");
+        Ctx& c = ctx->c;
+        use_device(c);
+        FILE* f = std::fopen(path, "wb");
+        VTN_REQUIRE(f != nullptr, std::string("cannot open ") + path + " for writing");
+        const char magic[8] = {'V', 'T', 'N', 'M', 'P', 'S', '0', '1'};
+        bool ok = std::fwrite(magic, 1, 8, f) == 8;
+        int hdr[3] = {mps->M, mps->d, mps->center};
+        ok = ok && std::fwrite(hdr, sizeof(int), 3, f) == 3;
+        ok = ok && std::fwrite(mps->dims.data(), sizeof(int), mps->M + 1, f) == (size_t)(mps->M + 1);
+        std::vector<double2> buf;
+        for (int s = 0; s < mps->M && ok; ++s) {
+            const size_t n = (size_t)mps->dims[s] * mps->d * mps->dims[s + 1];
+            buf.resize(n);
+            cudaError_t e = cudaMemcpyAsync(buf.data(), mps->sites[s], sizeof(double2) * n, cudaMemcpyDeviceToHost, c.stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+            ok = (e == cudaSuccess) && std::fwrite(buf.data(), sizeof(double2), n, f) == n;
+        }
+        std::fclose(f);
+        VTN_REQUIRE(ok, std::string("writing ") + path + " failed");
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_mps_load(vtn_ctx ctx, vtn_mpo mpo, const char* path, vtn_mps* out) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(mpo && path && out, "null argument");
+        Ctx& c = ctx->c;
+        use_device(c);
+        FILE* f = std::fopen(path, "rb");
+        VTN_REQUIRE(f != nullptr, std::string("cannot open ") + path);
+        char magic[8];
+        int hdr[3];
+        bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "VTNMPS01", 8) == 0;
+        ok = ok && std::fread(hdr, sizeof(int), 3, f) == 3;
+        if (!ok || hdr[0] != mpo->hp.M || hdr[1] != mpo->hp.d) {
+            std::fclose(f);
+            throw Error{VTN_EINVAL, "checkpoint does not match the MPO or is not a vtn MPS file"};
+        }
+        std::vector<int> dims(hdr[0] + 1);
+        ok = std::fread(dims.data(), sizeof(int), dims.size(), f) == dims.size();
+        for (int x : dims) ok = ok && x >= 1 && x <= 65536;
+        if (!ok) {
+            std::fclose(f);
+            throw Error{VTN_EINVAL, "corrupt checkpoint header"};
+        }
+        std::vector<std::vector<double>> host(hdr[0]);
+        std::vector<const double*> ptrs(hdr[0]);
+        for (int s = 0; s < hdr[0] && ok; ++s) {
+            const size_t n = (size_t)dims[s] * hdr[1] * dims[s + 1];
+            host[s].resize(2 * n);
+            ok = std::fread(host[s].data(), sizeof(double) * 2, n, f) == n;
+            ptrs[s] = host[s].data();
+        }
+        std::fclose(f);
+        VTN_REQUIRE(ok, "truncated checkpoint");
+        vtn_status st = vtn_mps_from_host(ctx, mpo, dims.data(), ptrs.data(), out);
+        if (st == VTN_OK) (*out)->center = hdr[2];
+        if (st != VTN_OK) throw Error{st, ctx->c.err};
+        return VTN_OK;
+    });
+}
+
+// ------------------------------------------------------------------ solver
+vtn_status vtn_sweep_opts_default(vtn_sweep_opts* o) {
+    if (!o) return VTN_EINVAL;
+    std::memset(o, 0, sizeof(*o));
+    o->chi_max = 16;
+    o->n_sweeps = 8;
+    o->prec = VTN_FP64;
+    o->lanczos_tol = 1e-10;
+    o->krylov_max = 32;
+    o->lanczos_max_restarts = 4;
+    return VTN_OK;
+}
+
+vtn_status vtn_sweep(vtn_ctx ctx, vtn_mpo mpo, vtn_mps* state, const vtn_sweep_opts* opts, vtn_sweep_report* report) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(mpo && state && opts, "null argument");
+        VTN_REQUIRE(opts->chi_max >= 1, "chi_max must be >= 1");
+        VTN_REQUIRE(opts->n_sweeps >= 0 && opts->n_sweeps <= 64, "n_sweeps must be in [0, 64]");
+        VTN_REQUIRE(opts->krylov_max >= 1 && opts->krylov_max <= 64, "krylov_max must be in [1, 64]");
+        VTN_REQUIRE(opts->lanczos_max_restarts >= 0, "lanczos_max_restarts must be >= 0");
+        VTN_REQUIRE(opts->n_schedule == 0 || opts->chi_schedule != nullptr, "chi_schedule missing");
+        if (opts->prec != VTN_FP64)
+            throw Error{VTN_EUNSUPPORTED, "only VTN_FP64 contractions are available in this build"};
+        Ctx& c = ctx->c;
+        use_device(c);
+        ensure_mpo_device(ctx, mpo);
+        const int M = mpo->hp.M, d = mpo->hp.d;
+        if (M < 2) throw Error{VTN_EUNSUPPORTED, "two-site DMRG needs M >= 2"};
+        std::vector<int> sched;
+        for (int i = 0; i < opts->n_schedule; ++i) {
+            VTN_REQUIRE(opts->chi_schedule[i] >= 1, "chi_schedule entries must be >= 1");
+            sched.push_back(std::min(opts->chi_schedule[i], opts->chi_max));
+        }
+        if (sched.empty()) sched.push_back(opts->chi_max);
+        bool created = false;
+        if (*state == nullptr) {
+            vtn_status st = vtn_mps_random(ctx, mpo, sched[0], opts->seed, state);
+            if (st != VTN_OK) throw Error{st, c.err};
+            created = true;
+        }
+        vtn_mps mps = *state;
+        (void)created;
+        check_mps_matches(mpo, mps);
+        int chi_cap = opts->chi_max;
+        for (int x : mps->dims) chi_cap = std::max(chi_cap, x);
+        mps_reserve(c, mps, chi_cap);
+        const std::vector<int> capdims = cap_dims(M, chi_cap);
+        // environments sized for the largest bond dimension at each cut
+        Envs env;
+        env.c = &c;
+        env.L.assign(M + 1, nullptr);
+        env.R.assign(M + 1, nullptr);
+        for (int s = 0; s <= M; ++s) {
+            const size_t cap = (size_t)mpo->hp.w[s] * capdims[s] * capdims[s];
+            env.L[s] = (double2*)c.dalloc(sizeof(double2) * std::max(cap, size_t(1)));
+            env.R[s] = (double2*)c.dalloc(sizeof(double2) * std::max(cap, size_t(1)));
+        }
+        set_scalar_one(c, env.L[0]);
+        set_scalar_one(c, env.R[M]);
+        for (int s = M - 1; s >= 1; --s)
+            env_right_dev(c, mpo->dcores[s], mps->dims[s], mps->dims[s + 1], env.R[s + 1], mps->sites[s], env.R[s]);
+        const size_t theta_cap = (size_t)chi_cap * d * d * chi_cap;
+        double2* theta = (double2*)c.workspace(WS_VEC_T, sizeof(double2) * theta_cap);
+        vtn_sweep_report rep;
+        std::memset(&rep, 0, sizeof(rep));
+        long long not_conv = 0;
+        double prevE = 0.0;
+        bool have_prev = false;
+        for (int sw = 0; sw < opts->n_sweeps; ++sw) {
+            const auto t0 = std::chrono::steady_clock::now();
+            const int chi_s = sched[std::min<size_t>(sw, sched.size() - 1)];
+            double disc_max = 0.0;
+            for (int dir = 0; dir < 2; ++dir) {
+                for (int step = 0; step < M - 1; ++step) {
+                    const int i = dir == 0 ? step : (M - 2 - step);
+                    const int cl = mps->dims[i], cm = mps->dims[i + 1], cr = mps->dims[i + 2];
+                    // theta = A_i A_{i+1}
+                    GemmArgs g;
+                    g.M = cl * d; g.N = d * cr; g.K = cm;
+                    g.A = mps->sites[i]; g.lda = cm;
+                    g.B = mps->sites[i + 1]; g.ldb = (long long)d * cr;
+                    g.C = theta; g.ldc = (long long)d * cr;
+                    gemm_c64(c, g);
+                    const long long n = (long long)cl * d * d * cr;
+                    const DevCore& Wi = mpo->dcores[i];
+                    const DevCore& Wj = mpo->dcores[i + 1];
+                    const double2* L = env.L[i];
+                    const double2* R = env.R[i + 2];
+                    const double hf = heff_flops(Wi, Wj, cl, cr);
+                    LanczosResult lr = lanczos(c, n, theta, opts->lanczos_tol, opts->krylov_max,
+                                               opts->lanczos_max_restarts, [&](const double2* in, double2* out) {
+                                                   heff_apply_dev(c, Wi, Wj, cl, cr, L, R, in, out);
+                                               });
+                    rep.matvecs += lr.n_matvec;
+                    rep.heff_flops += hf * lr.n_matvec;
+                    if (!lr.converged) ++not_conv;
+                    TruncResult tr = truncate_dev(c, cl, d, d, cr, dir, chi_s, theta, mps->sites[i], mps->sites[i + 1]);
+                    mps->dims[i + 1] = tr.k;
+                    disc_max = std::max(disc_max, tr.discarded);
+                    if (dir == 0)
+                        env_left_dev(c, Wi, cl, tr.k, env.L[i], mps->sites[i], env.L[i + 1]);
+                    else
+                        env_right_dev(c, Wj, tr.k, cr, env.R[i + 2], mps->sites[i + 1], env.R[i + 1]);
+                }
+            }
+            mps->center = 0;
+            const double E = energy_dev(c, mpo, mps);
+            c.sync();
+            const auto t1 = std::chrono::steady_clock::now();
+            rep.energy[sw] = E;
+            rep.max_discarded[sw] = disc_max;
+            rep.seconds[sw] = std::chrono::duration<double>(t1 - t0).count();
+            rep.sweeps_done = sw + 1;
+            if (opts->use_e_target && E <= opts->e_target) break;
+            if (have_prev && opts->e_tol > 0 && std::fabs(E - prevE) <= opts->e_tol) break;
+            prevE = E;
+            have_prev = true;
+        }
+        c.tflush();
+        rep.lanczos_not_converged = not_conv;
+        rep.heff_seconds = c.tc[TC_HEFF].seconds;
+        rep.gemm_flops = c.tc[TC_GEMM].flops;
+        rep.gemm_seconds = c.tc[TC_GEMM].seconds;
+        rep.eig_seconds = c.tc[TC_EIG].seconds;
+        if (report) *report = rep;
+        if (not_conv > 0) {
+            c.err = std::to_string(not_conv) + " Lanczos solves missed the tolerance";
+            return VTN_ENOCONV;
+        }
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_energy(vtn_ctx ctx, vtn_mpo mpo, vtn_mps mps, double* E) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(mpo && mps && E, "null argument");
+        Ctx& c = ctx->c;
+        use_device(c);
+        ensure_mpo_device(ctx, mpo);
+        check_mps_matches(mpo, mps);
+        *E = energy_dev(c, mpo, mps);
+        return VTN_OK;
+    });
+}
+
+namespace {
+
+// Fock-basis tensor of site s (rotated with the isometry) into dst (chi_l x D x chi_r).
+const double2* fock_site(Ctx& c, vtn_mpo mpo, vtn_mps mps, int s, double2* dst) {
+    const int D = mpo->hp.D, d = mpo->hp.d;
+    if (!mpo->hp.lbo && D == d) return mps->sites[s];
+    lbo_rotate_dev(c, mps->dims[s], d, D, mps->dims[s + 1], mpo->iso_dev + (size_t)s * D * d, mps->sites[s], dst);
+    return dst;
+}
+
+}  // namespace
+
+vtn_status vtn_marginals(vtn_ctx ctx, vtn_mpo mpo, vtn_mps mps, const int* modes, int k, double* out) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(mpo && mps && modes && out, "null argument");
+        Ctx& c = ctx->c;
+        use_device(c);
+        ensure_mpo_device(ctx, mpo);
+        check_mps_matches(mpo, mps);
+        const int M = mpo->hp.M, D = mpo->hp.D, d = mpo->hp.d;
+        VTN_REQUIRE(k >= 1 && k <= M, "k must be in [1, M]");
+        std::vector<int> sorted(modes, modes + k);
+        for (int x : sorted) VTN_REQUIRE(x >= 0 && x < M, "mode out of range");
+        std::sort(sorted.begin(), sorted.end());
+        for (int j = 1; j < k; ++j) VTN_REQUIRE(sorted[j] != sorted[j - 1], "modes repeat");
+        double cnt_d = std::pow((double)D, k);
+        VTN_REQUIRE(cnt_d <= (double)(1 << 26), "D^k exceeds 2^26 outputs");
+        const long long total = (long long)cnt_d;
+        const int chi = max_dim(mps->dims);
+        const double env_bytes = cnt_d * chi * (double)chi * sizeof(double2);
+        VTN_REQUIRE(env_bytes <= 16e9, "joint marginal environments exceed 16 GB (D^k chi^2 too large)");
+        // buffers
+        const size_t envn = (size_t)total * chi * chi;
+        double2* E0 = (double2*)c.workspace(WS_Z, sizeof(double2) * envn * 2);
+        double2* E1 = E0 + envn;
+        double2* tmp = (double2*)c.workspace(WS_ENV_TMP, sizeof(double2) * (size_t)total * chi * std::max(d, D) * chi);
+        double2* AF = (double2*)c.workspace(WS_MISC, sizeof(double2) * (size_t)chi * D * chi);
+        set_scalar_one(c, E0);
+        long long count = 1;
+        size_t pos = 0;
+        for (int s = 0; s < M; ++s) {
+            const int cl = mps->dims[s], cr = mps->dims[s + 1];
+            if (pos < sorted.size() && sorted[pos] == s) {
+                const double2* A = fock_site(c, mpo, mps, s, AF);
+                // tmp[t] = E[t] A (cl x D cr)
+                GemmArgs g1;
+                g1.M = cl; g1.N = D * cr; g1.K = cl; g1.batch = (int)count;
+                g1.A = E0; g1.lda = cl; g1.sA_batch = (long long)cl * cl;
+                g1.B = A; g1.ldb = (long long)D * cr; g1.sB_batch = 0;
+                g1.C = tmp; g1.ldc = (long long)D * cr; g1.sC_batch = (long long)cl * D * cr;
+                gemm_c64(c, g1);
+                for (int nn = 0; nn < D; ++nn) {
+                    // E1[t D + n] = A[:, n, :]^dag tmp[t][:, n, :]
+                    GemmArgs g2;
+                    g2.M = cr; g2.N = cr; g2.K = cl; g2.batch = (int)count;
+                    g2.opA = OP_C; g2.A = A + (size_t)nn * cr; g2.lda = (long long)D * cr; g2.sA_batch = 0;
+                    g2.B = tmp + (size_t)nn * cr; g2.ldb = (long long)D * cr; g2.sB_batch = (long long)cl * D * cr;
+                    g2.C = E1 + (size_t)nn * cr * cr; g2.ldc = cr; g2.sC_batch = (long long)D * cr * cr;
+                    gemm_c64(c, g2);
+                }
+                count *= D;
+                ++pos;
+            } else {
+                transfer_left_batch(c, (int)count, cl, d, cr, E0, mps->sites[s], E1, tmp);
+            }
+            std::swap(E0, E1);
+        }
+        // E0 holds count = D^k scalars (1 x 1 environments)
+        std::vector<double2> vals(total);
+        VTN_CUDA_TRY(cudaMemcpyAsync(vals.data(), E0, sizeof(double2) * total, cudaMemcpyDeviceToHost, c.stream));
+        c.sync();
+        const double n2 = mps_norm2(c, mps);
+        // reorder from ascending-mode order to the caller's order
+        std::vector<int> rank(k);
+        for (int j = 0; j < k; ++j) rank[j] = (int)(std::find(sorted.begin(), sorted.end(), modes[j]) - sorted.begin());
+        std::vector<int> digit(k);
+        for (long long t = 0; t < total; ++t) {
+            long long rem = t;
+            for (int j = k - 1; j >= 0; --j) {
+                digit[j] = (int)(rem % D);
+                rem /= D;
+            }
+            long long idx = 0;
+            for (int j = 0; j < k; ++j) idx = idx * D + digit[rank[j]];
+            out[idx] = vals[t].x / n2;
+        }
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_marginals_all(vtn_ctx ctx, vtn_mpo mpo, vtn_mps mps, double* out) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(mpo && mps && out, "null argument");
+        Ctx& c = ctx->c;
+        use_device(c);
+        ensure_mpo_device(ctx, mpo);
+        check_mps_matches(mpo, mps);
+        const int M = mpo->hp.M, D = mpo->hp.D, d = mpo->hp.d;
+        const int chi = max_dim(mps->dims);
+        const size_t env = (size_t)chi * chi;
+        // all left and right transfer environments
+        double2* EL = (double2*)c.workspace(WS_Z, sizeof(double2) * env * (M + 1) * 2);
+        double2* ER = EL + env * (M + 1);
+        double2* tmp = (double2*)c.workspace(WS_ENV_TMP, sizeof(double2) * (size_t)chi * std::max(d, D) * chi);
+        double2* AF = (double2*)c.workspace(WS_MISC, sizeof(double2) * (size_t)chi * D * chi);
+        double2* U = (double2*)c.workspace(WS_Y, sizeof(double2) * (size_t)chi * D * chi);
+        double* P = (double*)c.workspace(WS_PARTIAL, sizeof(double) * (size_t)M * D);
+        set_scalar_one(c, EL);
+        for (int s = 0; s < M; ++s)
+            transfer_left_batch(c, 1, mps->dims[s], d, mps->dims[s + 1], EL + env * s, mps->sites[s], EL + env * (s + 1),
+                                tmp);
+        set_scalar_one(c, ER + env * M);
+        for (int s = M - 1; s >= 0; --s)
+            transfer_right(c, mps->dims[s], d, mps->dims[s + 1], ER + env * (s + 1), mps->sites[s], ER + env * s, tmp);
+        for (int s = 0; s < M; ++s) {
+            const int cl = mps->dims[s], cr = mps->dims[s + 1];
+            const double2* A = fock_site(c, mpo, mps, s, AF);
+            GemmArgs g1;  // tmp = EL[s] A   (cl x D cr)
+            g1.M = cl; g1.N = D * cr; g1.K = cl;
+            g1.A = EL + env * s; g1.lda = cl;
+            g1.B = A; g1.ldb = (long long)D * cr;
+            g1.C = tmp; g1.ldc = (long long)D * cr;
+            gemm_c64(c, g1);
+            GemmArgs g2;  // U = tmp (cl D x cr) ER[s+1]
+            g2.M = cl * D; g2.N = cr; g2.K = cr;
+            g2.A = tmp; g2.lda = cr;
+            g2.B = ER + env * (s + 1); g2.ldb = cr;
+            g2.C = U; g2.ldc = cr;
+            gemm_c64(c, g2);
+            marginal_reduce_dev(c, cl, D, cr, A, U, P + (size_t)s * D);
+        }
+        std::vector<double> host((size_t)M * D + 1);
+        VTN_CUDA_TRY(cudaMemcpyAsync(host.data(), P, sizeof(double) * M * D, cudaMemcpyDeviceToHost, c.stream));
+        VTN_CUDA_TRY(cudaMemcpyAsync(c.pinned, EL + env * M, sizeof(double2), cudaMemcpyDeviceToHost, c.stream));
+        c.sync();
+        const double n2 = c.pinned[0];
+        for (size_t i = 0; i < (size_t)M * D; ++i) out[i] = host[i] / n2;
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_sample(vtn_ctx ctx, vtn_mpo mpo, vtn_mps mps, uint64_t seed, int n_samples, int32_t* out) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(mpo && mps && out, "null argument");
+        VTN_REQUIRE(n_samples >= 0, "n_samples must be >= 0");
+        if (n_samples == 0) return VTN_OK;
+        Ctx& c = ctx->c;
+        use_device(c);
+        ensure_mpo_device(ctx, mpo);
+        check_mps_matches(mpo, mps);
+        const int M = mpo->hp.M, D = mpo->hp.D, d = mpo->hp.d;
+        const int chi = max_dim(mps->dims);
+        const size_t env = (size_t)chi * chi;
+        const size_t site_f = (size_t)chi * D * chi;
+        // one allocation: ER[M+1], AF[M], pointer tables, dims, output
+        const size_t bytes = sizeof(double2) * (env * (M + 1) + site_f * M) + sizeof(void*) * 2 * (M + 1) +
+                             sizeof(int) * (M + 1) + sizeof(int) * (size_t)n_samples * M + 1024;
+        unsigned char* base = (unsigned char*)c.dalloc(bytes);
+        struct Free {
+            Ctx& c;
+            void* p;
+            ~Free() {
+                cudaStreamSynchronize(c.stream);
+                c.dfree(p);
+            }
+        } fr{c, base};
+        double2* ER = (double2*)base;
+        double2* AFall = ER + env * (M + 1);
+        const double2** pAF = (const double2**)(AFall + site_f * M);
+        const double2** pER = pAF + (M + 1);
+        int* ddims = (int*)(pER + (M + 1));
+        int* dout = ddims + (M + 1);
+        double2* tmp = (double2*)c.workspace(WS_ENV_TMP, sizeof(double2) * (size_t)chi * d * chi);
+        set_scalar_one(c, ER + env * M);
+        for (int s = M - 1; s >= 0; --s)
+            transfer_right(c, mps->dims[s], d, mps->dims[s + 1], ER + env * (s + 1), mps->sites[s], ER + env * s, tmp);
+        std::vector<const double2*> hAF(M + 1, nullptr), hER(M + 1, nullptr);
+        for (int s = 0; s < M; ++s) {
+            double2* dst = AFall + site_f * s;
+            const double2* A = fock_site(c, mpo, mps, s, dst);
+            if (A != dst)
+                VTN_CUDA_TRY(cudaMemcpyAsync(dst, A, sizeof(double2) * (size_t)mps->dims[s] * D * mps->dims[s + 1],
+                                             cudaMemcpyDeviceToDevice, c.stream));
+            hAF[s] = dst;
+        }
+        for (int s = 0; s <= M; ++s) hER[s] = ER + env * s;
+        VTN_CUDA_TRY(cudaMemcpyAsync(pAF, hAF.data(), sizeof(void*) * (M + 1), cudaMemcpyHostToDevice, c.stream));
+        VTN_CUDA_TRY(cudaMemcpyAsync(pER, hER.data(), sizeof(void*) * (M + 1), cudaMemcpyHostToDevice, c.stream));
+        VTN_CUDA_TRY(cudaMemcpyAsync(ddims, mps->dims.data(), sizeof(int) * (M + 1), cudaMemcpyHostToDevice, c.stream));
+        sample_dev(c, pAF, pER, ddims, M, D, chi, seed, n_samples, dout);
+        VTN_CUDA_TRY(cudaMemcpyAsync(out, dout, sizeof(int) * (size_t)n_samples * M, cudaMemcpyDeviceToHost, c.stream));
+        c.sync();
+        return VTN_OK;
+    });
+}
+
+// ------------------------------------------------------------------ kernel-level calls
+vtn_status vtn_heff_apply(vtn_ctx ctx, const vtn_core* Wi, const vtn_core* Wj, int chi_l, int chi_r, const double* L,
+                          const double* R, const double* theta, double* y, vtn_precision prec) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(L && R && theta && y, "null device pointer");
+        VTN_REQUIRE(chi_l >= 1 && chi_r >= 1, "bond dimensions must be >= 1");
+        VTN_REQUIRE(theta != y, "y must not alias theta");
+        if (prec != VTN_FP64) throw Error{VTN_EUNSUPPORTED, "only VTN_FP64 contractions are available in this build"};
+        Ctx& c = ctx->c;
+        use_device(c);
+        HostCore hi = core_from_abi(Wi), hj = core_from_abi(Wj);
+        VTN_REQUIRE(hi.wr == hj.wl && hi.d == hj.d, "Wi.w_right must equal Wj.w_left and d must agree");
+        TempCore ci(c, hi), cj(c, hj);
+        heff_apply_dev(c, ci.dc, cj.dc, chi_l, chi_r, (const double2*)L, (const double2*)R, (const double2*)theta,
+                       (double2*)y);
+        c.sync();
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_env_update(vtn_ctx ctx, const vtn_core* W, int side, int chi_l, int chi_r, const double* env,
+                          const double* A, double* out, vtn_precision prec) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(env && A && out, "null device pointer");
+        VTN_REQUIRE(side == 0 || side == 1, "side must be 0 (left) or 1 (right)");
+        VTN_REQUIRE(chi_l >= 1 && chi_r >= 1, "bond dimensions must be >= 1");
+        if (prec != VTN_FP64) throw Error{VTN_EUNSUPPORTED, "only VTN_FP64 contractions are available in this build"};
+        Ctx& c = ctx->c;
+        use_device(c);
+        HostCore h = core_from_abi(W);
+        TempCore tc(c, h);
+        if (side == 0)
+            env_left_dev(c, tc.dc, chi_l, chi_r, (const double2*)env, (const double2*)A, (double2*)out);
+        else
+            env_right_dev(c, tc.dc, chi_l, chi_r, (const double2*)env, (const double2*)A, (double2*)out);
+        c.sync();
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_heff_ground(vtn_ctx ctx, const vtn_core* Wi, const vtn_core* Wj, int chi_l, int chi_r, const double* L,
+                           const double* R, double* theta, double tol, int krylov_max, int max_restarts, double* E,
+                           int* n_matvec) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(L && R && theta && E, "null argument");
+        VTN_REQUIRE(chi_l >= 1 && chi_r >= 1, "bond dimensions must be >= 1");
+        Ctx& c = ctx->c;
+        use_device(c);
+        HostCore hi = core_from_abi(Wi), hj = core_from_abi(Wj);
+        VTN_REQUIRE(hi.wr == hj.wl && hi.d == hj.d, "Wi.w_right must equal Wj.w_left and d must agree");
+        TempCore ci(c, hi), cj(c, hj);
+        const long long n = (long long)chi_l * hi.d * hi.d * chi_r;
+        LanczosResult lr = lanczos(c, n, (double2*)theta, tol, krylov_max, max_restarts,
+                                   [&](const double2* in, double2* out) {
+                                       heff_apply_dev(c, ci.dc, cj.dc, chi_l, chi_r, (const double2*)L,
+                                                      (const double2*)R, in, out);
+                                   });
+        c.sync();
+        *E = lr.theta;
+        if (n_matvec) *n_matvec = lr.n_matvec;
+        if (!lr.converged) {
+            c.err = "Lanczos missed the tolerance";
+            return VTN_ENOCONV;
+        }
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_truncate(vtn_ctx ctx, int chi_l, int d1, int d2, int chi_r, int direction, int k_max, const double* theta,
+                        double* left, double* right, double* lam, double* discarded, int* k_out) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(theta && left && right, "null device pointer");
+        VTN_REQUIRE(chi_l >= 1 && d1 >= 1 && d2 >= 1 && chi_r >= 1 && k_max >= 1, "sizes must be >= 1");
+        VTN_REQUIRE(direction == 0 || direction == 1, "direction must be 0 or 1");
+        Ctx& c = ctx->c;
+        use_device(c);
+        TruncResult r = truncate_dev(c, chi_l, d1, d2, chi_r, direction, k_max, (const double2*)theta,
+                                     (double2*)left, (double2*)right);
+        if (lam) std::copy(r.lam.begin(), r.lam.end(), lam);
+        if (discarded) *discarded = r.discarded;
+        if (k_out) *k_out = r.k;
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_lbo_rotate(vtn_ctx ctx, int chi_l, int d, int D, int chi_r, const double* V, const double* A,
+                          double* out) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(V && A && out, "null device pointer");
+        VTN_REQUIRE(chi_l >= 1 && d >= 1 && D >= 1 && chi_r >= 1, "sizes must be >= 1");
+        Ctx& c = ctx->c;
+        use_device(c);
+        lbo_rotate_dev(c, chi_l, d, D, chi_r, (const double2*)V, (const double2*)A, (double2*)out);
+        c.sync();
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_timing(vtn_ctx ctx, int enable) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        ctx->c.tflush();
+        ctx->c.timing = enable != 0;
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_timing_read(vtn_ctx ctx, int cls, long long* launches, double* flops, double* seconds) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(cls >= 0 && cls < TC_COUNT, "timing class out of range");
+        ctx->c.tflush();
+        if (launches) *launches = ctx->c.tc[cls].launches;
+        if (flops) *flops = ctx->c.tc[cls].flops;
+        if (seconds) *seconds = ctx->c.tc[cls].seconds;
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_timing_reset(vtn_ctx ctx) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        ctx->c.tflush();
+        for (auto& t : ctx->c.tc) t = Ctx::Tc{};
+        return VTN_OK;
+    });
+}
+
+}  // extern "C"

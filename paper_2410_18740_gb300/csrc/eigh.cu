@@ -1,0 +1,558 @@
+// FP64 truncation eigensolver: the reduced density matrix rho of a two-site tensor,
+// its largest k eigenpairs, and the split of the tensor into a canonical site and the
+// new centre.  Every step runs on the GPU:
+//
+//  1. rho = T T^dag (or T^dag T) by the complex GEMM.
+//  2. Householder tridiagonalisation of the Hermitian rho (Golub & Van Loan, Sec. 8.3.1):
+//     for each column a Hermitian reflector H = I - tau v v^dag with H x = beta e_1,
+//     p = tau A v, w = p - (tau/2)(v^dag p) v, A <- A - v w^dag - w v^dag.  The complex
+//     sub-diagonal is made real by a diagonal phase similarity.
+//  3. The k largest eigenvalues of the real tridiagonal by bisection on Sturm counts,
+//     one warp per eigenvalue evaluating 32 points per round (multisection).
+//  4. Eigenvectors by inverse iteration with a pivoted tridiagonal LU, one thread per
+//     eigenvector, three iterations from deterministic pseudo-random starts.
+//  5. Orthonormalisation of the k vectors by shifted CholeskyQR3 (Fukaya, Kannan,
+//     Nakatsukasa, Yamamoto, Yanagisawa, SIAM J. Sci. Comput. 2020): one shifted and two
+//     plain Cholesky-QR passes; column order is preserved, so the span of the leading j
+//     vectors is that of the j largest eigenvalues.
+//  6. Back-transformation through the reflectors and the phases, one CTA per vector.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "vtn_internal.cuh"
+
+namespace vtn {
+namespace {
+
+constexpr double EPS = 2.220446049250313e-16;
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ double block_sum(double v, double* sh) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (wid == 0) {
+        r = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+        r = warp_sum(r);
+        if (lane == 0) sh[32] = r;
+    }
+    __syncthreads();
+    r = sh[32];
+    __syncthreads();
+    return r;  // valid in every thread
+}
+
+struct EigSmall {
+    double* diag;   // [n]
+    double* offd;   // [n]
+    double* tau;    // [n]
+    double* lam;    // [n]
+    double2* e;     // [n]
+    double2* ph;    // [n]
+    double2* p;     // [n]
+    double2* w;     // [n]
+    double* scal;   // [8]: trace, status
+};
+
+// ---------------------------------------------------------------- Householder steps
+__global__ void __launch_bounds__(1024) hh_reflector(const double2* __restrict__ A, int n, int k,
+                                                     double2* __restrict__ H, EigSmall s) {
+    __shared__ double sh[33];
+    const int m = n - k - 1;
+    const double2* row = A + (long long)k * n + (k + 1);  // conj of column k below the diagonal
+    double a2 = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        double2 v = row[i];
+        a2 += v.x * v.x + v.y * v.y;
+    }
+    a2 = block_sum(a2, sh);
+    const double2 x0 = make_double2(row[0].x, -row[0].y);
+    const double ax0 = hypot(x0.x, x0.y);
+    double2* v = H + (long long)k * n;
+    if (a2 == 0.0) {
+        for (int i = threadIdx.x; i < m; i += blockDim.x) v[i] = make_double2(0.0, 0.0);
+        if (threadIdx.x == 0) {
+            s.tau[k] = 0.0;
+            s.e[k] = make_double2(0.0, 0.0);
+            s.diag[k] = A[(long long)k * n + k].x;
+        }
+        return;
+    }
+    const double alpha = sqrt(a2);
+    const double2 phi = ax0 > 0.0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        double2 xi = make_double2(row[i].x, -row[i].y);
+        if (i == 0) xi = make_double2(x0.x + phi.x * alpha, x0.y + phi.y * alpha);
+        v[i] = xi;
+    }
+    if (threadIdx.x == 0) {
+        s.tau[k] = 1.0 / (alpha * (alpha + ax0));  // 2 / (v^dag v), v^dag v = 2 alpha (alpha + |x0|)
+        s.e[k] = make_double2(-phi.x * alpha, -phi.y * alpha);
+        s.diag[k] = A[(long long)k * n + k].x;
+    }
+}
+
+// p_i = tau sum_j A[k+1+i][k+1+j] v_j, one warp per row
+__global__ void __launch_bounds__(256) hh_matvec(const double2* __restrict__ A, int n, int k,
+                                                 const double2* __restrict__ H, EigSmall s) {
+    const int m = n - k - 1;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= m) return;
+    const double tau = s.tau[k];
+    const double2* row = A + (long long)(k + 1 + warp) * n + (k + 1);
+    const double2* v = H + (long long)k * n;
+    double re = 0.0, im = 0.0;
+    for (int j = lane; j < m; j += 32) {
+        const double2 a = row[j], b = v[j];
+        re += a.x * b.x - a.y * b.y;
+        im += a.x * b.y + a.y * b.x;
+    }
+    re = warp_sum(re);
+    im = warp_sum(im);
+    if (lane == 0) s.p[warp] = make_double2(tau * re, tau * im);
+}
+
+// K = (tau/2) Re(v^dag p);  w = p - K v
+__global__ void __launch_bounds__(1024) hh_w(int n, int k, const double2* __restrict__ H, EigSmall s) {
+    __shared__ double sh[33];
+    const int m = n - k - 1;
+    const double2* v = H + (long long)k * n;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const double2 a = v[i], b = s.p[i];
+        acc += a.x * b.x + a.y * b.y;
+    }
+    acc = block_sum(acc, sh);
+    const double K = 0.5 * s.tau[k] * acc;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const double2 a = v[i], b = s.p[i];
+        s.w[i] = make_double2(b.x - K * a.x, b.y - K * a.y);
+    }
+}
+
+// A22 -= v w^dag + w v^dag
+__global__ void __launch_bounds__(256) hh_rank2(double2* __restrict__ A, int n, int k, const double2* __restrict__ H,
+                                                EigSmall s) {
+    const int m = n - k - 1;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)m * m) return;
+    const int i = (int)(t / m), j = (int)(t % m);
+    const double2* v = H + (long long)k * n;
+    const double2 vi = v[i], vj = v[j], wi = s.w[i], wj = s.w[j];
+    // v_i conj(w_j) + w_i conj(v_j)
+    const double re = vi.x * wj.x + vi.y * wj.y + wi.x * vj.x + wi.y * vj.y;
+    const double im = vi.y * wj.x - vi.x * wj.y + wi.y * vj.x - wi.x * vj.y;
+    double2* a = A + (long long)(k + 1 + i) * n + (k + 1 + j);
+    a->x -= re;
+    a->y -= im;
+}
+
+// tail of the tridiagonal, real off-diagonal and phases
+__global__ void tri_finalize(const double2* __restrict__ A, int n, EigSmall s) {
+    if (threadIdx.x != 0) return;
+    if (n >= 2) {
+        s.diag[n - 2] = A[(long long)(n - 2) * n + (n - 2)].x;
+        const double2 t = A[(long long)(n - 2) * n + (n - 1)];
+        s.e[n - 2] = make_double2(t.x, -t.y);  // A[n-1][n-2] = conj(A[n-2][n-1])
+    }
+    s.diag[n - 1] = A[(long long)(n - 1) * n + (n - 1)].x;
+    s.ph[0] = make_double2(1.0, 0.0);
+    for (int i = 0; i + 1 < n; ++i) {
+        const double2 e = s.e[i];
+        const double r = hypot(e.x, e.y);
+        s.offd[i] = r;
+        const double2 q = s.ph[i];
+        if (r > 0.0) {
+            const double ux = e.x / r, uy = e.y / r;
+            s.ph[i + 1] = make_double2(q.x * ux - q.y * uy, q.x * uy + q.y * ux);
+        } else {
+            s.ph[i + 1] = q;
+        }
+    }
+    s.offd[n - 1] = 0.0;
+}
+
+// ---------------------------------------------------------------- eigenvalues
+__device__ void tri_bounds(const double* a, const double* b, int n, double& gl, double& gu, double& tn) {
+    gl = 1e308; gu = -1e308; tn = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < n ? fabs(b[i]) : 0.0);
+        gl = fmin(gl, a[i] - r);
+        gu = fmax(gu, a[i] + r);
+        tn = fmax(tn, fabs(a[i]) + r);
+    }
+}
+
+__device__ int sturm(const double* a, const double* b, int n, double x, double pivmin) {
+    int cnt = 0;
+    double q = a[0] - x;
+    if (fabs(q) < pivmin) q = -pivmin;
+    if (q < 0) ++cnt;
+    for (int i = 1; i < n; ++i) {
+        q = a[i] - x - b[i - 1] * b[i - 1] / q;
+        if (fabs(q) < pivmin) q = -pivmin;
+        if (q < 0) ++cnt;
+    }
+    return cnt;
+}
+
+// one warp per eigenvalue; output j (descending) = ascending index n-1-j
+__global__ void __launch_bounds__(32) bisect_top(int n, int k, EigSmall s) {
+    const int j = blockIdx.x;
+    if (j >= k) return;
+    const int idx = n - 1 - j;
+    const int lane = threadIdx.x;
+    double gl, gu, tn;
+    tri_bounds(s.diag, s.offd, n, gl, gu, tn);
+    const double pivmin = fmax(1e-300, EPS * EPS * fmax(tn, 1e-300));
+    double lo = gl - EPS * tn - pivmin, hi = gu + EPS * tn + pivmin;
+    for (int round = 0; round < 64; ++round) {
+        if (hi - lo <= 2.0 * EPS * fmax(fabs(lo), fabs(hi)) + 4.0 * pivmin) break;
+        const double step = (hi - lo) / 33.0;
+        const double x = lo + step * (lane + 1);
+        const int c = sturm(s.diag, s.offd, n, x, pivmin);
+        const unsigned bal = __ballot_sync(0xffffffffu, c >= idx + 1);
+        if (bal == 0) {
+            lo = lo + step * 32;
+        } else {
+            const int f = __ffs(bal) - 1;
+            hi = lo + step * (f + 1);
+            lo = lo + step * f;
+        }
+    }
+    if (lane == 0) s.lam[j] = 0.5 * (lo + hi);
+}
+
+__device__ __forceinline__ double hash_uniform(unsigned i, unsigned j) {
+    unsigned h = i * 0x9E3779B1u ^ (j + 0x7F4A7C15u) * 0x85EBCA77u;
+    h ^= h >> 15; h *= 0x2C1B3C6Du; h ^= h >> 12; h *= 0x297A2D39u; h ^= h >> 15;
+    return (double)h * (2.0 / 4294967296.0) - 1.0;
+}
+
+// Inverse iteration: thread j computes the eigenvector of lam[j] into Z[:, j] (row-major n x k).
+// work holds 4 n k doubles (dd, du, du2, dl) and n k ints (pivots), all laid out [i*k + j].
+__global__ void __launch_bounds__(128) inverse_iteration(int n, int k, EigSmall s, double* __restrict__ work,
+                                                         int* __restrict__ piv, double* __restrict__ Z) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= k) return;
+    const double* a = s.diag;
+    const double* b = s.offd;
+    double gl, gu, tn;
+    tri_bounds(a, b, n, gl, gu, tn);
+    const double tiny = EPS * fmax(tn, 1e-300);
+    const double lam = s.lam[j];
+    const long long K = k;
+    double* dd = work;
+    double* du = work + (long long)n * K;
+    double* du2 = work + 2LL * n * K;
+    double* dl = work + 3LL * n * K;
+#define AT(arr, i) arr[(long long)(i) * K + j]
+    for (int i = 0; i < n; ++i) {
+        AT(dd, i) = a[i] - lam;
+        AT(du, i) = (i + 1 < n) ? b[i] : 0.0;
+        AT(dl, i) = (i + 1 < n) ? b[i] : 0.0;
+        AT(du2, i) = 0.0;
+    }
+    for (int i = 0; i + 1 < n; ++i) {
+        double di = AT(dd, i), li = AT(dl, i);
+        if (fabs(di) >= fabs(li)) {
+            AT(piv, i) = 0;
+            if (di == 0.0) { di = tiny; AT(dd, i) = di; }
+            const double f = li / di;
+            AT(dl, i) = f;
+            AT(dd, i + 1) -= f * AT(du, i);
+        } else {
+            AT(piv, i) = 1;
+            const double f = di / li;
+            AT(dd, i) = li;
+            AT(dl, i) = f;
+            const double t = AT(du, i);
+            AT(du, i) = AT(dd, i + 1);
+            AT(dd, i + 1) = t - f * AT(dd, i + 1);
+            if (i + 2 < n) {
+                AT(du2, i) = AT(du, i + 1);
+                AT(du, i + 1) = -f * AT(du, i + 1);
+            }
+        }
+    }
+    for (int i = 0; i < n; ++i) {
+        const double di = AT(dd, i);
+        if (fabs(di) < tiny) AT(dd, i) = (di < 0.0) ? -tiny : tiny;
+    }
+    for (int i = 0; i < n; ++i) AT(Z, i) = hash_uniform((unsigned)i, (unsigned)j);
+    for (int it = 0; it < 3; ++it) {
+        for (int i = 0; i + 1 < n; ++i) {
+            if (AT(piv, i) == 0) {
+                AT(Z, i + 1) -= AT(dl, i) * AT(Z, i);
+            } else {
+                const double t = AT(Z, i);
+                AT(Z, i) = AT(Z, i + 1);
+                AT(Z, i + 1) = t - AT(dl, i) * AT(Z, i + 1);
+            }
+        }
+        AT(Z, n - 1) /= AT(dd, n - 1);
+        if (n >= 2) AT(Z, n - 2) = (AT(Z, n - 2) - AT(du, n - 2) * AT(Z, n - 1)) / AT(dd, n - 2);
+        for (int i = n - 3; i >= 0; --i)
+            AT(Z, i) = (AT(Z, i) - AT(du, i) * AT(Z, i + 1) - AT(du2, i) * AT(Z, i + 2)) / AT(dd, i);
+        double mx = 0.0;
+        for (int i = 0; i < n; ++i) mx = fmax(mx, fabs(AT(Z, i)));
+        const double inv = 1.0 / mx;
+        for (int i = 0; i < n; ++i) AT(Z, i) *= inv;
+    }
+    double nrm = 0.0;
+    for (int i = 0; i < n; ++i) nrm += AT(Z, i) * AT(Z, i);
+    const double inv = 1.0 / sqrt(nrm);
+    for (int i = 0; i < n; ++i) AT(Z, i) *= inv;
+#undef AT
+}
+
+// ---------------------------------------------------------------- CholeskyQR
+// G[a][b] = sum_i Z[i][a] Z[i][b] (+ shift on the diagonal), 16 x 16 tile per block
+__global__ void __launch_bounds__(256) gram_kernel(const double* __restrict__ Z, int n, int k, double* __restrict__ G,
+                                                   double shift) {
+    __shared__ double za[32][17], zb[32][17];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int a0 = blockIdx.y * 16, b0 = blockIdx.x * 16;
+    double acc = 0.0;
+    for (int i0 = 0; i0 < n; i0 += 32) {
+        for (int t = threadIdx.x; t < 32 * 16; t += 256) {
+            const int r = t / 16, c = t % 16;
+            const int i = i0 + r;
+            za[r][c] = (i < n && a0 + c < k) ? Z[(long long)i * k + a0 + c] : 0.0;
+            zb[r][c] = (i < n && b0 + c < k) ? Z[(long long)i * k + b0 + c] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int r = 0; r < 32; ++r) acc = fma(za[r][ty], zb[r][tx], acc);
+        __syncthreads();
+    }
+    const int a = a0 + ty, b = b0 + tx;
+    if (a < k && b < k) G[(long long)a * k + b] = acc + (a == b ? shift : 0.0);
+}
+
+// in-place lower Cholesky of the k x k G (single CTA); status[0] = 1 on a non-positive pivot
+__global__ void __launch_bounds__(1024) cholesky_kernel(double* __restrict__ G, int k, int* __restrict__ status) {
+    __shared__ double piv;
+    for (int j = 0; j < k; ++j) {
+        if (threadIdx.x == 0) {
+            double djj = G[(long long)j * k + j];
+            if (!(djj > 0.0)) {
+                status[0] = 1;
+                djj = 1e-300;
+            }
+            piv = sqrt(djj);
+            G[(long long)j * k + j] = piv;
+        }
+        __syncthreads();
+        const double p = piv;
+        for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) G[(long long)i * k + j] /= p;
+        __syncthreads();
+        const int m = k - j - 1;
+        for (long long t = threadIdx.x; t < (long long)m * m; t += blockDim.x) {
+            const int i = j + 1 + (int)(t / m), l = j + 1 + (int)(t % m);
+            if (l <= i) G[(long long)i * k + l] -= G[(long long)i * k + j] * G[(long long)l * k + j];
+        }
+        __syncthreads();
+    }
+}
+
+// Z <- Z L^{-T}: row-wise forward substitution q_j = (z_j - sum_{l<j} q_l L[j][l]) / L[j][j]
+__global__ void __launch_bounds__(128) trsm_rows(double* __restrict__ Z, int n, int k, const double* __restrict__ L) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double* z = Z + (long long)i * k;
+    for (int j = 0; j < k; ++j) {
+        double acc = z[j];
+        const double* Lj = L + (long long)j * k;
+        for (int l = 0; l < j; ++l) acc -= z[l] * Lj[l];
+        z[j] = acc / Lj[j];
+    }
+}
+
+__global__ void sumsq_kernel(const double* __restrict__ Z, long long cnt, double* __restrict__ out) {
+    __shared__ double sh[33];
+    double acc = 0.0;
+    for (long long t = threadIdx.x; t < cnt; t += blockDim.x) acc += Z[t] * Z[t];
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) *out = acc;
+}
+
+// ---------------------------------------------------------------- back-transformation
+// Block j: y = ph .* Z[:, j]; y <- H_0 ... H_{n-3} y; write column (mode 0: U[i][j] = y_i)
+// or conjugated row (mode 1: B[j][i] = conj(y_i)).
+__global__ void __launch_bounds__(256) backtransform(int n, int k, const double2* __restrict__ H, EigSmall s,
+                                                     const double* __restrict__ Z, int mode,
+                                                     double2* __restrict__ out) {
+    extern __shared__ double2 y[];
+    __shared__ double sh[33];
+    const int j = blockIdx.x;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double z = Z[(long long)i * k + j];
+        const double2 q = s.ph[i];
+        y[i] = make_double2(q.x * z, q.y * z);
+    }
+    __syncthreads();
+    for (int kk = n - 3; kk >= 0; --kk) {
+        const double tau = s.tau[kk];
+        if (tau == 0.0) continue;
+        const int m = n - kk - 1;
+        const double2* v = H + (long long)kk * n;
+        double re = 0.0, im = 0.0;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            const double2 a = v[i], b = y[kk + 1 + i];
+            re += a.x * b.x + a.y * b.y;   // conj(a) * b
+            im += a.x * b.y - a.y * b.x;
+        }
+        re = block_sum(re, sh);
+        im = block_sum(im, sh);
+        re *= tau;
+        im *= tau;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            const double2 a = v[i];
+            double2 b = y[kk + 1 + i];
+            b.x -= a.x * re - a.y * im;
+            b.y -= a.x * im + a.y * re;
+            y[kk + 1 + i] = b;
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double2 v = y[i];
+        if (mode == 0) out[(long long)i * k + j] = v;
+        else out[(long long)j * n + i] = make_double2(v.x, -v.y);
+    }
+}
+
+}  // namespace
+
+TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int direction, int k_max,
+                         const double2* theta, double2* left, double2* right) {
+    const int nL = chi_l * d1, nR = d2 * chi_r;
+    const int n = direction == 0 ? nL : nR;
+    const int k = std::min(k_max, std::min(nL, nR));
+    VTN_REQUIRE(k >= 1, "truncation keeps no state");
+    VTN_REQUIRE(n <= 12288, "reduced density matrix larger than 12288 is not supported");
+    int tt = ctx.tbegin(TC_EIG, 0.0);
+    double2* A = (double2*)ctx.workspace(WS_EIG_A, sizeof(double2) * (size_t)n * n);
+    double2* H = (double2*)ctx.workspace(WS_EIG_H, sizeof(double2) * (size_t)n * n);
+    double* small = (double*)ctx.workspace(WS_EIG_U, sizeof(double) * (12 * (size_t)n + 16));
+    EigSmall s;
+    s.diag = small;
+    s.offd = small + n;
+    s.tau = small + 2 * (size_t)n;
+    s.lam = small + 3 * (size_t)n;
+    s.e = (double2*)(small + 4 * (size_t)n);
+    s.ph = (double2*)(small + 6 * (size_t)n);
+    s.p = (double2*)(small + 8 * (size_t)n);
+    s.w = (double2*)(small + 10 * (size_t)n);
+    s.scal = small + 12 * (size_t)n;
+    double* Z = (double*)ctx.workspace(WS_EIG_Y, sizeof(double) * (size_t)n * k);
+    double* work = (double*)ctx.workspace(WS_EIG_WORK, sizeof(double) * (5 * (size_t)n * k + (size_t)k * k + 16));
+    int* piv = (int*)(work + 4 * (size_t)n * k);
+    double* G = work + 5 * (size_t)n * k;
+    int* status = (int*)(G + (size_t)k * k);
+    // 1. rho
+    GemmArgs g;
+    if (direction == 0) {
+        g.M = nL; g.N = nL; g.K = nR;
+        g.A = theta; g.lda = nR;
+        g.opB = OP_C; g.B = theta; g.ldb = nR;
+    } else {
+        g.M = nR; g.N = nR; g.K = nL;
+        g.opA = OP_C; g.A = theta; g.lda = nR;
+        g.B = theta; g.ldb = nR;
+    }
+    g.C = A; g.ldc = n;
+    gemm_c64(ctx, g);
+    norm2_dev(ctx, theta, (long long)nL * nR, &s.scal[0]);
+    VTN_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int) * 4, ctx.stream));
+    // 2. tridiagonalisation
+    for (int kk = 0; kk + 2 < n; ++kk) {
+        const int m = n - kk - 1;
+        hh_reflector<<<1, 1024, 0, ctx.stream>>>(A, n, kk, H, s);
+        hh_matvec<<<(m + 7) / 8, 256, 0, ctx.stream>>>(A, n, kk, H, s);
+        hh_w<<<1, 1024, 0, ctx.stream>>>(n, kk, H, s);
+        const long long mm = (long long)m * m;
+        hh_rank2<<<(unsigned)((mm + 255) / 256), 256, 0, ctx.stream>>>(A, n, kk, H, s);
+        ctx.count_launch(4);
+    }
+    tri_finalize<<<1, 32, 0, ctx.stream>>>(A, n, s);
+    ctx.count_launch();
+    ctx.check_launch("tridiagonalisation");
+    // 3. eigenvalues
+    bisect_top<<<k, 32, 0, ctx.stream>>>(n, k, s);
+    // 4. eigenvectors of the real tridiagonal
+    inverse_iteration<<<(k + 127) / 128, 128, 0, ctx.stream>>>(n, k, s, work, piv, Z);
+    ctx.count_launch(2);
+    ctx.check_launch("eigenpairs");
+    // 5. shifted CholeskyQR3
+    dim3 gg((k + 15) / 16, (k + 15) / 16);
+    for (int pass = 0; pass < 3; ++pass) {
+        double shift = 0.0;
+        if (pass == 0) {
+            // ||Z||_F^2 = k for unit columns; shift 11 (n k + k (k + 1)) u ||Z||_2^2 bounded by that
+            shift = 11.0 * ((double)n * k + (double)k * (k + 1)) * EPS * (double)k;
+        }
+        gram_kernel<<<gg, 256, 0, ctx.stream>>>(Z, n, k, G, shift);
+        cholesky_kernel<<<1, 1024, 0, ctx.stream>>>(G, k, status);
+        trsm_rows<<<(n + 127) / 128, 128, 0, ctx.stream>>>(Z, n, k, G);
+        ctx.count_launch(3);
+    }
+    ctx.check_launch("orthonormalisation");
+    // 6. back-transformation into the site tensors
+    const size_t shm = sizeof(double2) * (size_t)n;
+    static bool attr_set = false;
+    if (!attr_set) {
+        VTN_CUDA_TRY(cudaFuncSetAttribute(backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr_set = true;
+    }
+    if (direction == 0) {
+        backtransform<<<k, 256, shm, ctx.stream>>>(n, k, H, s, Z, 0, left);
+        // right = U^dag T
+        GemmArgs c;
+        c.M = k; c.N = nR; c.K = nL;
+        c.opA = OP_C; c.A = left; c.lda = k;
+        c.B = theta; c.ldb = nR;
+        c.C = right; c.ldc = nR;
+        ctx.count_launch();
+        gemm_c64(ctx, c);
+    } else {
+        backtransform<<<k, 256, shm, ctx.stream>>>(n, k, H, s, Z, 1, right);
+        // left = T V = T (V^dag)^dag
+        GemmArgs c;
+        c.M = nL; c.N = k; c.K = nR;
+        c.A = theta; c.lda = nR;
+        c.opB = OP_C; c.B = right; c.ldb = nR;
+        c.C = left; c.ldc = k;
+        ctx.count_launch();
+        gemm_c64(ctx, c);
+    }
+    ctx.check_launch("back-transformation");
+    ctx.tend(tt);
+    // results to the host
+    VTN_CUDA_TRY(cudaMemcpyAsync(ctx.pinned, s.lam, sizeof(double) * k, cudaMemcpyDeviceToHost, ctx.stream));
+    VTN_CUDA_TRY(cudaMemcpyAsync(ctx.pinned + k, s.scal, sizeof(double), cudaMemcpyDeviceToHost, ctx.stream));
+    VTN_CUDA_TRY(cudaMemcpyAsync(ctx.pinned + k + 1, status, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
+    ctx.sync();
+    TruncResult r;
+    r.k = k;
+    r.lam.assign(ctx.pinned, ctx.pinned + k);
+    const double tr = ctx.pinned[k];
+    double kept = 0.0;
+    for (double l : r.lam) kept += l;
+    r.discarded = tr > 0 ? 1.0 - kept / tr : 0.0;
+    int st = 0;
+    std::memcpy(&st, ctx.pinned + k + 1, sizeof(int));
+    (void)st;
+    return r;
+}
+
+}  // namespace vtn

@@ -1,0 +1,135 @@
+// Complex FP64 GEMM for the FP64 solver path (SIMT DFMA; GB300 has no FP64 tensor-core
+// rate worth using, and FP64 FMA throughput is the roofline of this kernel):
+//   C[batch] (=|+=) sum_{kb} op(A[batch, kb]) op(B[batch, kb]),  op in {X, X^dag}.
+// Every contraction of the two-site effective Hamiltonian, the environment updates and
+// the reduced density matrix is one call.  Tiles of 64 x 64 outputs per 256-thread CTA,
+// 4 x 4 complex micro-tile per thread, K staged through shared memory in steps of 8.
+#include "vtn_internal.cuh"
+
+namespace vtn {
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 8, TM = 4, TN = 4, NT = 256;
+
+struct GemmP {
+    int M, N, K, kb;
+    int opA, opB;
+    const double2* A; long long lda, sA_batch, sA_kb;
+    const double2* B; long long ldb, sB_batch, sB_kb;
+    double2* C; long long ldc, sC_batch;
+    int accumulate;
+};
+
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+
+__global__ void __launch_bounds__(NT) gemm_c64_kernel(GemmP p) {
+    __shared__ double2 As[BK][BM];
+    __shared__ double2 Bs[BK][BN];
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const long long bz = blockIdx.z;
+    double2 acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = make_double2(0.0, 0.0);
+
+    for (int kb = 0; kb < p.kb; ++kb) {
+        const double2* A = p.A + bz * p.sA_batch + (long long)kb * p.sA_kb;
+        const double2* B = p.B + bz * p.sB_batch + (long long)kb * p.sB_kb;
+        for (int k0 = 0; k0 < p.K; k0 += BK) {
+            // ---- stage op(A)[m0:m0+64, k0:k0+8]
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                int idx = tid + r * NT;
+                int ml, kl;
+                if (p.opA == OP_N) { ml = idx / BK; kl = idx % BK; }
+                else { ml = idx % BM; kl = idx / BM; }
+                int m = m0 + ml, k = k0 + kl;
+                double2 v = make_double2(0.0, 0.0);
+                if (m < p.M && k < p.K) {
+                    v = (p.opA == OP_N) ? A[(long long)m * p.lda + k] : cconj(A[(long long)k * p.lda + m]);
+                }
+                As[kl][ml] = v;
+            }
+            // ---- stage op(B)[k0:k0+8, n0:n0+64]
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                int idx = tid + r * NT;
+                int nl, kl;
+                if (p.opB == OP_N) { nl = idx % BN; kl = idx / BN; }
+                else { kl = idx % BK; nl = idx / BK; }
+                int n = n0 + nl, k = k0 + kl;
+                double2 v = make_double2(0.0, 0.0);
+                if (n < p.N && k < p.K) {
+                    v = (p.opB == OP_N) ? B[(long long)k * p.ldb + n] : cconj(B[(long long)n * p.ldb + k]);
+                }
+                Bs[kl][nl] = v;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < BK; ++kk) {
+                double2 a[TM], b[TN];
+#pragma unroll
+                for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+                for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+                for (int i = 0; i < TM; ++i)
+#pragma unroll
+                    for (int j = 0; j < TN; ++j) {
+                        acc[i][j].x = fma(a[i].x, b[j].x, acc[i][j].x);
+                        acc[i][j].x = fma(-a[i].y, b[j].y, acc[i][j].x);
+                        acc[i][j].y = fma(a[i].x, b[j].y, acc[i][j].y);
+                        acc[i][j].y = fma(a[i].y, b[j].x, acc[i][j].y);
+                    }
+            }
+            __syncthreads();
+        }
+    }
+    double2* C = p.C + bz * p.sC_batch;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        int m = m0 + ty + 16 * i;
+        if (m >= p.M) continue;
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            int n = n0 + tx + 16 * j;
+            if (n >= p.N) continue;
+            double2* c = C + (long long)m * p.ldc + n;
+            if (p.accumulate) {
+                double2 o = *c;
+                *c = make_double2(o.x + acc[i][j].x, o.y + acc[i][j].y);
+            } else {
+                *c = acc[i][j];
+            }
+        }
+    }
+}
+
+}  // namespace
+
+void gemm_c64(Ctx& ctx, const GemmArgs& g, int timing_class) {
+    if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
+    VTN_REQUIRE(g.batch <= 65535, "gemm batch too large");
+    GemmP p;
+    p.M = g.M; p.N = g.N; p.K = g.K; p.kb = g.kb;
+    p.opA = g.opA; p.opB = g.opB;
+    p.A = g.A; p.lda = g.lda; p.sA_batch = g.sA_batch; p.sA_kb = g.sA_kb;
+    p.B = g.B; p.ldb = g.ldb; p.sB_batch = g.sB_batch; p.sB_kb = g.sB_kb;
+    p.C = g.C; p.ldc = g.ldc; p.sC_batch = g.sC_batch;
+    p.accumulate = g.accumulate ? 1 : 0;
+    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.batch);
+    VTN_REQUIRE(grid.y <= 65535, "gemm M too large");
+    double flops = 8.0 * g.M * (double)g.N * g.K * g.kb * g.batch;
+    int t0 = ctx.tbegin(TC_GEMM, flops);
+    int t1 = (timing_class != TC_GEMM) ? ctx.tbegin(timing_class, flops) : -1;
+    gemm_c64_kernel<<<grid, NT, 0, ctx.stream>>>(p);
+    ctx.count_launch();
+    ctx.check_launch("gemm_c64_kernel");
+    ctx.tend(t1);
+    ctx.tend(t0);
+}
+
+}  // namespace vtn

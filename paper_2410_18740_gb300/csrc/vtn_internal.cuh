@@ -1,0 +1,205 @@
+// Internal declarations shared by the CUDA translation units of libvtn.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <functional>
+#include <string>
+#include <vector>
+
+#include "host_mpo.h"
+#include "vtn.h"
+
+namespace vtn {
+
+// ------------------------------------------------------------------ errors
+struct Error {
+    vtn_status status;
+    std::string msg;
+};
+
+#define VTN_CUDA_TRY(expr)                                                                  \
+    do {                                                                                    \
+        cudaError_t e_ = (expr);                                                            \
+        if (e_ != cudaSuccess) throw ::vtn::Error{VTN_ECUDA, std::string(#expr) + ": " +     \
+                                                             cudaGetErrorString(e_)};       \
+    } while (0)
+
+#define VTN_REQUIRE(cond, msg)                                                              \
+    do {                                                                                    \
+        if (!(cond)) throw ::vtn::Error{VTN_EINVAL, (msg)};                                 \
+    } while (0)
+
+// ------------------------------------------------------------------ timing classes
+enum TimingClass { TC_GEMM = 0, TC_HEFF = 1, TC_EIG = 2, TC_LANCZOS = 3, TC_MIX = 4, TC_COUNT = 5 };
+
+struct Ctx;
+
+// Device buffer owned through the context's allocator.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+// Device copy of one sparse MPO core, indexed for the mixing kernel in both directions.
+struct DevCore {
+    int wl = 0, wr = 0, d = 0, nnz = 0;
+    // entries grouped by output channel for "apply along columns" (output = column b)
+    int* col_ptr = nullptr;   // [wr + 1]
+    int* col_src = nullptr;   // [nnz] source row a
+    int* col_op = nullptr;    // [nnz] operator index
+    // grouped by output row for "apply along rows" (output = row a, source = column b)
+    int* row_ptr = nullptr;   // [wl + 1]
+    int* row_src = nullptr;   // [nnz]
+    int* row_op = nullptr;    // [nnz]
+    double2* ops = nullptr;   // [nnz][d][d]
+    unsigned char* ident = nullptr;  // [nnz]
+    double flops_ident = 0, flops_dense = 0;  // counts for the flop model
+    int n_ident = 0, n_dense = 0;
+    std::vector<DevBuf> bufs;
+};
+
+struct Ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    vtn_allocator alloc{};
+    bool has_alloc = false;
+    std::string err;
+    long long launches = 0;
+    bool timing = false;
+    struct Tc {
+        long long launches = 0;
+        double flops = 0, seconds = 0;
+    } tc[TC_COUNT];
+    struct Pending {
+        cudaEvent_t a, b;
+        int cls;
+        double flops;
+    };
+    std::vector<Pending> pending;
+    int open_intervals = 0;
+    std::vector<cudaEvent_t> event_pool;
+    // named workspace slots
+    std::vector<DevBuf> ws;
+    double* pinned = nullptr;  // pinned host scratch (4096 doubles)
+    int num_sms = 0;
+
+    void* dalloc(size_t bytes);
+    void dfree(void* p);
+    void* workspace(int slot, size_t bytes);  // grows, never shrinks
+    void count_launch(int n = 1) { launches += n; }
+    // timing: begin() returns an index (or -1 when timing is off); end() closes it
+    int tbegin(int cls, double flops);
+    void tend(int idx);
+    void tflush();  // synchronise and accumulate pending intervals
+    void sync() { VTN_CUDA_TRY(cudaStreamSynchronize(stream)); }
+    void check_launch(const char* what);
+};
+
+enum WsSlot {
+    WS_X = 0, WS_Y, WS_Z, WS_KRYLOV, WS_VEC_W, WS_VEC_T, WS_PARTIAL, WS_SCAL, WS_EIG_A, WS_EIG_H,
+    WS_EIG_Y, WS_EIG_WORK, WS_EIG_U, WS_CORE_A, WS_CORE_B, WS_ENV_TMP, WS_MISC, WS_COUNT
+};
+
+// ------------------------------------------------------------------ cores
+void upload_core(Ctx& ctx, const HostCore& hc, DevCore& dc);
+void free_core(Ctx& ctx, DevCore& dc);
+HostCore core_from_abi(const vtn_core* c);
+
+// ------------------------------------------------------------------ GEMM (complex FP64)
+enum Op { OP_N = 0, OP_C = 1 };  // op(X) = X or X^dag (conjugate transpose)
+
+struct GemmArgs {
+    int M, N, K;          // op(A): M x K, op(B): K x N, C: M x N
+    int batch = 1;        // independent problems
+    int kb = 1;           // C += sum over kb of op(A_kb) op(B_kb)
+    Op opA = OP_N, opB = OP_N;
+    const double2* A; long long lda; long long sA_batch = 0, sA_kb = 0;
+    const double2* B; long long ldb; long long sB_batch = 0, sB_kb = 0;
+    double2* C; long long ldc; long long sC_batch = 0;
+    bool accumulate = false;  // C += result (else C = result)
+};
+void gemm_c64(Ctx& ctx, const GemmArgs& g, int timing_class = TC_GEMM);
+
+// ------------------------------------------------------------------ W mixing
+// out[b][p][s'][q] = sum_{entries (src -> b)} op[s'][s] in[src][p][s][q]
+// by_col: output channel = core column (left-to-right use); else output = core row.
+void mix_apply(Ctx& ctx, const DevCore& core, bool by_col, int P, int Q, const double2* in,
+               double2* out);
+
+// ------------------------------------------------------------------ contractions
+void heff_apply_dev(Ctx& ctx, const DevCore& Wi, const DevCore& Wj, int chi_l, int chi_r,
+                    const double2* L, const double2* R, const double2* theta, double2* y);
+double heff_flops(const DevCore& Wi, const DevCore& Wj, int chi_l, int chi_r);
+void env_left_dev(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const double2* L,
+                  const double2* A, double2* out);
+void env_right_dev(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const double2* R,
+                   const double2* A, double2* out);
+
+// ------------------------------------------------------------------ vector kernels (Lanczos)
+// dots[i] = sum_e conj(V[i][e]) w[e], i < nv (deterministic two-stage reduction)
+void multi_dot(Ctx& ctx, const double2* V, long long ld, int nv, const double2* w, long long n,
+               double2* dots_dev);
+// w -= sum_i V[i] c[i]
+void multi_axpy(Ctx& ctx, const double2* V, long long ld, int nv, const double2* c_dev, double2* w,
+                long long n);
+// out = sum_i V[i] y[i] (y real, device)
+void lincomb_real(Ctx& ctx, const double2* V, long long ld, int nv, const double* y_dev, double2* out,
+                  long long n);
+// norm2 (sum |x|^2) into dev scalar
+void norm2_dev(Ctx& ctx, const double2* x, long long n, double* out_dev);
+// x *= 1/sqrt(*nrm2_dev)
+void scale_inv_sqrt(Ctx& ctx, double2* x, long long n, const double* nrm2_dev);
+
+struct LanczosResult {
+    double theta;
+    int n_matvec;
+    bool converged;
+};
+// Lowest eigenpair of the operator applied by `matvec(in, out)` (device vectors of n complex).
+LanczosResult lanczos(Ctx& ctx, long long n, double2* x, double tol, int kmax, int restarts,
+                      const std::function<void(const double2*, double2*)>& matvec);
+
+// ------------------------------------------------------------------ truncation eigensolver
+struct TruncResult {
+    int k;
+    double discarded;
+    std::vector<double> lam;
+};
+TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int direction, int k_max,
+                         const double2* theta, double2* left, double2* right);
+
+// ------------------------------------------------------------------ misc kernels
+void fill_random_normal(Ctx& ctx, double2* out, long long count, uint64_t seed, int site);
+void orthonormalize_rows(Ctx& ctx, double2* A, int rows, int cols);
+void lbo_rotate_dev(Ctx& ctx, int chi_l, int d, int D, int chi_r, const double2* V, const double2* A,
+                    double2* out);
+void set_scalar_one(Ctx& ctx, double2* p);
+void marginal_reduce_dev(Ctx& ctx, int chi_l, int D, int chi_r, const double2* AF, const double2* U, double* P);
+void sample_dev(Ctx& ctx, const double2* const* AF_dev, const double2* const* ER_dev, const int* dims_dev, int M,
+                int D, int chi_max, uint64_t seed, int n_samples, int* out_dev);
+
+}  // namespace vtn
+
+// ------------------------------------------------------------------ handles
+struct vtn_ctx_s {
+    vtn::Ctx c;
+};
+
+struct vtn_mpo_s {
+    vtn::HostProblem hp;
+    int device = -1;
+    vtn_ctx owner = nullptr;
+    std::vector<vtn::DevCore> dcores;
+    double2* iso_dev = nullptr;  // M * D * d
+};
+
+struct vtn_mps_s {
+    int M = 0, d = 0, chi_cap = 0;
+    std::vector<int> dims;                 // M + 1
+    std::vector<double2*> sites;           // device, capacity chi_cap*d*chi_cap each
+    std::vector<size_t> cap;               // complex capacity per site
+    vtn_ctx owner = nullptr;
+    int center = -1;                       // -1 unknown
+};

@@ -1,0 +1,435 @@
+"""Thin Python binding of libvtn (include/vtn.h): one function per C entry point, same
+names, argument marshalling only.  Every computation happens in the CUDA library; if the
+library is missing this module raises instead of falling back to anything else.
+
+Device buffers are passed as torch CUDA tensors (complex128, contiguous); host arrays as
+numpy arrays.  By default the library draws device memory from PyTorch's caching
+allocator through the vtn_allocator callbacks, on the stream given to vtn_create.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libvtn.so")
+
+VTN_OK, VTN_EINVAL, VTN_ENOMEM, VTN_ECUDA, VTN_ENOCONV, VTN_ETIMEOUT, VTN_EUNSUPPORTED = range(7)
+VTN_FP64, VTN_TF32X3, VTN_BF16X3 = 0, 1, 2
+VTN_FLAG_LBO = 1
+TIMING_CLASSES = {"gemm": 0, "heff": 1, "eig": 2, "lanczos": 3, "mix": 4}
+STATUS_NAMES = {0: "VTN_OK", 1: "VTN_EINVAL", 2: "VTN_ENOMEM", 3: "VTN_ECUDA", 4: "VTN_ENOCONV",
+                5: "VTN_ETIMEOUT", 6: "VTN_EUNSUPPORTED"}
+
+
+class VtnError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+        self.msg = msg
+
+
+class vtn_allocator(C.Structure):
+    _fields_ = [("alloc", C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)),
+                ("free", C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)),
+                ("user", C.c_void_p)]
+
+
+class vtn_sweep_opts(C.Structure):
+    _fields_ = [("chi_max", C.c_int), ("chi_schedule", C.POINTER(C.c_int)), ("n_schedule", C.c_int),
+                ("n_sweeps", C.c_int), ("prec", C.c_int), ("lanczos_tol", C.c_double),
+                ("krylov_max", C.c_int), ("lanczos_max_restarts", C.c_int), ("e_tol", C.c_double),
+                ("e_target", C.c_double), ("use_e_target", C.c_int), ("seed", C.c_uint64)]
+
+
+class vtn_sweep_report(C.Structure):
+    _fields_ = [("sweeps_done", C.c_int), ("energy", C.c_double * 64), ("max_discarded", C.c_double * 64),
+                ("seconds", C.c_double * 64), ("matvecs", C.c_longlong), ("lanczos_not_converged", C.c_longlong),
+                ("heff_flops", C.c_double), ("heff_seconds", C.c_double), ("gemm_flops", C.c_double),
+                ("gemm_seconds", C.c_double), ("eig_seconds", C.c_double)]
+
+
+class vtn_core(C.Structure):
+    _fields_ = [("w_left", C.c_int), ("w_right", C.c_int), ("d", C.c_int), ("nnz", C.c_int),
+                ("rows", C.POINTER(C.c_int)), ("cols", C.POINTER(C.c_int)), ("ops", C.POINTER(C.c_double))]
+
+
+_lib = None
+_keep = []   # callbacks and buffers that must outlive the calls using them
+
+_P = C.c_void_p
+_I = C.c_int
+_D = C.c_double
+_PD = C.POINTER(C.c_double)
+_PI = C.POINTER(C.c_int)
+
+_SIGS = {
+    "vtn_create": [C.POINTER(_P), _I, _P, C.POINTER(vtn_allocator)],
+    "vtn_destroy": [_P],
+    "vtn_last_error": [_P],
+    "vtn_launch_count": [_P, C.POINTER(C.c_longlong)],
+    "vtn_build_mpo": [_P, _I, _PD, _PD, _I, _I, C.c_uint, C.POINTER(_P)],
+    "vtn_mpo_free": [_P],
+    "vtn_mpo_info": [_P, _PI, _PI, _PI, _PI],
+    "vtn_mpo_coefficients": [_P, _PD],
+    "vtn_mpo_covariance": [_P, _PD],
+    "vtn_mpo_isometry": [_P, _I, _PD],
+    "vtn_mpo_core": [_P, _I, _PI, _PI, _PI, _PD],
+    "vtn_mpo_norm_bound": [_P, _PD],
+    "vtn_mps_random": [_P, _P, _I, C.c_uint64, C.POINTER(_P)],
+    "vtn_mps_from_host": [_P, _P, _PI, C.POINTER(_PD), C.POINTER(_P)],
+    "vtn_mps_free": [_P],
+    "vtn_mps_info": [_P, _PI, _PI, _PI],
+    "vtn_mps_get_site": [_P, _P, _I, _PD],
+    "vtn_mps_save": [_P, _P, C.c_char_p],
+    "vtn_mps_load": [_P, _P, C.c_char_p, C.POINTER(_P)],
+    "vtn_sweep_opts_default": [C.POINTER(vtn_sweep_opts)],
+    "vtn_sweep": [_P, _P, C.POINTER(_P), C.POINTER(vtn_sweep_opts), C.POINTER(vtn_sweep_report)],
+    "vtn_energy": [_P, _P, _P, _PD],
+    "vtn_marginals": [_P, _P, _P, _PI, _I, _PD],
+    "vtn_marginals_all": [_P, _P, _P, _PD],
+    "vtn_sample": [_P, _P, _P, C.c_uint64, _I, _PI],
+    "vtn_heff_apply": [_P, C.POINTER(vtn_core), C.POINTER(vtn_core), _I, _I, _P, _P, _P, _P, _I],
+    "vtn_env_update": [_P, C.POINTER(vtn_core), _I, _I, _I, _P, _P, _P, _I],
+    "vtn_heff_ground": [_P, C.POINTER(vtn_core), C.POINTER(vtn_core), _I, _I, _P, _P, _P, _D, _I, _I, _PD, _PI],
+    "vtn_truncate": [_P, _I, _I, _I, _I, _I, _I, _P, _P, _P, _PD, _PD, _PI],
+    "vtn_lbo_rotate": [_P, _I, _I, _I, _I, _P, _P, _P],
+    "vtn_timing": [_P, _I],
+    "vtn_timing_read": [_P, _I, C.POINTER(C.c_longlong), _PD, _PD],
+    "vtn_timing_reset": [_P],
+}
+
+
+def lib():
+    """Load libvtn.so (built by ``paper_2410_18740_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2410_18740_gb300.build.build() "
+                               "(there is no fallback implementation)")
+        L = C.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_char_p if name == "vtn_last_error" else C.c_int
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(ctx, st, ok=(VTN_OK,)):
+    if st not in ok:
+        raise VtnError(st, vtn_last_error(ctx))
+    return st
+
+
+def _dptr(x):
+    """Device pointer of a torch CUDA tensor (must be contiguous)."""
+    if x is None:
+        return None
+    if not x.is_contiguous():
+        raise ValueError("device tensor must be contiguous")
+    return C.c_void_p(x.data_ptr())
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _cplx_interleaved(a):
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    return a.view(np.float64)
+
+
+# ----------------------------------------------------------------------- context
+def _torch_allocator(device):
+    import torch
+
+    def _alloc(nbytes, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device, torch.cuda.current_stream(device))
+        except Exception:
+            return None
+
+    def _free(ptr, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a = vtn_allocator(vtn_allocator._fields_[0][1](_alloc), vtn_allocator._fields_[1][1](_free), None)
+    _keep.append(a)
+    return a
+
+
+def vtn_create(device=0, stream=None, torch_allocator=True):
+    """Context on CUDA device `device`.  stream: torch.cuda.Stream, raw cudaStream_t int,
+    or None for torch's current stream."""
+    L = lib()
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream(device)
+    raw = getattr(stream, "cuda_stream", stream)
+    alloc = _torch_allocator(device) if torch_allocator else None
+    out = C.c_void_p()
+    st = L.vtn_create(C.byref(out), int(device), C.c_void_p(int(raw) if raw else 0),
+                      C.byref(alloc) if alloc is not None else None)
+    _check(None, st)
+    return out
+
+
+def vtn_destroy(ctx):
+    return lib().vtn_destroy(ctx)
+
+
+def vtn_last_error(ctx):
+    r = lib().vtn_last_error(ctx)
+    return r.decode() if r else ""
+
+
+def vtn_launch_count(ctx):
+    v = C.c_longlong()
+    _check(ctx, lib().vtn_launch_count(ctx, C.byref(v)))
+    return v.value
+
+
+# ----------------------------------------------------------------------- MPO
+def vtn_build_mpo(ctx, r, U, D, d, flags=0):
+    """ctx may be None: host-only MPO (queries only; uploaded on first use by a context)."""
+    r = _f64(r)
+    Ui = _cplx_interleaved(U)
+    M = r.shape[0]
+    assert Ui.size == 2 * M * M
+    out = C.c_void_p()
+    st = lib().vtn_build_mpo(ctx, M, r.ctypes.data_as(_PD), Ui.ctypes.data_as(_PD), int(D), int(d),
+                             int(flags), C.byref(out))
+    _check(ctx, st)
+    return out
+
+
+def vtn_mpo_free(mpo):
+    return lib().vtn_mpo_free(mpo)
+
+
+def vtn_mpo_info(mpo):
+    M, d, D = C.c_int(), C.c_int(), C.c_int()
+    lib().vtn_mpo_info(mpo, C.byref(M), C.byref(d), C.byref(D), None)
+    w = np.zeros(M.value + 1, dtype=np.int32)
+    _check(None, lib().vtn_mpo_info(mpo, None, None, None, w.ctypes.data_as(_PI)))
+    return M.value, d.value, D.value, w
+
+
+def vtn_mpo_coefficients(mpo):
+    M = vtn_mpo_info(mpo)[0]
+    G = np.zeros((2 * M, 2 * M))
+    _check(None, lib().vtn_mpo_coefficients(mpo, G.ctypes.data_as(_PD)))
+    return G
+
+
+def vtn_mpo_covariance(mpo):
+    M = vtn_mpo_info(mpo)[0]
+    V = np.zeros((2 * M, 2 * M))
+    _check(None, lib().vtn_mpo_covariance(mpo, V.ctypes.data_as(_PD)))
+    return V
+
+
+def vtn_mpo_isometry(mpo, site):
+    _, d, D, _ = vtn_mpo_info(mpo)
+    V = np.zeros((D, d, 2))
+    _check(None, lib().vtn_mpo_isometry(mpo, int(site), V.ctypes.data_as(_PD)))
+    return V.view(np.complex128)[..., 0]
+
+
+def vtn_mpo_core(mpo, site):
+    _, d, _, w = vtn_mpo_info(mpo)
+    n = C.c_int(0)
+    _check(None, lib().vtn_mpo_core(mpo, int(site), C.byref(n), None, None, None))
+    rows = np.zeros(n.value, np.int32)
+    cols = np.zeros(n.value, np.int32)
+    ops = np.zeros((max(n.value, 1), d, d, 2))
+    _check(None, lib().vtn_mpo_core(mpo, int(site), C.byref(n), rows.ctypes.data_as(_PI),
+                                    cols.ctypes.data_as(_PI), ops.ctypes.data_as(_PD)))
+    return int(w[site]), int(w[site + 1]), rows, cols, ops.view(np.complex128)[..., 0][: n.value]
+
+
+def vtn_mpo_norm_bound(mpo):
+    v = C.c_double()
+    _check(None, lib().vtn_mpo_norm_bound(mpo, C.byref(v)))
+    return v.value
+
+
+# ----------------------------------------------------------------------- MPS
+def vtn_mps_random(ctx, mpo, chi, seed):
+    out = C.c_void_p()
+    _check(ctx, lib().vtn_mps_random(ctx, mpo, int(chi), C.c_uint64(int(seed)), C.byref(out)))
+    return out
+
+
+def vtn_mps_from_host(ctx, mpo, sites):
+    dims = np.array([1] + [s.shape[2] for s in sites], dtype=np.int32)
+    bufs = [_cplx_interleaved(s) for s in sites]
+    arr = (_PD * len(bufs))(*[b.ctypes.data_as(_PD) for b in bufs])
+    out = C.c_void_p()
+    _check(ctx, lib().vtn_mps_from_host(ctx, mpo, dims.ctypes.data_as(_PI), arr, C.byref(out)))
+    return out
+
+
+def vtn_mps_free(mps):
+    return lib().vtn_mps_free(mps)
+
+
+def vtn_mps_info(mps):
+    M, d = C.c_int(), C.c_int()
+    lib().vtn_mps_info(mps, C.byref(M), C.byref(d), None)
+    dims = np.zeros(M.value + 1, np.int32)
+    _check(None, lib().vtn_mps_info(mps, None, None, dims.ctypes.data_as(_PI)))
+    return M.value, d.value, dims
+
+
+def vtn_mps_get_site(ctx, mps, site):
+    _, d, dims = vtn_mps_info(mps)
+    out = np.zeros((dims[site], d, dims[site + 1], 2))
+    _check(ctx, lib().vtn_mps_get_site(ctx, mps, int(site), out.ctypes.data_as(_PD)))
+    return out.view(np.complex128)[..., 0]
+
+
+def vtn_mps_save(ctx, mps, path):
+    _check(ctx, lib().vtn_mps_save(ctx, mps, str(path).encode()))
+
+
+def vtn_mps_load(ctx, mpo, path):
+    out = C.c_void_p()
+    _check(ctx, lib().vtn_mps_load(ctx, mpo, str(path).encode(), C.byref(out)))
+    return out
+
+
+# ----------------------------------------------------------------------- solver
+def vtn_sweep_opts_default(**kw):
+    o = vtn_sweep_opts()
+    lib().vtn_sweep_opts_default(C.byref(o))
+    sched = kw.pop("chi_schedule", None)
+    for k, v in kw.items():
+        setattr(o, k, v)
+    if sched:
+        arr = (C.c_int * len(sched))(*sched)
+        _keep.append(arr)
+        o.chi_schedule = C.cast(arr, C.POINTER(C.c_int))
+        o.n_schedule = len(sched)
+    return o
+
+
+def _report_dict(rep):
+    n = rep.sweeps_done
+    return {"sweeps_done": n, "energy": list(rep.energy[:n]), "max_discarded": list(rep.max_discarded[:n]),
+            "seconds": list(rep.seconds[:n]), "matvecs": rep.matvecs,
+            "lanczos_not_converged": rep.lanczos_not_converged, "heff_flops": rep.heff_flops,
+            "heff_seconds": rep.heff_seconds, "gemm_flops": rep.gemm_flops, "gemm_seconds": rep.gemm_seconds,
+            "eig_seconds": rep.eig_seconds}
+
+
+def vtn_sweep(ctx, mpo, state=None, opts=None, **kw):
+    """Returns (status, mps, report).  VTN_ENOCONV is returned, not raised."""
+    if opts is None:
+        opts = vtn_sweep_opts_default(**kw)
+    st_ptr = C.c_void_p(state.value if state is not None else None)
+    rep = vtn_sweep_report()
+    st = lib().vtn_sweep(ctx, mpo, C.byref(st_ptr), C.byref(opts), C.byref(rep))
+    _check(ctx, st, ok=(VTN_OK, VTN_ENOCONV))
+    return st, st_ptr, _report_dict(rep)
+
+
+def vtn_energy(ctx, mpo, mps):
+    v = C.c_double()
+    _check(ctx, lib().vtn_energy(ctx, mpo, mps, C.byref(v)))
+    return v.value
+
+
+def vtn_marginals(ctx, mpo, mps, modes):
+    _, _, D, _ = vtn_mpo_info(mpo)
+    modes = np.ascontiguousarray(modes, dtype=np.int32)
+    k = modes.size
+    out = np.zeros(D ** k)
+    _check(ctx, lib().vtn_marginals(ctx, mpo, mps, modes.ctypes.data_as(_PI), int(k), out.ctypes.data_as(_PD)))
+    return out.reshape((D,) * k)
+
+
+def vtn_marginals_all(ctx, mpo, mps):
+    M, _, D, _ = vtn_mpo_info(mpo)
+    out = np.zeros((M, D))
+    _check(ctx, lib().vtn_marginals_all(ctx, mpo, mps, out.ctypes.data_as(_PD)))
+    return out
+
+
+def vtn_sample(ctx, mpo, mps, seed, n_samples):
+    M = vtn_mpo_info(mpo)[0]
+    out = np.zeros((n_samples, M), np.int32)
+    _check(ctx, lib().vtn_sample(ctx, mpo, mps, C.c_uint64(int(seed)), int(n_samples), out.ctypes.data_as(_PI)))
+    return out
+
+
+# ----------------------------------------------------------------------- kernel-level
+def make_core(w_left, w_right, d, rows, cols, ops):
+    rows = np.ascontiguousarray(rows, np.int32)
+    cols = np.ascontiguousarray(cols, np.int32)
+    opsf = _cplx_interleaved(ops)
+    c = vtn_core(int(w_left), int(w_right), int(d), int(rows.size), rows.ctypes.data_as(_PI),
+                 cols.ctypes.data_as(_PI), opsf.ctypes.data_as(_PD))
+    c._bufs = (rows, cols, opsf)
+    return c
+
+
+def core_from_sparse(sc):
+    """vtn_core from a paper_2410_18740_gb300.inputs.SparseCore."""
+    return make_core(sc.w_left, sc.w_right, sc.d, sc.rows, sc.cols, sc.ops)
+
+
+def vtn_heff_apply(ctx, Wi, Wj, chi_l, chi_r, L, R, theta, y, prec=VTN_FP64):
+    _check(ctx, lib().vtn_heff_apply(ctx, C.byref(Wi), C.byref(Wj), int(chi_l), int(chi_r), _dptr(L), _dptr(R),
+                                     _dptr(theta), _dptr(y), int(prec)))
+
+
+def vtn_env_update(ctx, W, side, chi_l, chi_r, env, A, out, prec=VTN_FP64):
+    _check(ctx, lib().vtn_env_update(ctx, C.byref(W), int(side), int(chi_l), int(chi_r), _dptr(env), _dptr(A),
+                                     _dptr(out), int(prec)))
+
+
+def vtn_heff_ground(ctx, Wi, Wj, chi_l, chi_r, L, R, theta, tol=1e-10, krylov_max=32, max_restarts=4):
+    E = C.c_double()
+    nmv = C.c_int()
+    st = lib().vtn_heff_ground(ctx, C.byref(Wi), C.byref(Wj), int(chi_l), int(chi_r), _dptr(L), _dptr(R),
+                               _dptr(theta), float(tol), int(krylov_max), int(max_restarts), C.byref(E),
+                               C.byref(nmv))
+    _check(ctx, st, ok=(VTN_OK, VTN_ENOCONV))
+    return st, E.value, nmv.value
+
+
+def vtn_truncate(ctx, chi_l, d1, d2, chi_r, direction, k_max, theta, left, right):
+    kmax_eff = min(k_max, chi_l * d1, d2 * chi_r)
+    lam = np.zeros(kmax_eff)
+    disc = C.c_double()
+    k = C.c_int()
+    _check(ctx, lib().vtn_truncate(ctx, int(chi_l), int(d1), int(d2), int(chi_r), int(direction), int(k_max),
+                                   _dptr(theta), _dptr(left), _dptr(right), lam.ctypes.data_as(_PD),
+                                   C.byref(disc), C.byref(k)))
+    return k.value, lam[: k.value], disc.value
+
+
+def vtn_lbo_rotate(ctx, chi_l, d, D, chi_r, V, A, out):
+    _check(ctx, lib().vtn_lbo_rotate(ctx, int(chi_l), int(d), int(D), int(chi_r), _dptr(V), _dptr(A), _dptr(out)))
+
+
+def vtn_timing(ctx, enable):
+    _check(ctx, lib().vtn_timing(ctx, int(bool(enable))))
+
+
+def vtn_timing_read(ctx, cls):
+    cls = TIMING_CLASSES.get(cls, cls)
+    n, fl, s = C.c_longlong(), C.c_double(), C.c_double()
+    _check(ctx, lib().vtn_timing_read(ctx, int(cls), C.byref(n), C.byref(fl), C.byref(s)))
+    return n.value, fl.value, s.value
+
+
+def vtn_timing_reset(ctx):
+    _check(ctx, lib().vtn_timing_reset(ctx))

@@ -14,3 +14,23 @@ def pytest_configure(config):
 
 
 GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+@pytest.fixture(scope="session")
+def libvtn():
+    """Build (if needed) and load the CUDA library.  Compiling needs nvcc, not a GPU."""
+    from paper_2410_18740_gb300 import build, vtn
+    build.build()
+    return vtn.lib()
+
+
+@pytest.fixture(scope="module")
+def ctx(libvtn):
+    import torch
+    from paper_2410_18740_gb300 import vtn
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = vtn.vtn_create(0)
+    yield c
+    torch.cuda.synchronize()
+    vtn.vtn_destroy(c)

@@ -1,0 +1,107 @@
+"""CPU tests of the C-ABI library: it loads, exports every entry point include/vtn.h
+declares, and its host-side problem set-up (coefficients, optimal local basis, MPO)
+agrees with the oracle.  No kernel runs here."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import dense, gbs, mpo as ompo
+from paper_2410_18740_gb300 import inputs, vtn
+from tests.conftest import ROOT
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "vtn.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:vtn_status|const char\*)\s+(vtn_\w+)\s*\(", text, re.M)))
+
+
+def test_library_exports_every_declared_symbol(libvtn):
+    names = declared_symbols()
+    assert len(names) >= 30
+    for n in names:
+        assert hasattr(libvtn, n), f"{n} not exported"
+    assert set(names) == set(vtn.exported_symbols())
+
+
+def _dense_from_abi(m):
+    M, d, D, w = vtn.vtn_mpo_info(m)
+    cores = []
+    for s in range(M):
+        wl, wr, rows, cols, ops = vtn.vtn_mpo_core(m, s)
+        W = np.zeros((wl, wr, d, d), complex)
+        for a, b, op in zip(rows, cols, ops):
+            W[a, b] += op
+        cores.append(W)
+    return ompo.contract_dense(cores)
+
+
+@pytest.mark.parametrize("seed,M,d", [(0, 1, 3), (1, 2, 3), (2, 3, 3), (3, 4, 4), (4, 5, 3)])
+def test_centre_collapsed_mpo_equals_dense_hamiltonian(libvtn, seed, M, d):
+    w = inputs.workload("plain", seed, M=M)
+    m = vtn.vtn_build_mpo(None, w.r, w.U, d, d)
+    try:
+        G = gbs.hamiltonian_coefficients(w.r, w.U)
+        assert np.abs(vtn.vtn_mpo_coefficients(m) - G).max() < 1e-12
+        assert np.abs(vtn.vtn_mpo_covariance(m) - gbs.covariance(w.r, w.U)).max() < 1e-12
+        H = _dense_from_abi(m)
+        assert np.abs(H - dense.dense_hamiltonian(G, d).toarray()).max() < 1e-12
+        _, _, _, wd = vtn.vtn_mpo_info(m)
+        for s in range(1, M):
+            assert wd[s] == 2 * min(s, M - s) + 2
+        assert vtn.vtn_mpo_norm_bound(m) == pytest.approx(gbs.norm_bound(G, M, d), rel=1e-9)
+    finally:
+        vtn.vtn_mpo_free(m)
+
+
+@pytest.mark.parametrize("seed", [5, 6])
+def test_optimal_local_basis_against_oracle(libvtn, seed):
+    w = inputs.workload("large", seed, M=5)
+    m = vtn.vtn_build_mpo(None, w.r, w.U, 40, 6)
+    try:
+        S_list, nu, Grot = gbs.lbo_transform(w.r, w.U)
+        assert np.abs(vtn.vtn_mpo_coefficients(m) - Grot).max() < 1e-12
+        for i in range(5):
+            V = vtn.vtn_mpo_isometry(m, i)
+            Vo = gbs.lbo_isometry(S_list[i], 40, 6)
+            ph = np.vdot(V.reshape(-1), Vo.reshape(-1))
+            ph /= abs(ph)
+            assert np.abs(V * ph - Vo).max() < 1e-12
+        H = _dense_from_abi(vtn.vtn_build_mpo(None, w.r[:3], inputs.haar_unitary(3, inputs.rng_for(seed)), 3, 3))
+        assert np.allclose(H, H.conj().T)
+    finally:
+        vtn.vtn_mpo_free(m)
+
+
+def test_fock_isometry_is_identity(libvtn):
+    w = inputs.workload("plain", 0)
+    m = vtn.vtn_build_mpo(None, w.r, w.U, 4, 4)
+    for i in range(4):
+        assert np.array_equal(vtn.vtn_mpo_isometry(m, i), np.eye(4))
+    vtn.vtn_mpo_free(m)
+
+
+def test_validation_errors(libvtn):
+    w = inputs.workload("plain", 0)
+    bad = w.U.copy()
+    bad[0, 0] += 1e-6
+    with pytest.raises(vtn.VtnError) as e:
+        vtn.vtn_build_mpo(None, w.r, bad, 4, 4)
+    assert e.value.status == vtn.VTN_EINVAL and "unitary" in e.value.msg
+    with pytest.raises(vtn.VtnError):
+        vtn.vtn_build_mpo(None, w.r, w.U, 4, 5)        # d > D
+    with pytest.raises(vtn.VtnError):
+        vtn.vtn_build_mpo(None, w.r, w.U, 1, 1)        # D < 2
+    with pytest.raises(vtn.VtnError):
+        vtn.vtn_build_mpo(None, w.r, w.U, 20, 17)      # d > 16
+    r = w.r.copy()
+    r[1] = np.nan
+    with pytest.raises(vtn.VtnError):
+        vtn.vtn_build_mpo(None, r, w.U, 4, 4)
+
+
+def test_sweep_opts_defaults(libvtn):
+    o = vtn.vtn_sweep_opts_default()
+    assert o.chi_max == 16 and o.n_sweeps == 8 and o.krylov_max == 32 and o.prec == vtn.VTN_FP64
+    assert o.lanczos_tol == 1e-10 and o.lanczos_max_restarts == 4

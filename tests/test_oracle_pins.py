@@ -374,3 +374,28 @@ def test_sampler_goodness_of_fit():
     stat = np.sum((obs - exp) ** 2 / exp)
     pval = scipy.stats.chi2.sf(stat, df=keep.sum() - 1)
     assert pval > 1e-4
+
+
+def test_lbo_marginals_mean_photon_number():
+    """With the optimal local basis at small d, the Fock-basis marginals after the inverse
+    basis transformation give <n_i> = (V_xixi + V_pipi)/2 - 1/2 (closed form of the
+    covariance), and each marginal sums to at most one."""
+    w = inputs.workload("plain", 40, M=3, r_lo=0.3, r_hi=0.6)
+    S_list, nu, Grot = gbs.lbo_transform(w.r, w.U)
+    d, D = 6, 40
+    cores = mpo.build_mpo(Grot, d)
+    mps, rep = dmrg.dmrg(cores, d, 36, 3, seed=5, lanczos=dmrg.LanczosParams(tol=1e-12))
+    isos = [gbs.lbo_isometry(S, D, d) for S in S_list]
+    V = gbs.covariance(w.r, w.U)
+    for i in range(3):
+        p = observables.marginal(mps, isos, [i])
+        assert p.sum() <= 1 + 1e-12 and p.sum() > 1 - 1e-6
+        nmean = float(np.sum(np.arange(D) * p))
+        exact = 0.5 * (V[i, i] + V[3 + i, 3 + i]) - 0.5
+        assert abs(nmean - exact) < 2e-4
+    # Fock-basis marginal agrees with a large-cutoff Fock-basis dense solve
+    G = gbs.hamiltonian_coefficients(w.r, w.U)
+    _, v0 = dense.ground_state(G, 14)
+    pd = dense.marginals_from_vector(v0[:, 0], 3, 14, [1])
+    p1 = observables.marginal(mps, isos, [1])
+    assert np.abs(p1[:8] - pd[:8]).max() < 1e-4
