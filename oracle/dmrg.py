@@ -8,7 +8,7 @@ This restatement is the two-site variant, step by step in plain numpy:
 * environments L[s] (sites 0..s-1) with index order (channel, bra, ket) and
   R[s] (sites s..N-1) with index order (channel, ket, bra); L[0] = R[N] = 1.
 * two-site effective Hamiltonian product (the contraction
-  Y = sum L W_i W_{i+1} Theta R written out as one einsum),
+  Y = sum L W_i W_{i+1} Theta R, evaluated one index group at a time),
 * Lanczos with full re-orthogonalisation (classical Gram-Schmidt, two passes) and
   explicit restarts; the Ritz pair of the tridiagonal matrix by scipy's
   ``eigh_tridiagonal`` (library primitive),
@@ -60,18 +60,26 @@ def initial_mps(N, d, chi0, seed):
 
 # ---------------------------------------------------------------- contractions
 def env_left(L, A, W):
-    """L'[b, l, k] = sum conj(A[i,t,l]) L[a,i,j] W[a,b,t,s] A[j,s,k]."""
-    return np.einsum("itl,aij,abts,jsk->blk", A.conj(), L, W, A, optimize=True)
+    """L'[b, l, k] = sum conj(A[i,t,l]) L[a,i,j] W[a,b,t,s] A[j,s,k], evaluated pairwise."""
+    T = np.einsum("aij,jsk->aisk", L, A, optimize=True)
+    U = np.einsum("abts,aisk->bitk", W, T, optimize=True)
+    return np.einsum("itl,bitk->blk", A.conj(), U, optimize=True)
 
 
 def env_right(R, A, W):
-    """R'[b, j, i] = sum W[b,c,t,s] A[j,s,g] conj(A[i,t,p]) R[c,g,p]."""
-    return np.einsum("bcts,jsg,itp,cgp->bji", W, A, A.conj(), R, optimize=True)
+    """R'[b, j, i] = sum W[b,c,t,s] A[j,s,g] conj(A[i,t,p]) R[c,g,p], evaluated pairwise."""
+    T = np.einsum("jsg,cgp->cjsp", A, R, optimize=True)
+    U = np.einsum("bcts,cjsp->bjtp", W, T, optimize=True)
+    return np.einsum("bjtp,itp->bji", U, A.conj(), optimize=True)
 
 
 def heff_apply(L, W1, W2, R, theta):
-    """Y[i,t,u,l] = sum L[a,i,j] W1[a,b,t,s] W2[b,c,u,v] theta[j,s,v,k] R[c,k,l]."""
-    return np.einsum("aij,abts,bcuv,jsvk,ckl->itul", L, W1, W2, theta, R, optimize=True)
+    """Y[i,t,u,l] = sum L[a,i,j] W1[a,b,t,s] W2[b,c,u,v] theta[j,s,v,k] R[c,k,l],
+    evaluated one index group at a time (L, then W1, then W2, then R)."""
+    T1 = np.einsum("aij,jsvk->aisvk", L, theta, optimize=True)
+    T2 = np.einsum("abts,aisvk->bitvk", W1, T1, optimize=True)
+    T3 = np.einsum("bcuv,bitvk->cituk", W2, T2, optimize=True)
+    return np.einsum("cituk,ckl->itul", T3, R, optimize=True)
 
 
 # ---------------------------------------------------------------- Lanczos
@@ -153,7 +161,7 @@ def truncate(theta, direction, chi_max):
 def norm2(mps):
     E = np.ones((1, 1), dtype=np.complex128)
     for A in mps:
-        E = np.einsum("ij,isk,jsl->kl", E, A.conj(), A, optimize=True)
+        E = np.einsum("isk,isl->kl", A.conj(), np.einsum("ij,jsl->isl", E, A, optimize=True), optimize=True)
     return float(E[0, 0].real)
 
 
@@ -198,7 +206,7 @@ def dmrg(cores, d, chi_max, n_sweeps, seed, chi_schedule=(), lanczos=None,
         disc_max = 0.0
         for direction, bonds in (("right", range(0, N - 1)), ("left", range(N - 2, -1, -1))):
             for i in bonds:
-                theta = np.einsum("asb,btc->astc", mps[i], mps[i + 1])
+                theta = np.einsum("asb,btc->astc", mps[i], mps[i + 1], optimize=True)
                 shape = theta.shape
                 L, R, W1, W2 = Lenv[i], Renv[i + 2], cores[i], cores[i + 1]
                 mv = lambda x: heff_apply(L, W1, W2, R, x.reshape(shape)).reshape(-1)

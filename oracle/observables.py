@@ -22,7 +22,7 @@ from . import philox
 def fock_tensors(mps, isometries):
     if isometries is None:
         return [A.copy() for A in mps]
-    return [np.einsum("nm,amb->anb", V, A) for A, V in zip(mps, isometries)]
+    return [np.einsum("nm,amb->anb", V, A, optimize=True) for A, V in zip(mps, isometries)]
 
 
 def _right_envs(mps):
@@ -32,14 +32,14 @@ def _right_envs(mps):
     E[N] = np.ones((1, 1), dtype=np.complex128)
     for s in range(N - 1, -1, -1):
         A = mps[s]
-        E[s] = np.einsum("asb,csd,bd->ac", A, A.conj(), E[s + 1], optimize=True)
+        E[s] = np.einsum("asb,csb->ac", A, np.einsum("csd,bd->csb", A.conj(), E[s + 1], optimize=True), optimize=True)
     return E
 
 
 def norm2_solver_basis(mps):
     E = np.ones((1, 1), dtype=np.complex128)
     for A in mps:
-        E = np.einsum("ij,isk,jsl->kl", E, A.conj(), A, optimize=True)
+        E = np.einsum("isk,isl->kl", A.conj(), np.einsum("ij,jsl->isl", E, A, optimize=True), optimize=True)
     return float(E[0, 0].real)
 
 
@@ -62,7 +62,7 @@ def marginal(mps, isometries, modes):
                     new[key + (n,)] = An.conj().T @ E @ An
             else:
                 As = mps[s]   # traced mode: solver basis
-                new[key] = np.einsum("ij,isk,jsl->kl", E, As.conj(), As, optimize=True)
+                new[key] = np.einsum("isk,isl->kl", As.conj(), np.einsum("ij,jsl->isl", E, As, optimize=True), optimize=True)
         envs = new
     D = mpsF[0].shape[1]
     out = np.zeros((D,) * len(modes))
@@ -87,8 +87,8 @@ def sample(mps, isometries, seed, n_samples):
         l = np.ones((1,), dtype=np.complex128)
         for s in range(N):
             A = mpsF[s]
-            cand = np.einsum("a,anb->nb", l, A)
-            p = np.real(np.einsum("nb,nc,bc->n", cand, cand.conj(), Er[s + 1]))
+            cand = np.einsum("a,anb->nb", l, A, optimize=True)
+            p = np.real(np.einsum("nb,nb->n", cand @ Er[s + 1], cand.conj(), optimize=True))
             p = np.maximum(p, 0.0)
             cdf = np.cumsum(p)
             u = float(philox.sample_uniforms(seed, np.array([t], dtype=np.uint64), s)[0])
