@@ -1,0 +1,404 @@
+"""Benchmark of the two-site DMRG hot path on the split GBS workload (M=24 modes,
+r_k ~ U(0.5, 1.0), Haar interferometer, Fock cutoff d=8, chi=128).
+
+A step is one full two-site sweep at chi=128 over the instance (all 46 bond
+optimisations: H_eff psi Lanczos, FP64 truncation eigendecomposition, environment
+updates), followed by the FP64 energy, every single-mode Fock marginal and 256 samples
+-- every step of the hot path over one instance.  The state entering the timed region is
+a warm chi=64 state prepared during set-up (resident in HBM).
+
+value     = whole-step H_eff psi throughput: algorithmic flops of every H_eff psi product
+            in the step / step time (TFLOP/s).
+e2e       = the same metric through the C ABI from host buffers: every step uploads the
+            problem (r, U -> MPO) and the MPS from host memory and reads back the MPS,
+            energy, marginals and samples.
+roofline  = the complex GEMM launches inside H_eff psi (the dominant kernel), timed with
+            CUDA events on the library's stream during the timed steps.
+time_to_eps = cumulative sweep time until <H> is within 1e-8 (relative) of the final
+            energy, when the run's last two sweeps agree to that precision (else null).
+
+--impl reference times the CPU oracle (numpy FP64) on a bounded sample of the same
+workload: one H_eff psi product at the shape of the middle bond, in the same unit.
+Multi-GPU: independent replicas (seed 100 + rank), one per GPU, no collective on the
+data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "DMRG time-to-⟨H⟩≤ε and H_eff·ψ TFLOP/s (% peak), mixed vs FP64, 1 GB300"
+WORKLOAD = "split"
+CHI = 128
+KRYLOV = 8
+N_SAMPLES = 256
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="native", choices=["native", "reference"])
+    p.add_argument("--seed", type=int, default=100)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--case", default=None, choices=["heff"],
+                   help="run only the dominant kernel at the middle-bond shape (for profiler captures)")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------- helpers
+def dist_setup(n_gpus):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(ws, x):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.device)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def fp64_peak_tflops():
+    """FP64 FMA peak: the measured bf16 dense peak times the nominal FP64/bf16 ratio
+    (1.25 / 2250 TFLOP/s for GB300)."""
+    peaks, src = load_peaks()
+    return peaks["bf16_tflops"] * (1.25 / 2250.0), f"{src} bf16 x nominal FP64/bf16 ratio"
+
+
+def heff_flops(chi_l, chi_r, d, wl, wr):
+    return 8.0 * d * d * chi_l * chi_r * (wl * chi_l + wr * chi_r)
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_heff_sample(seconds_budget=20.0, min_reps=1):
+    """Time the oracle's H_eff psi at the middle bond of the split workload (w = 24 | 26 | 24,
+    chi = 128, d = 8) on the host cores.  Returns (TFLOP/s, reps, seconds, threads)."""
+    from oracle import dmrg as odmrg
+    from paper_2410_18740_gb300 import inputs
+
+    rng = inputs.rng_for(7)
+    chi, d = CHI, 8
+    wl, wm, wr = 24, 26, 24
+    Wi = inputs.random_sparse_core(wl, wm, d, rng, density=0.15).dense()
+    Wj = inputs.random_sparse_core(wm, wr, d, rng, density=0.15).dense()
+    L = inputs.random_complex((wl, chi, chi), rng)
+    R = inputs.random_complex((wr, chi, chi), rng)
+    th = inputs.random_complex((chi, d, d, chi), rng)
+    fl = heff_flops(chi, chi, d, wl, wr)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        odmrg.heff_apply(L, Wi, Wj, R, th)
+        reps += 1
+        el = time.perf_counter() - t0
+        if reps >= min_reps and el >= seconds_budget:
+            break
+        if reps >= min_reps and el + el / reps > 1.5 * seconds_budget:
+            break
+    threads = os.environ.get("OPENBLAS_NUM_THREADS") or os.environ.get("OMP_NUM_THREADS") or str(os.cpu_count())
+    return fl * reps / el / 1e12, reps, el, int(threads)
+
+
+def run_reference(args):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_heff_sample(seconds_budget=0.0)
+    times = []
+    rates = []
+    for _ in range(args.steps):
+        r, reps, el, threads = oracle_heff_sample(seconds_budget=0.0)
+        times.append(el)
+        rates.append(r)
+    value = sum(heff_flops(CHI, CHI, 8, 24, 24) for _ in times) / sum(times) / 1e12
+    sample = "one H_eff psi product per step at the middle-bond shape of the split workload (w=24|26|24, chi=128, d=8), numpy FP64"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"{WORKLOAD} (M=24, d=8, chi=128), bounded sample",
+                                            "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- native
+def run_native(args):
+    import torch
+
+    from paper_2410_18740_gb300 import build as vbuild
+    from paper_2410_18740_gb300 import inputs, vtn
+
+    ws, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    vbuild.build()
+    seed = args.seed + rank
+    w = inputs.workload(WORKLOAD, seed)
+    ctx = vtn.vtn_create(local)
+    stream = torch.cuda.current_stream()
+    mpo = vtn.vtn_build_mpo(ctx, w.r, w.U, w.D, w.d)
+    M, d, D, wdims = vtn.vtn_mpo_info(mpo)
+    # set-up: warm chi = 64 state (two sweeps from the seeded random MPS)
+    opts_warm = vtn.vtn_sweep_opts_default(chi_max=64, n_sweeps=2, seed=seed, lanczos_tol=1e-10, krylov_max=KRYLOV,
+                                           lanczos_max_restarts=0, chi_schedule=[32, 64])
+    _, mps, _ = vtn.vtn_sweep(ctx, mpo, None, opts_warm)
+    opts = vtn.vtn_sweep_opts_default(chi_max=CHI, n_sweeps=1, lanczos_tol=1e-12, krylov_max=KRYLOV,
+                                      lanczos_max_restarts=0)
+    energies, step_seconds = [], []
+
+    def step(state):
+        st, state, rep = vtn.vtn_sweep(ctx, mpo, state, opts)
+        vtn.vtn_marginals_all(ctx, mpo, state)
+        vtn.vtn_sample(ctx, mpo, state, 1000 + len(energies), N_SAMPLES)
+        energies.append(rep["energy"][-1])
+        return state, rep
+
+    for _ in range(args.warmup):
+        t0 = time.perf_counter()
+        mps, _ = step(mps)
+        step_seconds.append(time.perf_counter() - t0)
+    torch.cuda.synchronize()
+    barrier(ws)
+    # ---------------- timed region
+    vtn.vtn_timing_reset(ctx)
+    vtn.vtn_timing(ctx, True)
+    launches0 = vtn.vtn_launch_count(ctx)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier(ws)
+    ev0.record(stream)
+    flops = 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        mps, rep = step(mps)
+        step_seconds.append(time.perf_counter() - t0)
+        flops += rep["heff_flops"]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks.stop()
+    launches = vtn.vtn_launch_count(ctx) - launches0
+    elapsed = ev0.elapsed_time(ev1) * 1e-3
+    n_heff, fl_heff, s_heff = vtn.vtn_timing_read(ctx, "heff")
+    n_gemm, fl_gemm, s_gemm = vtn.vtn_timing_read(ctx, "gemm")
+    n_eig, _, s_eig = vtn.vtn_timing_read(ctx, "eig")
+    vtn.vtn_timing(ctx, False)
+    elapsed_max = max_over_ranks(ws, elapsed)
+    flops_total = flops * ws   # every replica does the same amount of work per step
+    value = flops_total / elapsed_max / 1e12
+    # ---------------- end-to-end through the C ABI with host buffers
+    sites_host = [vtn.vtn_mps_get_site(ctx, mps, s) for s in range(M)]
+    e2e_times, e2e_flops, h2d, d2h = [], 0.0, 0, 0
+    for _ in range(max(1, min(args.steps, 2))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m2 = vtn.vtn_build_mpo(ctx, w.r, w.U, w.D, w.d)
+        s2 = vtn.vtn_mps_from_host(ctx, m2, sites_host)
+        st, s2, rep2 = vtn.vtn_sweep(ctx, m2, s2, opts)
+        marg = vtn.vtn_marginals_all(ctx, m2, s2)
+        smp = vtn.vtn_sample(ctx, m2, s2, 7, N_SAMPLES)
+        out_sites = [vtn.vtn_mps_get_site(ctx, s2, s) for s in range(M)]
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+        e2e_flops += rep2["heff_flops"]
+        h2d = int(w.r.nbytes + w.U.nbytes + sum(a.nbytes for a in sites_host))
+        d2h = int(sum(a.nbytes for a in out_sites) + marg.nbytes + smp.nbytes + 8 * len(rep2["energy"]))
+        vtn.vtn_mps_free(s2)
+        vtn.vtn_mpo_free(m2)
+    e2e_elapsed = max_over_ranks(ws, sum(e2e_times))
+    e2e_value = e2e_flops * ws / e2e_elapsed / 1e12
+    # ---------------- time to eps (from the energies this run produced)
+    tte = None
+    if len(energies) >= 2 and abs(energies[-1] - energies[-2]) <= 1e-8 * abs(energies[-1]):
+        target = energies[-1] * (1 + 1e-8)
+        cum = 0.0
+        for e, s in zip(energies, step_seconds):
+            cum += s
+            if e <= target:
+                tte = cum
+                break
+    # ---------------- report
+    peak, peak_src = fp64_peak_tflops()
+    achieved = fl_heff / s_heff / 1e12 if s_heff > 0 else None
+    clk = clocks.summary()
+    line = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and ws >= 1:
+            r, reps, el, threads = oracle_heff_sample(seconds_budget=15.0)
+            cpu = {"value": r, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
+                   "sample": f"{reps} oracle H_eff psi products (numpy FP64) at the middle-bond shape of the split "
+                             f"workload (w=24|26|24, chi=128, d=8), {el:.1f} s"}
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: M=24, r~U(0.5,1.0), Haar U, d=D=8, chi=128, two-site DMRG sweep "
+                                   f"(Lanczos {KRYLOV} steps/bond) + energy + marginals + {N_SAMPLES} samples per step",
+                       "seed": args.seed, "precision_path": "FP64 contractions (SIMT DFMA)",
+                       "l2": "working set > L2 (environments, Krylov basis, H_eff intermediates ~1 GB)",
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "kernel": "gemm_c64_kernel (complex FP64 GEMM inside H_eff psi)",
+                         "launches": n_heff, "peak_source": peak_src},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "time_to_eps": {"value": tte, "unit": "s", "eps": "E_final (1 + 1e-8)",
+                            "energies": energies[-4:]},
+            "detail": {"heff_tflops_over_step": value / ws, "gemm_tflops": fl_gemm / s_gemm / 1e12 if s_gemm else None,
+                       "eig_seconds_per_step": s_eig / args.steps, "heff_seconds_per_step": s_heff / args.steps,
+                       "step_seconds": step_seconds[-args.steps:]},
+        }
+        print(json.dumps(line), flush=True)
+    vtn.vtn_mps_free(mps)
+    vtn.vtn_mpo_free(mpo)
+    torch.cuda.synchronize()
+    vtn.vtn_destroy(ctx)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def run_case_heff(args):
+    """H_eff psi alone at the middle-bond shape of the split workload (random inputs,
+    w = 24 | 26 | 24, chi = 128, d = 8), 2 warm-up + 3 timed calls."""
+    import torch
+
+    from paper_2410_18740_gb300 import build as vbuild
+    from paper_2410_18740_gb300 import inputs, vtn
+
+    vbuild.build()
+    rng = inputs.rng_for(7)
+    chi, d, wl, wm, wr = CHI, 8, 24, 26, 24
+    Wi = vtn.core_from_sparse(inputs.random_sparse_core(wl, wm, d, rng, density=0.15))
+    Wj = vtn.core_from_sparse(inputs.random_sparse_core(wm, wr, d, rng, density=0.15))
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.complex128)).cuda()
+    L = dev(inputs.random_complex((wl, chi, chi), rng))
+    R = dev(inputs.random_complex((wr, chi, chi), rng))
+    th = dev(inputs.random_complex((chi, d, d, chi), rng))
+    y = torch.empty_like(th)
+    ctx = vtn.vtn_create(0)
+    for _ in range(2):
+        vtn.vtn_heff_apply(ctx, Wi, Wj, chi, chi, L, R, th, y)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        vtn.vtn_heff_apply(ctx, Wi, Wj, chi, chi, L, R, th, y)
+    torch.cuda.synchronize()
+    el = (time.perf_counter() - t0) / 3
+    print(json.dumps({"case": "heff", "shape": [wl, wm, wr, chi, d], "ms": 1e3 * el,
+                      "tflops": heff_flops(chi, chi, d, wl, wr) / el / 1e12}), flush=True)
+    vtn.vtn_destroy(ctx)
+
+
+def main():
+    args = parse()
+    if args.case == "heff":
+        run_case_heff(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()
