@@ -262,6 +262,39 @@ vtn_status vtn_truncate(vtn_ctx ctx, int chi_l, int d1, int d2, int chi_r, int d
 vtn_status vtn_lbo_rotate(vtn_ctx ctx, int chi_l, int d, int D, int chi_r, const double* V,
                           const double* A, double* out);
 
+/* H_eff psi for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a facility of the library, not a step of the method.
+ *
+ * Who it is for: code that must not call cudaMalloc -- for example an application that
+ * owns every byte of GPU memory through its own pool under a fixed budget, or a
+ * latency-critical loop in which cudaMalloc / cudaFree (which can synchronise the whole
+ * device) are not acceptable.  It needs no vtn_ctx (creating one allocates) and allocates
+ * nothing: the caller passes inputs and outputs, and every intermediate lives in one
+ * file-scope device array of 32 MiB that every GPU which loads the library keeps until the
+ * process exits.
+ *
+ * Same contraction, layouts and argument meaning as vtn_heff_apply (FP64):
+ *   y[i,t,u,l] = sum L[a,i,j] Wi[a,b,t,s] Wj[b,c,u,v] theta[j,s,v,k] R[c,k,l]
+ * Limits (larger requests return VTN_EINVAL before any work is queued): d <= 16;
+ * w_left, w_right <= 512 and nnz <= 4096 for each core; the two cores together need at most
+ * 1 MiB of device storage (about nnz * d * d * 16 bytes each); and
+ * max(Wi.w_left, Wi.w_right, Wj.w_right) * chi_l * d * d * chi_r <= 1,015,808.
+ * Set-up: the first call on a device looks up the array's device address with that device
+ * current; make that first call before any stream capture.
+ * Sharing: all calls use the same array, which keeps what the previous call left (each call
+ * writes every element before reading it, so nothing needs clearing).  Calls whose GPU work
+ * overlaps -- on different streams or from different host threads -- race on the array:
+ * serialise them.
+ * cuda_stream: cudaStream_t the work is queued on (NULL = legacy default stream).  The call
+ * returns once the work is queued; the cores' host arrays may be reused immediately.
+ * L, R, theta, y: device pointers as for vtn_heff_apply; y must not alias theta.
+ * Errors: VTN_EINVAL (limits, null or aliased pointers, inconsistent cores), VTN_ECUDA
+ * (symbol lookup, copy or launch failure).  No message is recorded (vtn_last_error does
+ * not apply: there is no context). */
+vtn_status vtn_heff_apply_static(const vtn_core* Wi, const vtn_core* Wj, int chi_l, int chi_r,
+                                 const double* L, const double* R, const double* theta, double* y,
+                                 void* cuda_stream);
+
 /* Turn per-kernel device timing (CUDA events on the context stream) on or off and read
  * the accumulated figures: launches, algorithmic flops and seconds per kernel class.
  * classes: 0 = complex GEMM (all), 1 = GEMMs inside H_eff psi, 2 = truncation eigensolver,

@@ -96,6 +96,7 @@ _SIGS = {
     "vtn_heff_ground": [_P, C.POINTER(vtn_core), C.POINTER(vtn_core), _I, _I, _P, _P, _P, _D, _I, _I, _PD, _PI],
     "vtn_truncate": [_P, _I, _I, _I, _I, _I, _I, _P, _P, _P, _PD, _PD, _PI],
     "vtn_lbo_rotate": [_P, _I, _I, _I, _I, _P, _P, _P],
+    "vtn_heff_apply_static": [C.POINTER(vtn_core), C.POINTER(vtn_core), _I, _I, _P, _P, _P, _P, _P],
     "vtn_timing": [_P, _I],
     "vtn_timing_read": [_P, _I, C.POINTER(C.c_longlong), _PD, _PD],
     "vtn_timing_reset": [_P],
@@ -418,6 +419,20 @@ def vtn_truncate(ctx, chi_l, d1, d2, chi_r, direction, k_max, theta, left, right
 
 def vtn_lbo_rotate(ctx, chi_l, d, D, chi_r, V, A, out):
     _check(ctx, lib().vtn_lbo_rotate(ctx, int(chi_l), int(d), int(D), int(chi_r), _dptr(V), _dptr(A), _dptr(out)))
+
+
+def vtn_heff_apply_static(Wi, Wj, chi_l, chi_r, L, R, theta, y, stream=None):
+    """H_eff psi with the library's static device scratch: no context, no allocation.
+    stream: torch.cuda.Stream, raw cudaStream_t int, or None for torch's current stream."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    raw = getattr(stream, "cuda_stream", stream)
+    st = lib().vtn_heff_apply_static(C.byref(Wi), C.byref(Wj), int(chi_l), int(chi_r), _dptr(L), _dptr(R),
+                                     _dptr(theta), _dptr(y), C.c_void_p(int(raw) if raw else 0))
+    if st != VTN_OK:
+        raise VtnError(st, "vtn_heff_apply_static: request beyond the static scratch limits, bad arguments, "
+                           "or a CUDA failure (see include/vtn.h)")
 
 
 def vtn_timing(ctx, enable):
