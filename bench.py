@@ -44,6 +44,9 @@ WORKLOAD = "split"
 CHI = 128
 KRYLOV = 8
 N_SAMPLES = 256
+# DRAM bytes (read + write) per H_eff GEMM launch at the middle-bond shape, from the ncu
+# capture summarised in profiles/gemm_c64_heff_split_middle_bond.md (mean of the two launches)
+GEMM_F64_TRAFFIC = 0.5 * ((28.662272 + 344.848640) + (416.211968 + 13.693440)) * 1e6
 
 
 def parse():
@@ -334,7 +337,8 @@ def run_native(args):
                        "l2": "working set > L2 (environments, Krylov basis, H_eff intermediates ~1 GB)",
                        "parallelism": f"replicas x{ws}"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "frac": (achieved / peak) if achieved else None, "traffic": GEMM_F64_TRAFFIC,
+                         "traffic_note": "ncu dram read+write per launch at the middle-bond shape",
                          "kernel": "gemm_c64_kernel (complex FP64 GEMM inside H_eff psi)",
                          "launches": n_heff, "peak_source": peak_src},
             "cpu_baseline": cpu,

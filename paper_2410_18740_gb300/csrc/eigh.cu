@@ -180,6 +180,203 @@ __global__ void tri_finalize(const double2* __restrict__ A, int n, EigSmall s) {
     s.offd[n - 1] = 0.0;
 }
 
+// ---------------------------------------------------------------- persistent tridiagonalisation
+// One cooperative launch for the whole reduction.  Column k's reflector is built by every
+// CTA redundantly from row k (Hermitian), the rank-2 update of column k-1 is applied lazily
+// while the next matrix-vector product p = tau A v streams the trailing block, so each
+// column costs one pass over the trailing block and one grid barrier.  Rows are owned by a
+// fixed warp; data written by other CTAs is read with ld.global.cg (L2, not L1).
+struct GridBar {
+    unsigned int count;
+    unsigned int gen;
+    int error;
+    int pad;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid barrier with a bounded wait: a CTA that waits more than 2 s sets bar->error and
+// every CTA returns false (the kernel then exits; the host reads the flag).
+__device__ bool grid_sync(GridBar* bar, unsigned int nblocks) {
+    __shared__ int ok_sh;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int* vgen = &bar->gen;
+        volatile int* verr = &bar->error;
+        const unsigned int g = *vgen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&bar->count, 1u);
+        int ok = 1;
+        if (arrived == nblocks - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (*vgen == g) {
+                if (*verr) { ok = 0; break; }
+                if (global_ns() - t0 > 2000000000ull) {
+                    atomicExch(&bar->error, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok_sh = ok && (*verr == 0);
+    }
+    __syncthreads();
+    return ok_sh != 0;
+}
+
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {  // a * conj(b)
+    return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+
+constexpr int TRI_THREADS = 512;
+constexpr int TRI_MAX_N = 4096;
+
+__global__ void __launch_bounds__(TRI_THREADS) tridiag_persistent(double2* __restrict__ A, int n,
+                                                                  double2* __restrict__ H, EigSmall s,
+                                                                  double2* __restrict__ pbuf, GridBar* bar) {
+    extern __shared__ double2 sm[];
+    double2* vprev = sm;           // pending reflector (local to the previous trailing block)
+    double2* wprev = sm + n;       // pending w
+    double2* vcur = sm + 2 * n;    // this column's reflector
+    __shared__ double red[33];
+    __shared__ double tau_sh;
+    const unsigned int nb = gridDim.x;
+    const int lane = threadIdx.x & 31;
+    const int nw = blockDim.x >> 5;
+    const int gwarp = blockIdx.x * nw + (threadIdx.x >> 5);
+    const int twarps = (int)nb * nw;
+    bool have_prev = false;
+    for (int k = 0; k + 2 < n; ++k) {
+        const int m = n - k - 1;
+        // ---- A: row k of the current matrix, reflector for column k
+        double a2 = 0.0;
+        for (int t = threadIdx.x; t < m; t += blockDim.x) {
+            double2 a = __ldcg(&A[(long long)k * n + (k + 1 + t)]);
+            if (have_prev) {
+                const double2 u = cmulc(vprev[0], wprev[t + 1]), v = cmulc(wprev[0], vprev[t + 1]);
+                a.x -= u.x + v.x;
+                a.y -= u.y + v.y;
+            }
+            const double2 x = make_double2(a.x, -a.y);
+            vcur[t] = x;
+            a2 += x.x * x.x + x.y * x.y;
+        }
+        a2 = block_sum(a2, red);
+        if (threadIdx.x == 0) {
+            const double2 x0 = vcur[0];
+            const double ax0 = hypot(x0.x, x0.y);
+            double tau = 0.0;
+            double2 beta = make_double2(0.0, 0.0);
+            if (a2 > 0.0) {
+                const double alpha = sqrt(a2);
+                const double2 phi = ax0 > 0.0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
+                vcur[0] = make_double2(x0.x + phi.x * alpha, x0.y + phi.y * alpha);
+                tau = 1.0 / (alpha * (alpha + ax0));
+                beta = make_double2(-phi.x * alpha, -phi.y * alpha);
+            }
+            tau_sh = tau;
+            if (blockIdx.x == 0) {
+                double dk = __ldcg(&A[(long long)k * n + k]).x;
+                if (have_prev) dk -= 2.0 * (vprev[0].x * wprev[0].x + vprev[0].y * wprev[0].y);
+                s.diag[k] = dk;
+                s.tau[k] = tau;
+                s.e[k] = beta;
+            }
+        }
+        __syncthreads();
+        const double tau = tau_sh;
+        if (tau == 0.0)
+            for (int t = threadIdx.x; t < m; t += blockDim.x) vcur[t] = make_double2(0.0, 0.0);
+        __syncthreads();
+        if (blockIdx.x == 0)
+            for (int t = threadIdx.x; t < m; t += blockDim.x) H[(long long)k * n + t] = vcur[t];
+        // ---- B: pending rank-2 update of rows k+1.. fused with p = tau A v
+        double2* pk = pbuf + (long long)(k & 1) * n;
+        int i0 = k + 1 + ((gwarp - (k + 1)) % twarps + twarps) % twarps;
+        for (int i = i0; i < n; i += twarps) {
+            double2* row = A + (long long)i * n;
+            const double2 vpi = have_prev ? vprev[i - k] : make_double2(0.0, 0.0);
+            const double2 wpi = have_prev ? wprev[i - k] : make_double2(0.0, 0.0);
+            double ar = 0.0, ai = 0.0;
+            for (int j = k + 1 + lane; j < n; j += 32) {
+                double2 a = __ldcg(&row[j]);
+                if (have_prev) {
+                    const double2 u = cmulc(vpi, wprev[j - k]), v = cmulc(wpi, vprev[j - k]);
+                    a.x -= u.x + v.x;
+                    a.y -= u.y + v.y;
+                    row[j] = a;
+                }
+                const double2 v = vcur[j - k - 1];
+                ar += a.x * v.x - a.y * v.y;
+                ai += a.x * v.y + a.y * v.x;
+            }
+            ar = warp_sum(ar);
+            ai = warp_sum(ai);
+            if (lane == 0) pk[i - k - 1] = make_double2(tau * ar, tau * ai);
+        }
+        if (!grid_sync(bar, nb)) return;
+        // ---- C: K = (tau/2) Re(v^dag p), w = p - K v; the pair becomes the pending update
+        double dot = 0.0;
+        for (int t = threadIdx.x; t < m; t += blockDim.x) {
+            const double2 p = __ldcg(&pk[t]), v = vcur[t];
+            dot += v.x * p.x + v.y * p.y;
+        }
+        dot = block_sum(dot, red);
+        const double K = 0.5 * tau * dot;
+        for (int t = threadIdx.x; t < m; t += blockDim.x) {
+            const double2 p = __ldcg(&pk[t]), v = vcur[t];
+            wprev[t] = make_double2(p.x - K * v.x, p.y - K * v.y);
+            vprev[t] = v;
+        }
+        __syncthreads();
+        have_prev = true;
+    }
+    // ---- tail (last 2 x 2 block with the pending update applied) and real off-diagonal
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (n >= 2) {
+            double2 a00 = __ldcg(&A[(long long)(n - 2) * n + (n - 2)]);
+            double2 a11 = __ldcg(&A[(long long)(n - 1) * n + (n - 1)]);
+            double2 a01 = __ldcg(&A[(long long)(n - 2) * n + (n - 1)]);
+            if (have_prev) {
+                a00.x -= 2.0 * (vprev[0].x * wprev[0].x + vprev[0].y * wprev[0].y);
+                a11.x -= 2.0 * (vprev[1].x * wprev[1].x + vprev[1].y * wprev[1].y);
+                const double2 u = cmulc(vprev[0], wprev[1]), v = cmulc(wprev[0], vprev[1]);
+                a01.x -= u.x + v.x;
+                a01.y -= u.y + v.y;
+            }
+            s.diag[n - 2] = a00.x;
+            s.diag[n - 1] = a11.x;
+            s.e[n - 2] = make_double2(a01.x, -a01.y);
+        } else {
+            s.diag[0] = __ldcg(&A[0]).x;
+        }
+        s.ph[0] = make_double2(1.0, 0.0);
+        for (int i = 0; i + 1 < n; ++i) {
+            const double2 e = s.e[i];
+            const double r = hypot(e.x, e.y);
+            s.offd[i] = r;
+            const double2 q = s.ph[i];
+            if (r > 0.0) {
+                const double ux = e.x / r, uy = e.y / r;
+                s.ph[i + 1] = make_double2(q.x * ux - q.y * uy, q.x * uy + q.y * ux);
+            } else {
+                s.ph[i + 1] = q;
+            }
+        }
+        s.offd[n - 1] = 0.0;
+    }
+}
+
 // ---------------------------------------------------------------- eigenvalues
 __device__ void tri_bounds(const double* a, const double* b, int n, double& gl, double& gu, double& tn) {
     gl = 1e308; gu = -1e308; tn = 0.0;
@@ -443,7 +640,7 @@ TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int dir
     int tt = ctx.tbegin(TC_EIG, 0.0);
     double2* A = (double2*)ctx.workspace(WS_EIG_A, sizeof(double2) * (size_t)n * n);
     double2* H = (double2*)ctx.workspace(WS_EIG_H, sizeof(double2) * (size_t)n * n);
-    double* small = (double*)ctx.workspace(WS_EIG_U, sizeof(double) * (12 * (size_t)n + 16));
+    double* small = (double*)ctx.workspace(WS_EIG_U, sizeof(double) * (16 * (size_t)n + 32));
     EigSmall s;
     s.diag = small;
     s.offd = small + n;
@@ -455,7 +652,7 @@ TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int dir
     s.w = (double2*)(small + 10 * (size_t)n);
     s.scal = small + 12 * (size_t)n;
     double* Z = (double*)ctx.workspace(WS_EIG_Y, sizeof(double) * (size_t)n * k);
-    double* work = (double*)ctx.workspace(WS_EIG_WORK, sizeof(double) * (5 * (size_t)n * k + (size_t)k * k + 16));
+    double* work = (double*)ctx.workspace(WS_EIG_WORK, sizeof(double) * (5 * (size_t)n * k + (size_t)k * k + 32));
     int* piv = (int*)(work + 4 * (size_t)n * k);
     double* G = work + 5 * (size_t)n * k;
     int* status = (int*)(G + (size_t)k * k);
@@ -473,19 +670,49 @@ TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int dir
     g.C = A; g.ldc = n;
     gemm_c64(ctx, g);
     norm2_dev(ctx, theta, (long long)nL * nR, &s.scal[0]);
-    VTN_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int) * 4, ctx.stream));
-    // 2. tridiagonalisation
-    for (int kk = 0; kk + 2 < n; ++kk) {
-        const int m = n - kk - 1;
-        hh_reflector<<<1, 1024, 0, ctx.stream>>>(A, n, kk, H, s);
-        hh_matvec<<<(m + 7) / 8, 256, 0, ctx.stream>>>(A, n, kk, H, s);
-        hh_w<<<1, 1024, 0, ctx.stream>>>(n, kk, H, s);
-        const long long mm = (long long)m * m;
-        hh_rank2<<<(unsigned)((mm + 255) / 256), 256, 0, ctx.stream>>>(A, n, kk, H, s);
-        ctx.count_launch(4);
+    VTN_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int) * 8, ctx.stream));
+    // 2. tridiagonalisation: one persistent cooperative launch when it fits, else one
+    //    launch per Householder step
+    bool done = false;
+    if (n <= TRI_MAX_N) {
+        const size_t shm = sizeof(double2) * 3 * (size_t)n;
+        static bool attr = false;
+        if (!attr) {
+            VTN_CUDA_TRY(cudaFuncSetAttribute(tridiag_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)(sizeof(double2) * 3 * TRI_MAX_N + 1024)));
+            attr = true;
+        }
+        int per_sm = 0;
+        VTN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tridiag_persistent, TRI_THREADS, shm));
+        int grid = std::min(ctx.num_sms * std::max(per_sm, 0), std::max(1, (n + 7) / 8));
+        if (per_sm >= 1 && grid >= 1) {
+            double2* pbuf = (double2*)(small + 12 * (size_t)n + 16);
+            GridBar* bar = (GridBar*)(status + 4);
+            VTN_CUDA_TRY(cudaMemsetAsync(bar, 0, sizeof(GridBar), ctx.stream));
+            double2* Ap = A;
+            double2* Hp = H;
+            int nn = n;
+            void* args[] = {&Ap, &nn, &Hp, &s, &pbuf, &bar};
+            VTN_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)tridiag_persistent, dim3(grid), dim3(TRI_THREADS),
+                                                     args, shm, ctx.stream));
+            ctx.count_launch();
+            ctx.check_launch("tridiag_persistent");
+            done = true;
+        }
     }
-    tri_finalize<<<1, 32, 0, ctx.stream>>>(A, n, s);
-    ctx.count_launch();
+    if (!done) {
+        for (int kk = 0; kk + 2 < n; ++kk) {
+            const int m = n - kk - 1;
+            hh_reflector<<<1, 1024, 0, ctx.stream>>>(A, n, kk, H, s);
+            hh_matvec<<<(m + 7) / 8, 256, 0, ctx.stream>>>(A, n, kk, H, s);
+            hh_w<<<1, 1024, 0, ctx.stream>>>(n, kk, H, s);
+            const long long mm = (long long)m * m;
+            hh_rank2<<<(unsigned)((mm + 255) / 256), 256, 0, ctx.stream>>>(A, n, kk, H, s);
+            ctx.count_launch(4);
+        }
+        tri_finalize<<<1, 32, 0, ctx.stream>>>(A, n, s);
+        ctx.count_launch();
+    }
     ctx.check_launch("tridiagonalisation");
     // 3. eigenvalues
     bisect_top<<<k, 32, 0, ctx.stream>>>(n, k, s);
@@ -540,7 +767,7 @@ TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int dir
     // results to the host
     VTN_CUDA_TRY(cudaMemcpyAsync(ctx.pinned, s.lam, sizeof(double) * k, cudaMemcpyDeviceToHost, ctx.stream));
     VTN_CUDA_TRY(cudaMemcpyAsync(ctx.pinned + k, s.scal, sizeof(double), cudaMemcpyDeviceToHost, ctx.stream));
-    VTN_CUDA_TRY(cudaMemcpyAsync(ctx.pinned + k + 1, status, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
+    VTN_CUDA_TRY(cudaMemcpyAsync(ctx.pinned + k + 1, status, sizeof(int) * 8, cudaMemcpyDeviceToHost, ctx.stream));
     ctx.sync();
     TruncResult r;
     r.k = k;
@@ -549,9 +776,10 @@ TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int dir
     double kept = 0.0;
     for (double l : r.lam) kept += l;
     r.discarded = tr > 0 ? 1.0 - kept / tr : 0.0;
-    int st = 0;
-    std::memcpy(&st, ctx.pinned + k + 1, sizeof(int));
-    (void)st;
+    int st[8];
+    std::memcpy(st, ctx.pinned + k + 1, sizeof(st));
+    if (st[6] != 0)  // GridBar::error of the persistent tridiagonalisation (ints 4..7 after status)
+        throw Error{VTN_ETIMEOUT, "tridiagonalisation grid barrier timed out"};
     return r;
 }
 
