@@ -5,7 +5,10 @@ A step is one full two-site sweep at chi=128 over the instance (all 46 bond
 optimisations: H_eff psi Lanczos, FP64 truncation eigendecomposition, environment
 updates), followed by the FP64 energy, every single-mode Fock marginal and 256 samples
 -- every step of the hot path over one instance.  The state entering the timed region is
-a warm chi=64 state prepared during set-up (resident in HBM).
+a warm chi=64 state prepared during set-up (resident in HBM).  By default H_eff psi runs in
+the split-precision tensor-core mode (--prec bf16x3: bf16 hi/lo products on tcgen05 with
+FP32 accumulation; everything else FP64); one FP64 sweep from the same state is timed
+afterwards for the mixed-vs-FP64 comparison.
 
 value     = whole-step H_eff psi throughput: algorithmic flops of every H_eff psi product
             in the step / step time (TFLOP/s).
@@ -57,6 +60,12 @@ def parse():
     p.add_argument("--impl", default="native", choices=["native", "reference"])
     p.add_argument("--seed", type=int, default=100)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--prec", default="bf16x3", choices=["bf16x3", "fp64"],
+                   help="contraction precision of H_eff psi in the timed steps")
+    p.add_argument("--no-fp64-compare", action="store_true",
+                   help="skip the single FP64 sweep measured after the timed region")
+    p.add_argument("--tte-sweeps", type=int, default=0,
+                   help="after the timed region, sweep up to this many times to measure time-to-eps")
     p.add_argument("--case", default=None, choices=["heff"],
                    help="run only the dominant kernel at the middle-bond shape (for profiler captures)")
     return p.parse_args()
@@ -238,8 +247,9 @@ def run_native(args):
     opts_warm = vtn.vtn_sweep_opts_default(chi_max=64, n_sweeps=2, seed=seed, lanczos_tol=1e-10, krylov_max=KRYLOV,
                                            lanczos_max_restarts=0, chi_schedule=[32, 64])
     _, mps, _ = vtn.vtn_sweep(ctx, mpo, None, opts_warm)
+    prec = vtn.VTN_BF16X3 if args.prec == "bf16x3" else vtn.VTN_FP64
     opts = vtn.vtn_sweep_opts_default(chi_max=CHI, n_sweeps=1, lanczos_tol=1e-12, krylov_max=KRYLOV,
-                                      lanczos_max_restarts=0)
+                                      lanczos_max_restarts=0, prec=prec)
     energies, step_seconds = [], []
 
     def step(state):
@@ -280,7 +290,45 @@ def run_native(args):
     n_heff, fl_heff, s_heff = vtn.vtn_timing_read(ctx, "heff")
     n_gemm, fl_gemm, s_gemm = vtn.vtn_timing_read(ctx, "gemm")
     n_eig, _, s_eig = vtn.vtn_timing_read(ctx, "eig")
+    n_tc, fl_tc, s_tc = vtn.vtn_timing_read(ctx, "tc")
+    n_mix, _, s_mix = vtn.vtn_timing_read(ctx, "mix")
+    n_lz, _, s_lz = vtn.vtn_timing_read(ctx, "lanczos")
     vtn.vtn_timing(ctx, False)
+    # ---------------- one FP64 sweep from the same state (mixed vs FP64)
+    fp64 = None
+    if not args.no_fp64_compare and prec != vtn.VTN_FP64:
+        sites_bak = [vtn.vtn_mps_get_site(ctx, mps, s) for s in range(M)]
+        probe = vtn.vtn_mps_from_host(ctx, mpo, sites_bak)
+        opts64 = vtn.vtn_sweep_opts_default(chi_max=CHI, n_sweeps=1, lanczos_tol=1e-12, krylov_max=KRYLOV,
+                                            lanczos_max_restarts=0, prec=vtn.VTN_FP64)
+        vtn.vtn_timing_reset(ctx)
+        vtn.vtn_timing(ctx, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, probe, rep64 = vtn.vtn_sweep(ctx, mpo, probe, opts64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        n64, fl64, s64 = vtn.vtn_timing_read(ctx, "heff")
+        vtn.vtn_timing(ctx, False)
+        t64 = e0.elapsed_time(e1) * 1e-3
+        fp64 = {"sweep_s": t64, "heff_tflops_over_sweep": rep64["heff_flops"] / t64 / 1e12,
+                "heff_gemm_tflops": fl64 / s64 / 1e12 if s64 else None, "energy": rep64["energy"][-1]}
+        vtn.vtn_mps_free(probe)
+    # ---------------- optional long run for time-to-eps
+    tte_run = None
+    if args.tte_sweeps > 0:
+        cum, hist = 0.0, []
+        for _ in range(args.tte_sweeps):
+            t0 = time.perf_counter()
+            _, mps, rep_t = vtn.vtn_sweep(ctx, mpo, mps, opts)
+            cum += time.perf_counter() - t0
+            hist.append((cum, rep_t["energy"][-1]))
+            if len(hist) >= 2 and abs(hist[-1][1] - hist[-2][1]) <= 1e-10 * abs(hist[-1][1]):
+                break
+        efin = hist[-1][1]
+        tte_val = next((t for t, e in hist if e <= efin * (1 + 1e-8)), None)
+        tte_run = {"sweeps": len(hist), "converged": len(hist) >= 2 and abs(hist[-1][1] - hist[-2][1]) <= 1e-10 * abs(efin),
+                   "time_to_eps_s": tte_val, "energies": [e for _, e in hist]}
     elapsed_max = max_over_ranks(ws, elapsed)
     flops_total = flops * ws   # every replica does the same amount of work per step
     value = flops_total / elapsed_max / 1e12
@@ -316,8 +364,24 @@ def run_native(args):
                 tte = cum
                 break
     # ---------------- report
-    peak, peak_src = fp64_peak_tflops()
-    achieved = fl_heff / s_heff / 1e12 if s_heff > 0 else None
+    peaks, peaks_src = load_peaks()
+    if prec == vtn.VTN_FP64:
+        peak, peak_src = fp64_peak_tflops()
+        achieved = fl_heff / s_heff / 1e12 if s_heff > 0 else None
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": GEMM_F64_TRAFFIC,
+                "traffic_note": "ncu dram read+write per launch at the middle-bond shape",
+                "kernel": "gemm_c64_kernel (complex FP64 GEMM inside H_eff psi)", "launches": n_heff,
+                "peak_source": peak_src}
+    else:
+        peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        achieved = fl_tc / s_tc / 1e12 if s_tc > 0 else None
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "kernel": "tc_gemm_kernel (tcgen05 bf16 GEMM, TMEM accumulators, TMA tiles) inside H_eff psi",
+                "launches": n_tc, "peak_source": f"{peaks_src} bf16 dense, sustained (kernel timed inside a long step)",
+                "useful_complex_tflops": fl_heff / s_heff / 1e12 if s_heff else None,
+                "note": "bf16 flops executed = 3 split products x 4 real per complex multiply-add of the useful work"}
     clk = clocks.summary()
     line = None
     if rank == 0:
@@ -330,25 +394,29 @@ def run_native(args):
         line = {
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16x3+f64" if prec != vtn.VTN_FP64 else "f64", "data": "synthetic",
             "config": {"workload": f"{WORKLOAD}: M=24, r~U(0.5,1.0), Haar U, d=D=8, chi=128, two-site DMRG sweep "
                                    f"(Lanczos {KRYLOV} steps/bond) + energy + marginals + {N_SAMPLES} samples per step",
-                       "seed": args.seed, "precision_path": "FP64 contractions (SIMT DFMA)",
+                       "seed": args.seed,
+                       "precision_path": ("H_eff psi: bf16x3 split products on tcgen05, FP32 accumulate; Lanczos, "
+                                          "truncation, environments, energy: FP64") if prec != vtn.VTN_FP64
+                       else "FP64 contractions (SIMT DFMA)",
                        "l2": "working set > L2 (environments, Krylov basis, H_eff intermediates ~1 GB)",
                        "parallelism": f"replicas x{ws}"},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": (achieved / peak) if achieved else None, "traffic": GEMM_F64_TRAFFIC,
-                         "traffic_note": "ncu dram read+write per launch at the middle-bond shape",
-                         "kernel": "gemm_c64_kernel (complex FP64 GEMM inside H_eff psi)",
-                         "launches": n_heff, "peak_source": peak_src},
+            "roofline": roof,
+            "fp64_compare": fp64,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "clocks": clk,
-            "time_to_eps": {"value": tte, "unit": "s", "eps": "E_final (1 + 1e-8)",
-                            "energies": energies[-4:]},
-            "detail": {"heff_tflops_over_step": value / ws, "gemm_tflops": fl_gemm / s_gemm / 1e12 if s_gemm else None,
-                       "eig_seconds_per_step": s_eig / args.steps, "heff_seconds_per_step": s_heff / args.steps,
+            "time_to_eps": {"value": tte_run["time_to_eps_s"] if tte_run else tte, "unit": "s",
+                            "eps": "E_final (1 + 1e-8)", "energies": energies[-4:], "long_run": tte_run},
+            "detail": {"heff_tflops_over_step": value / ws,
+                       "fp64_gemm_tflops": fl_gemm / s_gemm / 1e12 if s_gemm else None,
+                       "seconds_per_step": {"heff": s_heff / args.steps, "eig": s_eig / args.steps,
+                                            "mix": s_mix / args.steps, "lanczos_vectors": s_lz / args.steps,
+                                            "fp64_gemm_all": s_gemm / args.steps, "tc_gemm": s_tc / args.steps},
                        "step_seconds": step_seconds[-args.steps:]},
         }
         print(json.dumps(line), flush=True)
@@ -381,15 +449,16 @@ def run_case_heff(args):
     th = dev(inputs.random_complex((chi, d, d, chi), rng))
     y = torch.empty_like(th)
     ctx = vtn.vtn_create(0)
+    prec = vtn.VTN_BF16X3 if args.prec == "bf16x3" else vtn.VTN_FP64
     for _ in range(2):
-        vtn.vtn_heff_apply(ctx, Wi, Wj, chi, chi, L, R, th, y)
+        vtn.vtn_heff_apply(ctx, Wi, Wj, chi, chi, L, R, th, y, prec=prec)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(3):
-        vtn.vtn_heff_apply(ctx, Wi, Wj, chi, chi, L, R, th, y)
+        vtn.vtn_heff_apply(ctx, Wi, Wj, chi, chi, L, R, th, y, prec=prec)
     torch.cuda.synchronize()
     el = (time.perf_counter() - t0) / 3
-    print(json.dumps({"case": "heff", "shape": [wl, wm, wr, chi, d], "ms": 1e3 * el,
+    print(json.dumps({"case": "heff", "prec": args.prec, "shape": [wl, wm, wr, chi, d], "ms": 1e3 * el,
                       "tflops": heff_flops(chi, chi, d, wl, wr) / el / 1e12}), flush=True)
     vtn.vtn_destroy(ctx)
 

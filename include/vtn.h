@@ -61,9 +61,13 @@ typedef enum {
 } vtn_status;
 
 typedef enum {
-    VTN_FP64 = 0,          /* every contraction in IEEE double                           */
-    VTN_TF32X3 = 1,        /* reserved: three-term TF32 split products, FP32 accumulate  */
-    VTN_BF16X3 = 2         /* reserved: three-term BF16 split products, FP32 accumulate  */
+    VTN_FP64 = 0,          /* every contraction in IEEE double (SIMT FP64 FMA)           */
+    VTN_TF32X3 = 1,        /* reserved: three-term TF32 split products (VTN_EUNSUPPORTED) */
+    VTN_BF16X3 = 2         /* H_eff psi on the tensor cores: each FP64 operand split into
+                              bf16 hi + lo, products hi*hi + hi*lo + lo*hi accumulated in
+                              FP32 (relative error ~1e-5 per product); the MPO mixing
+                              between the two GEMMs in FP32.  Lanczos, the truncation
+                              eigendecomposition, environments and energies stay FP64. */
 } vtn_precision;
 
 /* Optional device-memory provider.  alloc returns device memory of at least `bytes`
@@ -295,10 +299,20 @@ vtn_status vtn_heff_apply_static(const vtn_core* Wi, const vtn_core* Wj, int chi
                                  const double* L, const double* R, const double* theta, double* y,
                                  void* cuda_stream);
 
+/* Real bf16 GEMM on the tensor cores (the kernel behind VTN_BF16X3):
+ *   D[m][n] = sum_k A[m][k] * B[n][k], FP32 accumulation,
+ * A: device bf16[M][lda], B: device bf16[N][ldb] (row-major, K contiguous, 16-byte aligned
+ * base and row strides), K a positive multiple of 64; D: device float[M][ldd]
+ * (d_fp64 = 0) or double[M][ldd] (d_fp64 != 0).  A library facility used by the solver's
+ * split-precision products; exposed for parity tests and kernel timing. */
+vtn_status vtn_gemm_bf16(vtn_ctx ctx, int M, int N, int K, const void* A, long long lda, const void* B,
+                         long long ldb, void* D, long long ldd, int d_fp64);
+
 /* Turn per-kernel device timing (CUDA events on the context stream) on or off and read
  * the accumulated figures: launches, algorithmic flops and seconds per kernel class.
  * classes: 0 = complex GEMM (all), 1 = GEMMs inside H_eff psi, 2 = truncation eigensolver,
- * 3 = Lanczos vector kernels, 4 = W mixing. */
+ * 3 = Lanczos vector kernels, 4 = W mixing, 5 = tensor-core GEMMs (bf16 flops executed;
+ * class 1 counts their useful complex flops). */
 vtn_status vtn_timing(vtn_ctx ctx, int enable);
 vtn_status vtn_timing_read(vtn_ctx ctx, int cls, long long* launches, double* flops, double* seconds);
 vtn_status vtn_timing_reset(vtn_ctx ctx);

@@ -277,10 +277,14 @@ vtn_status vtn_create(vtn_ctx* out, int device, void* cuda_stream, const vtn_all
         VTN_CUDA_TRY(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, device));
         VTN_CUDA_TRY(cudaMallocHost((void**)&c.pinned, sizeof(double) * 4096));
         c.ws.resize(WS_COUNT);
+        c.dstatus = (int*)c.dalloc(256);
+        VTN_CUDA_TRY(cudaMemsetAsync(c.dstatus, 0, 256, c.stream));
+        c.sync();
         return VTN_OK;
     });
     if (st != VTN_OK) {
         if (ctx) {
+            if (ctx->c.dstatus) ctx->c.dfree(ctx->c.dstatus);
             if (ctx->c.pinned) cudaFreeHost(ctx->c.pinned);
             delete ctx;
         }
@@ -296,6 +300,7 @@ vtn_status vtn_destroy(vtn_ctx ctx) {
     cudaSetDevice(c.device);
     cudaStreamSynchronize(c.stream);
     for (auto& b : c.ws) c.dfree(b.p);
+    c.dfree(c.dstatus);
     for (auto& p : c.pending) {
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
@@ -579,8 +584,9 @@ vtn_status vtn_sweep(vtn_ctx ctx, vtn_mpo mpo, vtn_mps* state, const vtn_sweep_o
         VTN_REQUIRE(opts->krylov_max >= 1 && opts->krylov_max <= 64, "krylov_max must be in [1, 64]");
         VTN_REQUIRE(opts->lanczos_max_restarts >= 0, "lanczos_max_restarts must be >= 0");
         VTN_REQUIRE(opts->n_schedule == 0 || opts->chi_schedule != nullptr, "chi_schedule missing");
-        if (opts->prec != VTN_FP64)
-            throw Error{VTN_EUNSUPPORTED, "only VTN_FP64 contractions are available in this build"};
+        if (opts->prec != VTN_FP64 && opts->prec != VTN_BF16X3)
+            throw Error{VTN_EUNSUPPORTED, "VTN_TF32X3 is not available in this build"};
+        const bool split = opts->prec == VTN_BF16X3;
         Ctx& c = ctx->c;
         use_device(c);
         ensure_mpo_device(ctx, mpo);
@@ -647,9 +653,12 @@ vtn_status vtn_sweep(vtn_ctx ctx, vtn_mpo mpo, vtn_mps* state, const vtn_sweep_o
                     const double2* L = env.L[i];
                     const double2* R = env.R[i + 2];
                     const double hf = heff_flops(Wi, Wj, cl, cr);
+                    HeffPacked pk;
+                    if (split) heff_pack_envs(c, Wi, Wj, cl, cr, L, R, pk);
                     LanczosResult lr = lanczos(c, n, theta, opts->lanczos_tol, opts->krylov_max,
                                                opts->lanczos_max_restarts, [&](const double2* in, double2* out) {
-                                                   heff_apply_dev(c, Wi, Wj, cl, cr, L, R, in, out);
+                                                   if (split) heff_apply_bf16x3(c, Wi, Wj, pk, in, out);
+                                                   else heff_apply_dev(c, Wi, Wj, cl, cr, L, R, in, out);
                                                });
                     rep.matvecs += lr.n_matvec;
                     rep.heff_flops += hf * lr.n_matvec;
@@ -677,6 +686,7 @@ vtn_status vtn_sweep(vtn_ctx ctx, vtn_mpo mpo, vtn_mps* state, const vtn_sweep_o
             have_prev = true;
         }
         c.tflush();
+        c.check_dstatus();
         rep.lanczos_not_converged = not_conv;
         rep.heff_seconds = c.tc[TC_HEFF].seconds;
         rep.gemm_flops = c.tc[TC_GEMM].flops;
@@ -911,15 +921,23 @@ vtn_status vtn_heff_apply(vtn_ctx ctx, const vtn_core* Wi, const vtn_core* Wj, i
         VTN_REQUIRE(L && R && theta && y, "null device pointer");
         VTN_REQUIRE(chi_l >= 1 && chi_r >= 1, "bond dimensions must be >= 1");
         VTN_REQUIRE(theta != y, "y must not alias theta");
-        if (prec != VTN_FP64) throw Error{VTN_EUNSUPPORTED, "only VTN_FP64 contractions are available in this build"};
+        if (prec != VTN_FP64 && prec != VTN_BF16X3)
+            throw Error{VTN_EUNSUPPORTED, "VTN_TF32X3 is not available in this build"};
         Ctx& c = ctx->c;
         use_device(c);
         HostCore hi = core_from_abi(Wi), hj = core_from_abi(Wj);
         VTN_REQUIRE(hi.wr == hj.wl && hi.d == hj.d, "Wi.w_right must equal Wj.w_left and d must agree");
         TempCore ci(c, hi), cj(c, hj);
-        heff_apply_dev(c, ci.dc, cj.dc, chi_l, chi_r, (const double2*)L, (const double2*)R, (const double2*)theta,
-                       (double2*)y);
+        if (prec == VTN_BF16X3) {
+            HeffPacked pk;
+            heff_pack_envs(c, ci.dc, cj.dc, chi_l, chi_r, (const double2*)L, (const double2*)R, pk);
+            heff_apply_bf16x3(c, ci.dc, cj.dc, pk, (const double2*)theta, (double2*)y);
+        } else {
+            heff_apply_dev(c, ci.dc, cj.dc, chi_l, chi_r, (const double2*)L, (const double2*)R,
+                           (const double2*)theta, (double2*)y);
+        }
         c.sync();
+        c.check_dstatus();
         return VTN_OK;
     });
 }
@@ -1002,6 +1020,32 @@ vtn_status vtn_lbo_rotate(vtn_ctx ctx, int chi_l, int d, int D, int chi_r, const
         use_device(c);
         lbo_rotate_dev(c, chi_l, d, D, chi_r, (const double2*)V, (const double2*)A, (double2*)out);
         c.sync();
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_gemm_bf16(vtn_ctx ctx, int M, int N, int K, const void* A, long long lda, const void* B,
+                         long long ldb, void* D, long long ldd, int d_fp64) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(A && B && D, "null device pointer");
+        VTN_REQUIRE(M >= 1 && N >= 1 && K >= 64 && K % 64 == 0, "need M, N >= 1 and K a positive multiple of 64");
+        Ctx& c = ctx->c;
+        use_device(c);
+        TcGemmArgs g;
+        g.M = M;
+        g.N = N;
+        g.K = K;
+        g.A = (const __nv_bfloat16*)A;
+        g.lda = lda;
+        g.B = (const __nv_bfloat16*)B;
+        g.ldb = ldb;
+        g.D = D;
+        g.ldd = ldd;
+        g.d_fp64 = d_fp64 != 0;
+        tc_gemm_bf16(c, g);
+        c.sync();
+        c.check_dstatus();
         return VTN_OK;
     });
 }

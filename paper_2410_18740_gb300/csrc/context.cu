@@ -84,6 +84,19 @@ void Ctx::tflush() {
     pending.clear();
 }
 
+void Ctx::check_dstatus() {
+    if (!dstatus) return;
+    VTN_CUDA_TRY(cudaMemcpyAsync(pinned + 4095, dstatus, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    sync();
+    int v = 0;
+    std::memcpy(&v, pinned + 4095, sizeof(int));
+    if (v != 0) {
+        VTN_CUDA_TRY(cudaMemsetAsync(dstatus, 0, sizeof(int), stream));
+        sync();
+        throw Error{VTN_ETIMEOUT, "a bounded device-side wait gave up (tensor-core pipeline)"};
+    }
+}
+
 void Ctx::check_launch(const char* what) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) throw Error{VTN_ECUDA, std::string(what) + ": " + cudaGetErrorString(e)};

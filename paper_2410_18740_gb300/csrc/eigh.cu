@@ -240,6 +240,7 @@ __device__ __forceinline__ double2 cmulc(double2 a, double2 b) {  // a * conj(b)
 
 constexpr int TRI_THREADS = 512;
 constexpr int TRI_MAX_N = 4096;
+constexpr int TRI_ROWS = 8;   // rows processed together per CTA in the matrix pass
 
 __global__ void __launch_bounds__(TRI_THREADS) tridiag_persistent(double2* __restrict__ A, int n,
                                                                   double2* __restrict__ H, EigSmall s,
@@ -250,11 +251,10 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_persistent(double2* __res
     double2* vcur = sm + 2 * n;    // this column's reflector
     __shared__ double red[33];
     __shared__ double tau_sh;
+    __shared__ double2 rowred[(TRI_THREADS / 32) * TRI_ROWS];
     const unsigned int nb = gridDim.x;
     const int lane = threadIdx.x & 31;
     const int nw = blockDim.x >> 5;
-    const int gwarp = blockIdx.x * nw + (threadIdx.x >> 5);
-    const int twarps = (int)nb * nw;
     bool have_prev = false;
     for (int k = 0; k + 2 < n; ++k) {
         const int m = n - k - 1;
@@ -300,29 +300,68 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_persistent(double2* __res
         __syncthreads();
         if (blockIdx.x == 0)
             for (int t = threadIdx.x; t < m; t += blockDim.x) H[(long long)k * n + t] = vcur[t];
-        // ---- B: pending rank-2 update of rows k+1.. fused with p = tau A v
+        // ---- B: pending rank-2 update of rows k+1.. fused with p = tau A v.  CTA b owns the
+        //      rows i = b (mod gridDim.x); all its threads stride the columns of all its rows
+        //      at once, so each thread keeps several independent L2 loads in flight.
         double2* pk = pbuf + (long long)(k & 1) * n;
-        int i0 = k + 1 + ((gwarp - (k + 1)) % twarps + twarps) % twarps;
-        for (int i = i0; i < n; i += twarps) {
-            double2* row = A + (long long)i * n;
-            const double2 vpi = have_prev ? vprev[i - k] : make_double2(0.0, 0.0);
-            const double2 wpi = have_prev ? wprev[i - k] : make_double2(0.0, 0.0);
-            double ar = 0.0, ai = 0.0;
-            for (int j = k + 1 + lane; j < n; j += 32) {
-                double2 a = __ldcg(&row[j]);
-                if (have_prev) {
-                    const double2 u = cmulc(vpi, wprev[j - k]), v = cmulc(wpi, vprev[j - k]);
-                    a.x -= u.x + v.x;
-                    a.y -= u.y + v.y;
-                    row[j] = a;
+        {
+            const int i0 = k + 1 + ((int)blockIdx.x - (k + 1) % (int)nb + (int)nb) % (int)nb;
+            const int nrows = (i0 < n) ? (n - 1 - i0) / (int)nb + 1 : 0;
+            for (int r0 = 0; r0 < nrows; r0 += TRI_ROWS) {
+                const int rcount = min(TRI_ROWS, nrows - r0);
+                double accr[TRI_ROWS], acci[TRI_ROWS];
+#pragma unroll
+                for (int r = 0; r < TRI_ROWS; ++r) accr[r] = acci[r] = 0.0;
+                for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) {
+                    const double2 v = vcur[j - k - 1];
+                    double2 vpj = make_double2(0.0, 0.0), wpj = make_double2(0.0, 0.0);
+                    if (have_prev) {
+                        vpj = vprev[j - k];
+                        wpj = wprev[j - k];
+                    }
+                    double2 a[TRI_ROWS];
+#pragma unroll
+                    for (int r = 0; r < TRI_ROWS; ++r)
+                        if (r < rcount) a[r] = __ldcg(&A[(long long)(i0 + (r0 + r) * (int)nb) * n + j]);
+#pragma unroll
+                    for (int r = 0; r < TRI_ROWS; ++r) {
+                        if (r >= rcount) break;
+                        const int i = i0 + (r0 + r) * (int)nb;
+                        if (have_prev) {
+                            const double2 p1 = cmulc(vprev[i - k], wpj), p2 = cmulc(wprev[i - k], vpj);
+                            a[r].x -= p1.x + p2.x;
+                            a[r].y -= p1.y + p2.y;
+                            A[(long long)i * n + j] = a[r];
+                        }
+                        accr[r] += a[r].x * v.x - a[r].y * v.y;
+                        acci[r] += a[r].x * v.y + a[r].y * v.x;
+                    }
                 }
-                const double2 v = vcur[j - k - 1];
-                ar += a.x * v.x - a.y * v.y;
-                ai += a.x * v.y + a.y * v.x;
+                // reduce the row sums over the CTA: warp shuffles, then across warps
+#pragma unroll
+                for (int r = 0; r < TRI_ROWS; ++r) {
+                    accr[r] = warp_sum(accr[r]);
+                    acci[r] = warp_sum(acci[r]);
+                }
+                if (lane == 0) {
+#pragma unroll
+                    for (int r = 0; r < TRI_ROWS; ++r) {
+                        rowred[(threadIdx.x >> 5) * TRI_ROWS + r] = make_double2(accr[r], acci[r]);
+                    }
+                }
+                __syncthreads();
+                if (threadIdx.x < rcount) {
+                    double sr = 0.0, si = 0.0;
+                    for (int w = 0; w < nw; ++w) {
+                        const double2 t = rowred[w * TRI_ROWS + threadIdx.x];
+                        sr += t.x;
+                        si += t.y;
+                    }
+                    const int i = i0 + (r0 + (int)threadIdx.x) * (int)nb;
+                    pk[i - k - 1] = make_double2(tau * sr, tau * si);
+                }
+                __syncthreads();
             }
-            ar = warp_sum(ar);
-            ai = warp_sum(ai);
-            if (lane == 0) pk[i - k - 1] = make_double2(tau * ar, tau * ai);
         }
         if (!grid_sync(bar, nb)) return;
         // ---- C: K = (tau/2) Re(v^dag p), w = p - K v; the pair becomes the pending update
@@ -684,7 +723,7 @@ TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int dir
         }
         int per_sm = 0;
         VTN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tridiag_persistent, TRI_THREADS, shm));
-        int grid = std::min(ctx.num_sms * std::max(per_sm, 0), std::max(1, (n + 7) / 8));
+        int grid = std::min(ctx.num_sms * std::max(per_sm, 0), std::max(1, (n + 3) / 4));
         if (per_sm >= 1 && grid >= 1) {
             double2* pbuf = (double2*)(small + 12 * (size_t)n + 16);
             GridBar* bar = (GridBar*)(status + 4);

@@ -1,0 +1,343 @@
+// Split-precision complex contractions on the tensor cores (precision mode VTN_BF16X3).
+//
+// A complex product C = op(A) op(B) (M x N, inner dimension Kt = kb * K) is evaluated as
+// one real bf16 GEMM D = A~ B~^T of the tensor-core kernel:
+//
+//   real 2x2 block form      row m of A^ = [Re a(m,:), Im a(m,:)]
+//                            rows 2n, 2n+1 of B^ = [Re b(:,n), -Im b(:,n)], [Im b(:,n), Re b(:,n)]
+//                            so that (A^ B^T)[m][2n] = Re C, [m][2n+1] = Im C (interleaved output)
+//   split precision          x = hi + lo with hi = bf16(x), lo = bf16(x - hi)
+//   three products           A~ = [A^_hi | A^_hi | A^_lo], B~ = [B^_hi | B^_lo | B^_hi] along K,
+//                            A~ B~^T = A_hi B_hi + A_hi B_lo + A_lo B_hi   (FP32 accumulation)
+//
+// K~ = 6 Kt rounded up to a multiple of 64 (zero padded).  The packers read FP64 or FP32
+// complex data through 32 x 32 shared-memory tiles so that both the read and the write side
+// are coalesced whatever the operand's transposition.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "vtn_internal.cuh"
+
+namespace vtn {
+namespace {
+
+template <typename T>
+struct CplxTraits;
+template <>
+struct CplxTraits<double2> {
+    static __device__ __forceinline__ void split(double x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+        hi = __double2bfloat16(x);
+        lo = __double2bfloat16(x - (double)__bfloat162float(hi));
+    }
+};
+template <>
+struct CplxTraits<float2> {
+    static __device__ __forceinline__ void split(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+        hi = __float2bfloat16(x);
+        lo = __float2bfloat16(x - __bfloat162float(hi));
+    }
+};
+
+struct PackP {
+    int rows;          // M (A) or N (B): output rows are rows (A) or 2 * rows (B)
+    int K, kb;         // complex inner dimension per block and number of blocks; Kt = K * kb
+    long long ld, s_kb;
+    int conj_t;        // 1: operand used as X^dag
+    int is_b;
+    __nv_bfloat16* out;
+    long long ldo;
+};
+
+// value of the operand element (r, kk) of op(X) as seen by the product:
+//   A: r = m -> op(A)(m, kk);   B: r = n -> op(B)(kk, n)
+template <typename T>
+__device__ __forceinline__ T load_elem(const T* X, const PackP& p, int r, int kk) {
+    const int c = kk / p.K, k = kk - c * p.K;
+    const T* base = X + (long long)c * p.s_kb;
+    // contiguous along kk: A with N, B with C; contiguous along r: A with C, B with N
+    T v;
+    if (p.is_b == p.conj_t) v = base[(long long)r * p.ld + k];
+    else v = base[(long long)k * p.ld + r];
+    if (p.conj_t) v.y = -v.y;
+    return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) pack_kernel(const T* __restrict__ X, PackP p) {
+    __shared__ T tile[32][33];
+    const int Kt = p.K * p.kb;
+    const int kk0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    const bool along_kk = (p.is_b == p.conj_t);
+    // load: make the fast thread index run along the contiguous source direction
+    for (int t = threadIdx.y; t < 32; t += 8) {
+        const int fast = threadIdx.x;
+        const int r = along_kk ? r0 + t : r0 + fast;
+        const int kk = along_kk ? kk0 + fast : kk0 + t;
+        T v;
+        v.x = 0;
+        v.y = 0;
+        if (r < p.rows && kk < Kt) v = load_elem(X, p, r, kk);
+        if (along_kk) tile[t][fast] = v;
+        else tile[fast][t] = v;
+    }
+    __syncthreads();
+    // write: fast index along kk (the contiguous output direction)
+    const int kk = kk0 + threadIdx.x;
+    if (kk >= Kt) return;
+    for (int t = threadIdx.y; t < 32; t += 8) {
+        const int r = r0 + t;
+        if (r >= p.rows) break;
+        const T v = tile[t][threadIdx.x];
+        __nv_bfloat16 rh, rl, ih, il;
+        CplxTraits<T>::split(v.x, rh, rl);
+        CplxTraits<T>::split(v.y, ih, il);
+        if (!p.is_b) {
+            __nv_bfloat16* o = p.out + (long long)r * p.ldo;
+            o[kk] = rh;
+            o[Kt + kk] = ih;
+            o[2 * Kt + kk] = rh;
+            o[3 * Kt + kk] = ih;
+            o[4 * Kt + kk] = rl;
+            o[5 * Kt + kk] = il;
+        } else {
+            __nv_bfloat16* o0 = p.out + (long long)(2 * r) * p.ldo;
+            __nv_bfloat16* o1 = o0 + p.ldo;
+            const __nv_bfloat16 nih = __hneg(ih), nil = __hneg(il);
+            // row 2n: [Re b, -Im b] in segments hi | lo | hi
+            o0[kk] = rh;
+            o0[Kt + kk] = nih;
+            o0[2 * Kt + kk] = rl;
+            o0[3 * Kt + kk] = nil;
+            o0[4 * Kt + kk] = rh;
+            o0[5 * Kt + kk] = nih;
+            // row 2n+1: [Im b, Re b]
+            o1[kk] = ih;
+            o1[Kt + kk] = rh;
+            o1[2 * Kt + kk] = il;
+            o1[3 * Kt + kk] = rl;
+            o1[4 * Kt + kk] = ih;
+            o1[5 * Kt + kk] = rh;
+        }
+    }
+}
+
+__global__ void zero_pad_kernel(__nv_bfloat16* out, long long ldo, int rows, int from, int to) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int w = to - from;
+    if (w <= 0 || t >= (long long)rows * w) return;
+    const long long r = t / w;
+    out[r * ldo + from + (t % w)] = __float2bfloat16(0.0f);
+}
+
+// out[b][p][s'][q] = sum_e op_e[s'][s] in[src_e][p][s][q] in FP32 (ops rounded to float).
+// All threads of a CTA share the output channel b, so the channel's operators are staged
+// in shared memory (as float2) in chunks, instead of being re-read by every thread.
+constexpr int MIX_SH = 4096;  // float2 operator entries per chunk (32 KiB)
+
+template <int DM>
+__global__ void __launch_bounds__(256) mix_f32_kernel(int P, int d, int Q, const int* __restrict__ ptr,
+                                                      const int* __restrict__ src, const int* __restrict__ opi,
+                                                      const double2* __restrict__ ops,
+                                                      const unsigned char* __restrict__ ident,
+                                                      const float2* __restrict__ in, float2* __restrict__ out) {
+    __shared__ float2 op_sh[MIX_SH];
+    __shared__ int src_sh[MIX_SH / 4];
+    __shared__ unsigned char id_sh[MIX_SH / 4];
+    const long long PQ = (long long)P * Q;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = t < PQ;
+    const int b = blockIdx.y;
+    const long long pp = active ? t / Q : 0, q = active ? t % Q : 0;
+    const long long blk = PQ * d;
+    const int dd = d * d;
+    const int chunk = min(MIX_SH / dd, MIX_SH / 4);
+    float2 acc[DM];
+#pragma unroll
+    for (int s = 0; s < DM; ++s) acc[s] = make_float2(0.f, 0.f);
+    const int e_begin = ptr[b], e_end = ptr[b + 1];
+    for (int e0 = e_begin; e0 < e_end; e0 += chunk) {
+        const int ne = min(chunk, e_end - e0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < ne * dd; i += blockDim.x) {
+            const int e = i / dd, j = i - e * dd;
+            const double2 o = ops[(long long)opi[e0 + e] * dd + j];
+            op_sh[i] = make_float2((float)o.x, (float)o.y);
+        }
+        for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+            src_sh[e] = src[e0 + e];
+            id_sh[e] = ident[opi[e0 + e]];
+        }
+        __syncthreads();
+        if (!active) continue;
+        for (int e = 0; e < ne; ++e) {
+            const float2* x = in + (long long)src_sh[e] * blk + pp * d * Q + q;
+            const float2* op = op_sh + e * dd;
+            if (id_sh[e]) {
+                const float sr = op[0].x, si = op[0].y;
+#pragma unroll
+                for (int sp = 0; sp < DM; ++sp) {
+                    if (sp < d) {
+                        const float2 v = x[(long long)sp * Q];
+                        acc[sp].x += sr * v.x - si * v.y;
+                        acc[sp].y += sr * v.y + si * v.x;
+                    }
+                }
+            } else {
+                float2 xv[DM];
+#pragma unroll
+                for (int s = 0; s < DM; ++s) xv[s] = (s < d) ? x[(long long)s * Q] : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int sp = 0; sp < DM; ++sp) {
+                    if (sp >= d) continue;
+#pragma unroll
+                    for (int s = 0; s < DM; ++s) {
+                        if (s < d) {
+                            const float2 o = op[sp * d + s];
+                            acc[sp].x += o.x * xv[s].x - o.y * xv[s].y;
+                            acc[sp].y += o.x * xv[s].y + o.y * xv[s].x;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (!active) return;
+    float2* y = out + (long long)b * blk + pp * d * Q + q;
+#pragma unroll
+    for (int sp = 0; sp < DM; ++sp)
+        if (sp < d) y[(long long)sp * Q] = acc[sp];
+}
+
+long long k6(long long Kt) { return ((6 * Kt + 63) / 64) * 64; }
+
+template <typename T>
+void pack_impl(Ctx& ctx, const T* X, int rows, int K, int kb, long long ld, long long s_kb, bool conj_t, bool is_b,
+               __nv_bfloat16* out) {
+    const long long Kt = (long long)K * kb;
+    const long long ldo = k6(Kt);
+    PackP p;
+    p.rows = rows;
+    p.K = K;
+    p.kb = kb;
+    p.ld = ld;
+    p.s_kb = s_kb;
+    p.conj_t = conj_t ? 1 : 0;
+    p.is_b = is_b ? 1 : 0;
+    p.out = out;
+    p.ldo = ldo;
+    dim3 grid((unsigned)((Kt + 31) / 32), (unsigned)((rows + 31) / 32));
+    VTN_REQUIRE(grid.y <= 65535, "pack: too many rows");
+    pack_kernel<T><<<grid, dim3(32, 8), 0, ctx.stream>>>(X, p);
+    const int orows = is_b ? 2 * rows : rows;
+    const int from = (int)(6 * Kt), to = (int)ldo;
+    if (to > from) {
+        const long long cnt = (long long)orows * (to - from);
+        zero_pad_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx.stream>>>(out, ldo, orows, from, to);
+        ctx.count_launch();
+    }
+    ctx.count_launch();
+    ctx.check_launch("pack_kernel");
+}
+
+}  // namespace
+
+long long tc_k6(long long Kt) { return k6(Kt); }
+
+void tc_pack(Ctx& ctx, const double2* X, int rows, int K, int kb, long long ld, long long s_kb, bool conj_t, bool is_b,
+             __nv_bfloat16* out) {
+    pack_impl<double2>(ctx, X, rows, K, kb, ld, s_kb, conj_t, is_b, out);
+}
+
+void tc_pack(Ctx& ctx, const float2* X, int rows, int K, int kb, long long ld, long long s_kb, bool conj_t, bool is_b,
+             __nv_bfloat16* out) {
+    pack_impl<float2>(ctx, X, rows, K, kb, ld, s_kb, conj_t, is_b, out);
+}
+
+void mix_apply_f32(Ctx& ctx, const DevCore& core, bool by_col, int P, int Q, const float2* in, float2* out) {
+    const int w_out = by_col ? core.wr : core.wl;
+    const int d = core.d;
+    const long long PQ = (long long)P * Q;
+    if (PQ == 0) return;
+    VTN_REQUIRE(w_out <= 65535, "too many MPO channels");
+    dim3 grid((unsigned)((PQ + 255) / 256), w_out);
+    const int* ptr = by_col ? core.col_ptr : core.row_ptr;
+    const int* src = by_col ? core.col_src : core.row_src;
+    const int* opi = by_col ? core.col_op : core.row_op;
+    double fl = 8.0 * PQ * ((double)core.n_ident * d + (double)core.n_dense * d * d);
+    int t = ctx.tbegin(TC_MIX, fl);
+    if (d <= 4)
+        mix_f32_kernel<4><<<grid, 256, 0, ctx.stream>>>(P, d, Q, ptr, src, opi, core.ops, core.ident, in, out);
+    else if (d <= 8)
+        mix_f32_kernel<8><<<grid, 256, 0, ctx.stream>>>(P, d, Q, ptr, src, opi, core.ops, core.ident, in, out);
+    else
+        mix_f32_kernel<16><<<grid, 256, 0, ctx.stream>>>(P, d, Q, ptr, src, opi, core.ops, core.ident, in, out);
+    ctx.count_launch();
+    ctx.check_launch("mix_f32_kernel");
+    ctx.tend(t);
+}
+
+// ----------------------------------------------------------------------------- H_eff
+void heff_pack_envs(Ctx& ctx, const DevCore& Wi, const DevCore& Wj, int chi_l, int chi_r, const double2* L,
+                    const double2* R, HeffPacked& pk) {
+    const int wl = Wi.wl, wr = Wj.wr;
+    pk.chi_l = chi_l;
+    pk.chi_r = chi_r;
+    pk.wl = wl;
+    pk.wr = wr;
+    pk.ldL = k6(chi_l);
+    pk.ldR = k6((long long)wr * chi_r);
+    pk.L = (__nv_bfloat16*)ctx.workspace(WS_TC_L, sizeof(__nv_bfloat16) * (size_t)wl * chi_l * pk.ldL);
+    pk.R = (__nv_bfloat16*)ctx.workspace(WS_TC_R, sizeof(__nv_bfloat16) * (size_t)2 * chi_r * pk.ldR);
+    // A operand of T1 = L theta: rows (a, i), inner index j
+    tc_pack(ctx, L, wl * chi_l, chi_l, 1, chi_l, 0, false, false, pk.L);
+    // B operand of y = sum_c T3[c] R[c]: output column l, inner index (c, k): R[c][k][l]
+    tc_pack(ctx, R, chi_r, chi_r, wr, chi_r, (long long)chi_r * chi_r, false, true, pk.R);
+}
+
+void heff_apply_bf16x3(Ctx& ctx, const DevCore& Wi, const DevCore& Wj, const HeffPacked& pk, const double2* theta,
+                       double2* y) {
+    const int d = Wi.d, chi_l = pk.chi_l, chi_r = pk.chi_r;
+    const long long n_theta = (long long)chi_l * d * d * chi_r;
+    const int wmax = std::max(Wi.wl, std::max(Wi.wr, Wj.wr));
+    const long long ldB1 = k6(chi_l);
+    const long long ldA2 = k6((long long)Wj.wr * chi_r);
+    __nv_bfloat16* B1 = (__nv_bfloat16*)ctx.workspace(WS_TC_B1, sizeof(__nv_bfloat16) * (size_t)2 * d * d * chi_r * ldB1);
+    float2* X = (float2*)ctx.workspace(WS_X, sizeof(float2) * (size_t)wmax * n_theta);
+    float2* Yb = (float2*)ctx.workspace(WS_Y, sizeof(float2) * (size_t)wmax * n_theta);
+    __nv_bfloat16* A2 = (__nv_bfloat16*)ctx.workspace(WS_TC_A2, sizeof(__nv_bfloat16) * (size_t)chi_l * d * d * ldA2);
+    const double useful1 = 8.0 * (double)Wi.wl * chi_l * (double)d * d * chi_r * chi_l;
+    const double useful2 = 8.0 * (double)chi_l * d * d * chi_r * (double)chi_r * Wj.wr;
+    // B operand of T1 = L theta: output column (s1 s2 k), inner index j: theta[j][(s1 s2 k)]
+    tc_pack(ctx, theta, d * d * chi_r, chi_l, 1, (long long)d * d * chi_r, 0, false, true, B1);
+    TcGemmArgs g1;
+    g1.M = Wi.wl * chi_l;
+    g1.N = 2 * d * d * chi_r;
+    g1.K = (int)ldB1;
+    g1.A = pk.L;
+    g1.lda = pk.ldL;
+    g1.B = B1;
+    g1.ldb = ldB1;
+    g1.D = X;
+    g1.ldd = 2LL * d * d * chi_r;
+    g1.d_fp64 = false;
+    tc_gemm_bf16(ctx, g1, TC_HEFF, useful1);
+    mix_apply_f32(ctx, Wi, true, chi_l, d * chi_r, X, Yb);
+    mix_apply_f32(ctx, Wj, true, chi_l * d, chi_r, Yb, X);
+    // A operand of y = sum_c T3[c] R[c]: rows (i t u), inner index (c, k): T3[c][(i t u)][k]
+    tc_pack(ctx, (const float2*)X, chi_l * d * d, chi_r, Wj.wr, chi_r, n_theta, false, false, A2);
+    TcGemmArgs g2;
+    g2.M = chi_l * d * d;
+    g2.N = 2 * chi_r;
+    g2.K = (int)ldA2;
+    g2.A = A2;
+    g2.lda = ldA2;
+    g2.B = pk.R;
+    g2.ldb = pk.ldR;
+    g2.D = y;
+    g2.ldd = 2LL * chi_r;
+    g2.d_fp64 = true;
+    tc_gemm_bf16(ctx, g2, TC_HEFF, useful2);
+}
+
+}  // namespace vtn

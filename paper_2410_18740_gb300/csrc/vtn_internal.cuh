@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of libvtn.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -32,7 +33,7 @@ struct Error {
     } while (0)
 
 // ------------------------------------------------------------------ timing classes
-enum TimingClass { TC_GEMM = 0, TC_HEFF = 1, TC_EIG = 2, TC_LANCZOS = 3, TC_MIX = 4, TC_COUNT = 5 };
+enum TimingClass { TC_GEMM = 0, TC_HEFF = 1, TC_EIG = 2, TC_LANCZOS = 3, TC_MIX = 4, TC_TC = 5, TC_COUNT = 6 };
 
 struct Ctx;
 
@@ -83,6 +84,7 @@ struct Ctx {
     // named workspace slots
     std::vector<DevBuf> ws;
     double* pinned = nullptr;  // pinned host scratch (4096 doubles)
+    int* dstatus = nullptr;    // device status word: non-zero after a bounded device wait gave up
     int num_sms = 0;
 
     void* dalloc(size_t bytes);
@@ -95,11 +97,13 @@ struct Ctx {
     void tflush();  // synchronise and accumulate pending intervals
     void sync() { VTN_CUDA_TRY(cudaStreamSynchronize(stream)); }
     void check_launch(const char* what);
+    void check_dstatus();  // synchronises; throws VTN_ETIMEOUT (and clears the word) if set
 };
 
 enum WsSlot {
     WS_X = 0, WS_Y, WS_Z, WS_KRYLOV, WS_VEC_W, WS_VEC_T, WS_PARTIAL, WS_SCAL, WS_EIG_A, WS_EIG_H,
-    WS_EIG_Y, WS_EIG_WORK, WS_EIG_U, WS_CORE_A, WS_CORE_B, WS_ENV_TMP, WS_MISC, WS_COUNT
+    WS_EIG_Y, WS_EIG_WORK, WS_EIG_U, WS_CORE_A, WS_CORE_B, WS_ENV_TMP, WS_MISC, WS_TC_L, WS_TC_R, WS_TC_B1,
+    WS_TC_A2, WS_TC_PART, WS_COUNT
 };
 
 // ------------------------------------------------------------------ cores
@@ -122,16 +126,49 @@ struct GemmArgs {
 };
 void gemm_c64(Ctx& ctx, const GemmArgs& g, int timing_class = TC_GEMM);
 
+// ------------------------------------------------------------------ tensor-core GEMM (bf16 -> fp32)
+// D[m][n] = sum_k A[m][k] B[n][k]; A: M x K, B: N x K (K-major bf16, K % 64 == 0); D fp32/fp64
+struct TcGemmArgs {
+    int M, N, K;
+    const __nv_bfloat16* A;
+    long long lda;
+    const __nv_bfloat16* B;
+    long long ldb;
+    void* D;
+    long long ldd;
+    bool d_fp64 = false;
+};
+void tc_gemm_bf16(Ctx& ctx, const TcGemmArgs& a, int timing_class = -1, double useful_flops = 0.0);
+long long tc_k6(long long Kt);
+// split-precision operand packing (see tc_ops.cu)
+void tc_pack(Ctx& ctx, const double2* X, int rows, int K, int kb, long long ld, long long s_kb, bool conj_t, bool is_b,
+             __nv_bfloat16* out);
+void tc_pack(Ctx& ctx, const float2* X, int rows, int K, int kb, long long ld, long long s_kb, bool conj_t, bool is_b,
+             __nv_bfloat16* out);
+
 // ------------------------------------------------------------------ W mixing
 // out[b][p][s'][q] = sum_{entries (src -> b)} op[s'][s] in[src][p][s][q]
 // by_col: output channel = core column (left-to-right use); else output = core row.
 void mix_apply(Ctx& ctx, const DevCore& core, bool by_col, int P, int Q, const double2* in,
                double2* out);
 
+void mix_apply_f32(Ctx& ctx, const DevCore& core, bool by_col, int P, int Q, const float2* in, float2* out);
+
 // ------------------------------------------------------------------ contractions
 void heff_apply_dev(Ctx& ctx, const DevCore& Wi, const DevCore& Wj, int chi_l, int chi_r,
                     const double2* L, const double2* R, const double2* theta, double2* y);
 double heff_flops(const DevCore& Wi, const DevCore& Wj, int chi_l, int chi_r);
+// split-precision (BF16X3) H_eff psi: environments packed once per bond
+struct HeffPacked {
+    int chi_l = 0, chi_r = 0, wl = 0, wr = 0;
+    long long ldL = 0, ldR = 0;
+    __nv_bfloat16* L = nullptr;
+    __nv_bfloat16* R = nullptr;
+};
+void heff_pack_envs(Ctx& ctx, const DevCore& Wi, const DevCore& Wj, int chi_l, int chi_r, const double2* L,
+                    const double2* R, HeffPacked& pk);
+void heff_apply_bf16x3(Ctx& ctx, const DevCore& Wi, const DevCore& Wj, const HeffPacked& pk, const double2* theta,
+                       double2* y);
 void env_left_dev(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const double2* L,
                   const double2* A, double2* out);
 void env_right_dev(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const double2* R,

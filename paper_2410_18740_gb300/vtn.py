@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libvtn.so")
 VTN_OK, VTN_EINVAL, VTN_ENOMEM, VTN_ECUDA, VTN_ENOCONV, VTN_ETIMEOUT, VTN_EUNSUPPORTED = range(7)
 VTN_FP64, VTN_TF32X3, VTN_BF16X3 = 0, 1, 2
 VTN_FLAG_LBO = 1
-TIMING_CLASSES = {"gemm": 0, "heff": 1, "eig": 2, "lanczos": 3, "mix": 4}
+TIMING_CLASSES = {"gemm": 0, "heff": 1, "eig": 2, "lanczos": 3, "mix": 4, "tc": 5}
 STATUS_NAMES = {0: "VTN_OK", 1: "VTN_EINVAL", 2: "VTN_ENOMEM", 3: "VTN_ECUDA", 4: "VTN_ENOCONV",
                 5: "VTN_ETIMEOUT", 6: "VTN_EUNSUPPORTED"}
 
@@ -97,6 +97,7 @@ _SIGS = {
     "vtn_truncate": [_P, _I, _I, _I, _I, _I, _I, _P, _P, _P, _PD, _PD, _PI],
     "vtn_lbo_rotate": [_P, _I, _I, _I, _I, _P, _P, _P],
     "vtn_heff_apply_static": [C.POINTER(vtn_core), C.POINTER(vtn_core), _I, _I, _P, _P, _P, _P, _P],
+    "vtn_gemm_bf16": [_P, _I, _I, _I, _P, C.c_longlong, _P, C.c_longlong, _P, C.c_longlong, _I],
     "vtn_timing": [_P, _I],
     "vtn_timing_read": [_P, _I, C.POINTER(C.c_longlong), _PD, _PD],
     "vtn_timing_reset": [_P],
@@ -433,6 +434,17 @@ def vtn_heff_apply_static(Wi, Wj, chi_l, chi_r, L, R, theta, y, stream=None):
     if st != VTN_OK:
         raise VtnError(st, "vtn_heff_apply_static: request beyond the static scratch limits, bad arguments, "
                            "or a CUDA failure (see include/vtn.h)")
+
+
+def vtn_gemm_bf16(ctx, A, B, D):
+    """D = A B^T on the tensor cores: A (M, K) and B (N, K) torch bf16 CUDA tensors, K a
+    multiple of 64; D (M, N) float32 or float64 CUDA tensor."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    _check(ctx, lib().vtn_gemm_bf16(ctx, int(M), int(N), int(K), _dptr(A), int(A.stride(0)), _dptr(B),
+                                    int(B.stride(0)), _dptr(D), int(D.stride(0)),
+                                    1 if D.dtype == torch.float64 else 0))
 
 
 def vtn_timing(ctx, enable):

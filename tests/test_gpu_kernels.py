@@ -218,5 +218,5 @@ def test_kernel_calls_reject_bad_arguments(ctx):
     with pytest.raises(vtn.VtnError):
         vtn.vtn_env_update(ctx, bad, 0, 1, 1, x, x, x)    # channel out of range
     with pytest.raises(vtn.VtnError) as e:
-        vtn.vtn_heff_apply(ctx, c, c, 1, 1, x, x, x, torch.zeros_like(x), prec=vtn.VTN_BF16X3)
+        vtn.vtn_heff_apply(ctx, c, c, 1, 1, x, x, x, torch.zeros_like(x), prec=vtn.VTN_TF32X3)
     assert e.value.status == vtn.VTN_EUNSUPPORTED

@@ -196,7 +196,7 @@ def test_error_paths(ctx):
     with pytest.raises(vtn.VtnError):
         vtn.vtn_sweep(ctx, m, mps, vtn.vtn_sweep_opts_default(n_sweeps=65))
     with pytest.raises(vtn.VtnError) as e:
-        vtn.vtn_sweep(ctx, m, mps, vtn.vtn_sweep_opts_default(prec=vtn.VTN_BF16X3))
+        vtn.vtn_sweep(ctx, m, mps, vtn.vtn_sweep_opts_default(prec=vtn.VTN_TF32X3))
     assert e.value.status == vtn.VTN_EUNSUPPORTED
     # Lanczos forced to miss its tolerance: VTN_ENOCONV, but the state is still valid
     st, mps2, rep = vtn.vtn_sweep(ctx, m, mps, vtn.vtn_sweep_opts_default(
