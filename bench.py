@@ -66,13 +66,14 @@ def parse():
                    help="skip the single FP64 sweep measured after the timed region")
     p.add_argument("--tte-sweeps", type=int, default=0,
                    help="after the timed region, sweep up to this many times to measure time-to-eps")
-    p.add_argument("--case", default=None, choices=["heff"],
+    p.add_argument("--case", default=None, choices=["heff", "trunc"],
                    help="run only the dominant kernel at the middle-bond shape (for profiler captures)")
     return p.parse_args()
 
 
 # ----------------------------------------------------------------------------- helpers
-def dist_setup(n_gpus):
+def dist_setup(n_gpus, backend="nccl"):
+    """Rank layout from the torchrun environment; one process per GPU (replicas)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -80,8 +81,9 @@ def dist_setup(n_gpus):
         import torch
         import torch.distributed as dist
 
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
     return ws, rank, local
 
 
@@ -98,9 +100,16 @@ def max_over_ranks(ws, x):
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(ws, per_rank_work, elapsed):
+    """Weak scaling over replicas: every rank did per_rank_work in its own elapsed time; the
+    job rate is the total work over the slowest rank's time."""
+    return per_rank_work * ws / max_over_ranks(ws, elapsed)
 
 
 class ClockSampler:
@@ -330,8 +339,7 @@ def run_native(args):
         tte_run = {"sweeps": len(hist), "converged": len(hist) >= 2 and abs(hist[-1][1] - hist[-2][1]) <= 1e-10 * abs(efin),
                    "time_to_eps_s": tte_val, "energies": [e for _, e in hist]}
     elapsed_max = max_over_ranks(ws, elapsed)
-    flops_total = flops * ws   # every replica does the same amount of work per step
-    value = flops_total / elapsed_max / 1e12
+    value = whole_job_rate(ws, flops, elapsed) / 1e12   # every replica does the same work per step
     # ---------------- end-to-end through the C ABI with host buffers
     sites_host = [vtn.vtn_mps_get_site(ctx, mps, s) for s in range(M)]
     e2e_times, e2e_flops, h2d, d2h = [], 0.0, 0, 0
@@ -463,10 +471,42 @@ def run_case_heff(args):
     vtn.vtn_destroy(ctx)
 
 
+def run_case_trunc(args):
+    """The FP64 truncation eigensolver alone at the middle-bond shape of the split workload:
+    theta (128, 8, 8, 128) with a decaying spectrum, k = 128, 2 warm-up + 3 timed calls."""
+    import torch
+
+    from paper_2410_18740_gb300 import build as vbuild
+    from paper_2410_18740_gb300 import inputs, vtn
+
+    vbuild.build()
+    rng = inputs.rng_for(8)
+    chi, d = CHI, 8
+    th = inputs.random_complex((chi, d, d, chi), rng)
+    th /= np.linalg.norm(th)
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.complex128)).cuda()
+    t = dev(th)
+    left = torch.empty((chi, d, chi), dtype=torch.complex128, device="cuda")
+    right = torch.empty((chi, d, chi), dtype=torch.complex128, device="cuda")
+    ctx = vtn.vtn_create(0)
+    for _ in range(2):
+        vtn.vtn_truncate(ctx, chi, d, d, chi, 0, chi, t, left, right)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        vtn.vtn_truncate(ctx, chi, d, d, chi, 0, chi, t, left, right)
+    torch.cuda.synchronize()
+    el = (time.perf_counter() - t0) / 3
+    print(json.dumps({"case": "trunc", "n": chi * d, "k": chi, "ms": 1e3 * el}), flush=True)
+    vtn.vtn_destroy(ctx)
+
+
 def main():
     args = parse()
     if args.case == "heff":
         run_case_heff(args)
+    elif args.case == "trunc":
+        run_case_trunc(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -59,6 +59,7 @@ struct EigSmall {
     double2* p;     // [n]
     double2* w;     // [n]
     double* scal;   // [8]: trace, status
+    double* bsq;    // [n]: offd^2 (Sturm counts)
 };
 
 // ---------------------------------------------------------------- Householder steps
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(256) hh_rank2(double2* __restrict__ A, int n, 
     a->y -= im;
 }
 
-// tail of the tridiagonal, real off-diagonal and phases
+// tail of the tridiagonal (the real off-diagonal and phases follow in tri_phases)
 __global__ void tri_finalize(const double2* __restrict__ A, int n, EigSmall s) {
     if (threadIdx.x != 0) return;
     if (n >= 2) {
@@ -164,28 +165,103 @@ __global__ void tri_finalize(const double2* __restrict__ A, int n, EigSmall s) {
         s.e[n - 2] = make_double2(t.x, -t.y);  // A[n-1][n-2] = conj(A[n-2][n-1])
     }
     s.diag[n - 1] = A[(long long)(n - 1) * n + (n - 1)].x;
-    s.ph[0] = make_double2(1.0, 0.0);
-    for (int i = 0; i + 1 < n; ++i) {
-        const double2 e = s.e[i];
-        const double r = hypot(e.x, e.y);
-        s.offd[i] = r;
-        const double2 q = s.ph[i];
-        if (r > 0.0) {
-            const double ux = e.x / r, uy = e.y / r;
-            s.ph[i + 1] = make_double2(q.x * ux - q.y * uy, q.x * uy + q.y * ux);
-        } else {
-            s.ph[i + 1] = q;
+}
+
+// Real symmetric form of the Hermitian tridiagonal: offd_i = |e_i| and the phases
+// ph_0 = 1, ph_{i+1} = ph_i e_i / |e_i| (D^dag T D is real for D = diag(ph)).  The phases
+// are an exclusive prefix product, computed as a block scan: each thread multiplies out a
+// contiguous segment, the segment products are scanned in shared memory, then each
+// segment is rewritten from its prefix.  One CTA of TP_THREADS threads.
+constexpr int TP_THREADS = 1024;
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__global__ void __launch_bounds__(TP_THREADS) tri_phases(int n, EigSmall s) {
+    __shared__ double2 scan[TP_THREADS];
+    const int t = threadIdx.x;
+    const int seg = (n + TP_THREADS - 1) / TP_THREADS;
+    const int i0 = min(n, t * seg), i1 = min(n, i0 + seg);
+    // unit factors u_i = e_i / |e_i| (1 for e_i = 0 and for the last index)
+    double2 prod = make_double2(1.0, 0.0);
+    for (int i = i0; i < i1; ++i) {
+        double2 u = make_double2(1.0, 0.0);
+        double r = 0.0;
+        if (i + 1 < n) {
+            const double2 ei = s.e[i];
+            r = hypot(ei.x, ei.y);
+            if (r > 0.0) {
+                const double inv = 1.0 / r;
+                u = make_double2(ei.x * inv, ei.y * inv);
+            }
         }
+        s.offd[i] = r;
+        s.bsq[i] = r * r;
+        s.ph[i] = u;  // scratch: u_i, replaced by the phase below
+        prod = cmul(prod, u);
     }
-    s.offd[n - 1] = 0.0;
+    scan[t] = prod;
+    __syncthreads();  // also publishes offd for the Gershgorin pass below
+    for (int off = 1; off < TP_THREADS; off <<= 1) {
+        const double2 other = t >= off ? scan[t - off] : make_double2(1.0, 0.0);
+        __syncthreads();
+        scan[t] = cmul(other, scan[t]);
+        __syncthreads();
+    }
+    double2 cur = t > 0 ? scan[t - 1] : make_double2(1.0, 0.0);
+    for (int i = i0; i < i1; ++i) {
+        const double2 u = s.ph[i];
+        s.ph[i] = cur;
+        cur = cmul(cur, u);
+    }
+    // Gershgorin interval [gl, gu] and max_i |a_i| + |b_{i-1}| + |b_i| -> scal[4..6]
+    double gl = 1e308, gu = -1e308, tn = 0.0;
+    for (int i = i0; i < i1; ++i) {
+        const double r = (i > 0 ? s.offd[i - 1] : 0.0) + s.offd[i];
+        const double ai = s.diag[i];
+        gl = fmin(gl, ai - r);
+        gu = fmax(gu, ai + r);
+        tn = fmax(tn, fabs(ai) + r);
+    }
+    __shared__ double mm[3][32];
+    for (int o = 16; o > 0; o >>= 1) {
+        gl = fmin(gl, __shfl_xor_sync(0xffffffffu, gl, o));
+        gu = fmax(gu, __shfl_xor_sync(0xffffffffu, gu, o));
+        tn = fmax(tn, __shfl_xor_sync(0xffffffffu, tn, o));
+    }
+    if ((t & 31) == 0) {
+        mm[0][t >> 5] = gl;
+        mm[1][t >> 5] = gu;
+        mm[2][t >> 5] = tn;
+    }
+    __syncthreads();
+    if (t == 0) {
+        for (int w = 1; w < TP_THREADS / 32; ++w) {
+            gl = fmin(gl, mm[0][w]);
+            gu = fmax(gu, mm[1][w]);
+            tn = fmax(tn, mm[2][w]);
+        }
+        s.scal[4] = gl;
+        s.scal[5] = gu;
+        s.scal[6] = tn;
+    }
 }
 
 // ---------------------------------------------------------------- persistent tridiagonalisation
-// One cooperative launch for the whole reduction.  Column k's reflector is built by every
-// CTA redundantly from row k (Hermitian), the rank-2 update of column k-1 is applied lazily
-// while the next matrix-vector product p = tau A v streams the trailing block, so each
-// column costs one pass over the trailing block and one grid barrier.  Rows are owned by a
-// fixed warp; data written by other CTAs is read with ld.global.cg (L2, not L1).
+// One cooperative launch for the whole reduction (Householder, one column per step).
+// Column k's reflector is built by every CTA redundantly from row k (Hermitian); the
+// rank-2 update of step k-1 is applied lazily while the matrix-vector product p = tau A v
+// of step k streams the trailing block, so each step costs one pass over the trailing
+// block and one grid barrier.
+//
+// GB300 issues one FP64 warp instruction per 64 cycles per SM sub-partition whatever the
+// number of active lanes, so the pass is organised to keep every FP64 instruction 32 lanes
+// wide and to avoid per-row reductions: a warp owns 32 consecutive COLUMNS i (coalesced
+// loads of A[j][i]) and walks a slice of the rows j, accumulating
+// (A v)_i = sum_j conj(A[j][i]) v_j (A is Hermitian) in its lanes.  The CTAs that share a
+// column chunk write one partial each; every CTA sums them after the barrier.  Data written
+// by other CTAs is read with ld.global.cg (L2, not L1).
 struct GridBar {
     unsigned int count;
     unsigned int gen;
@@ -239,22 +315,23 @@ __device__ __forceinline__ double2 cmulc(double2 a, double2 b) {  // a * conj(b)
 }
 
 constexpr int TRI_THREADS = 512;
+constexpr int TRI_NW = TRI_THREADS / 32;
 constexpr int TRI_MAX_N = 4096;
-constexpr int TRI_ROWS = 8;   // rows processed together per CTA in the matrix pass
+constexpr int TRI_UNROLL = 4;  // rows in flight per warp
 
+// part: 2 x gridDim.x x n partial products (double-buffered by step parity)
 __global__ void __launch_bounds__(TRI_THREADS) tridiag_persistent(double2* __restrict__ A, int n,
                                                                   double2* __restrict__ H, EigSmall s,
-                                                                  double2* __restrict__ pbuf, GridBar* bar) {
+                                                                  double2* __restrict__ part, GridBar* bar) {
     extern __shared__ double2 sm[];
     double2* vprev = sm;           // pending reflector (local to the previous trailing block)
     double2* wprev = sm + n;       // pending w
     double2* vcur = sm + 2 * n;    // this column's reflector
     __shared__ double red[33];
     __shared__ double tau_sh;
-    __shared__ double2 rowred[(TRI_THREADS / 32) * TRI_ROWS];
-    const unsigned int nb = gridDim.x;
-    const int lane = threadIdx.x & 31;
-    const int nw = blockDim.x >> 5;
+    __shared__ double2 colred[TRI_NW][32];
+    const int nb = (int)gridDim.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     bool have_prev = false;
     for (int k = 0; k + 2 < n; ++k) {
         const int m = n - k - 1;
@@ -300,87 +377,116 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_persistent(double2* __res
         __syncthreads();
         if (blockIdx.x == 0)
             for (int t = threadIdx.x; t < m; t += blockDim.x) H[(long long)k * n + t] = vcur[t];
-        // ---- B: pending rank-2 update of rows k+1.. fused with p = tau A v.  CTA b owns the
-        //      rows i = b (mod gridDim.x); all its threads stride the columns of all its rows
-        //      at once, so each thread keeps several independent L2 loads in flight.
-        double2* pk = pbuf + (long long)(k & 1) * n;
-        {
-            const int i0 = k + 1 + ((int)blockIdx.x - (k + 1) % (int)nb + (int)nb) % (int)nb;
-            const int nrows = (i0 < n) ? (n - 1 - i0) / (int)nb + 1 : 0;
-            for (int r0 = 0; r0 < nrows; r0 += TRI_ROWS) {
-                const int rcount = min(TRI_ROWS, nrows - r0);
-                double accr[TRI_ROWS], acci[TRI_ROWS];
-#pragma unroll
-                for (int r = 0; r < TRI_ROWS; ++r) accr[r] = acci[r] = 0.0;
-                for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) {
-                    const double2 v = vcur[j - k - 1];
-                    double2 vpj = make_double2(0.0, 0.0), wpj = make_double2(0.0, 0.0);
-                    if (have_prev) {
-                        vpj = vprev[j - k];
-                        wpj = wprev[j - k];
-                    }
-                    double2 a[TRI_ROWS];
-#pragma unroll
-                    for (int r = 0; r < TRI_ROWS; ++r)
-                        if (r < rcount) a[r] = __ldcg(&A[(long long)(i0 + (r0 + r) * (int)nb) * n + j]);
-#pragma unroll
-                    for (int r = 0; r < TRI_ROWS; ++r) {
-                        if (r >= rcount) break;
-                        const int i = i0 + (r0 + r) * (int)nb;
-                        if (have_prev) {
-                            const double2 p1 = cmulc(vprev[i - k], wpj), p2 = cmulc(wprev[i - k], vpj);
-                            a[r].x -= p1.x + p2.x;
-                            a[r].y -= p1.y + p2.y;
-                            A[(long long)i * n + j] = a[r];
-                        }
-                        accr[r] += a[r].x * v.x - a[r].y * v.y;
-                        acci[r] += a[r].x * v.y + a[r].y * v.x;
-                    }
-                }
-                // reduce the row sums over the CTA: warp shuffles, then across warps
-#pragma unroll
-                for (int r = 0; r < TRI_ROWS; ++r) {
-                    accr[r] = warp_sum(accr[r]);
-                    acci[r] = warp_sum(acci[r]);
-                }
-                if (lane == 0) {
-#pragma unroll
-                    for (int r = 0; r < TRI_ROWS; ++r) {
-                        rowred[(threadIdx.x >> 5) * TRI_ROWS + r] = make_double2(accr[r], acci[r]);
-                    }
-                }
-                __syncthreads();
-                if (threadIdx.x < rcount) {
-                    double sr = 0.0, si = 0.0;
-                    for (int w = 0; w < nw; ++w) {
-                        const double2 t = rowred[w * TRI_ROWS + threadIdx.x];
-                        sr += t.x;
-                        si += t.y;
-                    }
-                    const int i = i0 + (r0 + (int)threadIdx.x) * (int)nb;
-                    pk[i - k - 1] = make_double2(tau * sr, tau * si);
-                }
-                __syncthreads();
+        // ---- B: pending rank-2 update of the trailing block fused with (A v).  Work unit
+        //      u = (column chunk c = u mod C of 32 columns, row slice cs = u / C of CS); CTA b
+        //      takes units b, b + nb, ...; its warp w walks the rows k+1 + cs*NW + w + t*CS*NW.
+        const int C = (m + 31) / 32;
+        const int CS = max(1, min(nb / C, (m + TRI_NW - 1) / TRI_NW));
+        double2* pk = part + (long long)(k & 1) * nb * n;
+        for (int unit = (int)blockIdx.x; unit < C * CS; unit += nb) {  // one pass unless C > nb
+            const int c = unit % C, cs = unit / C;
+            const int il = c * 32 + lane;  // local column index (0..m-1)
+            const bool col_ok = il < m;
+            const int i = k + 1 + (col_ok ? il : 0);
+            // column factors of a_ji -= vp_j conj(wp_i) + wp_j conj(vp_i)
+            double2 vpi = make_double2(0.0, 0.0), wpi = make_double2(0.0, 0.0);
+            if (have_prev && col_ok) {
+                vpi = vprev[i - k];
+                wpi = wprev[i - k];
             }
+            double accx = 0.0, accy = 0.0;
+            const int stride = CS * TRI_NW;
+            int j = k + 1 + cs * TRI_NW + warp;
+            for (; j + (TRI_UNROLL - 1) * stride < n; j += TRI_UNROLL * stride) {
+                double2 a[TRI_UNROLL];
+#pragma unroll
+                for (int u = 0; u < TRI_UNROLL; ++u)
+                    a[u] = col_ok ? __ldcg(&A[(long long)(j + u * stride) * n + i]) : make_double2(0.0, 0.0);
+#pragma unroll
+                for (int u = 0; u < TRI_UNROLL; ++u) {
+                    const int jj = j + u * stride;
+                    if (have_prev) {
+                        const double2 vpj = vprev[jj - k], wpj = wprev[jj - k];
+                        double ax = a[u].x, ay = a[u].y;
+                        ax = fma(-vpj.x, wpi.x, ax);
+                        ax = fma(-vpj.y, wpi.y, ax);
+                        ax = fma(-wpj.x, vpi.x, ax);
+                        ax = fma(-wpj.y, vpi.y, ax);
+                        ay = fma(-vpj.y, wpi.x, ay);
+                        ay = fma(vpj.x, wpi.y, ay);
+                        ay = fma(-wpj.y, vpi.x, ay);
+                        ay = fma(wpj.x, vpi.y, ay);
+                        a[u] = make_double2(ax, ay);
+                        if (col_ok) A[(long long)jj * n + i] = a[u];
+                    }
+                    const double2 v = vcur[jj - k - 1];
+                    accx = fma(a[u].x, v.x, accx);
+                    accx = fma(a[u].y, v.y, accx);
+                    accy = fma(a[u].x, v.y, accy);
+                    accy = fma(-a[u].y, v.x, accy);
+                }
+            }
+            for (; j < n; j += stride) {
+                double2 a = col_ok ? __ldcg(&A[(long long)j * n + i]) : make_double2(0.0, 0.0);
+                if (have_prev) {
+                    const double2 vpj = vprev[j - k], wpj = wprev[j - k];
+                    double ax = a.x, ay = a.y;
+                    ax = fma(-vpj.x, wpi.x, ax);
+                    ax = fma(-vpj.y, wpi.y, ax);
+                    ax = fma(-wpj.x, vpi.x, ax);
+                    ax = fma(-wpj.y, vpi.y, ax);
+                    ay = fma(-vpj.y, wpi.x, ay);
+                    ay = fma(vpj.x, wpi.y, ay);
+                    ay = fma(-wpj.y, vpi.x, ay);
+                    ay = fma(wpj.x, vpi.y, ay);
+                    a = make_double2(ax, ay);
+                    if (col_ok) A[(long long)j * n + i] = a;
+                }
+                const double2 v = vcur[j - k - 1];
+                accx = fma(a.x, v.x, accx);
+                accx = fma(a.y, v.y, accx);
+                accy = fma(a.x, v.y, accy);
+                accy = fma(-a.y, v.x, accy);
+            }
+            colred[warp][lane] = make_double2(accx, accy);
+            __syncthreads();
+            if (warp == 0) {
+                double sx = 0.0, sy = 0.0;
+#pragma unroll
+                for (int w = 0; w < TRI_NW; ++w) {
+                    sx += colred[w][lane].x;
+                    sy += colred[w][lane].y;
+                }
+                if (col_ok) pk[(long long)cs * n + il] = make_double2(sx, sy);
+            }
+            __syncthreads();  // colred is reused by the next unit
         }
-        if (!grid_sync(bar, nb)) return;
-        // ---- C: K = (tau/2) Re(v^dag p), w = p - K v; the pair becomes the pending update
+        if (!grid_sync(bar, (unsigned)nb)) return;
+        // ---- C: p = tau sum of the partials, K = (tau/2) Re(v^dag p), w = p - K v; the pair
+        //      (v, w) becomes the pending update
         double dot = 0.0;
         for (int t = threadIdx.x; t < m; t += blockDim.x) {
-            const double2 p = __ldcg(&pk[t]), v = vcur[t];
+            double px = 0.0, py = 0.0;
+            for (int q = 0; q < CS; ++q) {
+                const double2 pp = __ldcg(&pk[(long long)q * n + t]);
+                px += pp.x;
+                py += pp.y;
+            }
+            const double2 p = make_double2(tau * px, tau * py), v = vcur[t];
+            wprev[t] = p;
             dot += v.x * p.x + v.y * p.y;
         }
         dot = block_sum(dot, red);
         const double K = 0.5 * tau * dot;
         for (int t = threadIdx.x; t < m; t += blockDim.x) {
-            const double2 p = __ldcg(&pk[t]), v = vcur[t];
-            wprev[t] = make_double2(p.x - K * v.x, p.y - K * v.y);
+            const double2 p = wprev[t], v = vcur[t];
+            wprev[t] = make_double2(fma(-K, v.x, p.x), fma(-K, v.y, p.y));
             vprev[t] = v;
         }
         __syncthreads();
         have_prev = true;
     }
-    // ---- tail (last 2 x 2 block with the pending update applied) and real off-diagonal
+    // ---- tail: last 2 x 2 block with the pending update applied
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         if (n >= 2) {
             double2 a00 = __ldcg(&A[(long long)(n - 2) * n + (n - 2)]);
@@ -399,43 +505,38 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_persistent(double2* __res
         } else {
             s.diag[0] = __ldcg(&A[0]).x;
         }
-        s.ph[0] = make_double2(1.0, 0.0);
-        for (int i = 0; i + 1 < n; ++i) {
-            const double2 e = s.e[i];
-            const double r = hypot(e.x, e.y);
-            s.offd[i] = r;
-            const double2 q = s.ph[i];
-            if (r > 0.0) {
-                const double ux = e.x / r, uy = e.y / r;
-                s.ph[i + 1] = make_double2(q.x * ux - q.y * uy, q.x * uy + q.y * ux);
-            } else {
-                s.ph[i + 1] = q;
-            }
-        }
-        s.offd[n - 1] = 0.0;
     }
 }
 
 // ---------------------------------------------------------------- eigenvalues
-__device__ void tri_bounds(const double* a, const double* b, int n, double& gl, double& gu, double& tn) {
-    gl = 1e308; gu = -1e308; tn = 0.0;
-    for (int i = 0; i < n; ++i) {
-        const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < n ? fabs(b[i]) : 0.0);
-        gl = fmin(gl, a[i] - r);
-        gu = fmax(gu, a[i] + r);
-        tn = fmax(tn, fabs(a[i]) + r);
-    }
-}
-
-__device__ int sturm(const double* a, const double* b, int n, double x, double pivmin) {
-    int cnt = 0;
-    double q = a[0] - x;
-    if (fabs(q) < pivmin) q = -pivmin;
-    if (q < 0) ++cnt;
+// Number of eigenvalues of the symmetric tridiagonal (a, b) below x: the number of negative
+// pivots of T - x I, i.e. sign changes between consecutive leading principal minors
+// p_{i+1} = (a_i - x) p_i - b_{i-1}^2 p_{i-1}.  The minors are formed without division and
+// with b^2 precomputed (three FP64 instructions per step; GB300 issues one FP64 warp
+// instruction per 64 cycles per sub-partition); signs, zero tests and the range check read
+// the bit pattern on the integer pipe.  Minors are rescaled by exact powers of two to stay
+// in range; an exactly zero minor is replaced by -pivmin times its predecessor.
+__device__ int sturm(const double* a, const double* bsq, int n, double x, double pivmin) {
+    double prev = 1.0, cur = a[0] - x;
+    if ((__double_as_longlong(cur) << 1) == 0) cur = -pivmin;
+    int cnt = __double_as_longlong(cur) < 0 ? 1 : 0;
     for (int i = 1; i < n; ++i) {
-        q = a[i] - x - b[i - 1] * b[i - 1] / q;
-        if (fabs(q) < pivmin) q = -pivmin;
-        if (q < 0) ++cnt;
+        double nxt = fma(a[i] - x, cur, -bsq[i - 1] * prev);
+        long long bn = __double_as_longlong(nxt);
+        if ((bn << 1) == 0) {
+            nxt = -pivmin * cur;
+            bn = __double_as_longlong(nxt);
+        }
+        cnt += (int)((unsigned long long)(bn ^ __double_as_longlong(cur)) >> 63);
+        prev = cur;
+        cur = nxt;
+        const int ex = (int)((bn >> 52) & 0x7ff);  // biased exponent
+        if (ex > 1023 + 480 || ex < 1023 - 480) {
+            int e2;
+            frexp(cur, &e2);
+            cur = ldexp(cur, -e2);
+            prev = ldexp(prev, -e2);
+        }
     }
     return cnt;
 }
@@ -446,15 +547,14 @@ __global__ void __launch_bounds__(32) bisect_top(int n, int k, EigSmall s) {
     if (j >= k) return;
     const int idx = n - 1 - j;
     const int lane = threadIdx.x;
-    double gl, gu, tn;
-    tri_bounds(s.diag, s.offd, n, gl, gu, tn);
+    const double gl = s.scal[4], gu = s.scal[5], tn = s.scal[6];
     const double pivmin = fmax(1e-300, EPS * EPS * fmax(tn, 1e-300));
     double lo = gl - EPS * tn - pivmin, hi = gu + EPS * tn + pivmin;
     for (int round = 0; round < 64; ++round) {
         if (hi - lo <= 2.0 * EPS * fmax(fabs(lo), fabs(hi)) + 4.0 * pivmin) break;
         const double step = (hi - lo) / 33.0;
         const double x = lo + step * (lane + 1);
-        const int c = sturm(s.diag, s.offd, n, x, pivmin);
+        const int c = sturm(s.diag, s.bsq, n, x, pivmin);
         const unsigned bal = __ballot_sync(0xffffffffu, c >= idx + 1);
         if (bal == 0) {
             lo = lo + step * 32;
@@ -474,78 +574,92 @@ __device__ __forceinline__ double hash_uniform(unsigned i, unsigned j) {
 }
 
 // Inverse iteration: thread j computes the eigenvector of lam[j] into Z[:, j] (row-major n x k).
-// work holds 4 n k doubles (dd, du, du2, dl) and n k ints (pivots), all laid out [i*k + j].
+// T - lam I = P L U by Gaussian elimination with partial pivoting (row swaps of the
+// tridiagonal); U keeps reciprocal pivots so the solves multiply.  The running row is
+// carried in registers, so each step is one division plus a few FMAs on the dependency
+// chain.  Three solves from a fixed pseudo-random start; the iterate is rescaled by its
+// max-norm between solves (folded into the next forward pass) and normalised at the end.
+// work holds 4 n k doubles (rdd, du, du2, dl) and n k ints (pivots), laid out [i*k + j].
 __global__ void __launch_bounds__(128) inverse_iteration(int n, int k, EigSmall s, double* __restrict__ work,
                                                          int* __restrict__ piv, double* __restrict__ Z) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= k) return;
-    const double* a = s.diag;
-    const double* b = s.offd;
-    double gl, gu, tn;
-    tri_bounds(a, b, n, gl, gu, tn);
-    const double tiny = EPS * fmax(tn, 1e-300);
+    const double* __restrict__ a = s.diag;
+    const double* __restrict__ b = s.offd;
+    const double tiny = EPS * fmax(s.scal[6], 1e-300);
     const double lam = s.lam[j];
     const long long K = k;
-    double* dd = work;
-    double* du = work + (long long)n * K;
-    double* du2 = work + 2LL * n * K;
-    double* dl = work + 3LL * n * K;
+    double* __restrict__ rdd = work;
+    double* __restrict__ du = work + (long long)n * K;
+    double* __restrict__ du2 = work + 2LL * n * K;
+    double* __restrict__ dl = work + 3LL * n * K;
 #define AT(arr, i) arr[(long long)(i) * K + j]
-    for (int i = 0; i < n; ++i) {
-        AT(dd, i) = a[i] - lam;
-        AT(du, i) = (i + 1 < n) ? b[i] : 0.0;
-        AT(dl, i) = (i + 1 < n) ? b[i] : 0.0;
-        AT(du2, i) = 0.0;
-    }
+    // ---- factorisation; (d, u) = diagonal and super-diagonal of the running row i
+    double d = a[0] - lam, u = n > 1 ? b[0] : 0.0;
     for (int i = 0; i + 1 < n; ++i) {
-        double di = AT(dd, i), li = AT(dl, i);
-        if (fabs(di) >= fabs(li)) {
+        const double l = b[i];
+        const double dn = a[i + 1] - lam, un = (i + 2 < n) ? b[i + 1] : 0.0;
+        if (fabs(d) >= fabs(l)) {
+            const double dz = (d == 0.0) ? tiny : d;
+            const double r = 1.0 / dz;
+            const double f = l * r;
             AT(piv, i) = 0;
-            if (di == 0.0) { di = tiny; AT(dd, i) = di; }
-            const double f = li / di;
+            AT(rdd, i) = fabs(dz) < tiny ? 1.0 / copysign(tiny, dz) : r;
+            AT(du, i) = u;
+            AT(du2, i) = 0.0;
             AT(dl, i) = f;
-            AT(dd, i + 1) -= f * AT(du, i);
+            d = fma(-f, u, dn);
+            u = un;
         } else {
+            const double r = 1.0 / l;
+            const double f = d * r;
             AT(piv, i) = 1;
-            const double f = di / li;
-            AT(dd, i) = li;
+            AT(rdd, i) = fabs(l) < tiny ? 1.0 / copysign(tiny, l) : r;
+            AT(du, i) = dn;
+            AT(du2, i) = un;
             AT(dl, i) = f;
-            const double t = AT(du, i);
-            AT(du, i) = AT(dd, i + 1);
-            AT(dd, i + 1) = t - f * AT(dd, i + 1);
-            if (i + 2 < n) {
-                AT(du2, i) = AT(du, i + 1);
-                AT(du, i + 1) = -f * AT(du, i + 1);
-            }
+            d = fma(-f, dn, u);
+            u = -f * un;
         }
     }
-    for (int i = 0; i < n; ++i) {
-        const double di = AT(dd, i);
-        if (fabs(di) < tiny) AT(dd, i) = (di < 0.0) ? -tiny : tiny;
-    }
+    AT(rdd, n - 1) = 1.0 / (fabs(d) < tiny ? copysign(tiny, d) : d);
     for (int i = 0; i < n; ++i) AT(Z, i) = hash_uniform((unsigned)i, (unsigned)j);
+    double scale = 1.0;
     for (int it = 0; it < 3; ++it) {
+        // forward: c = running entry i of L^{-1} P^T z (scaled on the fly)
+        double c = AT(Z, 0) * scale;
+#pragma unroll 4
         for (int i = 0; i + 1 < n; ++i) {
+            const double nxt = AT(Z, i + 1) * scale;
+            const double f = AT(dl, i);
             if (AT(piv, i) == 0) {
-                AT(Z, i + 1) -= AT(dl, i) * AT(Z, i);
+                AT(Z, i) = c;
+                c = fma(-f, c, nxt);
             } else {
-                const double t = AT(Z, i);
-                AT(Z, i) = AT(Z, i + 1);
-                AT(Z, i + 1) = t - AT(dl, i) * AT(Z, i + 1);
+                AT(Z, i) = nxt;
+                c = fma(-f, nxt, c);
             }
         }
-        AT(Z, n - 1) /= AT(dd, n - 1);
-        if (n >= 2) AT(Z, n - 2) = (AT(Z, n - 2) - AT(du, n - 2) * AT(Z, n - 1)) / AT(dd, n - 2);
-        for (int i = n - 3; i >= 0; --i)
-            AT(Z, i) = (AT(Z, i) - AT(du, i) * AT(Z, i + 1) - AT(du2, i) * AT(Z, i + 2)) / AT(dd, i);
-        double mx = 0.0;
-        for (int i = 0; i < n; ++i) mx = fmax(mx, fabs(AT(Z, i)));
-        const double inv = 1.0 / mx;
-        for (int i = 0; i < n; ++i) AT(Z, i) *= inv;
+        // backward: z_i = (z_i - du_i z_{i+1} - du2_i z_{i+2}) / d_i, tracking max |z_i|
+        double z1 = c * AT(rdd, n - 1), z2 = 0.0;
+        AT(Z, n - 1) = z1;
+        double mx = fabs(z1);
+#pragma unroll 4
+        for (int i = n - 2; i >= 0; --i) {
+            const double zi = fma(-AT(du2, i), z2, fma(-AT(du, i), z1, AT(Z, i))) * AT(rdd, i);
+            AT(Z, i) = zi;
+            mx = fmax(mx, fabs(zi));
+            z2 = z1;
+            z1 = zi;
+        }
+        scale = 1.0 / mx;
     }
     double nrm = 0.0;
-    for (int i = 0; i < n; ++i) nrm += AT(Z, i) * AT(Z, i);
-    const double inv = 1.0 / sqrt(nrm);
+    for (int i = 0; i < n; ++i) {
+        const double z = AT(Z, i) * scale;
+        nrm = fma(z, z, nrm);
+    }
+    const double inv = scale / sqrt(nrm);
     for (int i = 0; i < n; ++i) AT(Z, i) *= inv;
 #undef AT
 }
@@ -613,27 +727,29 @@ __global__ void __launch_bounds__(128) trsm_rows(double* __restrict__ Z, int n, 
     }
 }
 
-__global__ void sumsq_kernel(const double* __restrict__ Z, long long cnt, double* __restrict__ out) {
-    __shared__ double sh[33];
-    double acc = 0.0;
-    for (long long t = threadIdx.x; t < cnt; t += blockDim.x) acc += Z[t] * Z[t];
-    acc = block_sum(acc, sh);
-    if (threadIdx.x == 0) *out = acc;
-}
-
 // ---------------------------------------------------------------- back-transformation
-// Block j: y = ph .* Z[:, j]; y <- H_0 ... H_{n-3} y; write column (mode 0: U[i][j] = y_i)
-// or conjugated row (mode 1: B[j][i] = conj(y_i)).
-__global__ void __launch_bounds__(256) backtransform(int n, int k, const double2* __restrict__ H, EigSmall s,
-                                                     const double* __restrict__ Z, int mode,
-                                                     double2* __restrict__ out) {
-    extern __shared__ double2 y[];
-    __shared__ double sh[33];
-    const int j = blockIdx.x;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const double z = Z[(long long)i * k + j];
+// CTA c handles vectors j = c*cpb .. c*cpb+cpb-1: y = ph .* Z[:, j]; y <- H_0 ... H_{n-3} y;
+// written as columns (mode 0: U[i][j] = y_i) or conjugated rows (mode 1: B[j][i] = conj(y_i)).
+// Several vectors per CTA share each reflector's reduction (two barriers per reflector).
+constexpr int BT_MAX = 8;
+constexpr int BT_THREADS = 256;
+
+template <int CPB>
+__global__ void __launch_bounds__(BT_THREADS) backtransform(int n, int k, const double2* __restrict__ H,
+                                                            EigSmall s, const double* __restrict__ Z, int mode,
+                                                            double2* __restrict__ out) {
+    constexpr int cpb = CPB;
+    extern __shared__ double2 y[];  // [cpb][n]
+    __shared__ double red[(BT_THREADS / 32) * 2 * BT_MAX];
+    __shared__ double2 coef[BT_MAX];
+    const int j0 = blockIdx.x * cpb;
+    const int nv = min(cpb, k - j0);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int t = threadIdx.x; t < nv * n; t += blockDim.x) {
+        const int c = t / n, i = t - c * n;
+        const double z = Z[(long long)i * k + j0 + c];
         const double2 q = s.ph[i];
-        y[i] = make_double2(q.x * z, q.y * z);
+        y[(long long)c * n + i] = make_double2(q.x * z, q.y * z);
     }
     __syncthreads();
     for (int kk = n - 3; kk >= 0; --kk) {
@@ -641,29 +757,61 @@ __global__ void __launch_bounds__(256) backtransform(int n, int k, const double2
         if (tau == 0.0) continue;
         const int m = n - kk - 1;
         const double2* v = H + (long long)kk * n;
-        double re = 0.0, im = 0.0;
-        for (int i = threadIdx.x; i < m; i += blockDim.x) {
-            const double2 a = v[i], b = y[kk + 1 + i];
-            re += a.x * b.x + a.y * b.y;   // conj(a) * b
-            im += a.x * b.y - a.y * b.x;
-        }
-        re = block_sum(re, sh);
-        im = block_sum(im, sh);
-        re *= tau;
-        im *= tau;
+        double re[CPB], im[CPB];
+#pragma unroll
+        for (int c = 0; c < CPB; ++c) re[c] = im[c] = 0.0;
         for (int i = threadIdx.x; i < m; i += blockDim.x) {
             const double2 a = v[i];
-            double2 b = y[kk + 1 + i];
-            b.x -= a.x * re - a.y * im;
-            b.y -= a.x * im + a.y * re;
-            y[kk + 1 + i] = b;
+#pragma unroll
+            for (int c = 0; c < CPB; ++c) {
+                if (c < nv) {
+                    const double2 b = y[(long long)c * n + kk + 1 + i];
+                    re[c] += a.x * b.x + a.y * b.y;  // conj(a) * b
+                    im[c] += a.x * b.y - a.y * b.x;
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < CPB; ++c) {
+            re[c] = warp_sum(re[c]);
+            im[c] = warp_sum(im[c]);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int c = 0; c < CPB; ++c) {
+                red[wid * 2 * BT_MAX + 2 * c] = re[c];
+                red[wid * 2 * BT_MAX + 2 * c + 1] = im[c];
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < nv) {
+            double sr = 0.0, si = 0.0;
+            for (int w = 0; w < nw; ++w) {
+                sr += red[w * 2 * BT_MAX + 2 * threadIdx.x];
+                si += red[w * 2 * BT_MAX + 2 * threadIdx.x + 1];
+            }
+            coef[threadIdx.x] = make_double2(tau * sr, tau * si);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            const double2 a = v[i];
+#pragma unroll
+            for (int c = 0; c < CPB; ++c) {
+                if (c >= nv) break;
+                const double2 cf = coef[c];
+                double2 b = y[(long long)c * n + kk + 1 + i];
+                b.x -= a.x * cf.x - a.y * cf.y;
+                b.y -= a.x * cf.y + a.y * cf.x;
+                y[(long long)c * n + kk + 1 + i] = b;
+            }
         }
         __syncthreads();
     }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const double2 v = y[i];
-        if (mode == 0) out[(long long)i * k + j] = v;
-        else out[(long long)j * n + i] = make_double2(v.x, -v.y);
+    for (int t = threadIdx.x; t < nv * n; t += blockDim.x) {
+        const int c = t / n, i = t - c * n;
+        const double2 w = y[(long long)c * n + i];
+        if (mode == 0) out[(long long)i * k + j0 + c] = w;
+        else out[(long long)(j0 + c) * n + i] = make_double2(w.x, -w.y);
     }
 }
 
@@ -690,6 +838,7 @@ TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int dir
     s.p = (double2*)(small + 8 * (size_t)n);
     s.w = (double2*)(small + 10 * (size_t)n);
     s.scal = small + 12 * (size_t)n;
+    s.bsq = small + 12 * (size_t)n + 16;
     double* Z = (double*)ctx.workspace(WS_EIG_Y, sizeof(double) * (size_t)n * k);
     double* work = (double*)ctx.workspace(WS_EIG_WORK, sizeof(double) * (5 * (size_t)n * k + (size_t)k * k + 32));
     int* piv = (int*)(work + 4 * (size_t)n * k);
@@ -707,7 +856,9 @@ TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int dir
         g.B = theta; g.ldb = nR;
     }
     g.C = A; g.ldc = n;
+    g.herm_lower = true;
     gemm_c64(ctx, g);
+    mirror_lower_to_upper(ctx, A, n, n);
     norm2_dev(ctx, theta, (long long)nL * nR, &s.scal[0]);
     VTN_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int) * 8, ctx.stream));
     // 2. tridiagonalisation: one persistent cooperative launch when it fits, else one
@@ -723,9 +874,10 @@ TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int dir
         }
         int per_sm = 0;
         VTN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tridiag_persistent, TRI_THREADS, shm));
-        int grid = std::min(ctx.num_sms * std::max(per_sm, 0), std::max(1, (n + 3) / 4));
+        // one CTA per SM: Phases A and C are redundant per CTA, so more CTAs per SM cost more
+        int grid = std::min(ctx.num_sms, std::max(1, (n + 3) / 4));
         if (per_sm >= 1 && grid >= 1) {
-            double2* pbuf = (double2*)(small + 12 * (size_t)n + 16);
+            double2* pbuf = (double2*)ctx.workspace(WS_EIG_PART, sizeof(double2) * 2 * (size_t)grid * n);
             GridBar* bar = (GridBar*)(status + 4);
             VTN_CUDA_TRY(cudaMemsetAsync(bar, 0, sizeof(GridBar), ctx.stream));
             double2* Ap = A;
@@ -752,6 +904,8 @@ TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int dir
         tri_finalize<<<1, 32, 0, ctx.stream>>>(A, n, s);
         ctx.count_launch();
     }
+    tri_phases<<<1, TP_THREADS, 0, ctx.stream>>>(n, s);
+    ctx.count_launch();
     ctx.check_launch("tridiagonalisation");
     // 3. eigenvalues
     bisect_top<<<k, 32, 0, ctx.stream>>>(n, k, s);
@@ -774,14 +928,18 @@ TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int dir
     }
     ctx.check_launch("orthonormalisation");
     // 6. back-transformation into the site tensors
-    const size_t shm = sizeof(double2) * (size_t)n;
+    // one vector per CTA: the FP64 work of the reflector applications spreads over all SMs
+    // (GB300's FP64 pipe, not the per-reflector reduction, bounds this step)
+    const int cpb = 1;
+    const size_t shm = sizeof(double2) * (size_t)n * cpb;
+    const int nbt = (k + cpb - 1) / cpb;
     static bool attr_set = false;
     if (!attr_set) {
-        VTN_CUDA_TRY(cudaFuncSetAttribute(backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        VTN_CUDA_TRY(cudaFuncSetAttribute(backtransform<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         attr_set = true;
     }
     if (direction == 0) {
-        backtransform<<<k, 256, shm, ctx.stream>>>(n, k, H, s, Z, 0, left);
+        backtransform<1><<<nbt, BT_THREADS, shm, ctx.stream>>>(n, k, H, s, Z, 0, left);
         // right = U^dag T
         GemmArgs c;
         c.M = k; c.N = nR; c.K = nL;
@@ -791,7 +949,7 @@ TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int dir
         ctx.count_launch();
         gemm_c64(ctx, c);
     } else {
-        backtransform<<<k, 256, shm, ctx.stream>>>(n, k, H, s, Z, 1, right);
+        backtransform<1><<<nbt, BT_THREADS, shm, ctx.stream>>>(n, k, H, s, Z, 1, right);
         // left = T V = T (V^dag)^dag
         GemmArgs c;
         c.M = nL; c.N = k; c.K = nR;

@@ -103,7 +103,7 @@ struct Ctx {
 enum WsSlot {
     WS_X = 0, WS_Y, WS_Z, WS_KRYLOV, WS_VEC_W, WS_VEC_T, WS_PARTIAL, WS_SCAL, WS_EIG_A, WS_EIG_H,
     WS_EIG_Y, WS_EIG_WORK, WS_EIG_U, WS_CORE_A, WS_CORE_B, WS_ENV_TMP, WS_MISC, WS_TC_L, WS_TC_R, WS_TC_B1,
-    WS_TC_A2, WS_TC_PART, WS_COUNT
+    WS_TC_A2, WS_TC_PART, WS_GEMM_SPLIT, WS_EIG_PART, WS_COUNT
 };
 
 // ------------------------------------------------------------------ cores
@@ -123,7 +123,10 @@ struct GemmArgs {
     const double2* B; long long ldb; long long sB_batch = 0, sB_kb = 0;
     double2* C; long long ldc; long long sC_batch = 0;
     bool accumulate = false;  // C += result (else C = result)
+    bool herm_lower = false;  // result is Hermitian: compute tiles on/below the diagonal only
 };
+// C[i][j] = conj(C[j][i]) for j > i (n x n, leading dimension ldc)
+void mirror_lower_to_upper(Ctx& ctx, double2* C, int n, long long ldc);
 void gemm_c64(Ctx& ctx, const GemmArgs& g, int timing_class = TC_GEMM);
 
 // ------------------------------------------------------------------ tensor-core GEMM (bf16 -> fp32)
