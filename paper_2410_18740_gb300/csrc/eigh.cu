@@ -249,25 +249,30 @@ __global__ void __launch_bounds__(TP_THREADS) tri_phases(int n, EigSmall s) {
 }
 
 // ---------------------------------------------------------------- persistent tridiagonalisation
-// One cooperative launch for the whole reduction (Householder, one column per step).
-// Column k's reflector is built by every CTA redundantly from row k (Hermitian); the
-// rank-2 update of step k-1 is applied lazily while the matrix-vector product p = tau A v
-// of step k streams the trailing block, so each step costs one pass over the trailing
-// block and one grid barrier.
+// One cooperative launch for the whole Householder reduction, one column per step and one
+// grid barrier per step.
 //
 // GB300 issues one FP64 warp instruction per 64 cycles per SM sub-partition whatever the
-// number of active lanes, so the pass is organised to keep every FP64 instruction 32 lanes
-// wide and to avoid per-row reductions: a warp owns 32 consecutive COLUMNS i (coalesced
-// loads of A[j][i]) and walks a slice of the rows j, accumulating
-// (A v)_i = sum_j conj(A[j][i]) v_j (A is Hermitian) in its lanes.  The CTAs that share a
-// column chunk write one partial each; every CTA sums them after the barrier.  Data written
-// by other CTAs is read with ld.global.cg (L2, not L1).
+// number of active lanes, and a dependent FP64 instruction waits about as long, so the
+// kernel keeps every FP64 instruction 32 lanes wide and the per-step dependency chain short:
+//  B(k)   the rank-2 update of step k-1 is applied lazily while p = tau A v streams the
+//         trailing block.  A warp owns 32 consecutive COLUMNS i (coalesced loads of A[j][i])
+//         and walks a slice of the rows j, accumulating (A v)_i = sum_j conj(A[j][i]) v_j in
+//         its lanes (A is Hermitian), so no per-row reductions are needed.  The CTAs that
+//         share a column chunk each write a partial; the last of them to finish (an atomic
+//         arrival count) sums the partials in a fixed order into p.
+//  barrier
+//  C(k)+A(k+1), redundantly in every CTA: K = (tau/2) Re(v^dag p), w = p - K v becomes the
+//         pending pair, and in the same pass row k+1 of the current matrix is formed with
+//         the pending update applied; its norm gives the next reflector.
+// Data written by other CTAs is read with ld.global.cg (L2, not L1).
 struct GridBar {
     unsigned int count;
-    unsigned int gen;
-    int error;
+    unsigned int gen;   // bit 31: error
+    int error;          // read by the host
     int pad;
 };
+constexpr unsigned GEN_ERROR = 0x80000000u;
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -275,36 +280,40 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Grid barrier with a bounded wait: a CTA that waits more than 2 s sets bar->error and
-// every CTA returns false (the kernel then exits; the host reads the flag).
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier with a bounded wait: a CTA that waits more than 2 s sets the error bit of the
+// generation word (which releases every waiter) and bar->error; every CTA then returns false
+// and the kernel exits.
 __device__ bool grid_sync(GridBar* bar, unsigned int nblocks) {
     __shared__ int ok_sh;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned int* vgen = &bar->gen;
-        volatile int* verr = &bar->error;
-        const unsigned int g = *vgen;
+        const unsigned g = ld_acquire_u32(&bar->gen);
         __threadfence();
-        const unsigned int arrived = atomicAdd(&bar->count, 1u);
-        int ok = 1;
+        const unsigned arrived = atomicAdd(&bar->count, 1u);
+        unsigned now = g;
         if (arrived == nblocks - 1) {
             atomicExch(&bar->count, 0u);
             __threadfence();
-            atomicAdd(&bar->gen, 1u);
+            now = atomicAdd(&bar->gen, 1u) + 1u;
         } else {
             const unsigned long long t0 = global_ns();
-            while (*vgen == g) {
-                if (*verr) { ok = 0; break; }
-                if (global_ns() - t0 > 2000000000ull) {
+            unsigned polls = 0;
+            while ((now = ld_acquire_u32(&bar->gen)) == g) {
+                if ((++polls & 1023u) == 0 && global_ns() - t0 > 2000000000ull) {
                     atomicExch(&bar->error, 1);
-                    ok = 0;
+                    now = atomicOr(&bar->gen, GEN_ERROR) | GEN_ERROR;
                     break;
                 }
-                __nanosleep(64);
             }
         }
         __threadfence();
-        ok_sh = ok && (*verr == 0);
+        ok_sh = ((now | g) & GEN_ERROR) == 0;
     }
     __syncthreads();
     return ok_sh != 0;
@@ -317,37 +326,58 @@ __device__ __forceinline__ double2 cmulc(double2 a, double2 b) {  // a * conj(b)
 constexpr int TRI_THREADS = 512;
 constexpr int TRI_NW = TRI_THREADS / 32;
 constexpr int TRI_MAX_N = 4096;
+constexpr int TRI_MAX_CHUNKS = TRI_MAX_N / 32;
 constexpr int TRI_UNROLL = 4;  // rows in flight per warp
 
-// part: 2 x gridDim.x x n partial products (double-buffered by step parity)
+struct TriBufs {
+    double2* part;      // [2][nb][n] partial products (double-buffered by step parity)
+    double2* p;         // [2][n] p = tau A v
+    unsigned* arrive;   // [2][TRI_MAX_CHUNKS] arrivals per column chunk (zero at launch)
+};
+
+// x -= a conj(b) + c conj(d) for complex a..d, as 8 FMAs
+__device__ __forceinline__ double2 sub_two_cmulc(double2 x, double2 a, double2 b, double2 c, double2 d) {
+    x.x = fma(-a.x, b.x, x.x);
+    x.x = fma(-a.y, b.y, x.x);
+    x.x = fma(-c.x, d.x, x.x);
+    x.x = fma(-c.y, d.y, x.x);
+    x.y = fma(-a.y, b.x, x.y);
+    x.y = fma(a.x, b.y, x.y);
+    x.y = fma(-c.y, d.x, x.y);
+    x.y = fma(c.x, d.y, x.y);
+    return x;
+}
+
 __global__ void __launch_bounds__(TRI_THREADS) tridiag_persistent(double2* __restrict__ A, int n,
                                                                   double2* __restrict__ H, EigSmall s,
-                                                                  double2* __restrict__ part, GridBar* bar) {
+                                                                  TriBufs tb, GridBar* bar) {
     extern __shared__ double2 sm[];
-    double2* vprev = sm;           // pending reflector (local to the previous trailing block)
-    double2* wprev = sm + n;       // pending w
-    double2* vcur = sm + 2 * n;    // this column's reflector
+    // three rotating vectors: pending pair (vprev, wprev) of the previous step and the
+    // reflector vcur of this step; all local to the trailing block (index t <-> row k+1+t
+    // for vcur, row k+t for the pending pair)
+    double2* vprev = sm;
+    double2* wprev = sm + n;
+    double2* vcur = sm + 2 * n;
     __shared__ double red[33];
-    __shared__ double tau_sh;
+    __shared__ double tau_sh, dk_sh;
+    __shared__ double2 p0_sh;
+    __shared__ int last_sh;
     __shared__ double2 colred[TRI_NW][32];
     const int nb = (int)gridDim.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     bool have_prev = false;
+    // row 0 (no pending update): x = conj(A[0][1..n-1])
+    double a2 = 0.0;
+    for (int t = threadIdx.x; t < n - 1; t += blockDim.x) {
+        const double2 a = __ldcg(&A[1 + t]);
+        const double2 x = make_double2(a.x, -a.y);
+        vcur[t] = x;
+        a2 = fma(x.x, x.x, fma(x.y, x.y, a2));
+    }
+    if (threadIdx.x == 0) dk_sh = __ldcg(&A[0]).x;
     for (int k = 0; k + 2 < n; ++k) {
         const int m = n - k - 1;
-        // ---- A: row k of the current matrix, reflector for column k
-        double a2 = 0.0;
-        for (int t = threadIdx.x; t < m; t += blockDim.x) {
-            double2 a = __ldcg(&A[(long long)k * n + (k + 1 + t)]);
-            if (have_prev) {
-                const double2 u = cmulc(vprev[0], wprev[t + 1]), v = cmulc(wprev[0], vprev[t + 1]);
-                a.x -= u.x + v.x;
-                a.y -= u.y + v.y;
-            }
-            const double2 x = make_double2(a.x, -a.y);
-            vcur[t] = x;
-            a2 += x.x * x.x + x.y * x.y;
-        }
+        // ---- reflector for column k from x = vcur (norm^2 a2)
         a2 = block_sum(a2, red);
         if (threadIdx.x == 0) {
             const double2 x0 = vcur[0];
@@ -357,15 +387,13 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_persistent(double2* __res
             if (a2 > 0.0) {
                 const double alpha = sqrt(a2);
                 const double2 phi = ax0 > 0.0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
-                vcur[0] = make_double2(x0.x + phi.x * alpha, x0.y + phi.y * alpha);
+                vcur[0] = make_double2(fma(phi.x, alpha, x0.x), fma(phi.y, alpha, x0.y));
                 tau = 1.0 / (alpha * (alpha + ax0));
                 beta = make_double2(-phi.x * alpha, -phi.y * alpha);
             }
             tau_sh = tau;
             if (blockIdx.x == 0) {
-                double dk = __ldcg(&A[(long long)k * n + k]).x;
-                if (have_prev) dk -= 2.0 * (vprev[0].x * wprev[0].x + vprev[0].y * wprev[0].y);
-                s.diag[k] = dk;
+                s.diag[k] = dk_sh;
                 s.tau[k] = tau;
                 s.e[k] = beta;
             }
@@ -377,13 +405,15 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_persistent(double2* __res
         __syncthreads();
         if (blockIdx.x == 0)
             for (int t = threadIdx.x; t < m; t += blockDim.x) H[(long long)k * n + t] = vcur[t];
-        // ---- B: pending rank-2 update of the trailing block fused with (A v).  Work unit
-        //      u = (column chunk c = u mod C of 32 columns, row slice cs = u / C of CS); CTA b
-        //      takes units b, b + nb, ...; its warp w walks the rows k+1 + cs*NW + w + t*CS*NW.
+        // ---- B: work unit u = (column chunk c = u mod C of 32 columns, row slice cs = u / C
+        //      of CS); CTA b takes units b, b + nb, ...; warp w walks rows k+1 + cs*NW + w +
+        //      t*CS*NW.
         const int C = (m + 31) / 32;
         const int CS = max(1, min(nb / C, (m + TRI_NW - 1) / TRI_NW));
-        double2* pk = part + (long long)(k & 1) * nb * n;
-        for (int unit = (int)blockIdx.x; unit < C * CS; unit += nb) {  // one pass unless C > nb
+        double2* pk = tb.part + (long long)(k & 1) * nb * n;
+        double2* pfin = tb.p + (long long)(k & 1) * n;
+        unsigned* arrive = tb.arrive + (k & 1) * TRI_MAX_CHUNKS;
+        for (int unit = (int)blockIdx.x; unit < C * CS; unit += nb) {
             const int c = unit % C, cs = unit / C;
             const int il = c * 32 + lane;  // local column index (0..m-1)
             const bool col_ok = il < m;
@@ -406,17 +436,7 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_persistent(double2* __res
                 for (int u = 0; u < TRI_UNROLL; ++u) {
                     const int jj = j + u * stride;
                     if (have_prev) {
-                        const double2 vpj = vprev[jj - k], wpj = wprev[jj - k];
-                        double ax = a[u].x, ay = a[u].y;
-                        ax = fma(-vpj.x, wpi.x, ax);
-                        ax = fma(-vpj.y, wpi.y, ax);
-                        ax = fma(-wpj.x, vpi.x, ax);
-                        ax = fma(-wpj.y, vpi.y, ax);
-                        ay = fma(-vpj.y, wpi.x, ay);
-                        ay = fma(vpj.x, wpi.y, ay);
-                        ay = fma(-wpj.y, vpi.x, ay);
-                        ay = fma(wpj.x, vpi.y, ay);
-                        a[u] = make_double2(ax, ay);
+                        a[u] = sub_two_cmulc(a[u], vprev[jj - k], wpi, wprev[jj - k], vpi);
                         if (col_ok) A[(long long)jj * n + i] = a[u];
                     }
                     const double2 v = vcur[jj - k - 1];
@@ -429,17 +449,7 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_persistent(double2* __res
             for (; j < n; j += stride) {
                 double2 a = col_ok ? __ldcg(&A[(long long)j * n + i]) : make_double2(0.0, 0.0);
                 if (have_prev) {
-                    const double2 vpj = vprev[j - k], wpj = wprev[j - k];
-                    double ax = a.x, ay = a.y;
-                    ax = fma(-vpj.x, wpi.x, ax);
-                    ax = fma(-vpj.y, wpi.y, ax);
-                    ax = fma(-wpj.x, vpi.x, ax);
-                    ax = fma(-wpj.y, vpi.y, ax);
-                    ay = fma(-vpj.y, wpi.x, ay);
-                    ay = fma(vpj.x, wpi.y, ay);
-                    ay = fma(-wpj.y, vpi.x, ay);
-                    ay = fma(wpj.x, vpi.y, ay);
-                    a = make_double2(ax, ay);
+                    a = sub_two_cmulc(a, vprev[j - k], wpi, wprev[j - k], vpi);
                     if (col_ok) A[(long long)j * n + i] = a;
                 }
                 const double2 v = vcur[j - k - 1];
@@ -458,33 +468,70 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_persistent(double2* __res
                     sy += colred[w][lane].y;
                 }
                 if (col_ok) pk[(long long)cs * n + il] = make_double2(sx, sy);
+                __threadfence();
             }
-            __syncthreads();  // colred is reused by the next unit
+            __syncthreads();
+            // the last CTA of this chunk sums its CS partials in slice order
+            if (threadIdx.x == 0) {
+                __threadfence();
+                last_sh = atomicAdd(&arrive[c], 1u) == (unsigned)(CS - 1);
+            }
+            __syncthreads();
+            if (last_sh) {
+                if (warp == 0) {
+                    __threadfence();
+                    double sx = 0.0, sy = 0.0;
+                    for (int q = 0; q < CS; ++q) {
+                        if (col_ok) {
+                            const double2 pp = __ldcg(&pk[(long long)q * n + il]);
+                            sx += pp.x;
+                            sy += pp.y;
+                        }
+                    }
+                    if (col_ok) pfin[il] = make_double2(tau * sx, tau * sy);
+                    if (lane == 0) arrive[c] = 0u;  // reused two steps later, after two barriers
+                }
+            }
+            __syncthreads();  // colred and last_sh are reused by the next unit
         }
         if (!grid_sync(bar, (unsigned)nb)) return;
-        // ---- C: p = tau sum of the partials, K = (tau/2) Re(v^dag p), w = p - K v; the pair
-        //      (v, w) becomes the pending update
+        // ---- C(k): K = (tau/2) Re(v^dag p); p parked in wprev (its old content is spent)
         double dot = 0.0;
         for (int t = threadIdx.x; t < m; t += blockDim.x) {
-            double px = 0.0, py = 0.0;
-            for (int q = 0; q < CS; ++q) {
-                const double2 pp = __ldcg(&pk[(long long)q * n + t]);
-                px += pp.x;
-                py += pp.y;
-            }
-            const double2 p = make_double2(tau * px, tau * py), v = vcur[t];
+            const double2 p = __ldcg(&pfin[t]), v = vcur[t];
             wprev[t] = p;
-            dot += v.x * p.x + v.y * p.y;
+            if (t == 0) p0_sh = p;
+            dot = fma(v.x, p.x, fma(v.y, p.y, dot));
         }
         dot = block_sum(dot, red);
         const double K = 0.5 * tau * dot;
+        // rotate: the pending pair becomes (v_k, w_k); the free buffer takes row k+1
+        double2* vnew = vcur;
+        double2* wnew = wprev;
+        double2* xnext = vprev;
+        const double2 v0 = vnew[0];
+        const double2 w0 = make_double2(fma(-K, v0.x, p0_sh.x), fma(-K, v0.y, p0_sh.y));
+        const bool next = k + 3 < n;  // another reflector follows
+        a2 = 0.0;
         for (int t = threadIdx.x; t < m; t += blockDim.x) {
-            const double2 p = wprev[t], v = vcur[t];
-            wprev[t] = make_double2(fma(-K, v.x, p.x), fma(-K, v.y, p.y));
-            vprev[t] = v;
+            const double2 p = wnew[t], v = vnew[t];
+            const double2 w = make_double2(fma(-K, v.x, p.x), fma(-K, v.y, p.y));
+            wnew[t] = w;
+            if (next && t >= 1) {
+                // A(k+1): row k+1 with the pending update, x = conj(row)
+                double2 a = __ldcg(&A[(long long)(k + 1) * n + (k + 1 + t)]);
+                a = sub_two_cmulc(a, v0, w, w0, v);
+                const double2 x = make_double2(a.x, -a.y);
+                xnext[t - 1] = x;
+                a2 = fma(x.x, x.x, fma(x.y, x.y, a2));
+            }
         }
-        __syncthreads();
+        if (threadIdx.x == 0 && next) dk_sh = __ldcg(&A[(long long)(k + 1) * n + (k + 1)]).x - 2.0 * (v0.x * w0.x + v0.y * w0.y);
+        vprev = vnew;
+        wprev = wnew;
+        vcur = xnext;
         have_prev = true;
+        __syncthreads();
     }
     // ---- tail: last 2 x 2 block with the pending update applied
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -877,13 +924,19 @@ TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int dir
         // one CTA per SM: Phases A and C are redundant per CTA, so more CTAs per SM cost more
         int grid = std::min(ctx.num_sms, std::max(1, (n + 3) / 4));
         if (per_sm >= 1 && grid >= 1) {
-            double2* pbuf = (double2*)ctx.workspace(WS_EIG_PART, sizeof(double2) * 2 * (size_t)grid * n);
+            const size_t part_bytes = sizeof(double2) * (2 * (size_t)grid * n + 2 * (size_t)n);
+            char* wsp = (char*)ctx.workspace(WS_EIG_PART, part_bytes + sizeof(unsigned) * 2 * TRI_MAX_CHUNKS);
+            TriBufs tb;
+            tb.part = (double2*)wsp;
+            tb.p = tb.part + 2 * (size_t)grid * n;
+            tb.arrive = (unsigned*)(wsp + part_bytes);
+            VTN_CUDA_TRY(cudaMemsetAsync(tb.arrive, 0, sizeof(unsigned) * 2 * TRI_MAX_CHUNKS, ctx.stream));
             GridBar* bar = (GridBar*)(status + 4);
             VTN_CUDA_TRY(cudaMemsetAsync(bar, 0, sizeof(GridBar), ctx.stream));
             double2* Ap = A;
             double2* Hp = H;
             int nn = n;
-            void* args[] = {&Ap, &nn, &Hp, &s, &pbuf, &bar};
+            void* args[] = {&Ap, &nn, &Hp, &s, &tb, &bar};
             VTN_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)tridiag_persistent, dim3(grid), dim3(TRI_THREADS),
                                                      args, shm, ctx.stream));
             ctx.count_launch();
