@@ -6,8 +6,8 @@ optimisations: H_eff psi Lanczos, FP64 truncation eigendecomposition, environmen
 updates), followed by the FP64 energy, every single-mode Fock marginal and 256 samples
 -- every step of the hot path over one instance.  The state entering the timed region is
 a warm chi=64 state prepared during set-up (resident in HBM).  By default H_eff psi runs in
-the split-precision tensor-core mode (--prec bf16x3: bf16 hi/lo products on tcgen05 with
-FP32 accumulation; everything else FP64); one FP64 sweep from the same state is timed
+the split-precision tensor-core mode (--prec bf16x3: H_eff psi and the environment updates
+as bf16 hi/lo products on tcgen05 with FP32 accumulation; everything else FP64); one FP64 sweep from the same state is timed
 afterwards for the mixed-vs-FP64 comparison.
 
 value     = whole-step H_eff psi throughput: algorithmic flops of every H_eff psi product
@@ -15,7 +15,8 @@ value     = whole-step H_eff psi throughput: algorithmic flops of every H_eff ps
 e2e       = the same metric through the C ABI from host buffers: every step uploads the
             problem (r, U -> MPO) and the MPS from host memory and reads back the MPS,
             energy, marginals and samples.
-roofline  = the complex GEMM launches inside H_eff psi (the dominant kernel), timed with
+roofline  = the GEMM launches of the contractions (tcgen05 bf16 GEMM in H_eff psi and the
+            environment updates; FP64 complex GEMM in H_eff psi with --prec fp64), timed with
             CUDA events on the library's stream during the timed steps.
 time_to_eps = cumulative sweep time until <H> is within 1e-8 (relative) of the final
             energy, when the run's last two sweeps agree to that precision (else null).
@@ -386,7 +387,7 @@ def run_native(args):
         achieved = fl_tc / s_tc / 1e12 if s_tc > 0 else None
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": None,
-                "kernel": "tc_gemm_kernel (tcgen05 bf16 GEMM, TMEM accumulators, TMA tiles) inside H_eff psi",
+                "kernel": "tc_gemm_kernel (tcgen05 bf16 GEMM, TMEM accumulators, TMA tiles) in H_eff psi and the environment updates",
                 "launches": n_tc, "peak_source": f"{peaks_src} bf16 dense, sustained (kernel timed inside a long step)",
                 "useful_complex_tflops": fl_heff / s_heff / 1e12 if s_heff else None,
                 "note": "bf16 flops executed = 3 split products x 4 real per complex multiply-add of the useful work"}
@@ -407,8 +408,8 @@ def run_native(args):
             "config": {"workload": f"{WORKLOAD}: M=24, r~U(0.5,1.0), Haar U, d=D=8, chi=128, two-site DMRG sweep "
                                    f"(Lanczos {KRYLOV} steps/bond) + energy + marginals + {N_SAMPLES} samples per step",
                        "seed": args.seed,
-                       "precision_path": ("H_eff psi: bf16x3 split products on tcgen05, FP32 accumulate; Lanczos, "
-                                          "truncation, environments, energy: FP64") if prec != vtn.VTN_FP64
+                       "precision_path": ("H_eff psi and environment updates: bf16x3 split products on tcgen05, "
+                                          "FP32 accumulate; Lanczos, truncation, energy: FP64") if prec != vtn.VTN_FP64
                        else "FP64 contractions (SIMT DFMA)",
                        "l2": "working set > L2 (environments, Krylov basis, H_eff intermediates ~1 GB)",
                        "parallelism": f"replicas x{ws}"},

@@ -63,11 +63,12 @@ typedef enum {
 typedef enum {
     VTN_FP64 = 0,          /* every contraction in IEEE double (SIMT FP64 FMA)           */
     VTN_TF32X3 = 1,        /* reserved: three-term TF32 split products (VTN_EUNSUPPORTED) */
-    VTN_BF16X3 = 2         /* H_eff psi on the tensor cores: each FP64 operand split into
-                              bf16 hi + lo, products hi*hi + hi*lo + lo*hi accumulated in
-                              FP32 (relative error ~1e-5 per product); the MPO mixing
-                              between the two GEMMs in FP32.  Lanczos, the truncation
-                              eigendecomposition, environments and energies stay FP64. */
+    VTN_BF16X3 = 2         /* H_eff psi and the environment updates on the tensor cores:
+                              each FP64 operand split into bf16 hi + lo, products
+                              hi*hi + hi*lo + lo*hi accumulated in FP32 (relative error
+                              ~1e-5 per product); the MPO mixing between the GEMMs in
+                              FP32; environments stored in FP64.  Lanczos, the truncation
+                              eigendecomposition and energies stay FP64. */
 } vtn_precision;
 
 /* Optional device-memory provider.  alloc returns device memory of at least `bytes`
@@ -234,7 +235,10 @@ vtn_status vtn_heff_apply(vtn_ctx ctx, const vtn_core* Wi, const vtn_core* Wj, i
  *  side 0 (left):  out[b,l,k] = sum conj(A[i,t,l]) env[a,i,j] W[a,b,t,s] A[j,s,k]
  *                  env: complex[W.w_left*chi_l*chi_l] -> out: complex[W.w_right*chi_r*chi_r]
  *  side 1 (right): out[b,j,i] = sum W[b,c,t,s] A[j,s,g] conj(A[i,t,p]) env[c,g,p]
- *                  env: complex[W.w_right*chi_r*chi_r] -> out: complex[W.w_left*chi_l*chi_l] */
+ *                  env: complex[W.w_right*chi_r*chi_r] -> out: complex[W.w_left*chi_l*chi_l]
+ * prec VTN_FP64: FP64 contractions; VTN_BF16X3: both dense contractions as split-precision
+ * bf16 products on the tensor cores with FP32 accumulation, FP32 mixing, FP64 output (the
+ * mode vtn_sweep uses for its environments when opts->prec is VTN_BF16X3). */
 vtn_status vtn_env_update(vtn_ctx ctx, const vtn_core* W, int side, int chi_l, int chi_r,
                           const double* env, const double* A, double* out, vtn_precision prec);
 

@@ -623,8 +623,17 @@ vtn_status vtn_sweep(vtn_ctx ctx, vtn_mpo mpo, vtn_mps* state, const vtn_sweep_o
         }
         set_scalar_one(c, env.L[0]);
         set_scalar_one(c, env.R[M]);
+        // environment updates run in the same precision mode as H_eff psi
+        auto env_left = [&](const DevCore& W, int cl, int cr, const double2* Lin, const double2* A, double2* Lout) {
+            if (split) env_left_bf16x3(c, W, cl, cr, Lin, A, Lout);
+            else env_left_dev(c, W, cl, cr, Lin, A, Lout);
+        };
+        auto env_right = [&](const DevCore& W, int cl, int cr, const double2* Rin, const double2* A, double2* Rout) {
+            if (split) env_right_bf16x3(c, W, cl, cr, Rin, A, Rout);
+            else env_right_dev(c, W, cl, cr, Rin, A, Rout);
+        };
         for (int s = M - 1; s >= 1; --s)
-            env_right_dev(c, mpo->dcores[s], mps->dims[s], mps->dims[s + 1], env.R[s + 1], mps->sites[s], env.R[s]);
+            env_right(mpo->dcores[s], mps->dims[s], mps->dims[s + 1], env.R[s + 1], mps->sites[s], env.R[s]);
         const size_t theta_cap = (size_t)chi_cap * d * d * chi_cap;
         double2* theta = (double2*)c.workspace(WS_VEC_T, sizeof(double2) * theta_cap);
         vtn_sweep_report rep;
@@ -667,9 +676,9 @@ vtn_status vtn_sweep(vtn_ctx ctx, vtn_mpo mpo, vtn_mps* state, const vtn_sweep_o
                     mps->dims[i + 1] = tr.k;
                     disc_max = std::max(disc_max, tr.discarded);
                     if (dir == 0)
-                        env_left_dev(c, Wi, cl, tr.k, env.L[i], mps->sites[i], env.L[i + 1]);
+                        env_left(Wi, cl, tr.k, env.L[i], mps->sites[i], env.L[i + 1]);
                     else
-                        env_right_dev(c, Wj, tr.k, cr, env.R[i + 2], mps->sites[i + 1], env.R[i + 1]);
+                        env_right(Wj, tr.k, cr, env.R[i + 2], mps->sites[i + 1], env.R[i + 1]);
                 }
             }
             mps->center = 0;
@@ -949,15 +958,23 @@ vtn_status vtn_env_update(vtn_ctx ctx, const vtn_core* W, int side, int chi_l, i
         VTN_REQUIRE(env && A && out, "null device pointer");
         VTN_REQUIRE(side == 0 || side == 1, "side must be 0 (left) or 1 (right)");
         VTN_REQUIRE(chi_l >= 1 && chi_r >= 1, "bond dimensions must be >= 1");
-        if (prec != VTN_FP64) throw Error{VTN_EUNSUPPORTED, "only VTN_FP64 contractions are available in this build"};
+        if (prec != VTN_FP64 && prec != VTN_BF16X3)
+            throw Error{VTN_EUNSUPPORTED, "VTN_TF32X3 is not available in this build"};
         Ctx& c = ctx->c;
         use_device(c);
         HostCore h = core_from_abi(W);
         TempCore tc(c, h);
-        if (side == 0)
-            env_left_dev(c, tc.dc, chi_l, chi_r, (const double2*)env, (const double2*)A, (double2*)out);
-        else
-            env_right_dev(c, tc.dc, chi_l, chi_r, (const double2*)env, (const double2*)A, (double2*)out);
+        const double2* e = (const double2*)env;
+        const double2* a = (const double2*)A;
+        double2* o = (double2*)out;
+        if (prec == VTN_BF16X3) {
+            if (side == 0) env_left_bf16x3(c, tc.dc, chi_l, chi_r, e, a, o);
+            else env_right_bf16x3(c, tc.dc, chi_l, chi_r, e, a, o);
+        } else {
+            if (side == 0) env_left_dev(c, tc.dc, chi_l, chi_r, e, a, o);
+            else env_right_dev(c, tc.dc, chi_l, chi_r, e, a, o);
+        }
+        c.check_dstatus();
         c.sync();
         return VTN_OK;
     });

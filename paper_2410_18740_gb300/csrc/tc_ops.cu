@@ -45,6 +45,8 @@ struct PackP {
     long long ld, s_kb;
     int conj_t;        // 1: operand used as X^dag
     int is_b;
+    int rq;            // > 0: rows come in blocks of rq, block b starting at b * s_rq
+    long long s_rq;
     __nv_bfloat16* out;
     long long ldo;
 };
@@ -55,10 +57,16 @@ template <typename T>
 __device__ __forceinline__ T load_elem(const T* X, const PackP& p, int r, int kk) {
     const int c = kk / p.K, k = kk - c * p.K;
     const T* base = X + (long long)c * p.s_kb;
+    long long rb = 0;
+    int rr = r;
+    if (p.rq > 0) {
+        rb = (long long)(r / p.rq) * p.s_rq;
+        rr = r - (r / p.rq) * p.rq;
+    }
     // contiguous along kk: A with N, B with C; contiguous along r: A with C, B with N
     T v;
-    if (p.is_b == p.conj_t) v = base[(long long)r * p.ld + k];
-    else v = base[(long long)k * p.ld + r];
+    if (p.is_b == p.conj_t) v = base[rb + (long long)rr * p.ld + k];
+    else v = base[rb + (long long)k * p.ld + rr];
     if (p.conj_t) v.y = -v.y;
     return v;
 }
@@ -135,8 +143,13 @@ __global__ void zero_pad_kernel(__nv_bfloat16* out, long long ldo, int rows, int
 // in shared memory (as float2) in chunks, instead of being re-read by every thread.
 constexpr int MIX_SH = 4096;  // float2 operator entries per chunk (32 KiB)
 
+// element (channel c, p, s, q) of the mixing input sits at c * cs + p * ps + s * ss + q
+struct MixIn {
+    long long cs, ps, ss;
+};
+
 template <int DM>
-__global__ void __launch_bounds__(256) mix_f32_kernel(int P, int d, int Q, const int* __restrict__ ptr,
+__global__ void __launch_bounds__(256) mix_f32_kernel(int P, int d, int Q, MixIn st, const int* __restrict__ ptr,
                                                       const int* __restrict__ src, const int* __restrict__ opi,
                                                       const double2* __restrict__ ops,
                                                       const unsigned char* __restrict__ ident,
@@ -171,14 +184,14 @@ __global__ void __launch_bounds__(256) mix_f32_kernel(int P, int d, int Q, const
         __syncthreads();
         if (!active) continue;
         for (int e = 0; e < ne; ++e) {
-            const float2* x = in + (long long)src_sh[e] * blk + pp * d * Q + q;
+            const float2* x = in + (long long)src_sh[e] * st.cs + pp * st.ps + q;
             const float2* op = op_sh + e * dd;
             if (id_sh[e]) {
                 const float sr = op[0].x, si = op[0].y;
 #pragma unroll
                 for (int sp = 0; sp < DM; ++sp) {
                     if (sp < d) {
-                        const float2 v = x[(long long)sp * Q];
+                        const float2 v = x[(long long)sp * st.ss];
                         acc[sp].x += sr * v.x - si * v.y;
                         acc[sp].y += sr * v.y + si * v.x;
                     }
@@ -186,7 +199,7 @@ __global__ void __launch_bounds__(256) mix_f32_kernel(int P, int d, int Q, const
             } else {
                 float2 xv[DM];
 #pragma unroll
-                for (int s = 0; s < DM; ++s) xv[s] = (s < d) ? x[(long long)s * Q] : make_float2(0.f, 0.f);
+                for (int s = 0; s < DM; ++s) xv[s] = (s < d) ? x[(long long)s * st.ss] : make_float2(0.f, 0.f);
 #pragma unroll
                 for (int sp = 0; sp < DM; ++sp) {
                     if (sp >= d) continue;
@@ -209,11 +222,22 @@ __global__ void __launch_bounds__(256) mix_f32_kernel(int P, int d, int Q, const
         if (sp < d) y[(long long)sp * Q] = acc[sp];
 }
 
+// out[b][l][k] = T[l][b][k]  (T: rows l, row length nb * nk)
+__global__ void permute_blk(const double2* __restrict__ T, int nl, int nb, int nk, double2* __restrict__ out) {
+    const long long cnt = (long long)nl * nb * nk;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    const int k = (int)(t % nk);
+    const long long r = t / nk;
+    const int l = (int)(r % nl), b = (int)(r / nl);
+    out[t] = T[((long long)l * nb + b) * nk + k];
+}
+
 long long k6(long long Kt) { return ((6 * Kt + 63) / 64) * 64; }
 
 template <typename T>
 void pack_impl(Ctx& ctx, const T* X, int rows, int K, int kb, long long ld, long long s_kb, bool conj_t, bool is_b,
-               __nv_bfloat16* out) {
+               __nv_bfloat16* out, int rq, long long s_rq) {
     const long long Kt = (long long)K * kb;
     const long long ldo = k6(Kt);
     PackP p;
@@ -224,6 +248,8 @@ void pack_impl(Ctx& ctx, const T* X, int rows, int K, int kb, long long ld, long
     p.s_kb = s_kb;
     p.conj_t = conj_t ? 1 : 0;
     p.is_b = is_b ? 1 : 0;
+    p.rq = rq;
+    p.s_rq = s_rq;
     p.out = out;
     p.ldo = ldo;
     dim3 grid((unsigned)((Kt + 31) / 32), (unsigned)((rows + 31) / 32));
@@ -245,16 +271,17 @@ void pack_impl(Ctx& ctx, const T* X, int rows, int K, int kb, long long ld, long
 long long tc_k6(long long Kt) { return k6(Kt); }
 
 void tc_pack(Ctx& ctx, const double2* X, int rows, int K, int kb, long long ld, long long s_kb, bool conj_t, bool is_b,
-             __nv_bfloat16* out) {
-    pack_impl<double2>(ctx, X, rows, K, kb, ld, s_kb, conj_t, is_b, out);
+             __nv_bfloat16* out, int rq, long long s_rq) {
+    pack_impl<double2>(ctx, X, rows, K, kb, ld, s_kb, conj_t, is_b, out, rq, s_rq);
 }
 
 void tc_pack(Ctx& ctx, const float2* X, int rows, int K, int kb, long long ld, long long s_kb, bool conj_t, bool is_b,
-             __nv_bfloat16* out) {
-    pack_impl<float2>(ctx, X, rows, K, kb, ld, s_kb, conj_t, is_b, out);
+             __nv_bfloat16* out, int rq, long long s_rq) {
+    pack_impl<float2>(ctx, X, rows, K, kb, ld, s_kb, conj_t, is_b, out, rq, s_rq);
 }
 
-void mix_apply_f32(Ctx& ctx, const DevCore& core, bool by_col, int P, int Q, const float2* in, float2* out) {
+void mix_apply_f32(Ctx& ctx, const DevCore& core, bool by_col, int P, int Q, const float2* in, float2* out,
+                   const long long* in_strides) {
     const int w_out = by_col ? core.wr : core.wl;
     const int d = core.d;
     const long long PQ = (long long)P * Q;
@@ -265,13 +292,22 @@ void mix_apply_f32(Ctx& ctx, const DevCore& core, bool by_col, int P, int Q, con
     const int* src = by_col ? core.col_src : core.row_src;
     const int* opi = by_col ? core.col_op : core.row_op;
     double fl = 8.0 * PQ * ((double)core.n_ident * d + (double)core.n_dense * d * d);
+    MixIn st;
+    st.cs = PQ * d;
+    st.ps = (long long)d * Q;
+    st.ss = Q;
+    if (in_strides) {
+        st.cs = in_strides[0];
+        st.ps = in_strides[1];
+        st.ss = in_strides[2];
+    }
     int t = ctx.tbegin(TC_MIX, fl);
     if (d <= 4)
-        mix_f32_kernel<4><<<grid, 256, 0, ctx.stream>>>(P, d, Q, ptr, src, opi, core.ops, core.ident, in, out);
+        mix_f32_kernel<4><<<grid, 256, 0, ctx.stream>>>(P, d, Q, st, ptr, src, opi, core.ops, core.ident, in, out);
     else if (d <= 8)
-        mix_f32_kernel<8><<<grid, 256, 0, ctx.stream>>>(P, d, Q, ptr, src, opi, core.ops, core.ident, in, out);
+        mix_f32_kernel<8><<<grid, 256, 0, ctx.stream>>>(P, d, Q, st, ptr, src, opi, core.ops, core.ident, in, out);
     else
-        mix_f32_kernel<16><<<grid, 256, 0, ctx.stream>>>(P, d, Q, ptr, src, opi, core.ops, core.ident, in, out);
+        mix_f32_kernel<16><<<grid, 256, 0, ctx.stream>>>(P, d, Q, st, ptr, src, opi, core.ops, core.ident, in, out);
     ctx.count_launch();
     ctx.check_launch("mix_f32_kernel");
     ctx.tend(t);
@@ -338,6 +374,115 @@ void heff_apply_bf16x3(Ctx& ctx, const DevCore& Wi, const DevCore& Wj, const Hef
     g2.ldd = 2LL * chi_r;
     g2.d_fp64 = true;
     tc_gemm_bf16(ctx, g2, TC_HEFF, useful2);
+}
+
+// ----------------------------------------------------------------------------- environments
+// Split-precision (VTN_BF16X3) environment updates: the same three steps as the FP64
+// versions (dense contraction, MPO mixing, dense contraction with the conjugate site
+// tensor), with both dense steps on the tensor cores and the mixing in FP32.  Outputs are
+// FP64.
+
+// out[b][l][k] = sum_{a,i,j,s,t} conj(A[i][t][l]) L[a][i][j] W[a,b,t,s] A[j][s][k]
+void env_left_bf16x3(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const double2* L, const double2* A,
+                     double2* out) {
+    const int d = W.d, wl = W.wl, wr = W.wr;
+    const long long nA = (long long)chi_l * d * chi_r;
+    const int wmax = std::max(wl, wr);
+    // 1. T[(a,i)][(s,k)] = sum_j L[a][i][j] A[j][(s,k)]
+    const long long ld1 = k6(chi_l);
+    __nv_bfloat16* PA = (__nv_bfloat16*)ctx.workspace(WS_TC_L, sizeof(__nv_bfloat16) * (size_t)wl * chi_l * ld1);
+    __nv_bfloat16* PB = (__nv_bfloat16*)ctx.workspace(WS_TC_B1, sizeof(__nv_bfloat16) * (size_t)2 * d * chi_r * ld1);
+    float2* X = (float2*)ctx.workspace(WS_X, sizeof(float2) * (size_t)wmax * nA);
+    float2* Yb = (float2*)ctx.workspace(WS_Y, sizeof(float2) * (size_t)wmax * nA);
+    tc_pack(ctx, L, wl * chi_l, chi_l, 1, chi_l, 0, false, false, PA);
+    tc_pack(ctx, A, d * chi_r, chi_l, 1, (long long)d * chi_r, 0, false, true, PB);
+    TcGemmArgs g1;
+    g1.M = wl * chi_l;
+    g1.N = 2 * d * chi_r;
+    g1.K = (int)ld1;
+    g1.A = PA;
+    g1.lda = ld1;
+    g1.B = PB;
+    g1.ldb = ld1;
+    g1.D = X;
+    g1.ldd = 2LL * d * chi_r;
+    g1.d_fp64 = false;
+    tc_gemm_bf16(ctx, g1, -1, 8.0 * wl * chi_l * (double)chi_l * d * chi_r);
+    // 2. U[b][i][t][k] = sum W[a,b,t,s] T[a][i][s][k]
+    mix_apply_f32(ctx, W, true, chi_l, chi_r, X, Yb);
+    // 3. D[l][(b,k)] = sum_{(i,t)} conj(A[(i,t)][l]) U[b][(i,t)][k], then out[b][l][k] = D[l][b][k]
+    const long long ld3 = k6((long long)chi_l * d);
+    __nv_bfloat16* PA3 = (__nv_bfloat16*)ctx.workspace(WS_TC_A2, sizeof(__nv_bfloat16) * (size_t)chi_r * ld3);
+    __nv_bfloat16* PB3 = (__nv_bfloat16*)ctx.workspace(WS_TC_R, sizeof(__nv_bfloat16) * (size_t)2 * wr * chi_r * ld3);
+    double2* T = (double2*)ctx.workspace(WS_TC_ENV, sizeof(double2) * (size_t)chi_r * wr * chi_r);
+    tc_pack(ctx, A, chi_r, chi_l * d, 1, chi_r, 0, true, false, PA3);
+    tc_pack(ctx, (const float2*)Yb, wr * chi_r, chi_l * d, 1, chi_r, 0, false, true, PB3, chi_r, nA);
+    TcGemmArgs g3;
+    g3.M = chi_r;
+    g3.N = 2 * wr * chi_r;
+    g3.K = (int)ld3;
+    g3.A = PA3;
+    g3.lda = ld3;
+    g3.B = PB3;
+    g3.ldb = ld3;
+    g3.D = T;
+    g3.ldd = 2LL * wr * chi_r;
+    g3.d_fp64 = true;
+    tc_gemm_bf16(ctx, g3, -1, 8.0 * chi_r * (double)wr * chi_r * chi_l * d);
+    const long long cnt = (long long)wr * chi_r * chi_r;
+    permute_blk<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx.stream>>>(T, chi_r, wr, chi_r, out);
+    ctx.count_launch();
+    ctx.check_launch("permute_blk");
+}
+
+// out[b][j][i] = sum_{c,g,p,s,t} A[j][s][g] R[c][g][p] W[b,c,t,s] conj(A[i][t][p])
+void env_right_bf16x3(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const double2* R, const double2* A,
+                      double2* out) {
+    const int d = W.d, wl = W.wl, wr = W.wr;
+    const long long nA = (long long)chi_l * d * chi_r;
+    const int wmax = std::max(wl, wr);
+    // 1. T[(j,s)][(c,p)] = sum_g A[(j,s)][g] R[c][g][p]
+    const long long ld1 = k6(chi_r);
+    __nv_bfloat16* PA = (__nv_bfloat16*)ctx.workspace(WS_TC_L, sizeof(__nv_bfloat16) * (size_t)chi_l * d * ld1);
+    __nv_bfloat16* PB = (__nv_bfloat16*)ctx.workspace(WS_TC_R, sizeof(__nv_bfloat16) * (size_t)2 * wr * chi_r * ld1);
+    float2* X = (float2*)ctx.workspace(WS_X, sizeof(float2) * (size_t)wmax * nA);
+    float2* Yb = (float2*)ctx.workspace(WS_Y, sizeof(float2) * (size_t)wmax * nA);
+    tc_pack(ctx, A, chi_l * d, chi_r, 1, chi_r, 0, false, false, PA);
+    tc_pack(ctx, R, wr * chi_r, chi_r, 1, chi_r, 0, false, true, PB, chi_r, (long long)chi_r * chi_r);
+    TcGemmArgs g1;
+    g1.M = chi_l * d;
+    g1.N = 2 * wr * chi_r;
+    g1.K = (int)ld1;
+    g1.A = PA;
+    g1.lda = ld1;
+    g1.B = PB;
+    g1.ldb = ld1;
+    g1.D = X;
+    g1.ldd = 2LL * wr * chi_r;
+    g1.d_fp64 = false;
+    tc_gemm_bf16(ctx, g1, -1, 8.0 * chi_l * d * (double)wr * chi_r * chi_r);
+    // 2. U[b][j][t][p] = sum W[b,c,t,s] T[c][j][s][p]; T element (c, j, s, p) sits at
+    //    ((j d + s) wr + c) chi_r + p
+    const long long st[3] = {chi_r, (long long)d * wr * chi_r, (long long)wr * chi_r};
+    mix_apply_f32(ctx, W, false, chi_l, chi_r, X, Yb, st);
+    // 3. out[(b,j)][i] = sum_{(t,p)} U[(b,j)][(t,p)] conj(A[i][(t,p)])
+    const long long ld3 = k6((long long)d * chi_r);
+    __nv_bfloat16* PA3 = (__nv_bfloat16*)ctx.workspace(WS_TC_A2, sizeof(__nv_bfloat16) * (size_t)wl * chi_l * ld3);
+    __nv_bfloat16* PB3 = (__nv_bfloat16*)ctx.workspace(WS_TC_B1, sizeof(__nv_bfloat16) * (size_t)2 * chi_l * ld3);
+    tc_pack(ctx, (const float2*)Yb, wl * chi_l, d * chi_r, 1, (long long)d * chi_r, 0, false, false, PA3);
+    tc_pack(ctx, A, chi_l, d * chi_r, 1, (long long)d * chi_r, 0, true, true, PB3);
+    TcGemmArgs g3;
+    g3.M = wl * chi_l;
+    g3.N = 2 * chi_l;
+    g3.K = (int)ld3;
+    g3.A = PA3;
+    g3.lda = ld3;
+    g3.B = PB3;
+    g3.ldb = ld3;
+    g3.D = out;
+    g3.ldd = 2LL * chi_l;
+    g3.d_fp64 = true;
+    tc_gemm_bf16(ctx, g3, -1, 8.0 * wl * chi_l * (double)chi_l * d * chi_r);
 }
 
 }  // namespace vtn

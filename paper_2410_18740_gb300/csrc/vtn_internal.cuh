@@ -103,7 +103,7 @@ struct Ctx {
 enum WsSlot {
     WS_X = 0, WS_Y, WS_Z, WS_KRYLOV, WS_VEC_W, WS_VEC_T, WS_PARTIAL, WS_SCAL, WS_EIG_A, WS_EIG_H,
     WS_EIG_Y, WS_EIG_WORK, WS_EIG_U, WS_CORE_A, WS_CORE_B, WS_ENV_TMP, WS_MISC, WS_TC_L, WS_TC_R, WS_TC_B1,
-    WS_TC_A2, WS_TC_PART, WS_GEMM_SPLIT, WS_EIG_PART, WS_COUNT
+    WS_TC_A2, WS_TC_PART, WS_GEMM_SPLIT, WS_EIG_PART, WS_TC_ENV, WS_COUNT
 };
 
 // ------------------------------------------------------------------ cores
@@ -144,10 +144,11 @@ struct TcGemmArgs {
 void tc_gemm_bf16(Ctx& ctx, const TcGemmArgs& a, int timing_class = -1, double useful_flops = 0.0);
 long long tc_k6(long long Kt);
 // split-precision operand packing (see tc_ops.cu)
+// rq > 0: operand rows come in blocks of rq, block b starting s_rq elements after block b-1
 void tc_pack(Ctx& ctx, const double2* X, int rows, int K, int kb, long long ld, long long s_kb, bool conj_t, bool is_b,
-             __nv_bfloat16* out);
+             __nv_bfloat16* out, int rq = 0, long long s_rq = 0);
 void tc_pack(Ctx& ctx, const float2* X, int rows, int K, int kb, long long ld, long long s_kb, bool conj_t, bool is_b,
-             __nv_bfloat16* out);
+             __nv_bfloat16* out, int rq = 0, long long s_rq = 0);
 
 // ------------------------------------------------------------------ W mixing
 // out[b][p][s'][q] = sum_{entries (src -> b)} op[s'][s] in[src][p][s][q]
@@ -155,7 +156,9 @@ void tc_pack(Ctx& ctx, const float2* X, int rows, int K, int kb, long long ld, l
 void mix_apply(Ctx& ctx, const DevCore& core, bool by_col, int P, int Q, const double2* in,
                double2* out);
 
-void mix_apply_f32(Ctx& ctx, const DevCore& core, bool by_col, int P, int Q, const float2* in, float2* out);
+// in_strides (optional): channel, p and s strides of the input (default: standard layout)
+void mix_apply_f32(Ctx& ctx, const DevCore& core, bool by_col, int P, int Q, const float2* in, float2* out,
+                   const long long* in_strides = nullptr);
 
 // ------------------------------------------------------------------ contractions
 void heff_apply_dev(Ctx& ctx, const DevCore& Wi, const DevCore& Wj, int chi_l, int chi_r,
@@ -172,6 +175,10 @@ void heff_pack_envs(Ctx& ctx, const DevCore& Wi, const DevCore& Wj, int chi_l, i
                     const double2* R, HeffPacked& pk);
 void heff_apply_bf16x3(Ctx& ctx, const DevCore& Wi, const DevCore& Wj, const HeffPacked& pk, const double2* theta,
                        double2* y);
+void env_left_bf16x3(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const double2* L, const double2* A,
+                     double2* out);
+void env_right_bf16x3(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const double2* R, const double2* A,
+                      double2* out);
 void env_left_dev(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const double2* L,
                   const double2* A, double2* out);
 void env_right_dev(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const double2* R,

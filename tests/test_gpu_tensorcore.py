@@ -55,6 +55,30 @@ def test_heff_bf16x3_matches_oracle(ctx, chi_l, chi_r, d, ws):
     assert np.linalg.norm(got - expect) / np.linalg.norm(expect) < 5e-5
 
 
+@pytest.mark.parametrize("chi_l,chi_r,d,w", [(5, 7, 3, (4, 5)), (37, 70, 4, (6, 8)), (128, 128, 8, (24, 26)),
+                                            (1, 16, 4, (1, 4)), (16, 1, 4, (4, 1))])
+def test_env_update_bf16x3_matches_oracle(ctx, chi_l, chi_r, d, w):
+    """Split-precision environment updates (both sides) against the oracle's contraction."""
+    rng = inputs.rng_for(7000 + chi_l + chi_r)
+    wl, wr = w
+    W = inputs.random_sparse_core(wl, wr, d, rng)
+    A = inputs.random_complex((chi_l, d, chi_r), rng)
+    L = inputs.random_complex((wl, chi_l, chi_l), rng)
+    R = inputs.random_complex((wr, chi_r, chi_r), rng)
+    c = vtn.core_from_sparse(W)
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.complex128)).cuda()
+    outL = torch.full((wr, chi_r, chi_r), float("nan"), dtype=torch.complex128, device="cuda")
+    vtn.vtn_env_update(ctx, c, 0, chi_l, chi_r, dev(L), dev(A), outL, prec=vtn.VTN_BF16X3)
+    outR = torch.full((wl, chi_l, chi_l), float("nan"), dtype=torch.complex128, device="cuda")
+    vtn.vtn_env_update(ctx, c, 1, chi_l, chi_r, dev(R), dev(A), outR, prec=vtn.VTN_BF16X3)
+    torch.cuda.synchronize()
+    for got, expect in ((outL.cpu().numpy(), odmrg.env_left(L, A, W.dense())),
+                        (outR.cpu().numpy(), odmrg.env_right(R, A, W.dense()))):
+        assert np.isfinite(got).all()
+        assert np.abs(got - expect).max() / np.abs(expect).max() < 2e-4
+        assert np.linalg.norm(got - expect) / np.linalg.norm(expect) < 5e-5
+
+
 def test_bf16x3_sweep_energy_matches_fp64(ctx):
     """Mixed-precision sweeps reach the FP64 sweep's energy: the energy is evaluated in FP64
     and is quadratic in the state error, so it agrees far below the ~1e-5 product error."""
