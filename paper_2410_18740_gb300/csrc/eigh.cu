@@ -11,11 +11,13 @@
 //     one warp per eigenvalue evaluating 32 points per round (multisection).
 //  4. Eigenvectors by inverse iteration with a pivoted tridiagonal LU, one thread per
 //     eigenvector, three iterations from deterministic pseudo-random starts.
-//  5. Orthonormalisation of the k vectors by shifted CholeskyQR3 (Fukaya, Kannan,
-//     Nakatsukasa, Yamamoto, Yanagisawa, SIAM J. Sci. Comput. 2020): one shifted and two
-//     plain Cholesky-QR passes; column order is preserved, so the span of the leading j
-//     vectors is that of the j largest eigenvalues.
-//  6. Back-transformation through the reflectors and the phases, one CTA per vector.
+//  5. Orthonormalisation of the k vectors: one Cholesky-QR pass when they are already
+//     nearly orthonormal, else shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto,
+//     Yanagisawa, SIAM J. Sci. Comput. 2020): one shifted and two plain passes.  Column
+//     order is preserved, so the span of the leading j vectors is that of the j largest
+//     eigenvalues.
+//  6. Back-transformation through the reflectors (compact WY blocks) and the phases, one
+//     CTA per vector.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -712,9 +714,14 @@ __global__ void __launch_bounds__(128) inverse_iteration(int n, int k, EigSmall 
 }
 
 // ---------------------------------------------------------------- CholeskyQR
+// Kernels of the orthonormalisation take an optional predicate: they do nothing unless
+// *pred == want (the host enqueues both branches; the device picks one).
+__device__ __forceinline__ bool skip(const int* pred, int want) { return pred != nullptr && *pred != want; }
+
 // G[a][b] = sum_i Z[i][a] Z[i][b] (+ shift on the diagonal), 16 x 16 tile per block
 __global__ void __launch_bounds__(256) gram_kernel(const double* __restrict__ Z, int n, int k, double* __restrict__ G,
-                                                   double shift) {
+                                                   double shift, const int* pred, int want) {
+    if (skip(pred, want)) return;
     __shared__ double za[32][17], zb[32][17];
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     const int a0 = blockIdx.y * 16, b0 = blockIdx.x * 16;
@@ -735,9 +742,30 @@ __global__ void __launch_bounds__(256) gram_kernel(const double* __restrict__ Z,
     if (a < k && b < k) G[(long long)a * k + b] = acc + (a == b ? shift : 0.0);
 }
 
-// in-place lower Cholesky of the k x k G (single CTA); status[0] = 1 on a non-positive pivot
-__global__ void __launch_bounds__(1024) cholesky_kernel(double* __restrict__ G, int k, int* __restrict__ status) {
-    __shared__ double piv;
+// *flag = 1 if max |G - I| > tol (the vectors need the full shifted CholeskyQR3), else 0
+__global__ void __launch_bounds__(256) ortho_check(const double* __restrict__ G, int k, double tol, int* flag) {
+    __shared__ double red[33];
+    double mx = 0.0;
+    for (long long t = threadIdx.x; t < (long long)k * k; t += blockDim.x) {
+        const long long a = t / k, b = t - a * k;
+        mx = fmax(mx, fabs(G[t] - (a == b ? 1.0 : 0.0)));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
+        *flag = (mx > tol || !(mx == mx)) ? 1 : 0;
+    }
+}
+
+// In-place lower Cholesky of the k x k G (single CTA, right-looking); dinv[j] = 1 / L[j][j].
+// status[0] = 1 on a non-positive pivot.
+__global__ void __launch_bounds__(1024) cholesky_kernel(double* __restrict__ G, int k, double* __restrict__ dinv,
+                                                        int* __restrict__ status, const int* pred, int want) {
+    if (skip(pred, want)) return;
+    __shared__ double rj;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, nty = blockDim.x >> 5;
     for (int j = 0; j < k; ++j) {
         if (threadIdx.x == 0) {
             double djj = G[(long long)j * k + j];
@@ -745,120 +773,226 @@ __global__ void __launch_bounds__(1024) cholesky_kernel(double* __restrict__ G, 
                 status[0] = 1;
                 djj = 1e-300;
             }
-            piv = sqrt(djj);
-            G[(long long)j * k + j] = piv;
+            const double r = rsqrt(djj);
+            G[(long long)j * k + j] = djj * r;
+            dinv[j] = r;
+            rj = r;
         }
         __syncthreads();
-        const double p = piv;
-        for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) G[(long long)i * k + j] /= p;
+        const double r = rj;
+        for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) G[(long long)i * k + j] *= r;
         __syncthreads();
-        const int m = k - j - 1;
-        for (long long t = threadIdx.x; t < (long long)m * m; t += blockDim.x) {
-            const int i = j + 1 + (int)(t / m), l = j + 1 + (int)(t % m);
-            if (l <= i) G[(long long)i * k + l] -= G[(long long)i * k + j] * G[(long long)l * k + j];
+        for (int i = j + 1 + ty; i < k; i += nty) {
+            const double gij = G[(long long)i * k + j];
+            for (int l = j + 1 + tx; l <= i; l += 32)
+                G[(long long)i * k + l] = fma(-gij, G[(long long)l * k + j], G[(long long)i * k + l]);
         }
         __syncthreads();
     }
 }
 
-// Z <- Z L^{-T}: row-wise forward substitution q_j = (z_j - sum_{l<j} q_l L[j][l]) / L[j][j]
-__global__ void __launch_bounds__(128) trsm_rows(double* __restrict__ Z, int n, int k, const double* __restrict__ L) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double* z = Z + (long long)i * k;
+// Z <- Z L^{-T}: q_j = (z_j - sum_{l<j} q_l L[j][l]) / L[j][j] for 32 rows per CTA (one row
+// per lane); the warps split each inner sum, warp 0 finishes the column.
+constexpr int TS_WARPS = 8;
+__global__ void __launch_bounds__(32 * TS_WARPS) trsm_rows(double* __restrict__ Z, int n, int k,
+                                                           const double* __restrict__ L,
+                                                           const double* __restrict__ dinv, const int* pred,
+                                                           int want) {
+    if (skip(pred, want)) return;
+    extern __shared__ double q[];  // [k][33]: z, then q, of this CTA's rows
+    __shared__ double part[TS_WARPS][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r0 = blockIdx.x * 32;
+    const int nr = min(32, n - r0);
+    for (int t = threadIdx.x; t < nr * k; t += blockDim.x) {
+        const int l = t / k, j = t - l * k;
+        q[j * 33 + l] = Z[(long long)(r0 + l) * k + j];
+    }
+    __syncthreads();
     for (int j = 0; j < k; ++j) {
-        double acc = z[j];
+        double acc = 0.0;
         const double* Lj = L + (long long)j * k;
-        for (int l = 0; l < j; ++l) acc -= z[l] * Lj[l];
-        z[j] = acc / Lj[j];
+        for (int l = warp; l < j; l += TS_WARPS) acc = fma(q[l * 33 + lane], Lj[l], acc);
+        part[warp][lane] = acc;
+        __syncthreads();
+        if (warp == 0) {
+            double sum = 0.0;
+#pragma unroll
+            for (int w = 0; w < TS_WARPS; ++w) sum += part[w][lane];
+            q[j * 33 + lane] = (q[j * 33 + lane] - sum) * dinv[j];
+        }
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < nr * k; t += blockDim.x) {
+        const int l = t / k, j = t - l * k;
+        Z[(long long)(r0 + l) * k + j] = q[j * 33 + l];
     }
 }
 
 // ---------------------------------------------------------------- back-transformation
-// CTA c handles vectors j = c*cpb .. c*cpb+cpb-1: y = ph .* Z[:, j]; y <- H_0 ... H_{n-3} y;
-// written as columns (mode 0: U[i][j] = y_i) or conjugated rows (mode 1: B[j][i] = conj(y_i)).
-// Several vectors per CTA share each reflector's reduction (two barriers per reflector).
-constexpr int BT_MAX = 8;
+// y = ph .* Z[:, j], then y <- H_0 H_1 ... H_{n-3} y (H_kk = I - tau_kk v_kk v_kk^dag acting on
+// indices kk+1..n-1), written as columns (mode 0: U[i][j] = y_i) or conjugated rows
+// (mode 1: B[j][i] = conj(y_i)).
+//
+// The reflectors are applied in blocks of BT_NB in compact WY form (Schreiber and Van Loan):
+// Q_b = H_{b0} ... H_{b0+nb-1} = I - V T V^dag with T upper triangular, T_rr = tau_r and
+// T[0:r, r] = -tau_r T[0:r, 0:r] (V[:, 0:r]^dag v_r).  Each block costs one CTA-wide reduction
+// of its nb inner products instead of one per reflector.  One eigenvector per CTA.
+constexpr int BT_NB = 16;
 constexpr int BT_THREADS = 256;
 
-template <int CPB>
-__global__ void __launch_bounds__(BT_THREADS) backtransform(int n, int k, const double2* __restrict__ H,
-                                                            EigSmall s, const double* __restrict__ Z, int mode,
-                                                            double2* __restrict__ out) {
-    constexpr int cpb = CPB;
-    extern __shared__ double2 y[];  // [cpb][n]
-    __shared__ double red[(BT_THREADS / 32) * 2 * BT_MAX];
-    __shared__ double2 coef[BT_MAX];
-    const int j0 = blockIdx.x * cpb;
-    const int nv = min(cpb, k - j0);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int t = threadIdx.x; t < nv * n; t += blockDim.x) {
-        const int c = t / n, i = t - c * n;
-        const double z = Z[(long long)i * k + j0 + c];
-        const double2 q = s.ph[i];
-        y[(long long)c * n + i] = make_double2(q.x * z, q.y * z);
+__device__ __forceinline__ double2 refl_elem(const double2* __restrict__ H, int n, int kk, int g) {
+    return H[(long long)kk * n + (g - kk - 1)];  // v_kk at global index g >= kk + 1
+}
+
+// T factors of all blocks: Tall[b][q][r] (BT_NB x BT_NB, upper triangle used).  One CTA per
+// block: warps form the Gram entries S[q][r] = v_q^dag v_r (q < r), then warp 0 runs the
+// recurrence with lane q owning row q of T.
+__global__ void __launch_bounds__(256) wy_tfactor(int n, const double2* __restrict__ H, EigSmall s,
+                                                  double2* __restrict__ Tall) {
+    __shared__ double2 S[BT_NB][BT_NB];
+    __shared__ double2 T[BT_NB][BT_NB + 1];
+    const int b = blockIdx.x;
+    const int b0 = b * BT_NB;
+    const int nb = min(BT_NB, n - 2 - b0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int npair = nb * (nb - 1) / 2;
+    for (int pr = warp; pr < npair; pr += nw) {
+        // pair index -> (q, r), q < r
+        int r = 1, rem = pr;
+        while (rem >= r) {
+            rem -= r;
+            ++r;
+        }
+        const int q = rem;
+        const int kq = b0 + q, kr = b0 + r;
+        double sx = 0.0, sy = 0.0;
+        for (int g = kr + 1 + lane; g < n; g += 32) {  // common support of v_q and v_r
+            const double2 a = refl_elem(H, n, kq, g), c = refl_elem(H, n, kr, g);
+            sx = fma(a.x, c.x, fma(a.y, c.y, sx));  // conj(a) c
+            sy = fma(a.x, c.y, fma(-a.y, c.x, sy));
+        }
+        sx = warp_sum(sx);
+        sy = warp_sum(sy);
+        if (lane == 0) S[q][r] = make_double2(sx, sy);
     }
     __syncthreads();
-    for (int kk = n - 3; kk >= 0; --kk) {
-        const double tau = s.tau[kk];
-        if (tau == 0.0) continue;
-        const int m = n - kk - 1;
-        const double2* v = H + (long long)kk * n;
-        double re[CPB], im[CPB];
+    if (warp == 0) {
+        for (int r = 0; r < BT_NB; ++r) {
+            const double tau = r < nb ? s.tau[b0 + r] : 0.0;
+            if (lane == r) T[r][r] = make_double2(tau, 0.0);
+            if (lane < r) {
+                double ax = 0.0, ay = 0.0;
+                if (r < nb) {
+                    for (int p2 = lane; p2 < r; ++p2) {  // T[lane][p2] S[p2][r]
+                        const double2 t = T[lane][p2], sv = S[p2][r];
+                        ax = fma(t.x, sv.x, fma(-t.y, sv.y, ax));
+                        ay = fma(t.x, sv.y, fma(t.y, sv.x, ay));
+                    }
+                }
+                T[lane][r] = make_double2(-tau * ax, -tau * ay);
+            }
+            if (lane > r && lane < BT_NB) T[lane][r] = make_double2(0.0, 0.0);
+            __syncwarp();
+        }
+        if (lane < BT_NB)
+            for (int r = 0; r < BT_NB; ++r) Tall[((long long)b * BT_NB + lane) * BT_NB + r] = T[lane][r];
+    }
+}
+
+// Sum over the 32 lanes of 32 values per lane (butterfly reduce-scatter): afterwards lane l
+// holds the warp total of value l.  31 additions per lane, all 32 lanes busy.
+__device__ __forceinline__ double warp_reduce32(double (&v)[32]) {
+    const int lane = threadIdx.x & 31;
 #pragma unroll
-        for (int c = 0; c < CPB; ++c) re[c] = im[c] = 0.0;
-        for (int i = threadIdx.x; i < m; i += blockDim.x) {
-            const double2 a = v[i];
+    for (int off = 16; off >= 1; off >>= 1) {
+        const bool upper = (lane & off) != 0;
 #pragma unroll
-            for (int c = 0; c < CPB; ++c) {
-                if (c < nv) {
-                    const double2 b = y[(long long)c * n + kk + 1 + i];
-                    re[c] += a.x * b.x + a.y * b.y;  // conj(a) * b
-                    im[c] += a.x * b.y - a.y * b.x;
+        for (int i = 0; i < off; ++i) {
+            const double send = upper ? v[i] : v[i + off];
+            const double keep = upper ? v[i + off] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+    return v[0];
+}
+
+__global__ void __launch_bounds__(BT_THREADS) backtransform(int n, int k, const double2* __restrict__ H,
+                                                            EigSmall s, const double2* __restrict__ Tall,
+                                                            const double* __restrict__ Z, int mode,
+                                                            double2* __restrict__ out) {
+    extern __shared__ double2 y[];  // [n]
+    __shared__ double part[BT_THREADS / 32][32];
+    __shared__ double2 tvec[BT_NB];
+    const int j = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double z = Z[(long long)i * k + j];
+        const double2 q = s.ph[i];
+        y[i] = make_double2(q.x * z, q.y * z);
+    }
+    __syncthreads();
+    const int nblk = (n - 2 + BT_NB - 1) / BT_NB;
+    for (int b = nblk - 1; b >= 0; --b) {
+        const int b0 = b * BT_NB;
+        const int nb = min(BT_NB, n - 2 - b0);
+        // 1. w_r = v_r^dag y, r < nb (values 2r, 2r+1 = Re, Im)
+        double v[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = 0.0;
+        for (int g = b0 + 1 + threadIdx.x; g < n; g += blockDim.x) {
+            const double2 yv = y[g];
+#pragma unroll
+            for (int r = 0; r < BT_NB; ++r) {
+                const int kk = b0 + r;
+                if (r < nb && g > kk) {
+                    const double2 a = refl_elem(H, n, kk, g);
+                    v[2 * r] = fma(a.x, yv.x, fma(a.y, yv.y, v[2 * r]));
+                    v[2 * r + 1] = fma(a.x, yv.y, fma(-a.y, yv.x, v[2 * r + 1]));
                 }
             }
         }
-#pragma unroll
-        for (int c = 0; c < CPB; ++c) {
-            re[c] = warp_sum(re[c]);
-            im[c] = warp_sum(im[c]);
-        }
-        if (lane == 0) {
-#pragma unroll
-            for (int c = 0; c < CPB; ++c) {
-                red[wid * 2 * BT_MAX + 2 * c] = re[c];
-                red[wid * 2 * BT_MAX + 2 * c + 1] = im[c];
+        part[warp][lane] = warp_reduce32(v);
+        __syncthreads();
+        if (warp == 0) {
+            double tot = 0.0;
+            for (int w = 0; w < nw; ++w) tot += part[w][lane];
+            part[0][lane] = tot;
+            __syncwarp();
+            // 2. t = T w (T upper triangular)
+            if (lane < nb) {
+                const double2* Tq = Tall + ((long long)b * BT_NB + lane) * BT_NB;
+                double tx = 0.0, ty = 0.0;
+                for (int r = lane; r < nb; ++r) {
+                    const double2 t = Tq[r];
+                    const double wx = part[0][2 * r], wy = part[0][2 * r + 1];
+                    tx = fma(t.x, wx, fma(-t.y, wy, tx));
+                    ty = fma(t.x, wy, fma(t.y, wx, ty));
+                }
+                tvec[lane] = make_double2(tx, ty);
             }
         }
         __syncthreads();
-        if (threadIdx.x < nv) {
-            double sr = 0.0, si = 0.0;
-            for (int w = 0; w < nw; ++w) {
-                sr += red[w * 2 * BT_MAX + 2 * threadIdx.x];
-                si += red[w * 2 * BT_MAX + 2 * threadIdx.x + 1];
-            }
-            coef[threadIdx.x] = make_double2(tau * sr, tau * si);
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < m; i += blockDim.x) {
-            const double2 a = v[i];
+        // 3. y <- y - V t
+        for (int g = b0 + 1 + threadIdx.x; g < n; g += blockDim.x) {
+            double2 acc = y[g];
 #pragma unroll
-            for (int c = 0; c < CPB; ++c) {
-                if (c >= nv) break;
-                const double2 cf = coef[c];
-                double2 b = y[(long long)c * n + kk + 1 + i];
-                b.x -= a.x * cf.x - a.y * cf.y;
-                b.y -= a.x * cf.y + a.y * cf.x;
-                y[(long long)c * n + kk + 1 + i] = b;
+            for (int r = 0; r < BT_NB; ++r) {
+                const int kk = b0 + r;
+                if (r < nb && g > kk) {
+                    const double2 a = refl_elem(H, n, kk, g), t = tvec[r];
+                    acc.x = fma(-a.x, t.x, fma(a.y, t.y, acc.x));
+                    acc.y = fma(-a.x, t.y, fma(-a.y, t.x, acc.y));
+                }
             }
+            y[g] = acc;
         }
         __syncthreads();
     }
-    for (int t = threadIdx.x; t < nv * n; t += blockDim.x) {
-        const int c = t / n, i = t - c * n;
-        const double2 w = y[(long long)c * n + i];
-        if (mode == 0) out[(long long)i * k + j0 + c] = w;
-        else out[(long long)(j0 + c) * n + i] = make_double2(w.x, -w.y);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double2 w = y[i];
+        if (mode == 0) out[(long long)i * k + j] = w;
+        else out[(long long)j * n + i] = make_double2(w.x, -w.y);
     }
 }
 
@@ -966,33 +1100,56 @@ TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int dir
     inverse_iteration<<<(k + 127) / 128, 128, 0, ctx.stream>>>(n, k, s, work, piv, Z);
     ctx.count_launch(2);
     ctx.check_launch("eigenpairs");
-    // 5. shifted CholeskyQR3
+    // 5. orthonormalisation.  Inverse-iteration vectors of separated eigenvalues are already
+    //    orthonormal to O(u ||T|| / gap); if max |Z^T Z - I| <= 1e-3 one plain Cholesky-QR
+    //    pass suffices (its loss of orthogonality is O(u kappa(Z)^2) with kappa(Z)^2 <= 1.003).
+    //    Otherwise (clusters) the shifted CholeskyQR3 runs.  Both branches are enqueued; the
+    //    device flag selects one.
     dim3 gg((k + 15) / 16, (k + 15) / 16);
+    int* flag = status + 1;
+    double* dinv = small + 13 * (size_t)n + 32;
+    const size_t ts_shm = sizeof(double) * (size_t)k * 33;
+    static bool ts_attr = false;
+    if (!ts_attr) {
+        VTN_CUDA_TRY(cudaFuncSetAttribute(trsm_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        ts_attr = true;
+    }
+    VTN_REQUIRE(ts_shm <= 200 * 1024, "truncation keeps too many states for the orthonormalisation");
+    const unsigned ts_grid = (unsigned)((n + 31) / 32);
+    gram_kernel<<<gg, 256, 0, ctx.stream>>>(Z, n, k, G, 0.0, nullptr, 0);
+    ortho_check<<<1, 256, 0, ctx.stream>>>(G, k, 1e-3, flag);
+    cholesky_kernel<<<1, 1024, 0, ctx.stream>>>(G, k, dinv, status, flag, 0);
+    trsm_rows<<<ts_grid, 32 * TS_WARPS, ts_shm, ctx.stream>>>(Z, n, k, G, dinv, flag, 0);
+    ctx.count_launch(4);
     for (int pass = 0; pass < 3; ++pass) {
         double shift = 0.0;
         if (pass == 0) {
             // ||Z||_F^2 = k for unit columns; shift 11 (n k + k (k + 1)) u ||Z||_2^2 bounded by that
             shift = 11.0 * ((double)n * k + (double)k * (k + 1)) * EPS * (double)k;
         }
-        gram_kernel<<<gg, 256, 0, ctx.stream>>>(Z, n, k, G, shift);
-        cholesky_kernel<<<1, 1024, 0, ctx.stream>>>(G, k, status);
-        trsm_rows<<<(n + 127) / 128, 128, 0, ctx.stream>>>(Z, n, k, G);
+        gram_kernel<<<gg, 256, 0, ctx.stream>>>(Z, n, k, G, shift, flag, 1);
+        cholesky_kernel<<<1, 1024, 0, ctx.stream>>>(G, k, dinv, status, flag, 1);
+        trsm_rows<<<ts_grid, 32 * TS_WARPS, ts_shm, ctx.stream>>>(Z, n, k, G, dinv, flag, 1);
         ctx.count_launch(3);
     }
     ctx.check_launch("orthonormalisation");
-    // 6. back-transformation into the site tensors
-    // one vector per CTA: the FP64 work of the reflector applications spreads over all SMs
-    // (GB300's FP64 pipe, not the per-reflector reduction, bounds this step)
-    const int cpb = 1;
-    const size_t shm = sizeof(double2) * (size_t)n * cpb;
-    const int nbt = (k + cpb - 1) / cpb;
+    // 6. back-transformation into the site tensors: T factors of the reflector blocks, then
+    //    one vector per CTA (the FP64 work spreads over the SMs)
+    const size_t shm = sizeof(double2) * (size_t)n;
+    const int nbt = k;
     static bool attr_set = false;
     if (!attr_set) {
-        VTN_CUDA_TRY(cudaFuncSetAttribute(backtransform<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        VTN_CUDA_TRY(cudaFuncSetAttribute(backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         attr_set = true;
     }
+    const int nblk = n >= 3 ? (n - 2 + BT_NB - 1) / BT_NB : 0;
+    double2* Tall = (double2*)ctx.workspace(WS_EIG_T, sizeof(double2) * (size_t)std::max(nblk, 1) * BT_NB * BT_NB);
+    if (nblk > 0) {
+        wy_tfactor<<<nblk, 256, 0, ctx.stream>>>(n, H, s, Tall);
+        ctx.count_launch();
+    }
     if (direction == 0) {
-        backtransform<1><<<nbt, BT_THREADS, shm, ctx.stream>>>(n, k, H, s, Z, 0, left);
+        backtransform<<<nbt, BT_THREADS, shm, ctx.stream>>>(n, k, H, s, Tall, Z, 0, left);
         // right = U^dag T
         GemmArgs c;
         c.M = k; c.N = nR; c.K = nL;
@@ -1002,7 +1159,7 @@ TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int dir
         ctx.count_launch();
         gemm_c64(ctx, c);
     } else {
-        backtransform<1><<<nbt, BT_THREADS, shm, ctx.stream>>>(n, k, H, s, Z, 1, right);
+        backtransform<<<nbt, BT_THREADS, shm, ctx.stream>>>(n, k, H, s, Tall, Z, 1, right);
         // left = T V = T (V^dag)^dag
         GemmArgs c;
         c.M = nL; c.N = k; c.K = nR;
