@@ -67,8 +67,11 @@ def parse():
                    help="skip the single FP64 sweep measured after the timed region")
     p.add_argument("--tte-sweeps", type=int, default=0,
                    help="after the timed region, sweep up to this many times to measure time-to-eps")
-    p.add_argument("--case", default=None, choices=["heff", "trunc"],
-                   help="run only the dominant kernel at the middle-bond shape (for profiler captures)")
+    p.add_argument("--case", default=None, choices=["heff", "trunc", "tte"],
+                   help="heff / trunc: only that kernel at the middle-bond shape (for profiler captures); "
+                        "tte: time-to-eps of the mixed and the FP64 solver from the same random state")
+    p.add_argument("--ref-sweeps", type=int, default=10,
+                   help="--case tte: sweeps of the FP64 reference run")
     return p.parse_args()
 
 
@@ -502,12 +505,71 @@ def run_case_trunc(args):
     vtn.vtn_destroy(ctx)
 
 
+def run_case_tte(args):
+    """Time-to-eps on the split workload (M=24, d=8, chi=128): both solvers start from the
+    same seeded random MPS with the chi schedule 16, 32, 64, 128.  The FP64 solver runs
+    --ref-sweeps sweeps; E_ref is its last energy and eps = E_ref * 1e-8.  The mixed solver
+    (bf16x3 H_eff psi and environments) sweeps until its FP64 energy at a sweep boundary is
+    <= E_ref (1 + 1e-8), at most --ref-sweeps + 8 sweeps.  Times are the solver's own
+    per-sweep wall clock (MPO resident on the device), cumulated."""
+    import torch
+
+    from paper_2410_18740_gb300 import build as vbuild
+    from paper_2410_18740_gb300 import inputs, vtn
+
+    vbuild.build()
+    w = inputs.workload(WORKLOAD, args.seed)
+    ctx = vtn.vtn_create(0)
+    mpo = vtn.vtn_build_mpo(ctx, w.r, w.U, w.D, w.d)
+    sched = [16, 32, 64, CHI]
+
+    def run(prec, n_sweeps, e_target=None):
+        kw = dict(chi_max=CHI, n_sweeps=n_sweeps, seed=args.seed, lanczos_tol=1e-12, krylov_max=KRYLOV,
+                  lanczos_max_restarts=0, chi_schedule=sched, prec=prec)
+        if e_target is not None:
+            kw.update(e_target=e_target, use_e_target=1)
+        opts = vtn.vtn_sweep_opts_default(**kw)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, mps, rep = vtn.vtn_sweep(ctx, mpo, None, opts)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        vtn.vtn_mps_free(mps)
+        cum, out = 0.0, []
+        for e, sec in zip(rep["energy"], rep["seconds"]):
+            cum += sec
+            out.append((cum, e))
+        return out, wall
+
+    ref, wall64 = run(vtn.VTN_FP64, args.ref_sweeps)
+    e_ref = ref[-1][1]
+    target = e_ref * (1 + 1e-8)
+    mixed, wall16 = run(vtn.VTN_BF16X3, args.ref_sweeps + 8, target)
+    t64 = next((t for t, e in ref if e <= target), None)
+    t16 = next((t for t, e in mixed if e <= target), None)
+    line = {"case": "tte", "workload": f"{WORKLOAD}: M=24, r~U(0.5,1.0), Haar U, d=D=8, chi schedule {sched}, "
+                                      f"Lanczos {KRYLOV} steps/bond, seed {args.seed}",
+            "eps": "E_ref * 1e-8, E_ref = FP64 energy after the reference sweeps",
+            "e_ref": e_ref,
+            "ref_rel_change_last_sweep": abs(ref[-1][1] - ref[-2][1]) / abs(e_ref) if len(ref) > 1 else None,
+            "fp64": {"time_to_eps_s": t64, "sweeps": len(ref), "wall_s": wall64, "energies": [e for _, e in ref],
+                     "cum_seconds": [t for t, _ in ref]},
+            "mixed": {"time_to_eps_s": t16, "sweeps": len(mixed), "wall_s": wall16, "energies": [e for _, e in mixed],
+                      "cum_seconds": [t for t, _ in mixed]},
+            "speedup": (t64 / t16) if (t64 and t16) else None}
+    print(json.dumps(line), flush=True)
+    vtn.vtn_mpo_free(mpo)
+    vtn.vtn_destroy(ctx)
+
+
 def main():
     args = parse()
     if args.case == "heff":
         run_case_heff(args)
     elif args.case == "trunc":
         run_case_trunc(args)
+    elif args.case == "tte":
+        run_case_tte(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

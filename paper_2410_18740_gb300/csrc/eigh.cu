@@ -269,12 +269,11 @@ __global__ void __launch_bounds__(TP_THREADS) tri_phases(int n, EigSmall s) {
 //         the pending update applied; its norm gives the next reflector.
 // Data written by other CTAs is read with ld.global.cg (L2, not L1).
 struct GridBar {
-    unsigned int count;
-    unsigned int gen;   // bit 31: error
-    int error;          // read by the host
-    int pad;
+    unsigned int count;  // arrivals, monotonic over the launch
+    unsigned int pad0;
+    int error;           // set by a CTA whose wait timed out; read by the host
+    int pad1;
 };
-constexpr unsigned GEN_ERROR = 0x80000000u;
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -288,34 +287,37 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     return v;
 }
 
-// Grid barrier with a bounded wait: a CTA that waits more than 2 s sets the error bit of the
-// generation word (which releases every waiter) and bar->error; every CTA then returns false
-// and the kernel exits.
-__device__ bool grid_sync(GridBar* bar, unsigned int nblocks) {
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid barrier number `epoch` (0, 1, 2, ... in every CTA): each CTA adds its arrival to a
+// monotonic counter (fire-and-forget reduction) and polls it until it reaches
+// (epoch + 1) * nblocks (about 1.5 us for 152 CTAs on GB300; a CTA that releases the others
+// through a second word takes about 2.5 us).  Waits are bounded (2 s): a CTA that gives up
+// sets bar->error, which the other pollers check every 256 polls; all CTAs then return
+// false and the kernel exits.
+__device__ bool grid_sync(GridBar* bar, unsigned int nblocks, unsigned int epoch) {
     __shared__ int ok_sh;
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned g = ld_acquire_u32(&bar->gen);
         __threadfence();
-        const unsigned arrived = atomicAdd(&bar->count, 1u);
-        unsigned now = g;
-        if (arrived == nblocks - 1) {
-            atomicExch(&bar->count, 0u);
-            __threadfence();
-            now = atomicAdd(&bar->gen, 1u) + 1u;
-        } else {
-            const unsigned long long t0 = global_ns();
-            unsigned polls = 0;
-            while ((now = ld_acquire_u32(&bar->gen)) == g) {
-                if ((++polls & 1023u) == 0 && global_ns() - t0 > 2000000000ull) {
+        red_release_add(&bar->count, 1u);
+        const unsigned target = (epoch + 1u) * nblocks;
+        bool ok = true;
+        const unsigned long long t0 = global_ns();
+        unsigned polls = 0;
+        while (ld_acquire_u32(&bar->count) < target) {
+            if ((++polls & 255u) == 0) {
+                if (*(volatile int*)&bar->error != 0 || global_ns() - t0 > 2000000000ull) {
                     atomicExch(&bar->error, 1);
-                    now = atomicOr(&bar->gen, GEN_ERROR) | GEN_ERROR;
+                    ok = false;
                     break;
                 }
             }
         }
         __threadfence();
-        ok_sh = ((now | g) & GEN_ERROR) == 0;
+        ok_sh = ok ? 1 : 0;
     }
     __syncthreads();
     return ok_sh != 0;
@@ -382,16 +384,29 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_persistent(double2* __res
         // ---- reflector for column k from x = vcur (norm^2 a2)
         a2 = block_sum(a2, red);
         if (threadIdx.x == 0) {
+            // alpha = |x|, phi = x0 / |x0|: v0 = x0 + phi alpha, beta = -phi alpha,
+            // tau = 1 / (alpha (alpha + |x0|)); with few FP64 instructions (two reciprocal
+            // square roots, one division)
             const double2 x0 = vcur[0];
-            const double ax0 = hypot(x0.x, x0.y);
+            const double q0 = fma(x0.x, x0.x, x0.y * x0.y);
             double tau = 0.0;
             double2 beta = make_double2(0.0, 0.0);
             if (a2 > 0.0) {
-                const double alpha = sqrt(a2);
-                const double2 phi = ax0 > 0.0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
-                vcur[0] = make_double2(fma(phi.x, alpha, x0.x), fma(phi.y, alpha, x0.y));
-                tau = 1.0 / (alpha * (alpha + ax0));
-                beta = make_double2(-phi.x * alpha, -phi.y * alpha);
+                const double ra = rsqrt(a2);
+                const double alpha = a2 * ra;
+                double2 phia;  // phi * alpha
+                double ax0 = 0.0;
+                if (q0 > 0.0) {
+                    const double rq = rsqrt(q0);
+                    ax0 = q0 * rq;
+                    const double sc = alpha * rq;
+                    phia = make_double2(x0.x * sc, x0.y * sc);
+                } else {
+                    phia = make_double2(alpha, 0.0);
+                }
+                vcur[0] = make_double2(x0.x + phia.x, x0.y + phia.y);
+                tau = 1.0 / fma(alpha, ax0, a2);
+                beta = make_double2(-phia.x, -phia.y);
             }
             tau_sh = tau;
             if (blockIdx.x == 0) {
@@ -462,14 +477,18 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_persistent(double2* __res
             }
             colred[warp][lane] = make_double2(accx, accy);
             __syncthreads();
-            if (warp == 0) {
-                double sx = 0.0, sy = 0.0;
 #pragma unroll
-                for (int w = 0; w < TRI_NW; ++w) {
-                    sx += colred[w][lane].x;
-                    sy += colred[w][lane].y;
+            for (int h = TRI_NW / 2; h >= 2; h >>= 1) {  // tree over the warps' partials
+                if (warp < h) {
+                    const double2 o = colred[warp + h][lane];
+                    colred[warp][lane].x += o.x;
+                    colred[warp][lane].y += o.y;
                 }
-                if (col_ok) pk[(long long)cs * n + il] = make_double2(sx, sy);
+                __syncthreads();
+            }
+            if (warp == 0) {
+                const double2 a0 = colred[0][lane], a1 = colred[1][lane];
+                if (col_ok) pk[(long long)cs * n + il] = make_double2(a0.x + a1.x, a0.y + a1.y);
                 __threadfence();
             }
             __syncthreads();
@@ -496,11 +515,13 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_persistent(double2* __res
             }
             __syncthreads();  // colred and last_sh are reused by the next unit
         }
-        if (!grid_sync(bar, (unsigned)nb)) return;
+        if (!grid_sync(bar, (unsigned)nb, (unsigned)k)) return;
         // ---- C(k): K = (tau/2) Re(v^dag p); p parked in wprev (its old content is spent)
+        const bool next = k + 3 < n;  // another reflector follows
         double dot = 0.0;
         for (int t = threadIdx.x; t < m; t += blockDim.x) {
             const double2 p = __ldcg(&pfin[t]), v = vcur[t];
+            if (next && t >= 1) vprev[t - 1] = __ldcg(&A[(long long)(k + 1) * n + (k + 1 + t)]);  // row k+1, raw
             wprev[t] = p;
             if (t == 0) p0_sh = p;
             dot = fma(v.x, p.x, fma(v.y, p.y, dot));
@@ -513,15 +534,14 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_persistent(double2* __res
         double2* xnext = vprev;
         const double2 v0 = vnew[0];
         const double2 w0 = make_double2(fma(-K, v0.x, p0_sh.x), fma(-K, v0.y, p0_sh.y));
-        const bool next = k + 3 < n;  // another reflector follows
         a2 = 0.0;
         for (int t = threadIdx.x; t < m; t += blockDim.x) {
             const double2 p = wnew[t], v = vnew[t];
             const double2 w = make_double2(fma(-K, v.x, p.x), fma(-K, v.y, p.y));
             wnew[t] = w;
             if (next && t >= 1) {
-                // A(k+1): row k+1 with the pending update, x = conj(row)
-                double2 a = __ldcg(&A[(long long)(k + 1) * n + (k + 1 + t)]);
+                // A(k+1): row k+1 (prefetched into xnext) with the pending update, x = conj(row)
+                double2 a = xnext[t - 1];
                 a = sub_two_cmulc(a, v0, w, w0, v);
                 const double2 x = make_double2(a.x, -a.y);
                 xnext[t - 1] = x;
