@@ -50,9 +50,10 @@ WORKLOAD = "split"
 CHI = 128
 KRYLOV = 8
 N_SAMPLES = 256
-# DRAM bytes (read + write) per H_eff GEMM launch at the middle-bond shape, from the ncu
-# capture summarised in profiles/gemm_c64_heff_split_middle_bond.md (mean of the two launches)
-GEMM_F64_TRAFFIC = 0.5 * ((28.662272 + 344.848640) + (416.211968 + 13.693440)) * 1e6
+# DRAM bytes (read + write) per launch of the tcgen05 GEMM pair of H_eff psi at the middle
+# bond (ncu capture summarised in profiles/tc_gemm_heff_split_middle_bond.md): 181.2 MB and
+# 314.5 MB; their mean is the per-launch traffic figure of the bf16x3 roofline entry.
+TC_GEMM_TRAFFIC = 0.5 * ((32.556544 + 148.632320) + (311.492096 + 2.970624)) * 1e6
 
 
 def parse():
@@ -360,15 +361,17 @@ def run_native(args):
         peak, peak_src = fp64_peak_tflops()
         achieved = fl_heff / s_heff / 1e12 if s_heff > 0 else None
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": GEMM_F64_TRAFFIC,
-                "traffic_note": "ncu dram read+write per launch at the middle-bond shape",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "traffic_note": "no capture of the current FP64 GEMM at this shape",
                 "kernel": "gemm_c64_kernel (complex FP64 GEMM inside H_eff psi)", "launches": n_heff,
                 "peak_source": peak_src}
     else:
         peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
         achieved = fl_tc / s_tc / 1e12 if s_tc > 0 else None
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "frac": (achieved / peak) if achieved else None, "traffic": TC_GEMM_TRAFFIC,
+                "traffic_note": "ncu dram read+write per launch, mean of the middle-bond H_eff GEMM pair "
+                                "(algorithmic: 2 x 201 MB FP32 out + 302 MB packed operand in)",
                 "kernel": "tc_gemm_kernel (tcgen05 bf16 GEMM, TMEM accumulators, TMA tiles) in H_eff psi and the environment updates",
                 "launches": n_tc, "peak_source": f"{peaks_src} bf16 dense, sustained (kernel timed inside a long step)",
                 "useful_complex_tflops": fl_heff / s_heff / 1e12 if s_heff else None,
