@@ -2,14 +2,17 @@
 //   D[m][n] = sum_k A[m][k] * B[n][k]      (A: M x K, B: N x K, both K-major bf16)
 // accumulated in FP32 in tensor memory and written as FP32 or FP64.
 //
-// One CTA of 4 warps per 128 x 256 output tile:
+// Persistent kernel, one CTA of 6 warps per SM, looping over 128 x 256 output tiles:
 //   * warp 0, one lane: TMA producer -- cp.async.bulk.tensor loads of 128 x 64 (A) and
 //     256 x 64 (B) tiles with 128-byte swizzle into a 4-stage shared-memory ring, signalled
-//     through mbarrier transaction counts;
-//   * warp 1, one lane: MMA issuer -- four tcgen05.mma.kind::f16 (M=128, N=256, K=16) per
-//     stage into one TMEM accumulator, tcgen05.commit releases the stage;
-//   * warp 2 allocates / frees the 256 TMEM columns;
-//   * all 4 warps: epilogue -- tcgen05.ld of their 32 TMEM lanes, conversion, stores.
+//     through mbarrier transaction counts; the ring runs on across tiles;
+//   * warp 1: owns the 512 TMEM columns (two 256-column FP32 accumulators); one lane issues
+//     four tcgen05.mma.kind::f16 (M=128, N=256, K=16) per stage into the tile's accumulator,
+//     tcgen05.commit releases the stage and, after the last stage, hands the accumulator to
+//     the epilogue;
+//   * warps 2-5: epilogue -- tcgen05.ld of their 32 TMEM lanes, conversion, stores, then
+//     the accumulator goes back to the MMA warp; the epilogue of one tile overlaps the main
+//     loop of the next.
 // Every wait is bounded (1 s on %globaltimer); a wait that gives up sets the device status
 // word, and the CTA still frees its TMEM and exits.
 //
@@ -32,7 +35,7 @@ constexpr int A_TILE = BM * BK * 2;   // 16 KiB
 constexpr int B_TILE = BN * BK * 2;   // 32 KiB
 constexpr int STAGE_BYTES = A_TILE + B_TILE;
 constexpr int TMEM_COLS = 256;
-constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
+constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + 256;  // + barriers and the TMEM slot
 
 struct TcParams {
     int M, N, K;
@@ -40,7 +43,8 @@ struct TcParams {
     long long ldd;
     int d_fp64;
     int* status;
-    int kb_per;           // k-blocks per split (blockIdx.z selects the split)
+    int kb_per;           // k-blocks per split
+    int splits;           // work item t covers split t / (m tiles * n tiles)
     long long d_split;    // element stride between the per-split outputs (split-K partials)
 };
 
@@ -137,31 +141,44 @@ __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::aft
           "=r"(v[30]), "=r"(v[31])                                                                               \
         : "r"(taddr))
 
-__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
-                                                         const __grid_constant__ CUtensorMap tmB, TcParams p) {
+constexpr int TC_THREADS = 192;  // warp 0: TMA, warp 1: MMA + TMEM owner, warps 2-5: epilogue
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Persistent: CTA b takes work items b, b + gridDim.x, ...; item t = (split z, m tile, n tile).
+// The shared-memory ring's stage counter runs on across items; the two TMEM accumulators
+// alternate between items so that the epilogue of item i overlaps the MMAs of item i + 1.
+__global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                const __grid_constant__ CUtensorMap tmB, TcParams p) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + (size_t)STAGES * STAGE_BYTES);
     uint64_t* empty = full + STAGES;
-    uint64_t* done = empty + STAGES;
-    uint32_t* tmem_slot = (uint32_t*)(done + 1);
+    uint64_t* acc_full = empty + STAGES;   // [2] MMA -> epilogue
+    uint64_t* acc_empty = acc_full + 2;    // [2] epilogue -> MMA
+    uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int kb_begin = blockIdx.z * p.kb_per;
-    const int nkb = min(p.K / BK - kb_begin, p.kb_per);
+    const int tiles_n = (p.N + BN - 1) / BN, tiles_m = (p.M + BM - 1) / BM;
+    const int items = tiles_n * tiles_m * p.splits;
+    const int nkb_total = p.K / BK;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(done, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 4);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    if (warp == 2) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(TMEM_COLS));
+                     "r"(2 * TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     fence_before();
@@ -172,79 +189,110 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
 
     if (warp == 0) {
         if (lane == 0) {
-            for (int kb = 0; kb < nkb && ok; ++kb) {
-                const int s = kb % STAGES;
-                const uint32_t round = kb / STAGES;
-                if (kb >= STAGES) ok = mbar_wait(&empty[s], (round & 1) ^ 1, p.status);
-                if (!ok) break;
-                uint8_t* a_dst = smem + (size_t)s * STAGE_BYTES;
-                uint8_t* b_dst = a_dst + A_TILE;
-                mbar_expect_tx(&full[s], STAGE_BYTES);
-                tma_load_2d(a_dst, &tmA, &full[s], (kb_begin + kb) * BK, m0);
-                tma_load_2d(b_dst, &tmB, &full[s], (kb_begin + kb) * BK, n0);
+            uint32_t g = 0;  // stage counter over all items of this CTA
+            for (int t = blockIdx.x; t < items && ok; t += gridDim.x) {
+                const int nt = t % tiles_n, mt = (t / tiles_n) % tiles_m, z = t / (tiles_n * tiles_m);
+                const int kb0 = z * p.kb_per, nkb = min(nkb_total - kb0, p.kb_per);
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    const int s = g % STAGES;
+                    const uint32_t round = g / STAGES;
+                    if (g >= STAGES && !(ok = mbar_wait(&empty[s], (round & 1) ^ 1, p.status))) break;
+                    uint8_t* a_dst = smem + (size_t)s * STAGE_BYTES;
+                    mbar_expect_tx(&full[s], STAGE_BYTES);
+                    tma_load_2d(a_dst, &tmA, &full[s], (kb0 + kb) * BK, mt * BM);
+                    tma_load_2d(a_dst + A_TILE, &tmB, &full[s], (kb0 + kb) * BK, nt * BN);
+                }
             }
         }
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {
-            for (int kb = 0; kb < nkb && ok; ++kb) {
-                const int s = kb % STAGES;
-                const uint32_t round = kb / STAGES;
-                ok = mbar_wait(&full[s], round & 1, p.status);
-                if (!ok) break;
+            uint32_t g = 0;
+            int i = 0;  // item counter of this CTA
+            for (int t = blockIdx.x; t < items && ok; t += gridDim.x, ++i) {
+                const int z = t / (tiles_n * tiles_m);
+                const int kb0 = z * p.kb_per, nkb = min(nkb_total - kb0, p.kb_per);
+                const int acc = i & 1;
+                const uint32_t use = (uint32_t)i >> 1;
+                if (use >= 1 && !(ok = mbar_wait(&acc_empty[acc], (use & 1) ^ 1, p.status))) break;
                 fence_after();
-                const uint32_t a_addr = smem_u32(smem + (size_t)s * STAGE_BYTES);
-                const uint32_t b_addr = a_addr + A_TILE;
+                const uint32_t d_tmem = tmem + (uint32_t)(acc * TMEM_COLS);
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    const int s = g % STAGES;
+                    const uint32_t round = g / STAGES;
+                    if (!(ok = mbar_wait(&full[s], round & 1, p.status))) break;
+                    fence_after();
+                    const uint32_t a_addr = smem_u32(smem + (size_t)s * STAGE_BYTES);
+                    const uint32_t b_addr = a_addr + A_TILE;
 #pragma unroll
-                for (int k = 0; k < BK / 16; ++k) {
-                    mma_bf16(tmem, smem_desc(a_addr + 32 * k), smem_desc(b_addr + 32 * k), (kb | k) != 0 ? 1u : 0u);
+                    for (int k = 0; k < BK / 16; ++k)
+                        mma_bf16(d_tmem, smem_desc(a_addr + 32 * k), smem_desc(b_addr + 32 * k),
+                                 (kb | k) != 0 ? 1u : 0u);
+                    mma_commit(&empty[s]);
                 }
-                mma_commit(&empty[s]);
+                if (!ok) break;
+                mma_commit(&acc_full[acc]);
             }
-            mma_commit(done);
         }
         __syncwarp();
-    }
-
-    // ---------------- epilogue: all four warps, warp w owns TMEM lanes [32w, 32w + 32)
-    const bool acc_ready = mbar_wait(done, 0, p.status);
-    fence_after();
-    if (acc_ready) {
-        const int row = m0 + warp * 32 + lane;
-        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-        for (int c = 0; c < TMEM_COLS / 32; ++c) {
-            uint32_t v[32];
-            TC_LD32(lane_addr + c * 32, v);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (row < p.M) {
-                const int nbase = n0 + c * 32;
-                if (p.d_fp64) {
-                    double* out = (double*)p.D + blockIdx.z * p.d_split + (long long)row * p.ldd + nbase;
-                    if (nbase + 32 <= p.N && ((uintptr_t)out & 15) == 0) {
+    } else {
+        // ---------------- epilogue: warp w reads TMEM lanes [32 (w % 4), 32 (w % 4) + 32)
+        const int q = warp & 3;
+        int i = 0;
+        for (int t = blockIdx.x; t < items; t += gridDim.x, ++i) {
+            const int nt = t % tiles_n, mt = (t / tiles_n) % tiles_m, z = t / (tiles_n * tiles_m);
+            const int acc = i & 1;
+            const uint32_t use = (uint32_t)i >> 1;
+            if (!mbar_wait(&acc_full[acc], use & 1, p.status)) {
+                ok = false;
+                break;
+            }
+            fence_after();
+            const int row = mt * BM + q * 32 + lane;
+            const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * TMEM_COLS);
+            for (int c = 0; c < TMEM_COLS / 32; ++c) {
+                uint32_t v[32];
+                TC_LD32(lane_addr + c * 32, v);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (row < p.M) {
+                    const int nbase = nt * BN + c * 32;
+                    if (p.d_fp64) {
+                        double* out = (double*)p.D + z * p.d_split + (long long)row * p.ldd + nbase;
+                        if (nbase + 32 <= p.N && ((uintptr_t)out & 15) == 0) {
 #pragma unroll
-                        for (int i = 0; i < 32; i += 2)
-                            *(double2*)(out + i) = make_double2((double)__uint_as_float(v[i]), (double)__uint_as_float(v[i + 1]));
-                    } else {
-                        for (int i = 0; i < 32 && nbase + i < p.N; ++i) out[i] = (double)__uint_as_float(v[i]);
-                    }
-                } else {
-                    float* out = (float*)p.D + blockIdx.z * p.d_split + (long long)row * p.ldd + nbase;
-                    if (nbase + 32 <= p.N && ((uintptr_t)out & 15) == 0) {
+                            for (int j = 0; j < 32; j += 2)
+                                *(double2*)(out + j) =
+                                    make_double2((double)__uint_as_float(v[j]), (double)__uint_as_float(v[j + 1]));
+                        } else {
 #pragma unroll
-                        for (int i = 0; i < 32; i += 4)
-                            *(float4*)(out + i) = make_float4(__uint_as_float(v[i]), __uint_as_float(v[i + 1]),
-                                                              __uint_as_float(v[i + 2]), __uint_as_float(v[i + 3]));
+                            for (int j = 0; j < 32; ++j)
+                                if (nbase + j < p.N) out[j] = (double)__uint_as_float(v[j]);
+                        }
                     } else {
-                        for (int i = 0; i < 32 && nbase + i < p.N; ++i) out[i] = __uint_as_float(v[i]);
+                        float* out = (float*)p.D + z * p.d_split + (long long)row * p.ldd + nbase;
+                        if (nbase + 32 <= p.N && ((uintptr_t)out & 15) == 0) {
+#pragma unroll
+                            for (int j = 0; j < 32; j += 4)
+                                *(float4*)(out + j) = make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]),
+                                                                  __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j)
+                                if (nbase + j < p.N) out[j] = __uint_as_float(v[j]);
+                        }
                     }
                 }
             }
+            // this warp's lanes of the accumulator may be overwritten now
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[acc]);
         }
     }
     fence_before();
     __syncthreads();
-    if (warp == 2) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TMEM_COLS));
     }
 }
 
@@ -313,7 +361,7 @@ void tc_gemm_bf16(Ctx& ctx, const TcGemmArgs& a, int timing_class, double useful
     p.K = a.K;
     p.status = ctx.dstatus;
     dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, 1);
-    VTN_REQUIRE(grid.y <= 65535, "tensor-core GEMM M too large");
+    VTN_REQUIRE((long long)grid.x * grid.y * 8 < (1LL << 31), "tensor-core GEMM too large");
     // split K when the output tiles leave most SMs idle (fixed-order reduction afterwards)
     const int nkb = a.K / BK;
     const long long tiles = (long long)grid.x * grid.y;
@@ -337,11 +385,13 @@ void tc_gemm_bf16(Ctx& ctx, const TcGemmArgs& a, int timing_class, double useful
         p.d_fp64 = a.d_fp64 ? 1 : 0;
         p.d_split = 0;
     }
-    grid.z = splits;
+    p.splits = splits;
+    const long long items = tiles * splits;
+    const unsigned n_cta = (unsigned)std::min<long long>(items, std::max(ctx.num_sms, 1));
     const double flops = 2.0 * a.M * (double)a.N * a.K;
     int t0 = ctx.tbegin(TC_TC, flops);
     int t1 = timing_class >= 0 ? ctx.tbegin(timing_class, useful_flops) : -1;
-    tc_gemm_kernel<<<grid, 128, SMEM_BYTES, ctx.stream>>>(ma, mb, p);
+    tc_gemm_kernel<<<n_cta, TC_THREADS, SMEM_BYTES, ctx.stream>>>(ma, mb, p);
     ctx.count_launch();
     ctx.check_launch("tc_gemm_kernel");
     if (splits > 1) {
