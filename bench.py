@@ -15,9 +15,11 @@ value     = whole-step H_eff psi throughput: algorithmic flops of every H_eff ps
 e2e       = the same metric through the C ABI from host buffers: every step uploads the
             problem (r, U -> MPO) and the MPS from host memory and reads back the MPS,
             energy, marginals and samples.
-roofline  = the GEMM launches of the contractions (tcgen05 bf16 GEMM in H_eff psi and the
-            environment updates; FP64 complex GEMM in H_eff psi with --prec fp64), timed with
-            CUDA events on the library's stream during the timed steps.
+roofline  = the kernel that dominates the step's time, timed with CUDA events on the
+            library's stream during the timed steps: in the default mode the FP64 Householder
+            tridiagonalisation of the truncation (ALU-bound, 16/3 n^3 flops per launch); with
+            --prec fp64 the complex FP64 GEMMs of H_eff psi.  roofline_tensor_gemm = the same
+            figures for the tcgen05 GEMMs of H_eff psi and the environment updates.
 time_to_eps = from a seeded random MPS (chi schedule 16, 32, 64, 128): the FP64 solver runs
             --ref-sweeps sweeps and sets E_ref; value = the mixed solver's cumulative sweep
             time until its FP64 energy is <= E_ref (1 + 1e-8), beside the FP64 time to the
@@ -53,7 +55,10 @@ N_SAMPLES = 256
 # DRAM bytes (read + write) per launch of the tcgen05 GEMM pair of H_eff psi at the middle
 # bond (ncu capture summarised in profiles/tc_gemm_heff_split_middle_bond.md): 181.2 MB and
 # 314.5 MB; their mean is the per-launch traffic figure of the bf16x3 roofline entry.
-TC_GEMM_TRAFFIC = 0.5 * ((32.556544 + 148.632320) + (311.492096 + 2.970624)) * 1e6
+TC_GEMM_TRAFFIC = 0.5 * ((32.512000 + 145.623040) + (311.471872 + 3.002112)) * 1e6
+# DRAM bytes (read + write) of one tridiag_persistent launch at n = 1024 (ncu capture summarised
+# in profiles/truncation_eigensolver_n1024.md).
+TRI_TRAFFIC = (16.825088 + 3.555584) * 1e6
 
 
 def parse():
@@ -180,10 +185,15 @@ def load_peaks():
 
 
 def fp64_peak_tflops():
-    """FP64 FMA peak: the measured bf16 dense peak times the nominal FP64/bf16 ratio
-    (1.25 / 2250 TFLOP/s for GB300)."""
+    """FP64 FMA peak from unit counts and clock: every SM sub-partition issues one FP64 warp
+    instruction (32 FMAs) per 64 cycles (probe on the part), 4 sub-partitions per SM, 2 flops
+    per FMA: 4 flops per cycle per SM x SMs x the maximum SM clock."""
+    import torch
+
     peaks, src = load_peaks()
-    return peaks["bf16_tflops"] * (1.25 / 2250.0), f"{src} bf16 x nominal FP64/bf16 ratio"
+    sms = torch.cuda.get_device_properties(0).multi_processor_count if torch.cuda.is_available() else 152
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    return 4.0 * sms * mhz * 1e6 / 1e12, f"{sms} SMs x 4 sub-partitions x 32 FMA / 64 cycles x 2 x {mhz:.0f} MHz"
 
 
 def heff_flops(chi_l, chi_r, d, wl, wr):
@@ -309,6 +319,7 @@ def run_native(args):
     n_tc, fl_tc, s_tc = vtn.vtn_timing_read(ctx, "tc")
     n_mix, _, s_mix = vtn.vtn_timing_read(ctx, "mix")
     n_lz, _, s_lz = vtn.vtn_timing_read(ctx, "lanczos")
+    n_tri, fl_tri, s_tri = vtn.vtn_timing_read(ctx, "tridiag")
     vtn.vtn_timing(ctx, False)
     # ---------------- one FP64 sweep from the same state (mixed vs FP64)
     fp64 = None
@@ -357,25 +368,38 @@ def run_native(args):
     tte = None if args.no_tte else measure_tte(ctx, mpo, args.seed, args.ref_sweeps)
     # ---------------- report
     peaks, peaks_src = load_peaks()
+    fpeak, fpeak_src = fp64_peak_tflops()
+    tc_peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+    tc_ach = fl_tc / s_tc / 1e12 if s_tc > 0 else None
+    roof_tc = {"bound": "tensor", "achieved": tc_ach, "peak": tc_peak, "unit": "TFLOP/s",
+               "frac": (tc_ach / tc_peak) if tc_ach else None, "traffic": TC_GEMM_TRAFFIC,
+               "traffic_note": "ncu dram read+write per launch, mean of the middle-bond H_eff GEMM pair "
+                               "(algorithmic: 2 x 201 MB FP32 out + 302 MB packed operand in)",
+               "kernel": "tc_gemm_kernel (persistent tcgen05 bf16 GEMM, TMEM accumulators, TMA tiles) in H_eff psi "
+                         "and the environment updates",
+               "launches": n_tc, "seconds_per_step": s_tc / args.steps,
+               "peak_source": f"{peaks_src} bf16 dense, sustained (kernel timed inside a long step)",
+               "useful_complex_tflops": fl_heff / s_heff / 1e12 if s_heff else None,
+               "note": "bf16 flops executed = 3 split products x 4 real per complex multiply-add of the useful work"}
     if prec == vtn.VTN_FP64:
-        peak, peak_src = fp64_peak_tflops()
+        # the FP64 complex GEMMs of H_eff psi dominate the FP64-mode step
         achieved = fl_heff / s_heff / 1e12 if s_heff > 0 else None
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": None,
+        roof = {"bound": "alu", "achieved": achieved, "peak": fpeak, "unit": "TFLOP/s",
+                "frac": (achieved / fpeak) if achieved else None, "traffic": None,
                 "traffic_note": "no capture of the current FP64 GEMM at this shape",
                 "kernel": "gemm_c64_kernel (complex FP64 GEMM inside H_eff psi)", "launches": n_heff,
-                "peak_source": peak_src}
+                "seconds_per_step": s_heff / args.steps, "peak_source": fpeak_src}
     else:
-        peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
-        achieved = fl_tc / s_tc / 1e12 if s_tc > 0 else None
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": TC_GEMM_TRAFFIC,
-                "traffic_note": "ncu dram read+write per launch, mean of the middle-bond H_eff GEMM pair "
-                                "(algorithmic: 2 x 201 MB FP32 out + 302 MB packed operand in)",
-                "kernel": "tc_gemm_kernel (tcgen05 bf16 GEMM, TMEM accumulators, TMA tiles) in H_eff psi and the environment updates",
-                "launches": n_tc, "peak_source": f"{peaks_src} bf16 dense, sustained (kernel timed inside a long step)",
-                "useful_complex_tflops": fl_heff / s_heff / 1e12 if s_heff else None,
-                "note": "bf16 flops executed = 3 split products x 4 real per complex multiply-add of the useful work"}
+        # the Householder tridiagonalisation of the FP64 truncation dominates the mixed-mode step
+        achieved = fl_tri / s_tri / 1e12 if s_tri > 0 else None
+        roof = {"bound": "alu", "achieved": achieved, "peak": fpeak, "unit": "TFLOP/s",
+                "frac": (achieved / fpeak) if achieved else None, "traffic": TRI_TRAFFIC,
+                "traffic_note": "ncu dram read+write of one launch at n = 1024 (36 of the 46 launches per step "
+                                "have n = 1024): rho (16 MB) read once, the rest stays in L2",
+                "kernel": "tridiag_persistent (FP64 Householder tridiagonalisation of rho, one cooperative launch "
+                          "per truncation)",
+                "algorithmic": "16/3 n^3 real flops per launch (complex Hermitian n x n)",
+                "launches": n_tri, "seconds_per_step": s_tri / args.steps, "peak_source": fpeak_src}
     clk = clocks.summary()
     line = None
     if rank == 0:
@@ -399,6 +423,7 @@ def run_native(args):
                        "l2": "working set > L2 (environments, Krylov basis, H_eff intermediates ~1 GB)",
                        "parallelism": f"replicas x{ws}"},
             "roofline": roof,
+            "roofline_tensor_gemm": roof_tc if prec != vtn.VTN_FP64 else None,
             "fp64_compare": fp64,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -316,7 +316,8 @@ vtn_status vtn_gemm_bf16(vtn_ctx ctx, int M, int N, int K, const void* A, long l
  * the accumulated figures: launches, algorithmic flops and seconds per kernel class.
  * classes: 0 = complex GEMM (all), 1 = GEMMs inside H_eff psi, 2 = truncation eigensolver,
  * 3 = Lanczos vector kernels, 4 = W mixing, 5 = tensor-core GEMMs (bf16 flops executed;
- * class 1 counts their useful complex flops). */
+ * class 1 counts their useful complex flops), 6 = the Householder tridiagonalisation of the
+ * truncation (16/3 n^3 real flops per n x n Hermitian matrix). */
 vtn_status vtn_timing(vtn_ctx ctx, int enable);
 vtn_status vtn_timing_read(vtn_ctx ctx, int cls, long long* launches, double* flops, double* seconds);
 vtn_status vtn_timing_reset(vtn_ctx ctx);

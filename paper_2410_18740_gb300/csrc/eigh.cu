@@ -1091,8 +1091,11 @@ TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int dir
             double2* Hp = H;
             int nn = n;
             void* args[] = {&Ap, &nn, &Hp, &s, &tb, &bar};
+            // timing class: the standard 16/3 n^3 real flops of a complex Hermitian tridiagonalisation
+            const int ttri = ctx.tbegin(TC_TRI, 16.0 / 3.0 * (double)n * n * n);
             VTN_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)tridiag_persistent, dim3(grid), dim3(TRI_THREADS),
                                                      args, shm, ctx.stream));
+            ctx.tend(ttri);
             ctx.count_launch();
             ctx.check_launch("tridiag_persistent");
             done = true;

@@ -33,7 +33,7 @@ struct Error {
     } while (0)
 
 // ------------------------------------------------------------------ timing classes
-enum TimingClass { TC_GEMM = 0, TC_HEFF = 1, TC_EIG = 2, TC_LANCZOS = 3, TC_MIX = 4, TC_TC = 5, TC_COUNT = 6 };
+enum TimingClass { TC_GEMM = 0, TC_HEFF = 1, TC_EIG = 2, TC_LANCZOS = 3, TC_MIX = 4, TC_TC = 5, TC_TRI = 6, TC_COUNT = 7 };
 
 struct Ctx;
 

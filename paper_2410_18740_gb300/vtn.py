@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libvtn.so")
 VTN_OK, VTN_EINVAL, VTN_ENOMEM, VTN_ECUDA, VTN_ENOCONV, VTN_ETIMEOUT, VTN_EUNSUPPORTED = range(7)
 VTN_FP64, VTN_TF32X3, VTN_BF16X3 = 0, 1, 2
 VTN_FLAG_LBO = 1
-TIMING_CLASSES = {"gemm": 0, "heff": 1, "eig": 2, "lanczos": 3, "mix": 4, "tc": 5}
+TIMING_CLASSES = {"gemm": 0, "heff": 1, "eig": 2, "lanczos": 3, "mix": 4, "tc": 5, "tridiag": 6}
 STATUS_NAMES = {0: "VTN_OK", 1: "VTN_EINVAL", 2: "VTN_ENOMEM", 3: "VTN_ECUDA", 4: "VTN_ENOCONV",
                 5: "VTN_ETIMEOUT", 6: "VTN_EUNSUPPORTED"}
 
