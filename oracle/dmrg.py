@@ -173,6 +173,31 @@ def energy(mps, cores):
     return float(L[0, 0, 0].real) / norm2(mps)
 
 
+def env_left_h2(L2, A, W):
+    """Two-layer left environment of <psi|H H|psi> (Sec. "Assessing the error from finite bond
+    dimension": the variance of the variational state with respect to P H P):
+    L2'[c, b, l, k] = sum conj(A[i,u,l]) W[a,c,u,t] W[a',b,t,s] L2[a, a', i, j] A[j,s,k];
+    index a of L2 belongs to the H next to the bra, a' to the H next to the ket.  Evaluated
+    pairwise."""
+    T = np.einsum("xyij,jsk->xyisk", L2, A, optimize=True)
+    U = np.einsum("ybts,xyisk->xbitk", W, T, optimize=True)    # H next to the ket: s -> t
+    V = np.einsum("xcut,xbitk->cbiuk", W, U, optimize=True)    # H next to the bra: t -> u
+    return np.einsum("iul,cbiuk->cblk", A.conj(), V, optimize=True)
+
+
+def energy_variance(mps, cores):
+    """(E, <H^2>, sigma_H) with E = <psi|H|psi>/<psi|psi>, <H^2> = <psi|H H|psi>/<psi|psi> and
+    sigma_H = sqrt(max(0, <H^2> - E^2)) (Sec. "Assessing the error from finite bond
+    dimension"); H is the MPO's operator (the projected P H P)."""
+    L2 = np.ones((1, 1, 1, 1), dtype=np.complex128)
+    for A, W in zip(mps, cores):
+        L2 = env_left_h2(L2, A, W)
+    n2 = norm2(mps)
+    e = energy(mps, cores)
+    h2 = float(L2[0, 0, 0, 0].real) / n2
+    return e, h2, float(np.sqrt(max(0.0, h2 - e * e)))
+
+
 # ---------------------------------------------------------------- sweeps
 @dataclass
 class SweepReport:

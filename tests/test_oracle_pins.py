@@ -399,3 +399,57 @@ def test_lbo_marginals_mean_photon_number():
     pd = dense.marginals_from_vector(v0[:, 0], 3, 14, [1])
     p1 = observables.marginal(mps, isos, [1])
     assert np.abs(p1[:8] - pd[:8]).max() < 1e-4
+
+
+# ------------------------------------------------------------------ energy variance
+def _mps_to_vector(mps):
+    v = mps[0].reshape(-1, mps[0].shape[-1])
+    for A in mps[1:]:
+        v = (v @ A.reshape(A.shape[0], -1)).reshape(-1, A.shape[-1])
+    return v[:, 0]
+
+
+def _vector_to_mps(v, N, d):
+    """Exact MPS of a d^N vector by successive SVDs (no truncation)."""
+    sites, rest, cl = [], v.reshape(1, -1), 1
+    for s in range(N - 1):
+        U, S, Vh = np.linalg.svd(rest.reshape(cl * d, -1), full_matrices=False)
+        sites.append(U.reshape(cl, d, -1))
+        rest = (S[:, None] * Vh)
+        cl = U.shape[1]
+    sites.append(rest.reshape(cl, d, 1))
+    return sites
+
+
+@pytest.mark.parametrize("seed,M,d", [(0, 3, 3), (1, 4, 3), (2, 3, 4)])
+def test_energy_variance_matches_dense(seed, M, d):
+    """<H^2> by the two-layer environment contraction equals ||H v||^2 / ||v||^2 of the dense
+    vector of the same (non-canonical) MPS; E likewise; sigma_H > 0 off an eigenstate."""
+    w = inputs.workload("plain", seed, M=M, d=d, D=d)
+    G = gbs.hamiltonian_coefficients(w.r, w.U)
+    rng = inputs.rng_for(900 + seed)
+    dims = [1] + [min(5, d ** s, d ** (M - s)) for s in range(1, M)] + [1]
+    mps = [inputs.random_complex((dims[s], d, dims[s + 1]), rng) for s in range(M)]
+    v = _mps_to_vector(mps)
+    H = dense.dense_hamiltonian(G, d)
+    Hv = H @ v
+    n2 = np.vdot(v, v).real
+    e, h2, sig = dmrg.energy_variance(mps, mpo.build_mpo(G, d))
+    Hn = gbs.norm_bound(G, M, d)
+    assert abs(h2 - np.vdot(Hv, Hv).real / n2) <= 1e-12 * Hn * Hn
+    assert abs(e - np.vdot(v, Hv).real / n2) <= 1e-12 * Hn
+    assert sig > 1e-3
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_energy_variance_vanishes_on_the_ground_state(seed):
+    """The exact ground state (an eigenstate of P H P) has sigma_H = 0: <H^2> = E0^2."""
+    w = inputs.workload("plain", seed, M=3, d=4, D=4)
+    G = gbs.hamiltonian_coefficients(w.r, w.U)
+    e0, v0 = dense.ground_state(G, w.d)
+    mps = _vector_to_mps(v0[:, 0], w.M, w.d)
+    e, h2, sig = dmrg.energy_variance(mps, mpo.build_mpo(G, w.d))
+    Hn = gbs.norm_bound(G, w.M, w.d)
+    assert abs(e - e0[0]) <= 1e-12 * Hn
+    assert abs(h2 - e0[0] ** 2) <= 1e-12 * Hn * Hn
+    assert sig <= 1e-6 * Hn
