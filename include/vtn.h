@@ -195,6 +195,15 @@ vtn_status vtn_sweep(vtn_ctx ctx, vtn_mpo mpo, vtn_mps* state, const vtn_sweep_o
 /* <psi|H|psi> / <psi|psi> in FP64 by a full environment contraction (Eq. MagOfSimError). */
 vtn_status vtn_energy(vtn_ctx ctx, vtn_mpo mpo, vtn_mps mps, double* E);
 
+/* Energy variance of the variational state (Sec. "Assessing the error from finite bond
+ * dimension": sigma_H = sqrt(<(PHP)^2> - <PHP>^2), the compression-error estimate; sigma_H
+ * near 0 means the bond dimension is adequate).  Outputs (each may be NULL):
+ * E = <psi|H|psi>/<psi|psi>, H2 = <psi|H H|psi>/<psi|psi>, sigma = sqrt(max(0, H2 - E^2)),
+ * all FP64, H being the MPO's operator (the projected P H P).  Cost: two-layer environments of
+ * w_s^2 chi_s^2 complex per cut, 16 w^2 chi^3 d flops per site; returns VTN_EINVAL when the
+ * device buffers would exceed 24 GiB. */
+vtn_status vtn_energy_variance(vtn_ctx ctx, vtn_mpo mpo, vtn_mps mps, double* E, double* H2, double* sigma);
+
 /* Joint photon-number distribution of the k distinct modes `modes` in the Fock basis
  * (after the inverse basis transformation, Eq. InverseBasisTransformation):
  * out: double[D^k], index sum_j n_j D^(k-1-j) in the order of `modes`.  Normalised by

@@ -237,6 +237,32 @@ double energy_dev(Ctx& c, vtn_mpo mpo, vtn_mps mps) {
     return e / n2;
 }
 
+// (E, <H^2>) by the FP64 two-layer environment contraction, both divided by <psi|psi>
+std::pair<double, double> energy_h2_dev(Ctx& c, vtn_mpo mpo, vtn_mps mps) {
+    int wmax = 1;
+    for (int w : mpo->hp.w) wmax = std::max(wmax, w);
+    const int chi = max_dim(mps->dims);
+    const int d = mps->d;
+    const double env = (double)wmax * wmax * chi * chi;
+    const double na = (double)chi * d * chi;
+    const double bytes = 16.0 * (2.0 * env + 2.0 * (double)wmax * wmax * na);
+    VTN_REQUIRE(bytes <= 24.0 * (1ull << 30),
+                "energy variance: the two-layer environments would need more than 24 GiB of device memory");
+    double2* L0 = (double2*)c.workspace(WS_H2_ENV, sizeof(double2) * (size_t)(2 * env));
+    double2* L1 = L0 + (size_t)env;
+    double2* tv = (double2*)c.workspace(WS_X, sizeof(double2) * (size_t)((double)wmax * wmax * na));
+    double2* u = (double2*)c.workspace(WS_Y, sizeof(double2) * (size_t)((double)wmax * wmax * na));
+    set_scalar_one(c, L0);
+    for (int s = 0; s < mps->M; ++s) {
+        env_left2_dev(c, mpo->dcores[s], mps->dims[s], mps->dims[s + 1], L0, mps->sites[s], L1, tv, u);
+        std::swap(L0, L1);
+    }
+    const double h2 = read_scalar_re(c, L0);
+    const double n2 = mps_norm2(c, mps);
+    const double e = energy_dev(c, mpo, mps);
+    return {e, h2 / n2};
+}
+
 struct Envs {
     Ctx* c = nullptr;
     std::vector<double2*> L, R;
@@ -706,6 +732,23 @@ vtn_status vtn_sweep(vtn_ctx ctx, vtn_mpo mpo, vtn_mps* state, const vtn_sweep_o
             c.err = std::to_string(not_conv) + " Lanczos solves missed the tolerance";
             return VTN_ENOCONV;
         }
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_energy_variance(vtn_ctx ctx, vtn_mpo mpo, vtn_mps mps, double* E, double* H2, double* sigma) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(mpo && mps, "null argument");
+        Ctx& c = ctx->c;
+        use_device(c);
+        ensure_mpo_device(ctx, mpo);
+        check_mps_matches(mpo, mps);
+        const auto eh = energy_h2_dev(c, mpo, mps);
+        c.check_dstatus();
+        if (E) *E = eh.first;
+        if (H2) *H2 = eh.second;
+        if (sigma) *sigma = std::sqrt(std::max(0.0, eh.second - eh.first * eh.first));
         return VTN_OK;
     });
 }

@@ -175,4 +175,32 @@ void env_right_dev(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const doubl
     gemm_c64(ctx, g2);
 }
 
+// Two-layer left environment of <psi|H H|psi> (the energy variance):
+//   out[c][b][l][k] = sum conj(A[i,u,l]) W[a,c,u,t] W[a',b,t,s] L2[a][a'][i][j] A[j,s,k]
+// (index a: the H next to the bra; a': the H next to the ket).  T and V share the buffer
+// tv (max(w_l, w_r)^2 |A| complex), U uses u (w_l w_r |A|).
+void env_left2_dev(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const double2* L2, const double2* A,
+                   double2* out, double2* tv, double2* u) {
+    const int d = W.d, wl = W.wl, wr = W.wr;
+    const long long nA = (long long)chi_l * d * chi_r;
+    // T[a][a'][i][s k] = sum_j L2[a][a'][i][j] A[j][s k]
+    GemmArgs g1;
+    g1.M = wl * wl * chi_l; g1.N = d * chi_r; g1.K = chi_l;
+    g1.A = L2; g1.lda = chi_l;
+    g1.B = A; g1.ldb = (long long)d * chi_r;
+    g1.C = tv; g1.ldc = (long long)d * chi_r;
+    gemm_c64(ctx, g1);
+    // U[a][b][i][t][k] = sum_{a', s} W[a',b,t,s] T[a][a'][i][s][k]   (one mixing per a)
+    for (int a = 0; a < wl; ++a) mix_apply(ctx, W, true, chi_l, chi_r, tv + (long long)a * wl * nA, u + (long long)a * wr * nA);
+    // V[c][b][i][u][k] = sum_{a, t} W[a,c,u,t] U[a][b][i][t][k]   (p = (b, i))
+    mix_apply(ctx, W, true, wr * chi_l, chi_r, u, tv);
+    // out[c][b][l][k] = sum_{i u} conj(A[i u][l]) V[c][b][i u][k]
+    GemmArgs g2;
+    g2.M = chi_r; g2.N = chi_r; g2.K = chi_l * d; g2.batch = wr * wr;
+    g2.opA = OP_C; g2.A = A; g2.lda = chi_r; g2.sA_batch = 0;
+    g2.B = tv; g2.ldb = chi_r; g2.sB_batch = nA;
+    g2.C = out; g2.ldc = chi_r; g2.sC_batch = (long long)chi_r * chi_r;
+    gemm_c64(ctx, g2);
+}
+
 }  // namespace vtn

@@ -103,7 +103,7 @@ struct Ctx {
 enum WsSlot {
     WS_X = 0, WS_Y, WS_Z, WS_KRYLOV, WS_VEC_W, WS_VEC_T, WS_PARTIAL, WS_SCAL, WS_EIG_A, WS_EIG_H,
     WS_EIG_Y, WS_EIG_WORK, WS_EIG_U, WS_CORE_A, WS_CORE_B, WS_ENV_TMP, WS_MISC, WS_TC_L, WS_TC_R, WS_TC_B1,
-    WS_TC_A2, WS_TC_PART, WS_GEMM_SPLIT, WS_EIG_PART, WS_TC_ENV, WS_EIG_T, WS_COUNT
+    WS_TC_A2, WS_TC_PART, WS_GEMM_SPLIT, WS_EIG_PART, WS_TC_ENV, WS_EIG_T, WS_H2_ENV, WS_COUNT
 };
 
 // ------------------------------------------------------------------ cores
@@ -175,6 +175,8 @@ void heff_pack_envs(Ctx& ctx, const DevCore& Wi, const DevCore& Wj, int chi_l, i
                     const double2* R, HeffPacked& pk);
 void heff_apply_bf16x3(Ctx& ctx, const DevCore& Wi, const DevCore& Wj, const HeffPacked& pk, const double2* theta,
                        double2* y);
+void env_left2_dev(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const double2* L2, const double2* A,
+                   double2* out, double2* tv, double2* u);
 void env_left_bf16x3(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const double2* L, const double2* A,
                      double2* out);
 void env_right_bf16x3(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const double2* R, const double2* A,

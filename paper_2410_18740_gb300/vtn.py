@@ -88,6 +88,7 @@ _SIGS = {
     "vtn_sweep_opts_default": [C.POINTER(vtn_sweep_opts)],
     "vtn_sweep": [_P, _P, C.POINTER(_P), C.POINTER(vtn_sweep_opts), C.POINTER(vtn_sweep_report)],
     "vtn_energy": [_P, _P, _P, _PD],
+    "vtn_energy_variance": [_P, _P, _P, _PD, _PD, _PD],
     "vtn_marginals": [_P, _P, _P, _PI, _I, _PD],
     "vtn_marginals_all": [_P, _P, _P, _PD],
     "vtn_sample": [_P, _P, _P, C.c_uint64, _I, _PI],
@@ -346,6 +347,13 @@ def vtn_energy(ctx, mpo, mps):
     v = C.c_double()
     _check(ctx, lib().vtn_energy(ctx, mpo, mps, C.byref(v)))
     return v.value
+
+
+def vtn_energy_variance(ctx, mpo, mps):
+    """(E, <H^2>, sigma_H) of the MPS, FP64."""
+    e, h2, sg = C.c_double(), C.c_double(), C.c_double()
+    _check(ctx, lib().vtn_energy_variance(ctx, mpo, mps, C.byref(e), C.byref(h2), C.byref(sg)))
+    return e.value, h2.value, sg.value
 
 
 def vtn_marginals(ctx, mpo, mps, modes):

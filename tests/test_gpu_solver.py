@@ -254,3 +254,45 @@ def test_converged_mean_photon_number(ctx):
     assert err <= 5 * E          # observed: errors of observables scale like <H> (Fig. 4c)
     vtn.vtn_mps_free(mps)
     vtn.vtn_mpo_free(m)
+
+
+@pytest.mark.parametrize("seed,M,d,chi", [(0, 4, 4, 6), (1, 6, 3, 5), (2, 5, 5, 8)])
+def test_energy_variance_matches_oracle(ctx, seed, M, d, chi):
+    """<H^2> and sigma_H of the same random, non-canonical MPS: GPU two-layer environments
+    (centre-collapsed MPO) against the oracle's (w = 2N+2 MPO)."""
+    w = inputs.workload("split", seed, M=M, d=d, D=d)
+    G = gbs.hamiltonian_coefficients(w.r, w.U)
+    Hn = gbs.norm_bound(G, M, d)
+    m = vtn.vtn_build_mpo(ctx, w.r, w.U, w.D, w.d)
+    rng = inputs.rng_for(950 + seed)
+    dims = [1] + [min(chi, d ** s, d ** (M - s)) for s in range(1, M)] + [1]
+    sites = [inputs.random_complex((dims[s], d, dims[s + 1]), rng) for s in range(M)]
+    mps = vtn.vtn_mps_from_host(ctx, m, sites)
+    e, h2, sg = vtn.vtn_energy_variance(ctx, m, mps)
+    oe, oh2, osg = odmrg.energy_variance(sites, ompo.build_mpo(G, d))
+    assert abs(e - oe) <= 1e-10 * Hn
+    assert abs(h2 - oh2) <= 1e-10 * Hn * Hn
+    assert abs(sg - osg) <= 1e-8 * Hn
+    assert abs(e - vtn.vtn_energy(ctx, m, mps)) <= 1e-12 * Hn
+    vtn.vtn_mps_free(mps)
+    vtn.vtn_mpo_free(m)
+
+
+def test_energy_variance_of_the_converged_plain_state(ctx):
+    """Plain workload (exact at chi = 16): the converged state is an eigenstate of P H P to the
+    Lanczos tolerance, so sigma_H is tiny, while the seeded random start is far from one."""
+    w = inputs.workload("plain", 0)
+    G = gbs.hamiltonian_coefficients(w.r, w.U)
+    Hn = gbs.norm_bound(G, w.M, w.d)
+    m = vtn.vtn_build_mpo(ctx, w.r, w.U, w.D, w.d)
+    start = vtn.vtn_mps_random(ctx, m, 16, 5)
+    _, _, sg0 = vtn.vtn_energy_variance(ctx, m, start)
+    vtn.vtn_mps_free(start)
+    m2, mps, rep, st = solve(ctx, w, 16, 4, 100)
+    e, h2, sg = vtn.vtn_energy_variance(ctx, m2, mps)
+    assert sg <= 1e-5 * Hn
+    assert sg0 >= 1e-2
+    assert abs(e - rep["energy"][-1]) <= 1e-12 * Hn
+    vtn.vtn_mps_free(mps)
+    vtn.vtn_mpo_free(m2)
+    vtn.vtn_mpo_free(m)
