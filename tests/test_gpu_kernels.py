@@ -220,3 +220,29 @@ def test_kernel_calls_reject_bad_arguments(ctx):
     with pytest.raises(vtn.VtnError) as e:
         vtn.vtn_heff_apply(ctx, c, c, 1, 1, x, x, x, torch.zeros_like(x), prec=vtn.VTN_TF32X3)
     assert e.value.status == vtn.VTN_EUNSUPPORTED
+
+
+def test_truncation_at_the_large_workload_shape(ctx):
+    """Maximum size used by the solver: theta (512, 6, 6, 512) as at the middle bond of the
+    large workload (chi = 512, d = 6), n = 3072, k = 512.  Theta = U diag(s) V^dag is built with
+    a known SVD (Haar U, V; s_i = exp(-i / 300)), so the kept weights, the discarded weight and
+    the projected product are known without a CPU eigensolver."""
+    rng = inputs.rng_for(4242)
+    chi, d, k = 512, 6, 512
+    n = chi * d
+    U = inputs.haar_unitary(n, rng)
+    V = inputs.haar_unitary(n, rng)
+    s = np.exp(-np.arange(n) / 300.0)
+    s /= np.linalg.norm(s)
+    th = ((U * s) @ V.conj().T).reshape(chi, d, d, chi)
+    left = torch.empty((chi, d, k), dtype=torch.complex128, device="cuda")
+    right = torch.empty((k, d, chi), dtype=torch.complex128, device="cuda")
+    kk, lam, disc = vtn.vtn_truncate(ctx, chi, d, d, chi, 0, k, dev(th), left, right)
+    assert kk == k
+    assert np.abs(np.asarray(lam) - s[:k] ** 2).max() <= 1e-13
+    assert abs(disc - (s[k:] ** 2).sum()) <= 1e-12
+    Lm = host(left).reshape(n, k)
+    assert np.abs(Lm.conj().T @ Lm - np.eye(k)).max() < 1e-11
+    prod = Lm @ host(right).reshape(k, n)
+    expect = (U[:, :k] * s[:k]) @ V[:, :k].conj().T
+    assert np.abs(prod - expect).max() < 1e-11
