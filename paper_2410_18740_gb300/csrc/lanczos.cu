@@ -45,31 +45,39 @@ __device__ double block_sum(double v, double* sh) {
     return r;
 }
 
-// partial[blk][i] = sum over this block's elements of conj(V[i][e]) w[e], i in [g0, g0+cnt)
+// partial[blk][i] = sum over this block's elements of conj(V[i][e]) w[e], i in [g0, g0+cnt).
+// 4 FMAs per element and vector; the 2 * DOT_GROUP sums are reduced across the block by one
+// butterfly reduce-scatter per warp (lane l ends with value l) and one shared-memory pass.
 __global__ void __launch_bounds__(RB) multi_dot_partial(const double2* __restrict__ V, long long ld, int g0,
                                                         int cnt, const double2* __restrict__ w, long long n,
                                                         double2* __restrict__ partial, int nv_stride) {
-    __shared__ double sh[32];
-    double2 acc[DOT_GROUP];
+    static_assert(2 * DOT_GROUP <= 32, "one butterfly holds at most 32 values");
+    __shared__ double sh[RB / 32][32];
+    double v[32];
 #pragma unroll
-    for (int i = 0; i < DOT_GROUP; ++i) acc[i] = make_double2(0.0, 0.0);
+    for (int i = 0; i < 32; ++i) v[i] = 0.0;
     for (long long e = (long long)blockIdx.x * RB + threadIdx.x; e < n; e += (long long)gridDim.x * RB) {
         const double2 we = w[e];
 #pragma unroll
         for (int i = 0; i < DOT_GROUP; ++i) {
             if (i < cnt) {
-                double2 p = cmul_conj(V[(long long)(g0 + i) * ld + e], we);
-                acc[i].x += p.x;
-                acc[i].y += p.y;
+                const double2 a = V[(long long)(g0 + i) * ld + e];
+                v[2 * i] = fma(a.x, we.x, fma(a.y, we.y, v[2 * i]));          // Re conj(a) w
+                v[2 * i + 1] = fma(a.x, we.y, fma(-a.y, we.x, v[2 * i + 1]));  // Im conj(a) w
             }
         }
     }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    sh[wid][lane] = warp_reduce32(v);
+    __syncthreads();
+    if (wid == 0) {
+        double t = 0.0;
 #pragma unroll
-    for (int i = 0; i < DOT_GROUP; ++i) {
-        if (i >= cnt) break;
-        double re = block_sum(acc[i].x, sh);
-        double im = block_sum(acc[i].y, sh);
-        if (threadIdx.x == 0) partial[(long long)blockIdx.x * nv_stride + g0 + i] = make_double2(re, im);
+        for (int w2 = 0; w2 < RB / 32; ++w2) t += sh[w2][lane];
+        // lanes 2i, 2i+1 hold Re, Im of vector i
+        const double im = __shfl_down_sync(0xffffffffu, t, 1);
+        if ((lane & 1) == 0 && lane / 2 < cnt)
+            partial[(long long)blockIdx.x * nv_stride + g0 + lane / 2] = make_double2(t, im);
     }
 }
 
@@ -98,11 +106,11 @@ __global__ void __launch_bounds__(RB) multi_axpy_kernel(const double2* __restric
     __syncthreads();
     for (long long e = (long long)blockIdx.x * RB + threadIdx.x; e < n; e += (long long)gridDim.x * RB) {
         double2 acc = w[e];
-        for (int i = 0; i < nv; ++i) {
+        for (int i = 0; i < nv; ++i) {  // acc -= v c: 4 FMAs
             const double2 v = V[(long long)i * ld + e];
             const double2 ci = cs[i];
-            acc.x -= v.x * ci.x - v.y * ci.y;
-            acc.y -= v.x * ci.y + v.y * ci.x;
+            acc.x = fma(-v.x, ci.x, fma(v.y, ci.y, acc.x));
+            acc.y = fma(-v.x, ci.y, fma(-v.y, ci.x, acc.y));
         }
         w[e] = acc;
     }

@@ -14,6 +14,26 @@
 
 namespace vtn {
 
+#ifdef __CUDACC__
+// Sum over the 32 lanes of 32 values per lane (butterfly reduce-scatter): afterwards lane l
+// holds the warp total of value l.  31 additions per lane, all 32 lanes busy.
+__device__ __forceinline__ double warp_reduce32(double (&v)[32]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        const bool upper = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < off; ++i) {
+            const double send = upper ? v[i] : v[i + off];
+            const double keep = upper ? v[i + off] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+    return v[0];
+}
+#endif
+
+
 // ------------------------------------------------------------------ errors
 struct Error {
     vtn_status status;
