@@ -336,7 +336,6 @@ constexpr int TRI_UNROLL = 4;  // rows in flight per warp
 struct TriBufs {
     double2* part;      // [2][nb][n] partial products (double-buffered by step parity)
     double2* p;         // [2][n] p = tau A v
-    double2* z;         // [2][n] row k+1 less v0 conj(p): a'_t - v0 conj(p_t)
     unsigned* arrive;   // [2][TRI_MAX_CHUNKS] arrivals per column chunk (zero at launch)
 };
 
@@ -430,7 +429,6 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_persistent(double2* __res
         const int CS = max(1, min(nb / C, (m + TRI_NW - 1) / TRI_NW));
         double2* pk = tb.part + (long long)(k & 1) * nb * n;
         double2* pfin = tb.p + (long long)(k & 1) * n;
-        double2* pzk = tb.z + (long long)(k & 1) * n;
         unsigned* arrive = tb.arrive + (k & 1) * TRI_MAX_CHUNKS;
         for (int unit = (int)blockIdx.x; unit < C * CS; unit += nb) {
             const int c = unit % C, cs = unit / C;
@@ -511,18 +509,7 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_persistent(double2* __res
                             sy += pp.y;
                         }
                     }
-                    if (col_ok) {
-                        const double2 pv = make_double2(tau * sx, tau * sy);
-                        pfin[il] = pv;
-                        if (il >= 1) {
-                            // row k+1 at column k+1+il (its update of this step is complete: the
-                            // unit holding row k+1 has arrived) less v0 conj(p)
-                            const double2 a = __ldcg(&A[(long long)(k + 1) * n + (k + 1 + il)]);
-                            const double2 v0 = vcur[0];
-                            pzk[il] = make_double2(fma(-v0.x, pv.x, fma(-v0.y, pv.y, a.x)),
-                                                   fma(-v0.y, pv.x, fma(v0.x, pv.y, a.y)));
-                        }
-                    }
+                    if (col_ok) pfin[il] = make_double2(tau * sx, tau * sy);
                     if (lane == 0) arrive[c] = 0u;  // reused two steps later, after two barriers
                 }
             }
@@ -534,7 +521,7 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_persistent(double2* __res
         double dot = 0.0;
         for (int t = threadIdx.x; t < m; t += blockDim.x) {
             const double2 p = __ldcg(&pfin[t]), v = vcur[t];
-            if (next && t >= 1) vprev[t - 1] = __ldcg(&pzk[t]);  // row k+1 less v0 conj(p)
+            if (next && t >= 1) vprev[t - 1] = __ldcg(&A[(long long)(k + 1) * n + (k + 1 + t)]);  // row k+1, raw
             wprev[t] = p;
             if (t == 0) p0_sh = p;
             dot = fma(v.x, p.x, fma(v.y, p.y, dot));
@@ -547,19 +534,15 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_persistent(double2* __res
         double2* xnext = vprev;
         const double2 v0 = vnew[0];
         const double2 w0 = make_double2(fma(-K, v0.x, p0_sh.x), fma(-K, v0.y, p0_sh.y));
-        // row k+1 with the pending pair applied:
-        //   a - v0 conj(w_t) - w0 conj(v_t) = [a - v0 conj(p_t)] + (2 K v0 - p0) conj(v_t)
-        const double2 c1 = make_double2(fma(2.0 * K, v0.x, -p0_sh.x), fma(2.0 * K, v0.y, -p0_sh.y));
         a2 = 0.0;
         for (int t = threadIdx.x; t < m; t += blockDim.x) {
             const double2 p = wnew[t], v = vnew[t];
             const double2 w = make_double2(fma(-K, v.x, p.x), fma(-K, v.y, p.y));
             wnew[t] = w;
             if (next && t >= 1) {
-                // A(k+1): row k+1 with the pending update, x = conj(row)
+                // A(k+1): row k+1 (prefetched into xnext) with the pending update, x = conj(row)
                 double2 a = xnext[t - 1];
-                a.x = fma(c1.x, v.x, fma(c1.y, v.y, a.x));
-                a.y = fma(c1.y, v.x, fma(-c1.x, v.y, a.y));
+                a = sub_two_cmulc(a, v0, w, w0, v);
                 const double2 x = make_double2(a.x, -a.y);
                 xnext[t - 1] = x;
                 a2 = fma(x.x, x.x, fma(x.y, x.y, a2));
@@ -1078,12 +1061,11 @@ TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int dir
         // one CTA per SM: Phases A and C are redundant per CTA, so more CTAs per SM cost more
         int grid = std::min(ctx.num_sms, std::max(1, (n + 3) / 4));
         if (per_sm >= 1 && grid >= 1) {
-            const size_t part_bytes = sizeof(double2) * (2 * (size_t)grid * n + 4 * (size_t)n);
+            const size_t part_bytes = sizeof(double2) * (2 * (size_t)grid * n + 2 * (size_t)n);
             char* wsp = (char*)ctx.workspace(WS_EIG_PART, part_bytes + sizeof(unsigned) * 2 * TRI_MAX_CHUNKS);
             TriBufs tb;
             tb.part = (double2*)wsp;
             tb.p = tb.part + 2 * (size_t)grid * n;
-            tb.z = tb.p + 2 * (size_t)n;
             tb.arrive = (unsigned*)(wsp + part_bytes);
             VTN_CUDA_TRY(cudaMemsetAsync(tb.arrive, 0, sizeof(unsigned) * 2 * TRI_MAX_CHUNKS, ctx.stream));
             GridBar* bar = (GridBar*)(status + 4);
