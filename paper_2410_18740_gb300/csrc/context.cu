@@ -3,6 +3,10 @@
 #include <algorithm>
 #include <cstring>
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "vtn_internal.cuh"
 
 namespace vtn {
@@ -28,6 +32,16 @@ void Ctx::dfree(void* p) {
     if (!p) return;
     if (has_alloc) alloc.free(p, alloc.user);
     else cudaFree(p);
+}
+
+void set_smem_attr_once(const Ctx& ctx, const void* fn, int bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> done;
+    std::lock_guard<std::mutex> lock(mu);
+    int& have = done[{fn, ctx.device}];
+    if (have >= bytes) return;
+    VTN_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    have = bytes;
 }
 
 void* Ctx::workspace(int slot, size_t bytes) {

@@ -1050,12 +1050,7 @@ TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int dir
     bool done = false;
     if (n <= TRI_MAX_N) {
         const size_t shm = sizeof(double2) * 3 * (size_t)n;
-        static bool attr = false;
-        if (!attr) {
-            VTN_CUDA_TRY(cudaFuncSetAttribute(tridiag_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)(sizeof(double2) * 3 * TRI_MAX_N + 1024)));
-            attr = true;
-        }
+        set_smem_attr_once(ctx, (const void*)tridiag_persistent, (int)(sizeof(double2) * 3 * TRI_MAX_N + 1024));
         int per_sm = 0;
         VTN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tridiag_persistent, TRI_THREADS, shm));
         // one CTA per SM: Phases A and C are redundant per CTA, so more CTAs per SM cost more
@@ -1115,11 +1110,7 @@ TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int dir
     int* flag = status + 1;
     double* dinv = small + 13 * (size_t)n + 32;
     const size_t ts_shm = sizeof(double) * (size_t)k * 33;
-    static bool ts_attr = false;
-    if (!ts_attr) {
-        VTN_CUDA_TRY(cudaFuncSetAttribute(trsm_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        ts_attr = true;
-    }
+    set_smem_attr_once(ctx, (const void*)trsm_rows, 200 * 1024);
     VTN_REQUIRE(ts_shm <= 200 * 1024, "truncation keeps too many states for the orthonormalisation");
     const unsigned ts_grid = (unsigned)((n + 31) / 32);
     gram_kernel<<<gg, 256, 0, ctx.stream>>>(Z, n, k, G, 0.0, nullptr, 0);
@@ -1143,11 +1134,7 @@ TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int dir
     //    one vector per CTA (the FP64 work spreads over the SMs)
     const size_t shm = sizeof(double2) * (size_t)n;
     const int nbt = k;
-    static bool attr_set = false;
-    if (!attr_set) {
-        VTN_CUDA_TRY(cudaFuncSetAttribute(backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        attr_set = true;
-    }
+    set_smem_attr_once(ctx, (const void*)backtransform, 200 * 1024);
     const int nblk = n >= 3 ? (n - 2 + BT_NB - 1) / BT_NB : 0;
     double2* Tall = (double2*)ctx.workspace(WS_EIG_T, sizeof(double2) * (size_t)std::max(nblk, 1) * BT_NB * BT_NB);
     if (nblk > 0) {

@@ -246,11 +246,7 @@ void fill_random_normal(Ctx& ctx, double2* out, long long count, uint64_t seed, 
 void orthonormalize_rows(Ctx& ctx, double2* A, int rows, int cols) {
     VTN_REQUIRE(rows <= 4096 && rows <= cols, "row orthonormalisation needs rows <= min(cols, 4096)");
     const size_t shm = sizeof(double2) * (size_t)std::max(rows, 1);
-    static bool attr = false;
-    if (!attr) {
-        VTN_CUDA_TRY(cudaFuncSetAttribute(orth_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
-        attr = true;
-    }
+    set_smem_attr_once(ctx, (const void*)orth_rows_kernel, 64 * 1024);
     orth_rows_kernel<<<1, 1024, shm, ctx.stream>>>(A, rows, cols);
     ctx.count_launch();
     ctx.check_launch("orth_rows_kernel");
@@ -290,11 +286,7 @@ void sample_dev(Ctx& ctx, const double2* const* AF_dev, const double2* const* ER
     a.out = out_dev;
     const size_t shm = sizeof(double2) * (size_t)chi_max * (1 + D) + sizeof(double) * D;
     VTN_REQUIRE(shm <= 200 * 1024, "sampler working set exceeds shared memory (chi_max * (D + 1) too large)");
-    static bool attr = false;
-    if (!attr) {
-        VTN_CUDA_TRY(cudaFuncSetAttribute(sample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        attr = true;
-    }
+    set_smem_attr_once(ctx, (const void*)sample_kernel, 200 * 1024);
     sample_kernel<<<n_samples, 256, shm, ctx.stream>>>(a);
     ctx.count_launch();
     ctx.check_launch("sample_kernel");

@@ -348,11 +348,7 @@ void tc_gemm_bf16(Ctx& ctx, const TcGemmArgs& a, int timing_class, double useful
                 "tensor-core GEMM needs 16-byte aligned row strides");
     VTN_REQUIRE(((uintptr_t)a.A % 16) == 0 && ((uintptr_t)a.B % 16) == 0, "TMA operands must be 16-byte aligned");
     VTN_REQUIRE(ctx.dstatus != nullptr, "context has no device status word");
-    static bool attr = false;
-    if (!attr) {
-        VTN_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
-        attr = true;
-    }
+    set_smem_attr_once(ctx, (const void*)tc_gemm_kernel, (int)SMEM_BYTES);
     CUtensorMap ma = make_map(a.A, a.M, a.K, a.lda, BM);
     CUtensorMap mb = make_map(a.B, a.N, a.K, a.ldb, BN);
     TcParams p;

@@ -149,6 +149,10 @@ struct GemmArgs {
 void mirror_lower_to_upper(Ctx& ctx, double2* C, int n, long long ldc);
 void gemm_c64(Ctx& ctx, const GemmArgs& g, int timing_class = TC_GEMM);
 
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize, bytes) for kernel fn on the context's
+// device, once per (kernel, device) (the attribute is per device); thread-safe.
+void set_smem_attr_once(const Ctx& ctx, const void* fn, int bytes);
+
 // ------------------------------------------------------------------ tensor-core GEMM (bf16 -> fp32)
 // D[m][n] = sum_k A[m][k] B[n][k]; A: M x K, B: N x K (K-major bf16, K % 64 == 0); D fp32/fp64
 struct TcGemmArgs {
