@@ -24,6 +24,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include "vtn_internal.cuh"
 
@@ -313,7 +314,11 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeTiledFn encode_fn() {
+    // resolved once per process (thread-safe static initialisation); a failed lookup is
+    // retried on the next call
+    static std::mutex mu;
     static EncodeTiledFn fn = nullptr;
+    std::lock_guard<std::mutex> lock(mu);
     if (!fn) {
         void* p = nullptr;
         cudaDriverEntryPointQueryResult q;
