@@ -238,6 +238,35 @@ def test_split_workload_full_size_properties(ctx):
     vtn.vtn_mpo_free(m)
 
 
+def test_split_workload_full_size_bf16x3(ctx):
+    """The benchmark's own mode at full size (M=24, d=8, chi=128, bf16x3 H_eff psi and
+    environments, 8 Lanczos steps per bond, no restarts): the state it produces is checked by
+    the oracle's FP64 energy of that state and by its marginals on sampled modes; the sweep's
+    reported energy is the FP64 energy; the kept sites are isometries (right-canonical)."""
+    w = inputs.workload("split", 100)
+    G = gbs.hamiltonian_coefficients(w.r, w.U)
+    Hn = gbs.norm_bound(G, w.M, w.d)
+    m = vtn.vtn_build_mpo(ctx, w.r, w.U, w.D, w.d)
+    opts = vtn.vtn_sweep_opts_default(chi_max=128, n_sweeps=1, seed=1, lanczos_tol=1e-12, krylov_max=8,
+                                      lanczos_max_restarts=0, chi_schedule=[128], prec=vtn.VTN_BF16X3)
+    st, mps, rep = vtn.vtn_sweep(ctx, m, None, opts)
+    assert st in (vtn.VTN_OK, vtn.VTN_ENOCONV)
+    E = vtn.vtn_energy(ctx, m, mps)
+    assert abs(rep["energy"][-1] - E) <= 1e-12 * Hn
+    assert E >= -1e-10 * Hn
+    sites = gpu_sites(ctx, mps)
+    assert abs(odmrg.energy(sites, ompo.build_mpo(G, w.d)) - E) <= 1e-10 * Hn
+    for A in sites[1:]:
+        Am = A.reshape(A.shape[0], -1)
+        assert np.abs(Am @ Am.conj().T - np.eye(A.shape[0])).max() < 1e-10
+    marg = vtn.vtn_marginals_all(ctx, m, mps)
+    assert np.all(marg >= -1e-12) and np.abs(marg.sum(axis=1) - 1).max() < 1e-10
+    for i in (0, 12, 23):
+        assert np.abs(marg[i] - oobs.marginal(sites, None, [i])).max() <= 1e-9
+    vtn.vtn_mps_free(mps)
+    vtn.vtn_mpo_free(m)
+
+
 def test_converged_mean_photon_number(ctx):
     """Converged solve: Fock-basis <n_i> from the marginals agree with the covariance closed
     form (V_xx + V_pp)/2 - 1/2.  Rigorous bound: |d<n>| <= 2 (d-1) sqrt(1-F) with
