@@ -59,6 +59,9 @@ TC_GEMM_TRAFFIC = 0.5 * ((32.512000 + 145.623040) + (311.471872 + 3.002112)) * 1
 # DRAM bytes (read + write) of one tridiag_persistent launch at n = 1024 (ncu capture summarised
 # in profiles/truncation_eigensolver_n1024.md).
 TRI_TRAFFIC = (16.825088 + 3.555584) * 1e6
+# DRAM bytes (read + write) per launch of the FP64 complex GEMM pair of H_eff psi at the middle
+# bond (profiles/gemm_c64_heff_split_middle_bond.md), mean of the two launches.
+GEMM_F64_TRAFFIC = 0.5 * ((30.710272 + 345.032960) + (416.077056 + 13.165824)) * 1e6
 
 
 def parse():
@@ -385,8 +388,8 @@ def run_native(args):
         # the FP64 complex GEMMs of H_eff psi dominate the FP64-mode step
         achieved = fl_heff / s_heff / 1e12 if s_heff > 0 else None
         roof = {"bound": "alu", "achieved": achieved, "peak": fpeak, "unit": "TFLOP/s",
-                "frac": (achieved / fpeak) if achieved else None, "traffic": None,
-                "traffic_note": "no capture of the current FP64 GEMM at this shape",
+                "frac": (achieved / fpeak) if achieved else None, "traffic": GEMM_F64_TRAFFIC,
+                "traffic_note": "ncu dram read+write per launch, mean of the middle-bond H_eff GEMM pair",
                 "kernel": "gemm_c64_kernel (complex FP64 GEMM inside H_eff psi)", "launches": n_heff,
                 "seconds_per_step": s_heff / args.steps, "peak_source": fpeak_src}
     else:
