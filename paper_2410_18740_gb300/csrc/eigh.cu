@@ -8,7 +8,8 @@
 //     p = tau A v, w = p - (tau/2)(v^dag p) v, A <- A - v w^dag - w v^dag.  The complex
 //     sub-diagonal is made real by a diagonal phase similarity.
 //  3. The k largest eigenvalues of the real tridiagonal by bisection on Sturm counts,
-//     one warp per eigenvalue evaluating 32 points per round (multisection).
+//     one CTA per eigenvalue evaluating 128 points per round (multisection), to an
+//     absolute accuracy of 2 u |T|.
 //  4. Eigenvectors by inverse iteration with a pivoted tridiagonal LU, one thread per
 //     eigenvector, three iterations from deterministic pseudo-random starts.
 //  5. Orthonormalisation of the k vectors: one Cholesky-QR pass when they are already
@@ -610,30 +611,44 @@ __device__ int sturm(const double* a, const double* bsq, int n, double x, double
     return cnt;
 }
 
-// one warp per eigenvalue; output j (descending) = ascending index n-1-j
-__global__ void __launch_bounds__(32) bisect_top(int n, int k, EigSmall s) {
+// One CTA of BIS_THREADS threads per eigenvalue; output j (descending) = ascending index
+// n-1-j.  Each round evaluates BIS_THREADS Sturm counts at equally spaced interior points of
+// [lo, hi] (one per thread, the warps on different SM sub-partitions) and keeps the
+// subinterval that holds the eigenvalue: its upper end is the first point whose count
+// reaches idx+1.  Stop at an absolute width of 2 u |T| (+ pivmin terms): the eigenvalues of
+// the tridiagonal carry no more accuracy than the u |rho| of its computation.
+constexpr int BIS_THREADS = 128;
+
+__global__ void __launch_bounds__(BIS_THREADS) bisect_top(int n, int k, EigSmall s) {
+    __shared__ int first_sh[BIS_THREADS / 32];
     const int j = blockIdx.x;
     if (j >= k) return;
     const int idx = n - 1 - j;
-    const int lane = threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const double gl = s.scal[4], gu = s.scal[5], tn = s.scal[6];
     const double pivmin = fmax(1e-300, EPS * EPS * fmax(tn, 1e-300));
+    const double width = 2.0 * EPS * fmax(tn, 1e-300) + 4.0 * pivmin;
     double lo = gl - EPS * tn - pivmin, hi = gu + EPS * tn + pivmin;
     for (int round = 0; round < 64; ++round) {
-        if (hi - lo <= 2.0 * EPS * fmax(fabs(lo), fabs(hi)) + 4.0 * pivmin) break;
-        const double step = (hi - lo) / 33.0;
-        const double x = lo + step * (lane + 1);
+        if (hi - lo <= width) break;
+        const double step = (hi - lo) / (double)(BIS_THREADS + 1);
+        const double x = lo + step * (threadIdx.x + 1);
         const int c = sturm(s.diag, s.bsq, n, x, pivmin);
         const unsigned bal = __ballot_sync(0xffffffffu, c >= idx + 1);
-        if (bal == 0) {
-            lo = lo + step * 32;
+        if (lane == 0) first_sh[warp] = bal ? warp * 32 + __ffs(bal) - 1 : BIS_THREADS;
+        __syncthreads();
+        int f = BIS_THREADS;
+#pragma unroll
+        for (int w = 0; w < BIS_THREADS / 32; ++w) f = min(f, first_sh[w]);
+        __syncthreads();  // first_sh is rewritten next round
+        if (f == BIS_THREADS) {
+            lo = lo + step * BIS_THREADS;
         } else {
-            const int f = __ffs(bal) - 1;
             hi = lo + step * (f + 1);
             lo = lo + step * f;
         }
     }
-    if (lane == 0) s.lam[j] = 0.5 * (lo + hi);
+    if (threadIdx.x == 0) s.lam[j] = 0.5 * (lo + hi);
 }
 
 __device__ __forceinline__ double hash_uniform(unsigned i, unsigned j) {
@@ -1096,7 +1111,7 @@ TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int dir
     ctx.count_launch();
     ctx.check_launch("tridiagonalisation");
     // 3. eigenvalues
-    bisect_top<<<k, 32, 0, ctx.stream>>>(n, k, s);
+    bisect_top<<<k, BIS_THREADS, 0, ctx.stream>>>(n, k, s);
     // 4. eigenvectors of the real tridiagonal
     inverse_iteration<<<(k + 127) / 128, 128, 0, ctx.stream>>>(n, k, s, work, piv, Z);
     ctx.count_launch(2);
