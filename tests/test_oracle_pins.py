@@ -453,3 +453,53 @@ def test_energy_variance_vanishes_on_the_ground_state(seed):
     assert abs(e - e0[0]) <= 1e-12 * Hn
     assert abs(h2 - e0[0] ** 2) <= 1e-12 * Hn * Hn
     assert sig <= 1e-6 * Hn
+
+
+# ------------------------------------------------------------------ non-Gaussian (global CZ) workload
+from oracle import nongauss  # noqa: E402
+
+
+@pytest.mark.parametrize("seed,N,d,kappa", [(0, 3, 3, 0.3), (1, 4, 3, 0.2), (2, 3, 4, 0.5), (3, 2, 4, 0.7)])
+def test_nongauss_expansion_and_mpo_match_definition(seed, N, d, kappa):
+    """P H P of Eq. nonGBSHamiltonian three ways: from its definition (R' = (X, P + xi) as
+    padded-space operators, products as written, then restricted), from the term expansion,
+    and from the FSM MPO contracted to a matrix."""
+    w = inputs.workload("plain", seed, M=N, d=d, D=d)
+    G = gbs.hamiltonian_coefficients(w.r, w.U)
+    Hdef = nongauss.hamiltonian_definition(G, d, kappa).toarray()
+    Hexp = nongauss.dense_hamiltonian(G, d, kappa).toarray()
+    Hmpo = mpo.contract_dense(nongauss.build_mpo(G, d, kappa))
+    scale = np.abs(Hdef).max()
+    assert np.abs(Hdef - Hdef.conj().T).max() <= 1e-14 * scale
+    assert np.abs(Hexp - Hdef).max() <= 1e-13 * scale
+    assert np.abs(Hmpo - Hdef).max() <= 1e-13 * scale
+
+
+def test_nongauss_kappa_zero_is_gbs():
+    w = inputs.workload("plain", 0, M=3, d=4, D=4)
+    G = gbs.hamiltonian_coefficients(w.r, w.U)
+    H0 = nongauss.hamiltonian_definition(G, 4, 0.0).toarray()
+    assert np.abs(H0 - dense.dense_hamiltonian(G, 4).toarray()).max() < 1e-13
+
+
+def test_nongauss_transformed_gaussian_state_has_zero_energy():
+    """exp(-i kappa X1 X2 X3) applied to the Gaussian state (Eq. GlobalCZgate) is the zero-energy
+    state of Eq. nonGBSHamiltonian: its <H> falls geometrically with the Fock cutoff, while the
+    same state has O(kappa^2) energy under the Hamiltonian with the sign of xi flipped."""
+    import scipy.linalg as sla
+    w = inputs.workload("plain", 4, M=3, r_lo=0.15, r_hi=0.25)
+    G = gbs.hamiltonian_coefficients(w.r, w.U)
+    kappa = 0.1
+    es = []
+    for D in (6, 8, 10):
+        _, v0 = dense.ground_state(G, D)
+        X = gbs.local_ops(D)["X"]
+        psi = sla.expm(-1j * kappa * np.kron(np.kron(X, X), X)) @ v0[:, 0]
+        H = nongauss.hamiltonian_definition(G, D, kappa)
+        es.append(np.vdot(psi, H @ psi).real / np.vdot(psi, psi).real)
+        if D == 10:
+            Hm = nongauss.hamiltonian_definition(G, D, -kappa)
+            e_wrong = np.vdot(psi, Hm @ psi).real / np.vdot(psi, psi).real
+    assert es[0] > es[1] > es[2] > 0
+    assert es[2] < 1e-7
+    assert e_wrong > 1e3 * es[2] and e_wrong > 1e-4
