@@ -110,6 +110,19 @@ vtn_status vtn_launch_count(vtn_ctx ctx, long long* out);
  * bond dimension w_s = 2 min(s, M - s) + 2 inside, 1 at the ends. */
 vtn_status vtn_build_mpo(vtn_ctx ctx, int M, const double* r, const double* U,
                          int D, int d, unsigned flags, vtn_mpo* out);
+
+/* Build the MPO of the non-Gaussian workload of Sec. "Beyond GBS: fully connected CZ-gate":
+ * |psi> = exp(-i kappa prod_k X_k)|psi_G> (Eq. GlobalCZgate) for the Gaussian state of
+ * (r, U), whose parent Hamiltonian (Eq. nonGBSHamiltonian, zero means) is
+ * H = R'^T (V^-1/4) R' - N/2 with R' = (X, P + xi), xi_i = kappa prod_{n != i} X_n.
+ * Fock basis only (the local dimension is D; no optimal local basis); M >= 2; r, U, D
+ * validated as for vtn_build_mpo; kappa finite (kappa = 0 gives the GBS MPO).  Same-mode
+ * products are exactly projected.  The MPO is the Gaussian one with, at every inner cut s,
+ * 4 + 4s channels appended for the kappa and kappa^2 terms (full-chain products of X or X^2
+ * with at most two special modes).  Everything else (vtn_sweep, vtn_energy, marginals,
+ * sampling, vtn_energy_variance) accepts the result like any MPO. */
+vtn_status vtn_build_mpo_cz(vtn_ctx ctx, int M, const double* r, const double* U, int D, double kappa,
+                            vtn_mpo* out);
 vtn_status vtn_mpo_free(vtn_mpo mpo);
 /* Shape queries: M, d, D and the bond dimensions w[0..M] (w may be NULL). */
 vtn_status vtn_mpo_info(vtn_mpo mpo, int* M, int* d, int* D, int* w);

@@ -374,6 +374,31 @@ vtn_status vtn_build_mpo(vtn_ctx ctx, int M, const double* r, const double* U, i
     });
 }
 
+vtn_status vtn_build_mpo_cz(vtn_ctx ctx, int M, const double* r, const double* U, int D, double kappa,
+                            vtn_mpo* out) {
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(out && r && U, "null argument");
+        vtn_mpo mpo = new vtn_mpo_s();
+        std::string err = build_problem_cz(M, r, U, D, kappa, mpo->hp);
+        if (!err.empty()) {
+            delete mpo;
+            throw Error{VTN_EINVAL, err};
+        }
+        if (ctx) {
+            try {
+                use_device(ctx->c);
+                ensure_mpo_device(ctx, mpo);
+            } catch (...) {
+                for (auto& dc : mpo->dcores) free_core(ctx->c, dc);
+                delete mpo;
+                throw;
+            }
+        }
+        *out = mpo;
+        return VTN_OK;
+    });
+}
+
 vtn_status vtn_mpo_free(vtn_mpo mpo) {
     if (!mpo) return VTN_EINVAL;
     if (mpo->owner) {

@@ -340,4 +340,93 @@ std::string build_problem(int M, const double* r, const double* U, int D, int d,
     return "";
 }
 
+// ------------------------------------------------------------------------------------
+// Non-Gaussian workload (Sec. "Beyond GBS: fully connected CZ-gate", Eqs. GlobalCZgate,
+// nonGBSHamiltonian): H = R'^T G R' - N/2 with R' = (X, P + xi), xi_i = kappa Xi_i,
+// Xi_i = prod_{n != i} X_n.  Expanded with G symmetric:
+//   H = H_G + kappa sum_{a,i} G_{a p_i} (R_a Xi_i + Xi_i R_a) + kappa^2 sum_{i,j} G_{p_i p_j} Xi_i Xi_j,
+// every term a product over all modes of one exactly projected single-mode operator (the
+// bulk X for the kappa terms, X^2 for the kappa^2 terms, and at most two special modes).
+// The MPO is the Gaussian one with extra channels appended at every inner cut s:
+//   +0 bulk-X so far, +1 kappa term complete (bulk X continues), +2 bulk-X^2 so far,
+//   +3 kappa^2 term complete (bulk X^2 continues), +4+3f+t first special of type t
+//   (I, X^2, XP+PX) at site f < s (bulk X), +4+3s+f first special X at site f < s (bulk X^2).
+// A pair's coefficient is applied at its second special site; at cut 0 the bulk states are
+// the Gaussian start channel and at cut M every complete term lands in the final channel.
+std::string build_problem_cz(int M, const double* r, const double* U, int D, double kappa, HostProblem& out) {
+    if (!std::isfinite(kappa)) return "non-finite kappa";
+    if (M < 2) return "the global CZ workload needs M >= 2";
+    HostProblem P;
+    std::string e = build_problem(M, r, U, D, D, false, P);
+    if (!e.empty()) return e;
+    P.kappa = kappa;
+    const int d = D, n2 = 2 * M;
+    if (kappa == 0.0) {
+        out = std::move(P);
+        return "";
+    }
+    const LocalOps ops = make_local_ops(d);
+    auto g = [&](int a, int b) { return P.G[(size_t)a * n2 + b]; };
+    const std::vector<int> base = P.w;
+    auto inner = [&](int s) { return s > 0 && s < M; };
+    auto SX = [&](int s) { return s == 0 ? 0 : (inner(s) ? base[s] + 0 : -1); };
+    auto DX = [&](int s) { return s == M ? 0 : (inner(s) ? base[s] + 1 : -1); };
+    auto SX2 = [&](int s) { return s == 0 ? 0 : (inner(s) ? base[s] + 2 : -1); };
+    auto DX2 = [&](int s) { return s == M ? 0 : (inner(s) ? base[s] + 3 : -1); };
+    auto MX = [&](int s, int f, int t) { return (inner(s) && f < s) ? base[s] + 4 + 3 * f + t : -1; };
+    auto MX2 = [&](int s, int f) { return (inner(s) && f < s) ? base[s] + 4 + 3 * s + f : -1; };
+    const std::vector<cplx>* T1[3] = {&ops.I, &ops.X2, &ops.XPPX};
+    double sum_xp = 0.0;
+    for (int i = 0; i < M; ++i) sum_xp += 2.0 * g(i, M + i);
+    for (int s = 1; s < M; ++s) P.w[s] = base[s] + 4 + 4 * s;
+    for (int k = 0; k < M; ++k) {
+        CoreBuilder cb;
+        cb.ops = &ops;
+        cb.d = d;
+        cb.c = P.cores[k];
+        cb.c.wl = P.w[k];
+        cb.c.wr = P.w[k + 1];
+        const int L = k, R = k + 1;
+        const int xk = k, pk = M + k;
+        // ---- kappa terms, bulk X
+        cb.add(SX(L), SX(R), ops.X, 1.0, false);
+        for (int t = 0; t < 3; ++t) cb.add(SX(L), MX(R, k, t), *T1[t], 1.0, t == 0);
+        {
+            std::vector<cplx> single((size_t)d * d);
+            for (int i = 0; i < d * d; ++i)
+                single[i] = kappa * 2.0 * g(pk, pk) * ops.P[i] + (k == 0 ? kappa * sum_xp * ops.X[i] : cplx(0, 0));
+            cb.add(SX(L), DX(R), single, 1.0, false);
+        }
+        for (int f = 0; f < k; ++f) {
+            for (int t = 0; t < 3; ++t) cb.add(MX(L, f, t), MX(R, f, t), ops.X, 1.0, false);
+            // first special I at f: second X^2 (2 kappa G_{x_k p_f}) and XP+PX (kappa G_{p_k p_f}) at k
+            std::vector<cplx> op((size_t)d * d);
+            for (int i = 0; i < d * d; ++i)
+                op[i] = kappa * (2.0 * g(xk, M + f) * ops.X2[i] + g(pk, M + f) * ops.XPPX[i]);
+            cb.add(MX(L, f, 0), DX(R), op, 1.0, false);
+            // first special X^2 / XP+PX at f: identity at k
+            cb.add(MX(L, f, 1), DX(R), ops.I, kappa * 2.0 * g(f, pk), true);
+            cb.add(MX(L, f, 2), DX(R), ops.I, kappa * g(M + f, pk), true);
+        }
+        cb.add(DX(L), DX(R), ops.X, 1.0, false);
+        // ---- kappa^2 terms, bulk X^2
+        cb.add(SX2(L), SX2(R), ops.X2, 1.0, false);
+        cb.add(SX2(L), MX2(R, k), ops.X, 1.0, false);
+        cb.add(SX2(L), DX2(R), ops.I, kappa * kappa * g(pk, pk), true);
+        for (int f = 0; f < k; ++f) {
+            cb.add(MX2(L, f), MX2(R, f), ops.X2, 1.0, false);
+            cb.add(MX2(L, f), DX2(R), ops.X, kappa * kappa * 2.0 * g(M + f, pk), false);
+        }
+        cb.add(DX2(L), DX2(R), ops.X2, 1.0, false);
+        P.cores[k] = std::move(cb.c);
+    }
+    // |H| bound for tolerances: lambda_max(G) sum_a |R'_a|^2 + N/2 with |X|, |P| <= sqrt(2d)
+    const double cx = std::sqrt(2.0 * d);
+    const double cxi = std::abs(kappa) * std::pow(cx, M - 1);
+    const double lam = P.norm_bound / (M * (2.0 * d - 1.0));
+    P.norm_bound = lam * (M * cx * cx + M * (cx + cxi) * (cx + cxi)) + 0.5 * M;
+    out = std::move(P);
+    return "";
+}
+
 }  // namespace vtn

@@ -30,11 +30,17 @@ struct HostProblem {
     std::vector<int> w;             // bond dims, M + 1
     std::vector<HostCore> cores;    // M cores
     double norm_bound = 0.0;
+    double kappa = 0.0;             // non-Gaussian workload only
 };
 
 // Builds everything; returns "" on success, otherwise the validation error message.
 std::string build_problem(int M, const double* r, const double* U_interleaved, int D, int d,
                           bool force_lbo, HostProblem& out);
+
+// The non-Gaussian (global CZ) workload in the Fock basis (d = D): the Gaussian MPO with the
+// channels of the kappa and kappa^2 terms appended.
+std::string build_problem_cz(int M, const double* r, const double* U_interleaved, int D, double kappa,
+                             HostProblem& out);
 
 // Exactly projected single-mode operators of dimension d (closed-form entries).
 struct LocalOps {

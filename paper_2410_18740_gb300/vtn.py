@@ -87,6 +87,7 @@ _SIGS = {
     "vtn_mps_load": [_P, _P, C.c_char_p, C.POINTER(_P)],
     "vtn_sweep_opts_default": [C.POINTER(vtn_sweep_opts)],
     "vtn_sweep": [_P, _P, C.POINTER(_P), C.POINTER(vtn_sweep_opts), C.POINTER(vtn_sweep_report)],
+    "vtn_build_mpo_cz": [_P, _I, _PD, _PD, _I, _D, C.POINTER(C.c_void_p)],
     "vtn_energy": [_P, _P, _P, _PD],
     "vtn_energy_variance": [_P, _P, _P, _PD, _PD, _PD],
     "vtn_marginals": [_P, _P, _P, _PI, _I, _PD],
@@ -243,6 +244,19 @@ def vtn_mpo_isometry(mpo, site):
     V = np.zeros((D, d, 2))
     _check(None, lib().vtn_mpo_isometry(mpo, int(site), V.ctypes.data_as(_PD)))
     return V.view(np.complex128)[..., 0]
+
+
+def vtn_build_mpo_cz(ctx, r, U, D, kappa):
+    """Non-Gaussian (global CZ) workload MPO, Fock basis; ctx may be None (host-only)."""
+    r = _f64(r)
+    Ui = _cplx_interleaved(U)
+    M = r.shape[0]
+    assert Ui.size == 2 * M * M
+    out = C.c_void_p()
+    st = lib().vtn_build_mpo_cz(ctx, M, r.ctypes.data_as(_PD), Ui.ctypes.data_as(_PD), int(D), float(kappa),
+                                C.byref(out))
+    _check(ctx, st)
+    return out
 
 
 def vtn_mpo_core(mpo, site):

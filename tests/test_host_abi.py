@@ -7,7 +7,7 @@ import re
 import numpy as np
 import pytest
 
-from oracle import dense, gbs, mpo as ompo
+from oracle import dense, gbs, mpo as ompo, nongauss
 from paper_2410_18740_gb300 import inputs, vtn
 from tests.conftest import ROOT
 
@@ -105,3 +105,38 @@ def test_sweep_opts_defaults(libvtn):
     o = vtn.vtn_sweep_opts_default()
     assert o.chi_max == 16 and o.n_sweeps == 8 and o.krylov_max == 32 and o.prec == vtn.VTN_FP64
     assert o.lanczos_tol == 1e-10 and o.lanczos_max_restarts == 4
+
+
+@pytest.mark.parametrize("seed,M,d,kappa", [(0, 3, 3, 0.3), (1, 4, 3, 0.2), (2, 3, 4, -0.5), (3, 2, 4, 0.7)])
+def test_cz_mpo_equals_the_definition(libvtn, seed, M, d, kappa):
+    """The non-Gaussian (global CZ) MPO built by the library, contracted to a matrix, equals the
+    oracle's P H P of Eq. nonGBSHamiltonian built from its definition."""
+    w = inputs.workload("plain", seed, M=M, d=d, D=d)
+    m = vtn.vtn_build_mpo_cz(None, w.r, w.U, d, kappa)
+    try:
+        G = gbs.hamiltonian_coefficients(w.r, w.U)
+        H = _dense_from_abi(m)
+        Href = nongauss.hamiltonian_definition(G, d, kappa).toarray()
+        assert np.abs(H - Href).max() <= 1e-13 * np.abs(Href).max()
+        _, dd, D, wd = vtn.vtn_mpo_info(m)
+        assert dd == d and D == d
+        for s in range(1, M):
+            assert wd[s] == 2 * min(s, M - s) + 2 + 4 + 4 * s
+        assert vtn.vtn_mpo_norm_bound(m) >= np.abs(np.linalg.eigvalsh(Href)).max()
+    finally:
+        vtn.vtn_mpo_free(m)
+
+
+def test_cz_mpo_kappa_zero_and_validation(libvtn):
+    w = inputs.workload("plain", 0, M=3, d=3, D=3)
+    m0 = vtn.vtn_build_mpo_cz(None, w.r, w.U, 3, 0.0)
+    m1 = vtn.vtn_build_mpo(None, w.r, w.U, 3, 3)
+    try:
+        assert np.abs(_dense_from_abi(m0) - _dense_from_abi(m1)).max() == 0.0
+    finally:
+        vtn.vtn_mpo_free(m0)
+        vtn.vtn_mpo_free(m1)
+    with pytest.raises(vtn.VtnError):
+        vtn.vtn_build_mpo_cz(None, w.r[:1], w.U[:1, :1], 3, 0.1)          # M = 1
+    with pytest.raises(vtn.VtnError):
+        vtn.vtn_build_mpo_cz(None, w.r, w.U, 3, float("nan"))
