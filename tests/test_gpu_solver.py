@@ -10,7 +10,7 @@ import os
 import numpy as np
 import pytest
 
-from oracle import dense, dmrg as odmrg, gbs, mpo as ompo, observables as oobs, philox
+from oracle import dense, dmrg as odmrg, gbs, mpo as ompo, nongauss, observables as oobs, philox
 from paper_2410_18740_gb300 import inputs, vtn
 
 pytestmark = pytest.mark.gpu
@@ -324,4 +324,51 @@ def test_energy_variance_of_the_converged_plain_state(ctx):
     assert abs(e - rep["energy"][-1]) <= 1e-12 * Hn
     vtn.vtn_mps_free(mps)
     vtn.vtn_mpo_free(m2)
+    vtn.vtn_mpo_free(m)
+
+
+@pytest.mark.parametrize("seed,M,d,chi,kappa", [(0, 4, 4, 16, 0.3), (1, 5, 3, 9, 0.2), (2, 4, 3, 9, -0.4)])
+def test_cz_workload_ground_state(ctx, seed, M, d, chi, kappa):
+    """Non-Gaussian (global CZ) workload at sizes where the MPS is exact: the GPU sweep reaches
+    the ground energy of the oracle's P H P built from its definition, the marginals of the
+    dense ground state, and a vanishing energy variance."""
+    w = inputs.workload("plain", seed, M=M, d=d, D=d)
+    G = gbs.hamiltonian_coefficients(w.r, w.U)
+    Href = nongauss.hamiltonian_definition(G, d, kappa).toarray()
+    evals, evecs = np.linalg.eigh(Href)
+    Hn = np.abs(evals).max()
+    m = vtn.vtn_build_mpo_cz(ctx, w.r, w.U, d, kappa)
+    opts = vtn.vtn_sweep_opts_default(chi_max=chi, n_sweeps=4, seed=seed + 40, lanczos_tol=1e-12, krylov_max=32,
+                                      lanczos_max_restarts=8)
+    st, mps, rep = vtn.vtn_sweep(ctx, m, None, opts)
+    assert st == vtn.VTN_OK
+    E = vtn.vtn_energy(ctx, m, mps)
+    assert abs(E - evals[0]) <= 1e-10 * Hn
+    marg = vtn.vtn_marginals_all(ctx, m, mps)
+    for i in range(M):
+        assert np.abs(marg[i] - dense.marginals_from_vector(evecs[:, 0], M, d, [i])).max() <= 1e-8
+    _, _, sg = vtn.vtn_energy_variance(ctx, m, mps)
+    assert sg <= 1e-5 * Hn
+    vtn.vtn_mps_free(mps)
+    vtn.vtn_mpo_free(m)
+
+
+def test_cz_sweep_trajectory_matches_oracle(ctx):
+    """Same initial MPS, Lanczos rule and truncation rule with the bond dimension below exact:
+    energies after each sweep match the oracle's two-site DMRG on its own MPO of the same
+    Hamiltonian."""
+    M, d, chi, kappa = 6, 3, 8, 0.25
+    w = inputs.workload("plain", 7, M=M, d=d, D=d)
+    G = gbs.hamiltonian_coefficients(w.r, w.U)
+    m = vtn.vtn_build_mpo_cz(ctx, w.r, w.U, d, kappa)
+    Hn = np.abs(np.linalg.eigvalsh(nongauss.dense_hamiltonian(G, d, kappa).toarray())).max()
+    opts = vtn.vtn_sweep_opts_default(chi_max=chi, n_sweeps=3, seed=11, lanczos_tol=1e-12, krylov_max=32,
+                                      lanczos_max_restarts=8)
+    st, mps, rep = vtn.vtn_sweep(ctx, m, None, opts)
+    omps, orep = odmrg.dmrg(nongauss.build_mpo(G, d, kappa), d, chi, 3, seed=11,
+                            lanczos=odmrg.LanczosParams(krylov_max=32, max_restarts=8, tol=1e-12))
+    assert rep["sweeps_done"] == len(orep.energies)
+    for a, b in zip(rep["energy"], orep.energies):
+        assert abs(a - b) <= 1e-10 * Hn
+    vtn.vtn_mps_free(mps)
     vtn.vtn_mpo_free(m)
