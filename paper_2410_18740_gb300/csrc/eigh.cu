@@ -353,6 +353,147 @@ __device__ __forceinline__ double2 sub_two_cmulc(double2 x, double2 a, double2 b
     return x;
 }
 
+constexpr int TRI_MAX_CPL = 2;  // columns per lane in the trailing pass
+
+// chunks C of 32*cpl columns, row slices CS per chunk; work units C*CS over nb CTAs
+__device__ __forceinline__ void tri_layout(int m, int nb, int cpl, int& C, int& CS) {
+    const int w = 32 * cpl;
+    C = (m + w - 1) / w;
+    CS = max(1, min(C <= nb ? nb / C : 1, (m + TRI_NW - 1) / TRI_NW));
+}
+
+// modelled time of a trailing pass: passes over the CTAs x rows of the slowest warp x columns per lane
+__device__ __forceinline__ int tri_pass_cost(int m, int nb, int cpl) {
+    int C, CS;
+    tri_layout(m, nb, cpl, C, CS);
+    const int passes = (C * CS + nb - 1) / nb;
+    const int rows = (m + CS * TRI_NW - 1) / (CS * TRI_NW);
+    return passes * rows * cpl;
+}
+
+// Trailing pass of step k: pending rank-2 update of the trailing block fused with (A v).  Work
+// unit u = (column chunk c = u mod C of 32*CPL columns, row slice cs = u / C of CS); CTA b
+// takes units b, b + nb, ...; warp w walks the rows k+1 + cs*NW + w + t*CS*NW, lane l owns the
+// columns c*32*CPL + q*32 + l (q < CPL).  The CTAs of a chunk each write one partial (A v) per
+// column; the last to arrive sums them in slice order into p = tau A v.
+template <int CPL>
+__device__ void tri_pass(double2* __restrict__ A, int n, int k, int m, int nb, bool have_prev,
+                         const double2* vprev, const double2* wprev, const double2* vcur, double tau,
+                         double2* pk, double2* pfin, unsigned* arrive, double2* colred, int& last_sh) {
+    constexpr int U = TRI_UNROLL / CPL;  // rows in flight per warp
+    constexpr int LD = TRI_MAX_CPL * 32;  // colred row stride
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int C, CS;
+    tri_layout(m, nb, CPL, C, CS);
+    for (int unit = (int)blockIdx.x; unit < C * CS; unit += nb) {
+        const int c = unit % C, cs = unit / C;
+        int il[CPL], col[CPL];
+        bool ok[CPL];
+        double2 vpi[CPL], wpi[CPL];
+        double accx[CPL], accy[CPL];
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+            il[q] = c * 32 * CPL + q * 32 + lane;  // local column index (0..m-1)
+            ok[q] = il[q] < m;
+            col[q] = k + 1 + (ok[q] ? il[q] : 0);
+            // column factors of a_ji -= vp_j conj(wp_i) + wp_j conj(vp_i)
+            vpi[q] = make_double2(0.0, 0.0);
+            wpi[q] = make_double2(0.0, 0.0);
+            if (have_prev && ok[q]) {
+                vpi[q] = vprev[col[q] - k];
+                wpi[q] = wprev[col[q] - k];
+            }
+            accx[q] = accy[q] = 0.0;
+        }
+        const int stride = CS * TRI_NW;
+        int j = k + 1 + cs * TRI_NW + warp;
+        for (; j + (U - 1) * stride < n; j += U * stride) {
+            double2 a[U][CPL];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int q = 0; q < CPL; ++q)
+                    a[u][q] = ok[q] ? __ldcg(&A[(long long)(j + u * stride) * n + col[q]]) : make_double2(0.0, 0.0);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int jj = j + u * stride;
+                const double2 v = vcur[jj - k - 1];
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) {
+                    if (have_prev) {
+                        a[u][q] = sub_two_cmulc(a[u][q], vprev[jj - k], wpi[q], wprev[jj - k], vpi[q]);
+                        if (ok[q]) A[(long long)jj * n + col[q]] = a[u][q];
+                    }
+                    accx[q] = fma(a[u][q].x, v.x, accx[q]);
+                    accx[q] = fma(a[u][q].y, v.y, accx[q]);
+                    accy[q] = fma(a[u][q].x, v.y, accy[q]);
+                    accy[q] = fma(-a[u][q].y, v.x, accy[q]);
+                }
+            }
+        }
+        for (; j < n; j += stride) {
+            const double2 v = vcur[j - k - 1];
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) {
+                double2 a = ok[q] ? __ldcg(&A[(long long)j * n + col[q]]) : make_double2(0.0, 0.0);
+                if (have_prev) {
+                    a = sub_two_cmulc(a, vprev[j - k], wpi[q], wprev[j - k], vpi[q]);
+                    if (ok[q]) A[(long long)j * n + col[q]] = a;
+                }
+                accx[q] = fma(a.x, v.x, accx[q]);
+                accx[q] = fma(a.y, v.y, accx[q]);
+                accy[q] = fma(a.x, v.y, accy[q]);
+                accy[q] = fma(-a.y, v.x, accy[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) colred[warp * LD + q * 32 + lane] = make_double2(accx[q], accy[q]);
+        __syncthreads();
+#pragma unroll
+        for (int h = TRI_NW / 2; h >= 2; h >>= 1) {  // tree over the warps' partials
+            if (warp < h) {
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) {
+                    const double2 o = colred[(warp + h) * LD + q * 32 + lane];
+                    colred[warp * LD + q * 32 + lane].x += o.x;
+                    colred[warp * LD + q * 32 + lane].y += o.y;
+                }
+            }
+            __syncthreads();
+        }
+        if (warp == 0) {
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) {
+                const double2 a0 = colred[q * 32 + lane], a1 = colred[LD + q * 32 + lane];
+                if (ok[q]) pk[(long long)cs * n + il[q]] = make_double2(a0.x + a1.x, a0.y + a1.y);
+            }
+            __threadfence();
+        }
+        __syncthreads();
+        // the last CTA of this chunk sums its CS partials in slice order (warp q: columns q*32..)
+        if (threadIdx.x == 0) {
+            __threadfence();
+            last_sh = atomicAdd(&arrive[c], 1u) == (unsigned)(CS - 1);
+        }
+        __syncthreads();
+        if (last_sh && warp < CPL) {
+            __threadfence();
+            const int ilq = c * 32 * CPL + warp * 32 + lane;
+            if (ilq < m) {
+                double sx = 0.0, sy = 0.0;
+                for (int s2 = 0; s2 < CS; ++s2) {
+                    const double2 pp = __ldcg(&pk[(long long)s2 * n + ilq]);
+                    sx += pp.x;
+                    sy += pp.y;
+                }
+                pfin[ilq] = make_double2(tau * sx, tau * sy);
+            }
+            if (warp == 0 && lane == 0) arrive[c] = 0u;  // reused two steps later, after two barriers
+        }
+        __syncthreads();  // colred and last_sh are reused by the next unit
+    }
+}
+
 __global__ void __launch_bounds__(TRI_THREADS) tridiag_persistent(double2* __restrict__ A, int n,
                                                                   double2* __restrict__ H, EigSmall s,
                                                                   TriBufs tb, GridBar* bar) {
@@ -367,9 +508,8 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_persistent(double2* __res
     __shared__ double tau_sh, dk_sh;
     __shared__ double2 p0_sh;
     __shared__ int last_sh;
-    __shared__ double2 colred[TRI_NW][32];
+    __shared__ double2 colred[TRI_NW][TRI_MAX_CPL * 32];
     const int nb = (int)gridDim.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     bool have_prev = false;
     // row 0 (no pending update): x = conj(A[0][1..n-1])
     double a2 = 0.0;
@@ -423,99 +563,15 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_persistent(double2* __res
         __syncthreads();
         if (blockIdx.x == 0)
             for (int t = threadIdx.x; t < m; t += blockDim.x) H[(long long)k * n + t] = vcur[t];
-        // ---- B: work unit u = (column chunk c = u mod C of 32 columns, row slice cs = u / C
-        //      of CS); CTA b takes units b, b + nb, ...; warp w walks rows k+1 + cs*NW + w +
-        //      t*CS*NW.
-        const int C = (m + 31) / 32;
-        const int CS = max(1, min(nb / C, (m + TRI_NW - 1) / TRI_NW));
+        // ---- B: 32 or 64 columns per chunk (1 or 2 per lane), whichever leaves the slowest
+        //      warp fewer rows x columns this step (the same choice in every CTA)
         double2* pk = tb.part + (long long)(k & 1) * nb * n;
         double2* pfin = tb.p + (long long)(k & 1) * n;
         unsigned* arrive = tb.arrive + (k & 1) * TRI_MAX_CHUNKS;
-        for (int unit = (int)blockIdx.x; unit < C * CS; unit += nb) {
-            const int c = unit % C, cs = unit / C;
-            const int il = c * 32 + lane;  // local column index (0..m-1)
-            const bool col_ok = il < m;
-            const int i = k + 1 + (col_ok ? il : 0);
-            // column factors of a_ji -= vp_j conj(wp_i) + wp_j conj(vp_i)
-            double2 vpi = make_double2(0.0, 0.0), wpi = make_double2(0.0, 0.0);
-            if (have_prev && col_ok) {
-                vpi = vprev[i - k];
-                wpi = wprev[i - k];
-            }
-            double accx = 0.0, accy = 0.0;
-            const int stride = CS * TRI_NW;
-            int j = k + 1 + cs * TRI_NW + warp;
-            for (; j + (TRI_UNROLL - 1) * stride < n; j += TRI_UNROLL * stride) {
-                double2 a[TRI_UNROLL];
-#pragma unroll
-                for (int u = 0; u < TRI_UNROLL; ++u)
-                    a[u] = col_ok ? __ldcg(&A[(long long)(j + u * stride) * n + i]) : make_double2(0.0, 0.0);
-#pragma unroll
-                for (int u = 0; u < TRI_UNROLL; ++u) {
-                    const int jj = j + u * stride;
-                    if (have_prev) {
-                        a[u] = sub_two_cmulc(a[u], vprev[jj - k], wpi, wprev[jj - k], vpi);
-                        if (col_ok) A[(long long)jj * n + i] = a[u];
-                    }
-                    const double2 v = vcur[jj - k - 1];
-                    accx = fma(a[u].x, v.x, accx);
-                    accx = fma(a[u].y, v.y, accx);
-                    accy = fma(a[u].x, v.y, accy);
-                    accy = fma(-a[u].y, v.x, accy);
-                }
-            }
-            for (; j < n; j += stride) {
-                double2 a = col_ok ? __ldcg(&A[(long long)j * n + i]) : make_double2(0.0, 0.0);
-                if (have_prev) {
-                    a = sub_two_cmulc(a, vprev[j - k], wpi, wprev[j - k], vpi);
-                    if (col_ok) A[(long long)j * n + i] = a;
-                }
-                const double2 v = vcur[j - k - 1];
-                accx = fma(a.x, v.x, accx);
-                accx = fma(a.y, v.y, accx);
-                accy = fma(a.x, v.y, accy);
-                accy = fma(-a.y, v.x, accy);
-            }
-            colred[warp][lane] = make_double2(accx, accy);
-            __syncthreads();
-#pragma unroll
-            for (int h = TRI_NW / 2; h >= 2; h >>= 1) {  // tree over the warps' partials
-                if (warp < h) {
-                    const double2 o = colred[warp + h][lane];
-                    colred[warp][lane].x += o.x;
-                    colred[warp][lane].y += o.y;
-                }
-                __syncthreads();
-            }
-            if (warp == 0) {
-                const double2 a0 = colred[0][lane], a1 = colred[1][lane];
-                if (col_ok) pk[(long long)cs * n + il] = make_double2(a0.x + a1.x, a0.y + a1.y);
-                __threadfence();
-            }
-            __syncthreads();
-            // the last CTA of this chunk sums its CS partials in slice order
-            if (threadIdx.x == 0) {
-                __threadfence();
-                last_sh = atomicAdd(&arrive[c], 1u) == (unsigned)(CS - 1);
-            }
-            __syncthreads();
-            if (last_sh) {
-                if (warp == 0) {
-                    __threadfence();
-                    double sx = 0.0, sy = 0.0;
-                    for (int q = 0; q < CS; ++q) {
-                        if (col_ok) {
-                            const double2 pp = __ldcg(&pk[(long long)q * n + il]);
-                            sx += pp.x;
-                            sy += pp.y;
-                        }
-                    }
-                    if (col_ok) pfin[il] = make_double2(tau * sx, tau * sy);
-                    if (lane == 0) arrive[c] = 0u;  // reused two steps later, after two barriers
-                }
-            }
-            __syncthreads();  // colred and last_sh are reused by the next unit
-        }
+        if (tri_pass_cost(m, nb, 2) < tri_pass_cost(m, nb, 1))
+            tri_pass<2>(A, n, k, m, nb, have_prev, vprev, wprev, vcur, tau, pk, pfin, arrive, &colred[0][0], last_sh);
+        else
+            tri_pass<1>(A, n, k, m, nb, have_prev, vprev, wprev, vcur, tau, pk, pfin, arrive, &colred[0][0], last_sh);
         if (!grid_sync(bar, (unsigned)nb, (unsigned)k)) return;
         // ---- C(k): K = (tau/2) Re(v^dag p); p parked in wprev (its old content is spent)
         const bool next = k + 3 < n;  // another reflector follows
