@@ -58,7 +58,7 @@ N_SAMPLES = 256
 TC_GEMM_TRAFFIC = 0.5 * ((32.512000 + 145.623040) + (311.471872 + 3.002112)) * 1e6
 # DRAM bytes (read + write) of one tridiag_persistent launch at n = 1024 (ncu capture summarised
 # in profiles/truncation_eigensolver_n1024.md).
-TRI_TRAFFIC = (16.825088 + 3.555584) * 1e6
+TRI_TRAFFIC = (16.843264 + 3.543040) * 1e6
 # DRAM bytes (read + write) per launch of the FP64 complex GEMM pair of H_eff psi at the middle
 # bond (profiles/gemm_c64_heff_split_middle_bond.md), mean of the two launches.
 GEMM_F64_TRAFFIC = 0.5 * ((30.710272 + 345.032960) + (416.077056 + 13.165824)) * 1e6
@@ -81,6 +81,9 @@ def parse():
     p.add_argument("--case", default=None, choices=["heff", "trunc", "tte"],
                    help="heff / trunc: only that kernel at the middle-bond shape (for profiler captures); "
                         "tte: time-to-eps of the mixed and the FP64 solver from the same random state")
+    p.add_argument("--trunc-shape", type=int, nargs=2, default=None, metavar=("CHI", "D"),
+                   help="trunc: theta (CHI, D, D, CHI) with k = CHI (default: the split workload's middle "
+                        "bond, 128 8; the large workload's is 512 6)")
     p.add_argument("--ref-sweeps", type=int, default=6,
                    help="time-to-eps: sweeps of the FP64 reference run (chi schedule 16, 32, 64, 128, then 128)")
     return p.parse_args()
@@ -490,7 +493,7 @@ def run_case_heff(args):
 def run_case_trunc(args):
     """The FP64 truncation eigensolver alone at the middle-bond shape of the split workload:
     theta (128, 8, 8, 128) with an exponentially decaying Schmidt spectrum, k = 128, 2 warm-up
-    + 3 timed calls."""
+    + 3 timed calls (or theta (chi, d, d, chi), k = chi, with --trunc-shape chi d)."""
     import torch
 
     from paper_2410_18740_gb300 import build as vbuild
@@ -498,13 +501,13 @@ def run_case_trunc(args):
 
     vbuild.build()
     rng = inputs.rng_for(8)
-    chi, d = CHI, 8
-    # Schmidt spectrum s_i = exp(-i / 40) between Haar bases: the kept 128 values carry
-    # 99.8 % of the weight and the tail falls below the FP64 resolution of rho, as in a sweep
+    chi, d = args.trunc_shape if args.trunc_shape else (CHI, 8)
+    # Schmidt spectrum s_i = exp(-i / (40 chi / 128)) between Haar bases: the kept chi values
+    # carry 99.8 % of the weight and the tail falls below the FP64 resolution of rho, as in a sweep
     n = chi * d
     U = inputs.haar_unitary(n, rng)
     V = inputs.haar_unitary(n, rng)
-    sv = np.exp(-np.arange(n) / 40.0)
+    sv = np.exp(-np.arange(n) / (40.0 * chi / 128.0))
     th = ((U * sv) @ V.conj().T).reshape(chi, d, d, chi)
     th /= np.linalg.norm(th)
     dev = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.complex128)).cuda()
@@ -515,12 +518,17 @@ def run_case_trunc(args):
     for _ in range(2):
         vtn.vtn_truncate(ctx, chi, d, d, chi, 0, chi, t, left, right)
     torch.cuda.synchronize()
+    vtn.vtn_timing(ctx, True)
+    vtn.vtn_timing_reset(ctx)
     t0 = time.perf_counter()
     for _ in range(3):
         vtn.vtn_truncate(ctx, chi, d, d, chi, 0, chi, t, left, right)
     torch.cuda.synchronize()
     el = (time.perf_counter() - t0) / 3
-    print(json.dumps({"case": "trunc", "n": chi * d, "k": chi, "ms": 1e3 * el}), flush=True)
+    ntri, fltri, stri = vtn.vtn_timing_read(ctx, "tridiag")
+    print(json.dumps({"case": "trunc", "n": chi * d, "k": chi, "ms": 1e3 * el,
+                      "tridiag_ms": 1e3 * stri / max(ntri, 1),
+                      "tridiag_tflops": (fltri / stri / 1e12) if stri else None}), flush=True)
     vtn.vtn_destroy(ctx)
 
 
