@@ -52,29 +52,6 @@ __device__ double block_sum(double v, double* sh) {
     return r;  // valid in every thread
 }
 
-// Block sum for NT threads as a shared-memory tree down to one warp, then a warp butterfly:
-// 10 FP64 add instructions on the critical path of a 512-thread block instead of 25 for
-// a butterfly in every warp (GB300 issues one FP64 warp instruction per ~64 cycles per SM
-// sub-partition).  sh holds NT + 1 doubles; the result is valid in every thread.
-template <int NT>
-__device__ double block_sum_tree(double v, double* sh) {
-    sh[threadIdx.x] = v;
-    __syncthreads();
-#pragma unroll
-    for (int h = NT / 2; h >= 32; h >>= 1) {
-        if ((int)threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
-        __syncthreads();
-    }
-    if (threadIdx.x < 32) {
-        const double r = warp_sum(sh[threadIdx.x]);
-        if (threadIdx.x == 0) sh[NT] = r;
-    }
-    __syncthreads();
-    const double r = sh[NT];
-    __syncthreads();
-    return r;
-}
-
 struct EigSmall {
     double* diag;   // [n]
     double* offd;   // [n]
@@ -493,47 +470,25 @@ __device__ void tri_pass(double2* __restrict__ A, int n, int k, int m, int nb, b
             __threadfence();
         }
         __syncthreads();
-        // the last CTA of this chunk sums its CS partials: warp w loads slices w, w + NW, ..
-        // (one L2 round trip for CS <= NW), then a fixed-order tree over the warps
+        // the last CTA of this chunk sums its CS partials in slice order (warp q: columns q*32..)
         if (threadIdx.x == 0) {
             __threadfence();
             last_sh = atomicAdd(&arrive[c], 1u) == (unsigned)(CS - 1);
         }
         __syncthreads();
-        if (last_sh) {  // uniform over the CTA
+        if (last_sh && warp < CPL) {
             __threadfence();
-#pragma unroll
-            for (int q = 0; q < CPL; ++q) {
+            const int ilq = c * 32 * CPL + warp * 32 + lane;
+            if (ilq < m) {
                 double sx = 0.0, sy = 0.0;
-                if (ok[q])
-                    for (int s2 = warp; s2 < CS; s2 += TRI_NW) {
-                        const double2 pp = __ldcg(&pk[(long long)s2 * n + il[q]]);
-                        sx += pp.x;
-                        sy += pp.y;
-                    }
-                colred[warp * LD + q * 32 + lane] = make_double2(sx, sy);
-            }
-            __syncthreads();
-            int h = 1;
-            while (2 * h < min(CS, TRI_NW)) h *= 2;  // warps >= 2h hold zeros
-            if (CS == 1) h = 0;
-            for (; h >= 1; h >>= 1) {
-                if (warp < h) {
-#pragma unroll
-                    for (int q = 0; q < CPL; ++q) {
-                        const double2 o = colred[(warp + h) * LD + q * 32 + lane];
-                        colred[warp * LD + q * 32 + lane].x += o.x;
-                        colred[warp * LD + q * 32 + lane].y += o.y;
-                    }
+                for (int s2 = 0; s2 < CS; ++s2) {
+                    const double2 pp = __ldcg(&pk[(long long)s2 * n + ilq]);
+                    sx += pp.x;
+                    sy += pp.y;
                 }
-                __syncthreads();
+                pfin[ilq] = make_double2(tau * sx, tau * sy);
             }
-            if (warp < CPL) {
-                const int ilq = c * 32 * CPL + warp * 32 + lane;
-                const double2 sum = colred[warp * 32 + lane];
-                if (ilq < m) pfin[ilq] = make_double2(tau * sum.x, tau * sum.y);
-            }
-            if (threadIdx.x == 0) arrive[c] = 0u;  // reused two steps later, after two barriers
+            if (warp == 0 && lane == 0) arrive[c] = 0u;  // reused two steps later, after two barriers
         }
         __syncthreads();  // colred and last_sh are reused by the next unit
     }
@@ -549,7 +504,7 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_persistent(double2* __res
     double2* vprev = sm;
     double2* wprev = sm + n;
     double2* vcur = sm + 2 * n;
-    __shared__ double red[TRI_THREADS + 1];
+    __shared__ double red[33];
     __shared__ double tau_sh, dk_sh;
     __shared__ double2 p0_sh;
     __shared__ int last_sh;
@@ -568,7 +523,7 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_persistent(double2* __res
     for (int k = 0; k + 2 < n; ++k) {
         const int m = n - k - 1;
         // ---- reflector for column k from x = vcur (norm^2 a2)
-        a2 = block_sum_tree<TRI_THREADS>(a2, red);
+        a2 = block_sum(a2, red);
         if (threadIdx.x == 0) {
             // alpha = |x|, phi = x0 / |x0|: v0 = x0 + phi alpha, beta = -phi alpha,
             // tau = 1 / (alpha (alpha + |x0|)); with few FP64 instructions (two reciprocal
@@ -628,7 +583,7 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_persistent(double2* __res
             if (t == 0) p0_sh = p;
             dot = fma(v.x, p.x, fma(v.y, p.y, dot));
         }
-        dot = block_sum_tree<TRI_THREADS>(dot, red);
+        dot = block_sum(dot, red);
         const double K = 0.5 * tau * dot;
         // rotate: the pending pair becomes (v_k, w_k); the free buffer takes row k+1
         double2* vnew = vcur;
