@@ -21,6 +21,10 @@ Modules (each function cites the passage of the paper it follows):
                      brute-force hafnian amplitudes of the GBS state.
 * ``dmrg``        -- two-site DMRG (Sec. "Matrix Product States"): environments, effective
                      Hamiltonian product, Lanczos, truncation, sweeps, energy (Eq. MagOfSimError).
+* ``dmrg1``       -- single-site DMRG with subspace expansion (Secs. "Results" and
+                     "Discussion"): single-site effective Hamiltonian, expansion, sweeps.
+* ``nongauss``    -- the global-CZ (non-Gaussian) parent Hamiltonian (Eq. nonGBSHamiltonian):
+                     definition, term expansion and its MPO.
 * ``observables`` -- Fock-basis marginals after the inverse basis transformation and
                      sequential conditional sampling.
 
