@@ -205,6 +205,26 @@ vtn_status vtn_sweep_opts_default(vtn_sweep_opts* opts);
 vtn_status vtn_sweep(vtn_ctx ctx, vtn_mpo mpo, vtn_mps* state, const vtn_sweep_opts* opts,
                      vtn_sweep_report* report);
 
+/* Single-site DMRG with subspace expansion: the solver of the paper's results section
+ * (single-site DMRG), with the bond dimension grown during the sweeps as its discussion
+ * describes, by the strictly single-site expansion it cites (Hubig et al., Phys. Rev. B 91,
+ * 155115 (2015)).  FP64 only (opts->prec other than VTN_FP64: VTN_EUNSUPPORTED); the other
+ * opts fields as for vtn_sweep.  A sweep optimises sites 0 .. M-2 left to right, then
+ * M-1 .. 1 right to left, and ends with the centre on site 0.  At site i moving right:
+ *   1. Lanczos on y[l,t,r'] = sum L[a,l,l'] W_i[a,b,t,s] A[l',s,r] R[b,r,r'] (A = site i);
+ *   2. expansion Mx = [A | alpha_t P], P[(l t), (b r)] = sum L[a,l,l'] W_i[a,b,t,s] A[l',s,r],
+ *      a (chi_l d) x chi_r (1 + w_r) matrix (the next site gains zero rows: state unchanged);
+ *   3. FP64 eigendecomposition of Mx Mx^dag keeping k = min(chi, chi_l d, chi_r (1 + w_r),
+ *      d chi_{i+2}) eigenpairs, then only those with eigenvalue > cutoff * the largest;
+ *   4. site i <- U_k (left-canonical), site i+1 <- (U_k^dag A) site i+1, L_{i+1} updated.
+ * Moving left mirrors it (Mx = [A; alpha_t P], P[(a l), (t r')] = sum W_i[a,b,t,s] A[l,s,r]
+ * R[b,r,r']).  alpha_t = alpha * alpha_decay^t in sweep t (alpha >= 0, alpha_decay >= 0);
+ * cutoff in [0, 1).  Without the expansion (alpha = 0) the bonds never grow.  report as for
+ * vtn_sweep (heff_flops: 8 d chi_l chi_r (w_l chi_l + w_r chi_r) per product); returns
+ * VTN_ENOCONV (after finishing) if some Lanczos solve missed its tolerance. */
+vtn_status vtn_sweep_single_site(vtn_ctx ctx, vtn_mpo mpo, vtn_mps* state, const vtn_sweep_opts* opts,
+                                 double alpha, double alpha_decay, double cutoff, vtn_sweep_report* report);
+
 /* <psi|H|psi> / <psi|psi> in FP64 by a full environment contraction (Eq. MagOfSimError). */
 vtn_status vtn_energy(vtn_ctx ctx, vtn_mpo mpo, vtn_mps mps, double* E);
 
@@ -245,6 +265,15 @@ typedef struct {
     const double* ops;
 } vtn_core;
 
+/* An MPO given as its cores: cores[s] for s = 0..M-1 (vtn_core), with
+ * cores[0].w_left = cores[M-1].w_right = 1, cores[s].w_right = cores[s+1].w_left and one d
+ * for all.  For Hamiltonians other than the built-in workloads (and for checks that need a
+ * given MPO representation, which the single-site expansion depends on).  The basis is the
+ * local basis of the cores (no local-basis isometry: D = d); vtn_mpo_coefficients and
+ * vtn_mpo_covariance return VTN_EUNSUPPORTED and vtn_mpo_norm_bound returns 0 (unknown).
+ * The library copies the cores.  ctx may be NULL (host-only, uploaded on first use). */
+vtn_status vtn_mpo_from_cores(vtn_ctx ctx, int M, const vtn_core* cores, vtn_mpo* out);
+
 /* Two-site effective-Hamiltonian product (the hot path):
  *   y[i,t,u,l] = sum L[a,i,j] Wi[a,b,t,s] Wj[b,c,u,v] theta[j,s,v,k] R[c,k,l]
  * L: device complex[Wi.w_left*chi_l*chi_l]; R: device complex[Wj.w_right*chi_r*chi_r];
@@ -263,6 +292,25 @@ vtn_status vtn_heff_apply(vtn_ctx ctx, const vtn_core* Wi, const vtn_core* Wj, i
  * mode vtn_sweep uses for its environments when opts->prec is VTN_BF16X3). */
 vtn_status vtn_env_update(vtn_ctx ctx, const vtn_core* W, int side, int chi_l, int chi_r,
                           const double* env, const double* A, double* out, vtn_precision prec);
+
+/* Single-site effective-Hamiltonian product (step 1 of vtn_sweep_single_site):
+ *   y[l,t,r'] = sum L[a,l,l'] W[a,b,t,s] A[l',s,r] R[b,r,r']
+ * L: device complex[W.w_left*chi_l*chi_l]; R: device complex[W.w_right*chi_r*chi_r];
+ * A, y: device complex[chi_l*d*chi_r]; y must not alias A.  FP64. */
+vtn_status vtn_heff1_apply(vtn_ctx ctx, const vtn_core* W, int chi_l, int chi_r, const double* L,
+                           const double* R, const double* A, double* y);
+
+/* Subspace expansion of a centre tensor A (device complex[chi_l*d*chi_r]), step 2 of
+ * vtn_sweep_single_site, FP64:
+ *  side 0: env = L (complex[W.w_left*chi_l*chi_l]); out = Mx, complex[(chi_l d) x chi_r (1 + W.w_right)],
+ *          row (l t), column r < chi_r: A[l,t,r]; column chi_r (1 + b) + r:
+ *          alpha sum L[a,l,l'] W[a,b,t,s] A[l',s,r].
+ *  side 1: env = R (complex[W.w_right*chi_r*chi_r]); out = Mx, complex[chi_l (1 + W.w_left) x (d chi_r)],
+ *          row l < chi_l: A[l,:,:]; row chi_l (1 + a) + l, column (t r'):
+ *          alpha sum W[a,b,t,s] A[l,s,r] R[b,r,r'].
+ * out must not alias env or A. */
+vtn_status vtn_expand(vtn_ctx ctx, const vtn_core* W, int side, int chi_l, int chi_r, const double* env,
+                      const double* A, double alpha, double* out);
 
 /* Lowest eigenpair of the two-site H_eff by the solver's Lanczos (full
  * re-orthogonalisation, restarts).  theta: device complex[chi_l*d*d*chi_r], start vector

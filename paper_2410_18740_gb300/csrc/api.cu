@@ -411,6 +411,44 @@ vtn_status vtn_mpo_free(vtn_mpo mpo) {
     return VTN_OK;
 }
 
+vtn_status vtn_mpo_from_cores(vtn_ctx ctx, int M, const vtn_core* cores, vtn_mpo* out) {
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(out && cores, "null argument");
+        VTN_REQUIRE(M >= 1, "M must be >= 1");
+        HostProblem hp;
+        for (int s = 0; s < M; ++s) hp.cores.push_back(core_from_abi(&cores[s]));
+        const int d = hp.cores[0].d;
+        VTN_REQUIRE(hp.cores[0].wl == 1 && hp.cores[M - 1].wr == 1, "the end cores must have one outer channel");
+        for (int s = 0; s < M; ++s) {
+            VTN_REQUIRE(hp.cores[s].d == d, "all cores must have the same d");
+            if (s + 1 < M) VTN_REQUIRE(hp.cores[s].wr == hp.cores[s + 1].wl, "core channel counts do not chain");
+        }
+        hp.M = M;
+        hp.d = hp.D = d;
+        hp.lbo = false;
+        hp.w.assign(M + 1, 1);
+        for (int s = 0; s < M; ++s) hp.w[s + 1] = hp.cores[s].wr;
+        hp.iso.assign((size_t)M * d * d, cplx(0.0, 0.0));  // identity basis (no local basis)
+        for (int s = 0; s < M; ++s)
+            for (int n = 0; n < d; ++n) hp.iso[(size_t)s * d * d + (size_t)n * d + n] = cplx(1.0, 0.0);
+        hp.norm_bound = 0.0;  // unknown
+        vtn_mpo mpo = new vtn_mpo_s();
+        mpo->hp = std::move(hp);
+        if (ctx) {
+            try {
+                use_device(ctx->c);
+                ensure_mpo_device(ctx, mpo);
+            } catch (...) {
+                for (auto& dc : mpo->dcores) free_core(ctx->c, dc);
+                delete mpo;
+                throw;
+            }
+        }
+        *out = mpo;
+        return VTN_OK;
+    });
+}
+
 vtn_status vtn_mpo_info(vtn_mpo mpo, int* M, int* d, int* D, int* w) {
     if (!mpo) return VTN_EINVAL;
     if (M) *M = mpo->hp.M;
@@ -422,12 +460,14 @@ vtn_status vtn_mpo_info(vtn_mpo mpo, int* M, int* d, int* D, int* w) {
 
 vtn_status vtn_mpo_coefficients(vtn_mpo mpo, double* G) {
     if (!mpo || !G) return VTN_EINVAL;
+    if (mpo->hp.G.empty()) return VTN_EUNSUPPORTED;  // MPO given as cores
     std::copy(mpo->hp.G.begin(), mpo->hp.G.end(), G);
     return VTN_OK;
 }
 
 vtn_status vtn_mpo_covariance(vtn_mpo mpo, double* V) {
     if (!mpo || !V) return VTN_EINVAL;
+    if (mpo->hp.V.empty()) return VTN_EUNSUPPORTED;  // MPO given as cores
     std::copy(mpo->hp.V.begin(), mpo->hp.V.end(), V);
     return VTN_OK;
 }
@@ -761,6 +801,180 @@ vtn_status vtn_sweep(vtn_ctx ctx, vtn_mpo mpo, vtn_mps* state, const vtn_sweep_o
     });
 }
 
+// Single-site DMRG with subspace expansion.  At site i sweeping right: Lanczos on the
+// single-site H_eff, expansion Mx = [A | alpha P] ((chi_l d) x chi_r (1 + w_r)), FP64
+// eigendecomposition of Mx Mx^dag keeping k = min(chi, chi_l d, chi_r (1 + w_r), d chi_{i+2})
+// eigenpairs and then only those above cutoff * the largest, A_i <- U_k, the centre
+// (U_k^dag A) A_{i+1} moves right, L_{i+1} is updated; the left sweep mirrors it.
+vtn_status vtn_sweep_single_site(vtn_ctx ctx, vtn_mpo mpo, vtn_mps* state, const vtn_sweep_opts* opts,
+                                 double alpha, double alpha_decay, double cutoff, vtn_sweep_report* report) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(mpo && state && opts, "null argument");
+        VTN_REQUIRE(opts->chi_max >= 1, "chi_max must be >= 1");
+        VTN_REQUIRE(opts->n_sweeps >= 0 && opts->n_sweeps <= 64, "n_sweeps must be in [0, 64]");
+        VTN_REQUIRE(opts->krylov_max >= 1 && opts->krylov_max <= 64, "krylov_max must be in [1, 64]");
+        VTN_REQUIRE(opts->lanczos_max_restarts >= 0, "lanczos_max_restarts must be >= 0");
+        VTN_REQUIRE(opts->n_schedule == 0 || opts->chi_schedule != nullptr, "chi_schedule missing");
+        VTN_REQUIRE(std::isfinite(alpha) && alpha >= 0.0, "alpha must be finite and >= 0");
+        VTN_REQUIRE(std::isfinite(alpha_decay) && alpha_decay >= 0.0, "alpha_decay must be finite and >= 0");
+        VTN_REQUIRE(std::isfinite(cutoff) && cutoff >= 0.0 && cutoff < 1.0, "cutoff must be in [0, 1)");
+        if (opts->prec != VTN_FP64) throw Error{VTN_EUNSUPPORTED, "the single-site solver runs in FP64 only"};
+        Ctx& c = ctx->c;
+        use_device(c);
+        ensure_mpo_device(ctx, mpo);
+        const int M = mpo->hp.M, d = mpo->hp.d;
+        std::vector<int> sched;
+        for (int i = 0; i < opts->n_schedule; ++i) {
+            VTN_REQUIRE(opts->chi_schedule[i] >= 1, "chi_schedule entries must be >= 1");
+            sched.push_back(std::min(opts->chi_schedule[i], opts->chi_max));
+        }
+        if (sched.empty()) sched.push_back(opts->chi_max);
+        if (*state == nullptr) {
+            vtn_status st = vtn_mps_random(ctx, mpo, sched[0], opts->seed, state);
+            if (st != VTN_OK) throw Error{st, c.err};
+        }
+        vtn_mps mps = *state;
+        check_mps_matches(mpo, mps);
+        int chi_cap = opts->chi_max;
+        for (int x : mps->dims) chi_cap = std::max(chi_cap, x);
+        mps_reserve(c, mps, chi_cap);
+        const std::vector<int> capdims = cap_dims(M, chi_cap);
+        Envs env;
+        env.c = &c;
+        env.L.assign(M + 1, nullptr);
+        env.R.assign(M + 1, nullptr);
+        for (int s = 0; s <= M; ++s) {
+            const size_t cap = (size_t)mpo->hp.w[s] * capdims[s] * capdims[s];
+            env.L[s] = (double2*)c.dalloc(sizeof(double2) * std::max(cap, size_t(1)));
+            env.R[s] = (double2*)c.dalloc(sizeof(double2) * std::max(cap, size_t(1)));
+        }
+        set_scalar_one(c, env.L[0]);
+        set_scalar_one(c, env.R[M]);
+        for (int s = M - 1; s >= 1; --s)
+            env_right_dev(c, mpo->dcores[s], mps->dims[s], mps->dims[s + 1], env.R[s + 1], mps->sites[s], env.R[s]);
+        int wmax = 1;
+        for (int x : mpo->hp.w) wmax = std::max(wmax, x);
+        const size_t site_cap = (size_t)chi_cap * d * chi_cap;
+        double2* x = (double2*)c.workspace(WS_VEC_T, sizeof(double2) * site_cap);
+        double2* Mx = (double2*)c.workspace(WS_EXPAND, sizeof(double2) * site_cap * (1 + (size_t)wmax));
+        double2* TL = (double2*)c.workspace(WS_TRUNC_L, sizeof(double2) * site_cap);
+        double2* TR = (double2*)c.workspace(WS_TRUNC_R, sizeof(double2) * site_cap);
+        double2* Cb = (double2*)c.workspace(WS_CENTER, sizeof(double2) * site_cap);
+        vtn_sweep_report rep;
+        std::memset(&rep, 0, sizeof(rep));
+        long long not_conv = 0;
+        // Lanczos on the centre tensor of site i, in place on x
+        auto optimise = [&](int i) {
+            const int cl = mps->dims[i], cr = mps->dims[i + 1];
+            const long long n = (long long)cl * d * cr;
+            const DevCore& W = mpo->dcores[i];
+            VTN_CUDA_TRY(cudaMemcpyAsync(x, mps->sites[i], sizeof(double2) * n, cudaMemcpyDeviceToDevice, c.stream));
+            LanczosResult lr = lanczos(c, n, x, opts->lanczos_tol, opts->krylov_max, opts->lanczos_max_restarts,
+                                       [&](const double2* in, double2* out) {
+                                           heff1_apply_dev(c, W, cl, cr, env.L[i], env.R[i + 1], in, out);
+                                       });
+            rep.matvecs += lr.n_matvec;
+            rep.heff_flops += heff1_flops(W, cl, cr) * lr.n_matvec;
+            if (!lr.converged) ++not_conv;
+        };
+        auto kept = [&](const TruncResult& tr) {
+            int k = 0;
+            if (!tr.lam.empty() && tr.lam[0] > 0.0)
+                for (double l : tr.lam) k += l > cutoff * tr.lam[0] ? 1 : 0;
+            return std::max(1, k);
+        };
+        double prevE = 0.0;
+        bool have_prev = false;
+        for (int sw = 0; sw < opts->n_sweeps; ++sw) {
+            const auto t0 = std::chrono::steady_clock::now();
+            const int chi_s = sched[std::min<size_t>(sw, sched.size() - 1)];
+            const double a_s = alpha * std::pow(alpha_decay, (double)sw);
+            double disc_max = 0.0;
+            if (M == 1) {
+                optimise(0);
+                VTN_CUDA_TRY(cudaMemcpyAsync(mps->sites[0], x, sizeof(double2) * d, cudaMemcpyDeviceToDevice, c.stream));
+            }
+            for (int i = 0; i + 1 < M; ++i) {  // to the right
+                const int cl = mps->dims[i], cr = mps->dims[i + 1], cn = mps->dims[i + 2];
+                const DevCore& W = mpo->dcores[i];
+                optimise(i);
+                expand_right_dev(c, W, cl, cr, env.L[i], x, a_s, Mx);
+                const int K = cr * (1 + W.wr);
+                const int kmax = std::min(chi_s, d * cn);
+                TruncResult tr = truncate_dev(c, cl, d, 1, K, 0, kmax, Mx, TL, TR, cr);
+                const int k = kept(tr);
+                disc_max = std::max(disc_max, tr.discarded);
+                // A_i <- the first k columns of U (cl d x tr.k)
+                VTN_CUDA_TRY(cudaMemcpy2DAsync(mps->sites[i], sizeof(double2) * k, TL, sizeof(double2) * tr.k,
+                                               sizeof(double2) * k, (size_t)cl * d, cudaMemcpyDeviceToDevice,
+                                               c.stream));
+                // centre (U_k^dag A) A_{i+1}: k x (d cn)
+                GemmArgs g;
+                g.M = k; g.N = d * cn; g.K = cr;
+                g.A = TR; g.lda = cr;
+                g.B = mps->sites[i + 1]; g.ldb = (long long)d * cn;
+                g.C = Cb; g.ldc = (long long)d * cn;
+                gemm_c64(c, g);
+                VTN_CUDA_TRY(cudaMemcpyAsync(mps->sites[i + 1], Cb, sizeof(double2) * (size_t)k * d * cn,
+                                             cudaMemcpyDeviceToDevice, c.stream));
+                mps->dims[i + 1] = k;
+                env_left_dev(c, W, cl, k, env.L[i], mps->sites[i], env.L[i + 1]);
+            }
+            for (int i = M - 1; i >= 1; --i) {  // to the left
+                const int cp = mps->dims[i - 1], cl = mps->dims[i], cr = mps->dims[i + 1];
+                const DevCore& W = mpo->dcores[i];
+                optimise(i);
+                expand_left_dev(c, W, cl, cr, env.R[i + 1], x, a_s, Mx);
+                const int Kr = cl * (1 + W.wl);
+                const int kmax = std::min(chi_s, cp * d);
+                TruncResult tr = truncate_dev(c, Kr, 1, d, cr, 1, kmax, Mx, TL, TR, cl);
+                const int k = kept(tr);
+                disc_max = std::max(disc_max, tr.discarded);
+                // A_i <- the first k rows of V^dag (right-canonical, k x d cr)
+                VTN_CUDA_TRY(cudaMemcpyAsync(mps->sites[i], TR, sizeof(double2) * (size_t)k * d * cr,
+                                             cudaMemcpyDeviceToDevice, c.stream));
+                // centre A_{i-1} (A V_k): (cp d) x k, A V_k = the first cl rows of Mx V (ld tr.k)
+                GemmArgs g;
+                g.M = cp * d; g.N = k; g.K = cl;
+                g.A = mps->sites[i - 1]; g.lda = cl;
+                g.B = TL; g.ldb = tr.k;
+                g.C = Cb; g.ldc = k;
+                gemm_c64(c, g);
+                VTN_CUDA_TRY(cudaMemcpyAsync(mps->sites[i - 1], Cb, sizeof(double2) * (size_t)cp * d * k,
+                                             cudaMemcpyDeviceToDevice, c.stream));
+                mps->dims[i] = k;
+                env_right_dev(c, W, k, cr, env.R[i + 1], mps->sites[i], env.R[i]);
+            }
+            mps->center = 0;
+            const double E = energy_dev(c, mpo, mps);
+            c.sync();
+            const auto t1 = std::chrono::steady_clock::now();
+            rep.energy[sw] = E;
+            rep.max_discarded[sw] = disc_max;
+            rep.seconds[sw] = std::chrono::duration<double>(t1 - t0).count();
+            rep.sweeps_done = sw + 1;
+            if (opts->use_e_target && E <= opts->e_target) break;
+            if (have_prev && opts->e_tol > 0 && std::fabs(E - prevE) <= opts->e_tol) break;
+            prevE = E;
+            have_prev = true;
+        }
+        c.tflush();
+        c.check_dstatus();
+        rep.lanczos_not_converged = not_conv;
+        rep.heff_seconds = c.tc[TC_HEFF].seconds;
+        rep.gemm_flops = c.tc[TC_GEMM].flops;
+        rep.gemm_seconds = c.tc[TC_GEMM].seconds;
+        rep.eig_seconds = c.tc[TC_EIG].seconds;
+        if (report) *report = rep;
+        if (not_conv > 0) {
+            c.err = std::to_string(not_conv) + " Lanczos solves missed the tolerance";
+            return VTN_ENOCONV;
+        }
+        return VTN_OK;
+    });
+}
+
 vtn_status vtn_energy_variance(vtn_ctx ctx, vtn_mpo mpo, vtn_mps mps, double* E, double* H2, double* sigma) {
     if (!ctx) return VTN_EINVAL;
     return guard(ctx, [&]() -> vtn_status {
@@ -1044,6 +1258,47 @@ vtn_status vtn_env_update(vtn_ctx ctx, const vtn_core* W, int side, int chi_l, i
         }
         c.check_dstatus();
         c.sync();
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_heff1_apply(vtn_ctx ctx, const vtn_core* W, int chi_l, int chi_r, const double* L, const double* R,
+                           const double* A, double* y) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(L && R && A && y, "null device pointer");
+        VTN_REQUIRE(chi_l >= 1 && chi_r >= 1, "bond dimensions must be >= 1");
+        VTN_REQUIRE(A != y, "y must not alias A");
+        Ctx& c = ctx->c;
+        use_device(c);
+        HostCore h = core_from_abi(W);
+        TempCore tc(c, h);
+        heff1_apply_dev(c, tc.dc, chi_l, chi_r, (const double2*)L, (const double2*)R, (const double2*)A, (double2*)y);
+        c.sync();
+        c.check_dstatus();
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_expand(vtn_ctx ctx, const vtn_core* W, int side, int chi_l, int chi_r, const double* env,
+                      const double* A, double alpha, double* out) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(env && A && out, "null device pointer");
+        VTN_REQUIRE(side == 0 || side == 1, "side must be 0 (expand to the right) or 1 (to the left)");
+        VTN_REQUIRE(chi_l >= 1 && chi_r >= 1, "bond dimensions must be >= 1");
+        VTN_REQUIRE(std::isfinite(alpha), "alpha must be finite");
+        VTN_REQUIRE(A != out && env != out, "out must not alias the inputs");
+        Ctx& c = ctx->c;
+        use_device(c);
+        HostCore h = core_from_abi(W);
+        TempCore tc(c, h);
+        if (side == 0)
+            expand_right_dev(c, tc.dc, chi_l, chi_r, (const double2*)env, (const double2*)A, alpha, (double2*)out);
+        else
+            expand_left_dev(c, tc.dc, chi_l, chi_r, (const double2*)env, (const double2*)A, alpha, (double2*)out);
+        c.sync();
+        c.check_dstatus();
         return VTN_OK;
     });
 }

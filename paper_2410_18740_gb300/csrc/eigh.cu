@@ -1073,10 +1073,12 @@ __global__ void __launch_bounds__(BT_THREADS) backtransform(int n, int k, const 
 }  // namespace
 
 TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int direction, int k_max,
-                         const double2* theta, double2* left, double2* right) {
+                         const double2* theta, double2* left, double2* right, int outer) {
     const int nL = chi_l * d1, nR = d2 * chi_r;
     const int n = direction == 0 ? nL : nR;
     const int k = std::min(k_max, std::min(nL, nR));
+    if (outer < 0) outer = direction == 0 ? nR : nL;
+    VTN_REQUIRE(outer >= 1 && outer <= (direction == 0 ? nR : nL), "truncation output range out of bounds");
     VTN_REQUIRE(k >= 1, "truncation keeps no state");
     VTN_REQUIRE(n <= 12288, "reduced density matrix larger than 12288 is not supported");
     int tt = ctx.tbegin(TC_EIG, 0.0);
@@ -1214,19 +1216,19 @@ TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int dir
     }
     if (direction == 0) {
         backtransform<<<nbt, BT_THREADS, shm, ctx.stream>>>(n, k, H, s, Tall, Z, 0, left);
-        // right = U^dag T
+        // right = U^dag T (its first `outer` columns)
         GemmArgs c;
-        c.M = k; c.N = nR; c.K = nL;
+        c.M = k; c.N = outer; c.K = nL;
         c.opA = OP_C; c.A = left; c.lda = k;
         c.B = theta; c.ldb = nR;
-        c.C = right; c.ldc = nR;
+        c.C = right; c.ldc = outer;
         ctx.count_launch();
         gemm_c64(ctx, c);
     } else {
         backtransform<<<nbt, BT_THREADS, shm, ctx.stream>>>(n, k, H, s, Tall, Z, 1, right);
-        // left = T V = T (V^dag)^dag
+        // left = T V = T (V^dag)^dag (its first `outer` rows)
         GemmArgs c;
-        c.M = nL; c.N = k; c.K = nR;
+        c.M = outer; c.N = k; c.K = nR;
         c.A = theta; c.lda = nR;
         c.opB = OP_C; c.B = right; c.ldb = nR;
         c.C = left; c.ldc = k;

@@ -123,7 +123,8 @@ struct Ctx {
 enum WsSlot {
     WS_X = 0, WS_Y, WS_Z, WS_KRYLOV, WS_VEC_W, WS_VEC_T, WS_PARTIAL, WS_SCAL, WS_EIG_A, WS_EIG_H,
     WS_EIG_Y, WS_EIG_WORK, WS_EIG_U, WS_CORE_A, WS_CORE_B, WS_ENV_TMP, WS_MISC, WS_TC_L, WS_TC_R, WS_TC_B1,
-    WS_TC_A2, WS_TC_PART, WS_GEMM_SPLIT, WS_EIG_PART, WS_TC_ENV, WS_EIG_T, WS_H2_ENV, WS_COUNT
+    WS_TC_A2, WS_TC_PART, WS_GEMM_SPLIT, WS_EIG_PART, WS_TC_ENV, WS_EIG_T, WS_H2_ENV, WS_EXPAND,
+    WS_TRUNC_L, WS_TRUNC_R, WS_CENTER, WS_COUNT
 };
 
 // ------------------------------------------------------------------ cores
@@ -201,6 +202,14 @@ void heff_apply_bf16x3(Ctx& ctx, const DevCore& Wi, const DevCore& Wj, const Hef
                        double2* y);
 void env_left2_dev(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const double2* L2, const double2* A,
                    double2* out, double2* tv, double2* u);
+// single-site DMRG with subspace expansion (single_site.cu)
+double heff1_flops(const DevCore& W, int chi_l, int chi_r);
+void heff1_apply_dev(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const double2* L, const double2* R,
+                     const double2* A, double2* y);
+void expand_right_dev(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const double2* L, const double2* A,
+                      double alpha, double2* Mx);
+void expand_left_dev(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const double2* R, const double2* A,
+                     double alpha, double2* Mx);
 void env_left_bf16x3(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const double2* L, const double2* A,
                      double2* out);
 void env_right_bf16x3(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const double2* R, const double2* A,
@@ -240,8 +249,11 @@ struct TruncResult {
     double discarded;
     std::vector<double> lam;
 };
+// outer >= 0 limits the product formed after the eigendecomposition: direction 0 writes
+// only the first `outer` columns of right (leading dimension outer), direction 1 only the
+// first `outer` rows of left.
 TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int direction, int k_max,
-                         const double2* theta, double2* left, double2* right);
+                         const double2* theta, double2* left, double2* right, int outer = -1);
 
 // ------------------------------------------------------------------ misc kernels
 void fill_random_normal(Ctx& ctx, double2* out, long long count, uint64_t seed, int site);

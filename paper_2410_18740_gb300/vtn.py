@@ -88,6 +88,11 @@ _SIGS = {
     "vtn_sweep_opts_default": [C.POINTER(vtn_sweep_opts)],
     "vtn_sweep": [_P, _P, C.POINTER(_P), C.POINTER(vtn_sweep_opts), C.POINTER(vtn_sweep_report)],
     "vtn_build_mpo_cz": [_P, _I, _PD, _PD, _I, _D, C.POINTER(C.c_void_p)],
+    "vtn_mpo_from_cores": [_P, _I, C.POINTER(vtn_core), C.POINTER(_P)],
+    "vtn_sweep_single_site": [_P, _P, C.POINTER(_P), C.POINTER(vtn_sweep_opts), _D, _D, _D,
+                              C.POINTER(vtn_sweep_report)],
+    "vtn_heff1_apply": [_P, C.POINTER(vtn_core), _I, _I, _P, _P, _P, _P],
+    "vtn_expand": [_P, C.POINTER(vtn_core), _I, _I, _I, _P, _P, _D, _P],
     "vtn_energy": [_P, _P, _P, _PD],
     "vtn_energy_variance": [_P, _P, _P, _PD, _PD, _PD],
     "vtn_marginals": [_P, _P, _P, _PI, _I, _PD],
@@ -357,6 +362,19 @@ def vtn_sweep(ctx, mpo, state=None, opts=None, **kw):
     return st, st_ptr, _report_dict(rep)
 
 
+def vtn_sweep_single_site(ctx, mpo, state=None, opts=None, alpha=1e-2, alpha_decay=0.5, cutoff=1e-12, **kw):
+    """Single-site DMRG with subspace expansion.  Returns (status, mps, report);
+    VTN_ENOCONV is returned, not raised."""
+    if opts is None:
+        opts = vtn_sweep_opts_default(**kw)
+    st_ptr = C.c_void_p(state.value if state is not None else None)
+    rep = vtn_sweep_report()
+    st = lib().vtn_sweep_single_site(ctx, mpo, C.byref(st_ptr), C.byref(opts), float(alpha), float(alpha_decay),
+                                     float(cutoff), C.byref(rep))
+    _check(ctx, st, ok=(VTN_OK, VTN_ENOCONV))
+    return st, st_ptr, _report_dict(rep)
+
+
 def vtn_energy(ctx, mpo, mps):
     v = C.c_double()
     _check(ctx, lib().vtn_energy(ctx, mpo, mps, C.byref(v)))
@@ -407,6 +425,34 @@ def make_core(w_left, w_right, d, rows, cols, ops):
 def core_from_sparse(sc):
     """vtn_core from a paper_2410_18740_gb300.inputs.SparseCore."""
     return make_core(sc.w_left, sc.w_right, sc.d, sc.rows, sc.cols, sc.ops)
+
+
+def core_from_dense(W):
+    """vtn_core from a dense core W[a, b, s', s]: one entry per (a, b) block that is not zero."""
+    W = np.asarray(W, dtype=np.complex128)
+    wl, wr, d, _ = W.shape
+    pairs = [(a, b) for a in range(wl) for b in range(wr) if np.any(W[a, b] != 0)]
+    ops = np.array([W[a, b] for a, b in pairs]) if pairs else np.zeros((0, d, d), np.complex128)
+    return make_core(wl, wr, d, [a for a, _ in pairs], [b for _, b in pairs], ops)
+
+
+def vtn_mpo_from_cores(ctx, cores):
+    """MPO from its cores (dense W[a, b, s', s] arrays or vtn_core); ctx may be None."""
+    cs = [c if isinstance(c, vtn_core) else core_from_dense(c) for c in cores]
+    arr = (vtn_core * len(cs))(*cs)
+    out = C.c_void_p()
+    _check(ctx, lib().vtn_mpo_from_cores(ctx, len(cs), arr, C.byref(out)))
+    return out
+
+
+def vtn_heff1_apply(ctx, W, chi_l, chi_r, L, R, A, y):
+    _check(ctx, lib().vtn_heff1_apply(ctx, C.byref(W), int(chi_l), int(chi_r), _dptr(L), _dptr(R), _dptr(A),
+                                      _dptr(y)))
+
+
+def vtn_expand(ctx, W, side, chi_l, chi_r, env, A, alpha, out):
+    _check(ctx, lib().vtn_expand(ctx, C.byref(W), int(side), int(chi_l), int(chi_r), _dptr(env), _dptr(A),
+                                 float(alpha), _dptr(out)))
 
 
 def vtn_heff_apply(ctx, Wi, Wj, chi_l, chi_r, L, R, theta, y, prec=VTN_FP64):

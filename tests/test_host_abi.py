@@ -140,3 +140,37 @@ def test_cz_mpo_kappa_zero_and_validation(libvtn):
         vtn.vtn_build_mpo_cz(None, w.r[:1], w.U[:1, :1], 3, 0.1)          # M = 1
     with pytest.raises(vtn.VtnError):
         vtn.vtn_build_mpo_cz(None, w.r, w.U, 3, float("nan"))
+
+
+@pytest.mark.parametrize("seed,M,d", [(0, 1, 3), (1, 4, 3), (2, 3, 4)])
+def test_mpo_from_cores_round_trip(libvtn, seed, M, d):
+    """Cores handed over as dense arrays come back unchanged and contract to the same H."""
+    w = inputs.workload("plain", seed, M=M, d=d, D=d)
+    G = gbs.hamiltonian_coefficients(w.r, w.U)
+    cores = ompo.build_mpo(G, d)
+    m = vtn.vtn_mpo_from_cores(None, cores)
+    try:
+        Mo, do, Do, wd = vtn.vtn_mpo_info(m)
+        assert (Mo, do, Do) == (M, d, d)
+        assert list(wd) == [1] + [c.shape[1] for c in cores]
+        assert np.abs(_dense_from_abi(m) - dense.dense_hamiltonian(G, d).toarray()).max() < 1e-12
+        for s in range(M):
+            assert np.abs(vtn.vtn_mpo_isometry(m, s) - np.eye(d)).max() == 0.0
+        with pytest.raises(vtn.VtnError):
+            vtn.vtn_mpo_coefficients(m)
+        assert vtn.vtn_mpo_norm_bound(m) == 0.0
+    finally:
+        vtn.vtn_mpo_free(m)
+
+
+def test_mpo_from_cores_validation(libvtn):
+    w = inputs.workload("plain", 0, M=3, d=3, D=3)
+    cores = ompo.build_mpo(gbs.hamiltonian_coefficients(w.r, w.U), 3)
+    with pytest.raises(vtn.VtnError):
+        vtn.vtn_mpo_from_cores(None, [cores[0], cores[1][:5], cores[2]])  # channels do not chain
+    with pytest.raises(vtn.VtnError):
+        vtn.vtn_mpo_from_cores(None, cores[1:])                          # first core has w_left > 1
+    bad = [c.copy() for c in cores]
+    bad[1] = np.zeros(bad[1].shape[:2] + (2, 2), complex)
+    with pytest.raises(vtn.VtnError):
+        vtn.vtn_mpo_from_cores(None, bad)                                # mixed d
