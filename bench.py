@@ -78,9 +78,10 @@ def parse():
                    help="skip the single FP64 sweep measured after the timed region")
     p.add_argument("--no-tte", action="store_true",
                    help="skip the time-to-eps measurement (FP64 reference run + mixed run from a random state)")
-    p.add_argument("--case", default=None, choices=["heff", "trunc", "tte"],
+    p.add_argument("--case", default=None, choices=["heff", "trunc", "tte", "dmrg1"],
                    help="heff / trunc: only that kernel at the middle-bond shape (for profiler captures); "
-                        "tte: time-to-eps of the mixed and the FP64 solver from the same random state")
+                        "tte: time-to-eps of the mixed and the FP64 solver from the same random state; "
+                        "dmrg1: --ref-sweeps sweeps of the single-site solver with subspace expansion")
     p.add_argument("--trunc-shape", type=int, nargs=2, default=None, metavar=("CHI", "D"),
                    help="trunc: theta (CHI, D, D, CHI) with k = CHI (default: the split workload's middle "
                         "bond, 128 8; the large workload's is 512 6)")
@@ -597,6 +598,41 @@ def run_case_tte(args):
     vtn.vtn_destroy(ctx)
 
 
+def run_case_dmrg1(args):
+    """Single-site DMRG with subspace expansion (FP64) on the split workload from the seeded
+    random MPS at chi = 16, chi schedule 16, 32, 64, 128, expansion weight 1e-2 halved every
+    sweep, Lanczos as in the time-to-eps measurement (so its energies compare sweep by sweep
+    with the two-site FP64 solver's from the same start); one JSON line with the energy and
+    time of every sweep."""
+    from paper_2410_18740_gb300 import build as vbuild
+    from paper_2410_18740_gb300 import inputs, vtn
+
+    vbuild.build()
+    w = inputs.workload(WORKLOAD, args.seed)
+    ctx = vtn.vtn_create(0)
+    mpo = vtn.vtn_build_mpo(ctx, w.r, w.U, w.D, w.d)
+    sched = [16, 32, 64, CHI]
+    opts = vtn.vtn_sweep_opts_default(chi_max=CHI, n_sweeps=args.ref_sweeps, chi_schedule=sched, seed=args.seed,
+                                      lanczos_tol=1e-12, krylov_max=KRYLOV, lanczos_max_restarts=0)
+    vtn.vtn_timing(ctx, True)
+    vtn.vtn_timing_reset(ctx)
+    t0 = time.perf_counter()
+    st, mps, rep = vtn.vtn_sweep_single_site(ctx, mpo, None, opts, alpha=1e-2, alpha_decay=0.5, cutoff=1e-12)
+    wall = time.perf_counter() - t0
+    n = rep["sweeps_done"]
+    _, _, dims = vtn.vtn_mps_info(mps)
+    line = {"case": "dmrg1", "workload": f"split: M={w.M}, d=D={w.d}, seed {args.seed}",
+            "solver": "single-site DMRG with subspace expansion, FP64", "chi_schedule": sched,
+            "alpha": [1e-2 * 0.5 ** t for t in range(n)], "sweeps": n, "energies": rep["energy"][:n],
+            "seconds": rep["seconds"][:n], "wall_s": wall, "max_bond": int(max(dims)),
+            "heff_tflops": rep["heff_flops"] / rep["heff_seconds"] / 1e12 if rep["heff_seconds"] else None,
+            "matvecs": rep["matvecs"], "eig_s": rep["eig_seconds"]}
+    print(json.dumps(line), flush=True)
+    vtn.vtn_mps_free(mps)
+    vtn.vtn_mpo_free(mpo)
+    vtn.vtn_destroy(ctx)
+
+
 def main():
     args = parse()
     if args.case == "heff":
@@ -605,6 +641,8 @@ def main():
         run_case_trunc(args)
     elif args.case == "tte":
         run_case_tte(args)
+    elif args.case == "dmrg1":
+        run_case_dmrg1(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
