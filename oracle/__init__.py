@@ -25,6 +25,7 @@ Modules (each function cites the passage of the paper it follows):
                      "Discussion"): single-site effective Hamiltonian, expansion, sweeps.
 * ``nongauss``    -- the global-CZ (non-Gaussian) parent Hamiltonian (Eq. nonGBSHamiltonian):
                      definition, term expansion and its MPO.
+* ``mlp``         -- the warm start's multilayer perceptron: forward, MSE gradient, Adam.
 * ``observables`` -- Fock-basis marginals after the inverse basis transformation and
                      sequential conditional sampling.
 
