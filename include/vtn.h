@@ -48,6 +48,7 @@ extern "C" {
 typedef struct vtn_ctx_s* vtn_ctx;
 typedef struct vtn_mpo_s* vtn_mpo;
 typedef struct vtn_mps_s* vtn_mps;
+typedef struct vtn_mlp_s* vtn_mlp;
 
 typedef enum {
     VTN_OK = 0,
@@ -372,6 +373,39 @@ vtn_status vtn_lbo_rotate(vtn_ctx ctx, int chi_l, int d, int D, int chi_r, const
 vtn_status vtn_heff_apply_static(const vtn_core* Wi, const vtn_core* Wj, int chi_l, int chi_r,
                                  const double* L, const double* R, const double* theta, double* y,
                                  void* cuda_stream);
+
+/* ---------------------------------------------------------------- learned warm start
+ * The multilayer perceptron the warm start trains and evaluates (the paper has no learned
+ * component; the network maps instance features to solver inputs and the variational energy
+ * judges the result).  FP32 on the device: layers n_in -> width (x depth) -> n_out, ReLU after
+ * every layer but the last, mean-squared-error loss, Adam (beta1 0.9, beta2 0.999, eps 1e-8;
+ * Kingma and Ba 2015).  Parameters are one float array: per layer l, W_l (n_out_l x n_in_l,
+ * row-major) then b_l (n_out_l).  x: device float[batch*n_in], t and y: device float[batch*n_out],
+ * row-major.  Every call runs on the context's stream and returns after it finished; sums run
+ * in a fixed order, so results repeat bit for bit. */
+
+/* Create with He-uniform weights (W_l entries uniform in +-sqrt(6 / n_in_l) from a splitmix64
+ * stream seeded with seed), zero biases and zero Adam moments.  1 <= n_in, width, n_out <= 4096,
+ * 0 <= depth <= 16. */
+vtn_status vtn_mlp_create(vtn_ctx ctx, int n_in, int width, int depth, int n_out, uint64_t seed, vtn_mlp* out);
+vtn_status vtn_mlp_free(vtn_mlp mlp);
+/* Shape, parameter count and Adam steps taken (each pointer may be NULL). */
+vtn_status vtn_mlp_info(vtn_mlp mlp, int* n_in, int* width, int* depth, int* n_out, long long* n_params,
+                        long long* steps);
+/* Copy the parameters to / from host float[n_params]; set also clears the Adam moments and
+ * the step count. */
+vtn_status vtn_mlp_get_params(vtn_ctx ctx, vtn_mlp mlp, float* host);
+vtn_status vtn_mlp_set_params(vtn_ctx ctx, vtn_mlp mlp, const float* host);
+/* y = net(x) for batch rows (1 <= batch <= 4,000,000). */
+vtn_status vtn_mlp_forward(vtn_ctx ctx, vtn_mlp mlp, int batch, const float* x, float* y);
+/* loss = mean over batch*n_out entries of (net(x) - t)^2 (host float) and its gradient with
+ * respect to the parameters (host float[n_params]; may be NULL). */
+vtn_status vtn_mlp_loss_grad(vtn_ctx ctx, vtn_mlp mlp, int batch, const float* x, const float* t, float* loss,
+                             float* grad);
+/* One Adam step with learning rate lr > 0 on the batch; loss (host, may be NULL) is the loss
+ * before the step. */
+vtn_status vtn_mlp_train_step(vtn_ctx ctx, vtn_mlp mlp, int batch, const float* x, const float* t, float lr,
+                              float* loss);
 
 /* Real bf16 GEMM on the tensor cores (the kernel behind VTN_BF16X3):
  *   D[m][n] = sum_k A[m][k] * B[n][k], FP32 accumulation,

@@ -1364,6 +1364,182 @@ vtn_status vtn_lbo_rotate(vtn_ctx ctx, int chi_l, int d, int D, int chi_r, const
     });
 }
 
+// ------------------------------------------------------------------ learned warm start: MLP
+namespace {
+
+void destroy_mlp(vtn_mlp m) {
+    if (!m) return;
+    if (m->owner) {
+        Ctx& c = m->owner->c;
+        c.dfree(m->params);
+        c.dfree(m->m);
+        c.dfree(m->v);
+        c.dfree(m->grad);
+        c.dfree(m->loss);
+    }
+    delete m;
+}
+
+void check_mlp(vtn_ctx ctx, vtn_mlp mlp) {
+    VTN_REQUIRE(mlp != nullptr, "null MLP");
+    VTN_REQUIRE(mlp->owner == ctx, "MLP belongs to another context");
+}
+
+uint64_t splitmix64(uint64_t& state) {
+    uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+}  // namespace
+
+vtn_status vtn_mlp_create(vtn_ctx ctx, int n_in, int width, int depth, int n_out, uint64_t seed, vtn_mlp* out) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(out != nullptr, "null argument");
+        VTN_REQUIRE(n_in >= 1 && n_in <= 4096 && width >= 1 && width <= 4096 && n_out >= 1 && n_out <= 4096,
+                    "layer sizes must be in [1, 4096]");
+        VTN_REQUIRE(depth >= 0 && depth <= 16, "depth must be in [0, 16]");
+        Ctx& c = ctx->c;
+        use_device(c);
+        vtn_mlp m = new vtn_mlp_s();
+        m->shape = MlpShape(n_in, width, depth, n_out);
+        m->owner = ctx;
+        const long long n = m->shape.n_params;
+        try {
+            m->params = (float*)c.dalloc(sizeof(float) * n);
+            m->m = (float*)c.dalloc(sizeof(float) * n);
+            m->v = (float*)c.dalloc(sizeof(float) * n);
+            m->grad = (float*)c.dalloc(sizeof(float) * n);
+            m->loss = (float*)c.dalloc(sizeof(float));
+            std::vector<float> h((size_t)n, 0.0f);
+            uint64_t st = seed;
+            for (int l = 0; l <= depth; ++l) {
+                const int a = m->shape.in_of(l), b = m->shape.out_of(l);
+                const float lim = (float)std::sqrt(6.0 / a);
+                for (long long e = 0; e < (long long)a * b; ++e) {
+                    const float u = (float)(splitmix64(st) >> 40) * (1.0f / 16777216.0f);  // [0, 1)
+                    h[(size_t)(m->shape.offW[l] + e)] = (2.0f * u - 1.0f) * lim;
+                }
+            }
+            VTN_CUDA_TRY(cudaMemcpyAsync(m->params, h.data(), sizeof(float) * n, cudaMemcpyHostToDevice, c.stream));
+            VTN_CUDA_TRY(cudaMemsetAsync(m->m, 0, sizeof(float) * n, c.stream));
+            VTN_CUDA_TRY(cudaMemsetAsync(m->v, 0, sizeof(float) * n, c.stream));
+            c.sync();
+        } catch (...) {
+            destroy_mlp(m);
+            throw;
+        }
+        *out = m;
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_mlp_free(vtn_mlp mlp) {
+    if (!mlp) return VTN_EINVAL;
+    if (mlp->owner) cudaStreamSynchronize(mlp->owner->c.stream);
+    destroy_mlp(mlp);
+    return VTN_OK;
+}
+
+vtn_status vtn_mlp_info(vtn_mlp mlp, int* n_in, int* width, int* depth, int* n_out, long long* n_params,
+                        long long* steps) {
+    if (!mlp) return VTN_EINVAL;
+    if (n_in) *n_in = mlp->shape.n_in;
+    if (width) *width = mlp->shape.width;
+    if (depth) *depth = mlp->shape.depth;
+    if (n_out) *n_out = mlp->shape.n_out;
+    if (n_params) *n_params = mlp->shape.n_params;
+    if (steps) *steps = mlp->step;
+    return VTN_OK;
+}
+
+vtn_status vtn_mlp_get_params(vtn_ctx ctx, vtn_mlp mlp, float* host) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        check_mlp(ctx, mlp);
+        VTN_REQUIRE(host != nullptr, "null argument");
+        Ctx& c = ctx->c;
+        use_device(c);
+        VTN_CUDA_TRY(cudaMemcpyAsync(host, mlp->params, sizeof(float) * mlp->shape.n_params, cudaMemcpyDeviceToHost,
+                                     c.stream));
+        c.sync();
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_mlp_set_params(vtn_ctx ctx, vtn_mlp mlp, const float* host) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        check_mlp(ctx, mlp);
+        VTN_REQUIRE(host != nullptr, "null argument");
+        Ctx& c = ctx->c;
+        use_device(c);
+        const size_t bytes = sizeof(float) * mlp->shape.n_params;
+        VTN_CUDA_TRY(cudaMemcpyAsync(mlp->params, host, bytes, cudaMemcpyHostToDevice, c.stream));
+        VTN_CUDA_TRY(cudaMemsetAsync(mlp->m, 0, bytes, c.stream));
+        VTN_CUDA_TRY(cudaMemsetAsync(mlp->v, 0, bytes, c.stream));
+        c.sync();
+        mlp->step = 0;
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_mlp_forward(vtn_ctx ctx, vtn_mlp mlp, int batch, const float* x, float* y) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        check_mlp(ctx, mlp);
+        VTN_REQUIRE(x && y, "null device pointer");
+        VTN_REQUIRE(batch >= 1 && batch <= 4000000, "batch must be in [1, 4000000]");
+        Ctx& c = ctx->c;
+        use_device(c);
+        const MlpShape& s = mlp->shape;
+        float* acts = (float*)c.workspace(WS_MLP_ACT, sizeof(float) * ((size_t)std::max(s.depth, 1) * batch * s.width));
+        mlp_forward_dev(c, s, mlp->params, batch, x, acts, y);
+        c.sync();
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_mlp_loss_grad(vtn_ctx ctx, vtn_mlp mlp, int batch, const float* x, const float* t, float* loss,
+                             float* grad) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        check_mlp(ctx, mlp);
+        VTN_REQUIRE(x && t && loss, "null argument");
+        VTN_REQUIRE(batch >= 1 && batch <= 4000000, "batch must be in [1, 4000000]");
+        Ctx& c = ctx->c;
+        use_device(c);
+        mlp_loss_grad_dev(c, mlp->shape, mlp->params, batch, x, t, mlp->grad, mlp->loss);
+        VTN_CUDA_TRY(cudaMemcpyAsync(loss, mlp->loss, sizeof(float), cudaMemcpyDeviceToHost, c.stream));
+        if (grad)
+            VTN_CUDA_TRY(cudaMemcpyAsync(grad, mlp->grad, sizeof(float) * mlp->shape.n_params, cudaMemcpyDeviceToHost,
+                                         c.stream));
+        c.sync();
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_mlp_train_step(vtn_ctx ctx, vtn_mlp mlp, int batch, const float* x, const float* t, float lr,
+                              float* loss) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        check_mlp(ctx, mlp);
+        VTN_REQUIRE(x && t, "null device pointer");
+        VTN_REQUIRE(batch >= 1 && batch <= 4000000, "batch must be in [1, 4000000]");
+        VTN_REQUIRE(std::isfinite(lr) && lr > 0.0f, "lr must be finite and > 0");
+        Ctx& c = ctx->c;
+        use_device(c);
+        mlp_loss_grad_dev(c, mlp->shape, mlp->params, batch, x, t, mlp->grad, mlp->loss);
+        mlp_adam_dev(c, mlp->shape.n_params, mlp->params, mlp->m, mlp->v, mlp->grad, lr, mlp->step + 1);
+        if (loss) VTN_CUDA_TRY(cudaMemcpyAsync(loss, mlp->loss, sizeof(float), cudaMemcpyDeviceToHost, c.stream));
+        c.sync();
+        ++mlp->step;
+        return VTN_OK;
+    });
+}
+
 vtn_status vtn_gemm_bf16(vtn_ctx ctx, int M, int N, int K, const void* A, long long lda, const void* B,
                          long long ldb, void* D, long long ldd, int d_fp64) {
     if (!ctx) return VTN_EINVAL;

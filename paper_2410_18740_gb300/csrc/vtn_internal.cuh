@@ -124,7 +124,7 @@ enum WsSlot {
     WS_X = 0, WS_Y, WS_Z, WS_KRYLOV, WS_VEC_W, WS_VEC_T, WS_PARTIAL, WS_SCAL, WS_EIG_A, WS_EIG_H,
     WS_EIG_Y, WS_EIG_WORK, WS_EIG_U, WS_CORE_A, WS_CORE_B, WS_ENV_TMP, WS_MISC, WS_TC_L, WS_TC_R, WS_TC_B1,
     WS_TC_A2, WS_TC_PART, WS_GEMM_SPLIT, WS_EIG_PART, WS_TC_ENV, WS_EIG_T, WS_H2_ENV, WS_EXPAND,
-    WS_TRUNC_L, WS_TRUNC_R, WS_CENTER, WS_COUNT
+    WS_TRUNC_L, WS_TRUNC_R, WS_CENTER, WS_MLP_ACT, WS_MLP_Y, WS_MLP_G, WS_COUNT
 };
 
 // ------------------------------------------------------------------ cores
@@ -202,6 +202,21 @@ void heff_apply_bf16x3(Ctx& ctx, const DevCore& Wi, const DevCore& Wj, const Hef
                        double2* y);
 void env_left2_dev(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const double2* L2, const double2* A,
                    double2* out, double2* tv, double2* u);
+// multilayer perceptron of the learned warm start (mlp.cu)
+struct MlpShape {
+    int n_in = 0, width = 0, depth = 0, n_out = 0;
+    long long n_params = 0;
+    std::vector<long long> offW, offb;  // per layer: offsets of W_l and b_l in the flat parameters
+    MlpShape() = default;
+    MlpShape(int n_in, int width, int depth, int n_out);
+    int in_of(int l) const { return l == 0 ? n_in : width; }
+    int out_of(int l) const { return l == depth ? n_out : width; }
+};
+void mlp_forward_dev(Ctx& ctx, const MlpShape& s, const float* params, int B, const float* x, float* acts,
+                     float* y);
+void mlp_loss_grad_dev(Ctx& ctx, const MlpShape& s, const float* params, int B, const float* x, const float* t,
+                       float* grad, float* loss);
+void mlp_adam_dev(Ctx& ctx, long long n, float* p, float* m, float* v, const float* g, float lr, long long step);
 // single-site DMRG with subspace expansion (single_site.cu)
 double heff1_flops(const DevCore& W, int chi_l, int chi_r);
 void heff1_apply_dev(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const double2* L, const double2* R,
@@ -278,6 +293,17 @@ struct vtn_mpo_s {
     vtn_ctx owner = nullptr;
     std::vector<vtn::DevCore> dcores;
     double2* iso_dev = nullptr;  // M * D * d
+};
+
+struct vtn_mlp_s {
+    vtn::MlpShape shape;
+    float* params = nullptr;  // device, n_params each
+    float* m = nullptr;
+    float* v = nullptr;
+    float* grad = nullptr;
+    float* loss = nullptr;    // device scalar
+    long long step = 0;       // Adam steps taken
+    vtn_ctx owner = nullptr;
 };
 
 struct vtn_mps_s {

@@ -92,6 +92,14 @@ _SIGS = {
     "vtn_sweep_single_site": [_P, _P, C.POINTER(_P), C.POINTER(vtn_sweep_opts), _D, _D, _D,
                               C.POINTER(vtn_sweep_report)],
     "vtn_heff1_apply": [_P, C.POINTER(vtn_core), _I, _I, _P, _P, _P, _P],
+    "vtn_mlp_create": [_P, _I, _I, _I, _I, C.c_uint64, C.POINTER(_P)],
+    "vtn_mlp_free": [_P],
+    "vtn_mlp_info": [_P, _PI, _PI, _PI, _PI, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)],
+    "vtn_mlp_get_params": [_P, _P, C.POINTER(C.c_float)],
+    "vtn_mlp_set_params": [_P, _P, C.POINTER(C.c_float)],
+    "vtn_mlp_forward": [_P, _P, _I, _P, _P],
+    "vtn_mlp_loss_grad": [_P, _P, _I, _P, _P, C.POINTER(C.c_float), C.POINTER(C.c_float)],
+    "vtn_mlp_train_step": [_P, _P, _I, _P, _P, C.c_float, C.POINTER(C.c_float)],
     "vtn_expand": [_P, C.POINTER(vtn_core), _I, _I, _I, _P, _P, _D, _P],
     "vtn_energy": [_P, _P, _P, _PD],
     "vtn_energy_variance": [_P, _P, _P, _PD, _PD, _PD],
@@ -453,6 +461,61 @@ def vtn_heff1_apply(ctx, W, chi_l, chi_r, L, R, A, y):
 def vtn_expand(ctx, W, side, chi_l, chi_r, env, A, alpha, out):
     _check(ctx, lib().vtn_expand(ctx, C.byref(W), int(side), int(chi_l), int(chi_r), _dptr(env), _dptr(A),
                                  float(alpha), _dptr(out)))
+
+
+# ----------------------------------------------------------------------- learned warm start (MLP)
+_PF = C.POINTER(C.c_float)
+
+
+def vtn_mlp_create(ctx, n_in, width, depth, n_out, seed=0):
+    out = C.c_void_p()
+    _check(ctx, lib().vtn_mlp_create(ctx, int(n_in), int(width), int(depth), int(n_out), C.c_uint64(int(seed)),
+                                     C.byref(out)))
+    return out
+
+
+def vtn_mlp_free(mlp):
+    return lib().vtn_mlp_free(mlp)
+
+
+def vtn_mlp_info(mlp):
+    """(n_in, width, depth, n_out, n_params, steps)."""
+    v = [C.c_int() for _ in range(4)]
+    n, st = C.c_longlong(), C.c_longlong()
+    _check(None, lib().vtn_mlp_info(mlp, *[C.byref(x) for x in v], C.byref(n), C.byref(st)))
+    return tuple(x.value for x in v) + (n.value, st.value)
+
+
+def vtn_mlp_get_params(ctx, mlp):
+    out = np.zeros(vtn_mlp_info(mlp)[4], np.float32)
+    _check(ctx, lib().vtn_mlp_get_params(ctx, mlp, out.ctypes.data_as(_PF)))
+    return out
+
+
+def vtn_mlp_set_params(ctx, mlp, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    assert p.size == vtn_mlp_info(mlp)[4]
+    _check(ctx, lib().vtn_mlp_set_params(ctx, mlp, p.ctypes.data_as(_PF)))
+
+
+def vtn_mlp_forward(ctx, mlp, batch, x, y):
+    _check(ctx, lib().vtn_mlp_forward(ctx, mlp, int(batch), _dptr(x), _dptr(y)))
+
+
+def vtn_mlp_loss_grad(ctx, mlp, batch, x, t, with_grad=True):
+    """(loss, grad or None) on the batch (x, t device float32 tensors)."""
+    loss = C.c_float()
+    g = np.zeros(vtn_mlp_info(mlp)[4], np.float32) if with_grad else None
+    _check(ctx, lib().vtn_mlp_loss_grad(ctx, mlp, int(batch), _dptr(x), _dptr(t), C.byref(loss),
+                                        g.ctypes.data_as(_PF) if with_grad else None))
+    return loss.value, g
+
+
+def vtn_mlp_train_step(ctx, mlp, batch, x, t, lr):
+    """One Adam step; returns the loss before it."""
+    loss = C.c_float()
+    _check(ctx, lib().vtn_mlp_train_step(ctx, mlp, int(batch), _dptr(x), _dptr(t), float(lr), C.byref(loss)))
+    return loss.value
 
 
 def vtn_heff_apply(ctx, Wi, Wj, chi_l, chi_r, L, R, theta, y, prec=VTN_FP64):
