@@ -136,7 +136,7 @@ void destroy_mps(vtn_mps m) {
     delete m;
 }
 
-// A DevCore with w channels, each passing through with op (d x d) -- used for norms.
+// A core uploaded for the duration of one call (kernel-level entry points).
 struct TempCore {
     Ctx* c;
     DevCore dc;
@@ -148,17 +148,6 @@ struct TempCore {
         }
     }
 };
-
-HostCore identity_core(int d) {
-    HostCore h;
-    h.wl = 1; h.wr = 1; h.d = d;
-    h.rows.push_back(0);
-    h.cols.push_back(0);
-    h.ops.assign((size_t)d * d, cplx(0, 0));
-    for (int i = 0; i < d; ++i) h.ops[(size_t)i * d + i] = 1.0;
-    h.ident.push_back(1);
-    return h;
-}
 
 // batched left transfer: Eout[t] = sum_s A[:,s,:]^dag E[t] A[:,s,:], t < count
 void transfer_left_batch(Ctx& c, int count, int chi_l, int d, int chi_r, const double2* E, const double2* A,
@@ -689,14 +678,11 @@ vtn_status vtn_sweep(vtn_ctx ctx, vtn_mpo mpo, vtn_mps* state, const vtn_sweep_o
             sched.push_back(std::min(opts->chi_schedule[i], opts->chi_max));
         }
         if (sched.empty()) sched.push_back(opts->chi_max);
-        bool created = false;
         if (*state == nullptr) {
             vtn_status st = vtn_mps_random(ctx, mpo, sched[0], opts->seed, state);
             if (st != VTN_OK) throw Error{st, c.err};
-            created = true;
         }
         vtn_mps mps = *state;
-        (void)created;
         check_mps_matches(mpo, mps);
         int chi_cap = opts->chi_max;
         for (int x : mps->dims) chi_cap = std::max(chi_cap, x);

@@ -21,10 +21,6 @@ constexpr int RB = 256;          // threads per block of the reduction kernels
 constexpr int KMAX_DEV = 64;     // largest Krylov dimension handled on the device
 constexpr int DOT_GROUP = 8;     // vectors per pass of multi_dot
 
-__device__ __forceinline__ double2 cmul_conj(double2 a, double2 b) {  // conj(a) * b
-    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
-}
-
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
