@@ -14,7 +14,8 @@ Modules (each function cites the passage of the paper it follows):
 * ``gbs``         -- covariance matrix and Hamiltonian coefficients (Eq. GBSHamiltonian),
                      exactly projected local operators (Eq. ProjectionOperator, SM Sec. 5),
                      Gaussian optimal local basis and its isometry (Eqs. WilliamsonDecomposition,
-                     OLB, InverseBasisTransformation, Effectivecutoff).
+                     OLB, InverseBasisTransformation, Effectivecutoff), and the closed-form
+                     Gaussian bond spectra (symplectic eigenvalues of a block's covariance).
 * ``mpo``         -- matrix product operator of the Gaussian Hamiltonian (SM Sec. 8), built
                      with a plain "carry every quadrature" state machine (w = 2N + 2).
 * ``dense``       -- dense Fock-space P H P and its exact ground state for tiny N, and

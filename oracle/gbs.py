@@ -155,3 +155,36 @@ def norm_bound(G, N, d):
     """Deterministic bound on ||P H P||: P H P + N/2 <= lambda_max(G) sum_i P(X_i^2+P_i^2)P
     = lambda_max(G) sum_i (2 n_i + 1) <= lambda_max(G) N (2d - 1)."""
     return float(np.max(np.linalg.eigvalsh(G))) * N * (2 * d - 1)
+
+
+# ----------------------------------------------------------------------------------
+# Bond spectra of the Gaussian state (the multi-mode form of Eq. diagReducedGaussianDM):
+# the reduced state of modes 0..s-1 is, after a Williamson transformation, a product of
+# thermal states with nbar_j = nu_j - 1/2, nu_j the symplectic eigenvalues of the block's
+# covariance.  Its eigenvalues -- the squared Schmidt values of the cut -- are the products
+# prod_j (1 - q_j) q_j^{n_j}, q_j = nbar_j / (nbar_j + 1).  This is the infinite-cutoff
+# spectrum; the truncated P H P ground state approaches it as d grows.
+# ----------------------------------------------------------------------------------
+
+def symplectic_eigenvalues(Vsub):
+    """nu_j >= 1/2 of a 2m x 2m covariance (xxpp): the moduli of the eigenvalues of
+    i Omega V (library eigvals), each appearing twice; returned ascending, m of them."""
+    m = Vsub.shape[0] // 2
+    Om = np.block([[np.zeros((m, m)), np.eye(m)], [-np.eye(m), np.zeros((m, m))]])
+    ev = np.linalg.eigvals(1j * Om @ Vsub)
+    return np.sort(np.abs(ev.real))[::2]
+
+
+def gaussian_schmidt_spectrum(V, s, k, n_max=24):
+    """The k largest eigenvalues of the reduced state of modes 0..s-1 (descending)."""
+    N = V.shape[0] // 2
+    idx = list(range(s)) + [N + j for j in range(s)]
+    nu = symplectic_eigenvalues(V[np.ix_(idx, idx)])
+    nbar = np.maximum(nu - 0.5, 0.0)
+    q = nbar / (nbar + 1.0)
+    spec = np.ones(1)
+    for qj in q:
+        p = (1.0 - qj) * qj ** np.arange(n_max + 1)
+        spec = np.outer(spec, p).reshape(-1)
+        spec = np.sort(spec)[::-1][: max(k, 1) * 64]    # keep a generous head
+    return np.sort(spec)[::-1][:k]

@@ -503,3 +503,38 @@ def test_nongauss_transformed_gaussian_state_has_zero_energy():
     assert es[0] > es[1] > es[2] > 0
     assert es[2] < 1e-7
     assert e_wrong > 1e3 * es[2] and e_wrong > 1e-4
+
+
+# ------------------------------------------------------------------ bond spectra (a6)
+def test_symplectic_eigenvalues_special_cases():
+    """Product state (U = I): every block has nu = 1/2.  Pure state: a block and its
+    complement have the same symplectic spectrum beyond the vacuum values.  One mode:
+    nu = sqrt(det V_i), the Williamson value."""
+    w = inputs.workload("plain", 0, M=5, identity_U=True)
+    V = gbs.covariance(w.r, w.U)
+    assert np.abs(gbs.symplectic_eigenvalues(V[np.ix_([0, 1, 5, 6], [0, 1, 5, 6])]) - 0.5).max() < 1e-12
+    w = inputs.workload("plain", 1, M=5)
+    V = gbs.covariance(w.r, w.U)
+    a = gbs.symplectic_eigenvalues(V[np.ix_([0, 1, 5, 6], [0, 1, 5, 6])])
+    b = gbs.symplectic_eigenvalues(V[np.ix_([2, 3, 4, 7, 8, 9], [2, 3, 4, 7, 8, 9])])
+    assert np.abs(np.sort(b)[-2:] - np.sort(a)).max() < 1e-10 and abs(np.sort(b)[0] - 0.5) < 1e-10
+    for i in range(5):
+        Vi = gbs.reduced_covariance(V, i)
+        assert abs(gbs.symplectic_eigenvalues(Vi)[0] - gbs.williamson_single(Vi)[1]) < 1e-12
+
+
+@pytest.mark.parametrize("seed,N,d,cut", [(0, 3, 12, 1), (1, 3, 12, 2), (2, 2, 24, 1)])
+def test_bond_spectrum_of_the_ground_state_is_gaussian(seed, N, d, cut):
+    """The squared Schmidt values of the P H P ground state at a cut against the closed-form
+    Gaussian spectrum: with F >= 1 - E (Eq. MagOfSimError) and the contraction of the trace
+    norm under the partial trace, sum_i |lambda_i - mu_i| <= 2 sqrt(1 - F) <= 2 sqrt(E)."""
+    w = inputs.workload("plain", seed, M=N, r_lo=0.3, r_hi=0.5)
+    V = gbs.covariance(w.r, w.U)
+    G = gbs.hamiltonian_coefficients(w.r, w.U)
+    e0, v0 = dense.ground_state(G, d)
+    psi = v0[:, 0].reshape(d ** cut, d ** (N - cut))
+    lam = np.linalg.svd(psi, compute_uv=False) ** 2
+    lam /= lam.sum()
+    k = 12
+    mu = gbs.gaussian_schmidt_spectrum(V, cut, k)
+    assert np.sum(np.abs(lam[:k] - mu)) <= 2.0 * np.sqrt(max(e0[0], 0.0)) + 1e-12
