@@ -124,6 +124,17 @@ vtn_status vtn_build_mpo(vtn_ctx ctx, int M, const double* r, const double* U,
  * sampling, vtn_energy_variance) accepts the result like any MPO. */
 vtn_status vtn_build_mpo_cz(vtn_ctx ctx, int M, const double* r, const double* U, int D, double kappa,
                             vtn_mpo* out);
+/* Closed-form bond spectrum of the Gaussian state the MPO describes: the k largest
+ * eigenvalues (descending, zero-padded) of the reduced state of modes 0..cut-1, i.e. the
+ * squared Schmidt values of the cut, prod_j (1 - q_j) q_j^{n_j} with q_j = nbar_j/(nbar_j + 1),
+ * nbar_j = nu_j - 1/2 and nu_j the symplectic eigenvalues of the block's covariance (the
+ * multi-mode form of Eq. diagReducedGaussianDM).  Infinite Fock cutoff: the ground state of
+ * P H P approaches it as D grows (local bases leave it unchanged).  out: host double[k].
+ * VTN_EUNSUPPORTED for MPOs without a Gaussian state (given as cores, or kappa != 0).  Host only. */
+vtn_status vtn_gaussian_bond_spectrum(vtn_mpo mpo, int cut, int k, double* out);
+/* Per cut s = 0..M, the smallest bond dimension whose discarded weight in that closed-form
+ * spectrum is <= eps, capped at min(chi_max, d^s, d^(M-s)) (at least 1).  dims: host int[M+1]. */
+vtn_status vtn_gaussian_bond_dims(vtn_mpo mpo, double eps, int chi_max, int* dims);
 vtn_status vtn_mpo_free(vtn_mpo mpo);
 /* Shape queries: M, d, D and the bond dimensions w[0..M] (w may be NULL). */
 vtn_status vtn_mpo_info(vtn_mpo mpo, int* M, int* d, int* D, int* w);

@@ -11,6 +11,7 @@
 #include <cstring>
 #include <new>
 
+#include "host_spectrum.h"
 #include "vtn_internal.cuh"
 
 using namespace vtn;
@@ -434,6 +435,45 @@ vtn_status vtn_mpo_from_cores(vtn_ctx ctx, int M, const vtn_core* cores, vtn_mpo
             }
         }
         *out = mpo;
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_gaussian_bond_spectrum(vtn_mpo mpo, int cut, int k, double* out) {
+    return guard(nullptr, [&]() -> vtn_status {
+        VTN_REQUIRE(mpo && out, "null argument");
+        VTN_REQUIRE(k >= 1 && k <= (1 << 20), "k must be in [1, 2^20]");
+        VTN_REQUIRE(cut >= 0 && cut <= mpo->hp.M, "cut must be in [0, M]");
+        if (mpo->hp.V.empty()) throw Error{VTN_EUNSUPPORTED, "the MPO carries no covariance (given as cores)"};
+        if (mpo->hp.kappa != 0.0) throw Error{VTN_EUNSUPPORTED, "the state of this MPO is not Gaussian"};
+        const std::vector<double> spec = gaussian_bond_spectrum(mpo->hp.V, mpo->hp.M, cut, k);
+        std::copy(spec.begin(), spec.end(), out);
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_gaussian_bond_dims(vtn_mpo mpo, double eps, int chi_max, int* dims) {
+    return guard(nullptr, [&]() -> vtn_status {
+        VTN_REQUIRE(mpo && dims, "null argument");
+        VTN_REQUIRE(std::isfinite(eps) && eps >= 0.0 && eps < 1.0, "eps must be in [0, 1)");
+        VTN_REQUIRE(chi_max >= 1 && chi_max <= (1 << 20), "chi_max must be in [1, 2^20]");
+        if (mpo->hp.V.empty()) throw Error{VTN_EUNSUPPORTED, "the MPO carries no covariance (given as cores)"};
+        if (mpo->hp.kappa != 0.0) throw Error{VTN_EUNSUPPORTED, "the state of this MPO is not Gaussian"};
+        const int M = mpo->hp.M;
+        const std::vector<int> cap = bond_dims(M, mpo->hp.d, chi_max);
+        for (int s = 0; s <= M; ++s) {
+            const std::vector<double> spec = gaussian_bond_spectrum(mpo->hp.V, M, s, cap[s]);
+            double kept = 0.0;
+            int k = cap[s];
+            for (int i = 0; i < cap[s]; ++i) {
+                kept += spec[i];
+                if (1.0 - kept <= eps) {
+                    k = i + 1;
+                    break;
+                }
+            }
+            dims[s] = std::max(1, k);
+        }
         return VTN_OK;
     });
 }

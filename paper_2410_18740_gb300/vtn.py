@@ -89,6 +89,8 @@ _SIGS = {
     "vtn_sweep": [_P, _P, C.POINTER(_P), C.POINTER(vtn_sweep_opts), C.POINTER(vtn_sweep_report)],
     "vtn_build_mpo_cz": [_P, _I, _PD, _PD, _I, _D, C.POINTER(C.c_void_p)],
     "vtn_mpo_from_cores": [_P, _I, C.POINTER(vtn_core), C.POINTER(_P)],
+    "vtn_gaussian_bond_spectrum": [_P, _I, _I, _PD],
+    "vtn_gaussian_bond_dims": [_P, _D, _I, _PI],
     "vtn_sweep_single_site": [_P, _P, C.POINTER(_P), C.POINTER(vtn_sweep_opts), _D, _D, _D,
                               C.POINTER(vtn_sweep_report)],
     "vtn_heff1_apply": [_P, C.POINTER(vtn_core), _I, _I, _P, _P, _P, _P],
@@ -282,6 +284,19 @@ def vtn_mpo_core(mpo, site):
     _check(None, lib().vtn_mpo_core(mpo, int(site), C.byref(n), rows.ctypes.data_as(_PI),
                                     cols.ctypes.data_as(_PI), ops.ctypes.data_as(_PD)))
     return int(w[site]), int(w[site + 1]), rows, cols, ops.view(np.complex128)[..., 0][: n.value]
+
+
+def vtn_gaussian_bond_spectrum(mpo, cut, k):
+    out = np.zeros(int(k))
+    _check(None, lib().vtn_gaussian_bond_spectrum(mpo, int(cut), int(k), out.ctypes.data_as(_PD)))
+    return out
+
+
+def vtn_gaussian_bond_dims(mpo, eps, chi_max):
+    M = vtn_mpo_info(mpo)[0]
+    out = np.zeros(M + 1, np.int32)
+    _check(None, lib().vtn_gaussian_bond_dims(mpo, float(eps), int(chi_max), out.ctypes.data_as(_PI)))
+    return out
 
 
 def vtn_mpo_norm_bound(mpo):

@@ -174,3 +174,54 @@ def test_mpo_from_cores_validation(libvtn):
     bad[1] = np.zeros(bad[1].shape[:2] + (2, 2), complex)
     with pytest.raises(vtn.VtnError):
         vtn.vtn_mpo_from_cores(None, bad)                                # mixed d
+
+
+@pytest.mark.parametrize("seed,M", [(0, 2), (1, 6), (2, 9)])
+def test_gaussian_bond_spectrum_against_oracle(libvtn, seed, M):
+    w = inputs.workload("split", seed, M=M)
+    m = vtn.vtn_build_mpo(None, w.r, w.U, 4, 4)
+    try:
+        V = gbs.covariance(w.r, w.U)
+        for cut in range(0, M + 1):
+            got = vtn.vtn_gaussian_bond_spectrum(m, cut, 40)
+            if cut in (0, M):
+                assert got[0] == 1.0 and np.all(got[1:] == 0.0)
+                continue
+            ref = gbs.gaussian_schmidt_spectrum(V, cut, 40, n_max=60)
+            ref = np.concatenate([ref, np.zeros(40 - ref.size)])
+            assert np.abs(got - ref).max() <= 1e-11
+        # bond dimensions for a discarded weight of at most eps, against the oracle's spectrum
+        eps = 1e-3
+        dims = vtn.vtn_gaussian_bond_dims(m, eps, 64)
+        assert dims[0] == 1 and dims[M] == 1
+        for s in range(1, M):
+            mu = gbs.gaussian_schmidt_spectrum(V, s, 64, n_max=80)
+            cap = min(64, 4 ** s, 4 ** (M - s))
+            need = next((k + 1 for k in range(min(cap, mu.size)) if 1 - mu[: k + 1].sum() <= eps), cap)
+            assert dims[s] == need
+    finally:
+        vtn.vtn_mpo_free(m)
+
+
+def test_gaussian_bond_spectrum_special_cases(libvtn):
+    w = inputs.workload("plain", 0, M=4, identity_U=True)
+    m = vtn.vtn_build_mpo(None, w.r, w.U, 4, 4)
+    try:
+        for cut in range(5):
+            s = vtn.vtn_gaussian_bond_spectrum(m, cut, 5)
+            assert abs(s[0] - 1.0) < 1e-12 and np.abs(s[1:]).max() < 1e-12   # product state
+        with pytest.raises(vtn.VtnError):
+            vtn.vtn_gaussian_bond_spectrum(m, 5, 3)
+    finally:
+        vtn.vtn_mpo_free(m)
+    w = inputs.workload("plain", 1, M=3, d=3, D=3)
+    mcz = vtn.vtn_build_mpo_cz(None, w.r, w.U, 3, 0.2)
+    mc = vtn.vtn_mpo_from_cores(None, ompo.build_mpo(gbs.hamiltonian_coefficients(w.r, w.U), 3))
+    try:
+        for mm in (mcz, mc):
+            with pytest.raises(vtn.VtnError) as e:
+                vtn.vtn_gaussian_bond_spectrum(mm, 1, 3)
+            assert e.value.status == vtn.VTN_EUNSUPPORTED
+    finally:
+        vtn.vtn_mpo_free(mcz)
+        vtn.vtn_mpo_free(mc)
