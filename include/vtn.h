@@ -387,8 +387,8 @@ vtn_status vtn_heff_apply_static(const vtn_core* Wi, const vtn_core* Wj, int chi
 
 /* ---------------------------------------------------------------- learned warm start
  * The multilayer perceptron the warm start trains and evaluates (the paper has no learned
- * component; the network maps instance features to solver inputs and the variational energy
- * judges the result).  FP32 on the device: layers n_in -> width (x depth) -> n_out, ReLU after
+ * component; the network maps instance features to solver inputs, and the variational energy
+ * they lead to measures its quality).  FP32 on the device: layers n_in -> width (x depth) -> n_out, ReLU after
  * every layer but the last, mean-squared-error loss, Adam (beta1 0.9, beta2 0.999, eps 1e-8;
  * Kingma and Ba 2015).  Parameters are one float array: per layer l, W_l (n_out_l x n_in_l,
  * row-major) then b_l (n_out_l).  x: device float[batch*n_in], t and y: device float[batch*n_out],

@@ -1,7 +1,7 @@
 """Multilayer perceptron of the learned warm start -- oracle (test infrastructure only).
 
 The paper has no learned component; the warm start maps features of a GBS instance
-(per-mode reduced covariances) to solver inputs and is judged by the variational energy
+(per-mode reduced covariances) to solver inputs and is assessed by the variational energy
 <H> it leads to (Eq. MagOfSimError).  This module is the plain reference for the network
 itself: fully connected layers with ReLU between them, mean-squared-error loss, gradients
 by the chain rule written out layer by layer, and the Adam update (Kingma and Ba, ICLR
