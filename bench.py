@@ -23,7 +23,8 @@ roofline  = the kernel that dominates the step's time, timed with CUDA events on
 time_to_eps = from a seeded random MPS (chi schedule 16, 32, 64, 128): the FP64 solver runs
             --ref-sweeps sweeps and sets E_ref; value = the mixed solver's cumulative sweep
             time until its FP64 energy is <= E_ref (1 + 1e-8), beside the FP64 time to the
-            same point (E_ref is a fixed-budget reference, not a converged energy).
+            same point (E_ref is a fixed-budget reference, not a converged energy) and the
+            single-site FP64 solver's (subspace expansion) time to it from the same state.
 
 --impl reference times the CPU oracle (numpy FP64) on a bounded sample of the same
 workload: one H_eff psi product at the shape of the middle bond, in the same unit.
@@ -533,20 +534,21 @@ def run_case_trunc(args):
     vtn.vtn_destroy(ctx)
 
 
-def measure_tte(ctx, mpo, seed, ref_sweeps):
+def measure_tte(ctx, mpo, seed, ref_sweeps, single_site=True):
     """Time-to-eps on the split workload: both solvers start from the same seeded random MPS
     with the chi schedule 16, 32, 64, 128.  The FP64 solver runs ref_sweeps sweeps; E_ref is
     its last energy and eps = E_ref * 1e-8.  The mixed solver (bf16x3 H_eff psi and
     environments) sweeps until its FP64 energy at a sweep boundary is <= E_ref (1 + 1e-8),
-    at most ref_sweeps + 8 sweeps.  Times are the solver's own per-sweep wall clock (MPO
-    resident on the device), cumulated."""
+    at most ref_sweeps + 8 sweeps.  With single_site, the single-site FP64 solver with
+    subspace expansion (alpha 1e-2 halved per sweep) runs the same way from the same state.
+    Times are the solver's own per-sweep wall clock (MPO resident on the device), cumulated."""
     import torch
 
     from paper_2410_18740_gb300 import vtn
 
     sched = [16, 32, 64, CHI]
 
-    def run(prec, n_sweeps, e_target=None):
+    def run(prec, n_sweeps, e_target=None, one_site=False):
         kw = dict(chi_max=CHI, n_sweeps=n_sweeps, seed=seed, lanczos_tol=1e-12, krylov_max=KRYLOV,
                   lanczos_max_restarts=0, chi_schedule=sched, prec=prec)
         if e_target is not None:
@@ -554,7 +556,11 @@ def measure_tte(ctx, mpo, seed, ref_sweeps):
         opts = vtn.vtn_sweep_opts_default(**kw)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, mps, rep = vtn.vtn_sweep(ctx, mpo, None, opts)
+        if one_site:
+            _, mps, rep = vtn.vtn_sweep_single_site(ctx, mpo, None, opts, alpha=1e-2, alpha_decay=0.5,
+                                                    cutoff=1e-12)
+        else:
+            _, mps, rep = vtn.vtn_sweep(ctx, mpo, None, opts)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         vtn.vtn_mps_free(mps)
@@ -570,6 +576,16 @@ def measure_tte(ctx, mpo, seed, ref_sweeps):
     mixed, wall16 = run(vtn.VTN_BF16X3, ref_sweeps + 8, target)
     t64 = next((t for t, e in ref if e <= target), None)
     t16 = next((t for t, e in mixed if e <= target), None)
+    one = None
+    if single_site:
+        try:
+            ss, wall1 = run(vtn.VTN_FP64, ref_sweeps + 8, target, one_site=True)
+            t1 = next((t for t, e in ss if e <= target), None)
+            one = {"solver": "single-site DMRG with subspace expansion, FP64", "time_to_eps_s": t1,
+                   "sweeps": len(ss), "wall_s": wall1, "energies": [e for _, e in ss],
+                   "cum_seconds": [t for t, _ in ss], "speedup_vs_two_site_fp64": (t64 / t1) if (t64 and t1) else None}
+        except Exception as exc:  # reported, never fatal to the benchmark line
+            one = {"error": repr(exc)}
     return {"workload": f"{WORKLOAD}: M=24, r~U(0.5,1.0), Haar U, d=D=8, chi schedule {sched}, "
                         f"Lanczos {KRYLOV} steps/bond, seed {seed}",
             "eps": "E_ref * 1e-8, E_ref = FP64 energy after the reference sweeps (not converged: see "
@@ -580,6 +596,7 @@ def measure_tte(ctx, mpo, seed, ref_sweeps):
                      "cum_seconds": [t for t, _ in ref]},
             "mixed": {"time_to_eps_s": t16, "sweeps": len(mixed), "wall_s": wall16, "energies": [e for _, e in mixed],
                       "cum_seconds": [t for t, _ in mixed]},
+            "single_site_fp64": one,
             "speedup": (t64 / t16) if (t64 and t16) else None}
 
 
