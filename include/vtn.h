@@ -88,7 +88,8 @@ typedef struct {
 vtn_status vtn_create(vtn_ctx* out, int device, void* cuda_stream, const vtn_allocator* allocator);
 vtn_status vtn_destroy(vtn_ctx ctx);
 /* Last error message of the context ("" if none).  Valid until the next call on ctx.
- * vtn_last_error(NULL) returns the message of the last failed vtn_create. */
+ * vtn_last_error(NULL) returns the message of the calling thread's last failed call made
+ * without a context (vtn_create, the host-only MPO builders and queries). */
 const char* vtn_last_error(vtn_ctx ctx);
 /* Number of kernels this context has launched since creation (all entry points). */
 vtn_status vtn_launch_count(vtn_ctx ctx, long long* out);

@@ -18,7 +18,9 @@ using namespace vtn;
 
 namespace {
 
-std::string g_create_error;
+// message of the calling thread's last failed call made without a context (vtn_create, the
+// host-only MPO builders and queries)
+thread_local std::string g_create_error;
 
 template <class F>
 vtn_status guard(vtn_ctx ctx, F&& f) {
@@ -34,9 +36,11 @@ vtn_status guard(vtn_ctx ctx, F&& f) {
         return e.status;
     } catch (const std::bad_alloc&) {
         if (ctx) ctx->c.err = "host allocation failed";
+        else g_create_error = "host allocation failed";
         return VTN_ENOMEM;
     } catch (const std::exception& e) {
         if (ctx) ctx->c.err = e.what();
+        else g_create_error = e.what();
         return VTN_EINVAL;
     }
 }
