@@ -7,7 +7,8 @@
 // optimal local basis, Eq. diagReducedGaussianDM).  Its eigenvalues -- the squared Schmidt
 // values of the cut -- are the products prod_j (1 - q_j) q_j^{n_j}, q_j = nbar_j / (nbar_j + 1).
 // Local basis changes do not alter them; the Fock cutoff does (this is the infinite-cutoff
-// spectrum, which the truncated ground state approaches as the cutoff grows).
+// spectrum, which the truncated ground state approaches as the cutoff grows).  The state is
+// pure, so the smaller of the two blocks of a cut gives the spectrum.
 //
 // nu_j: with K = V^{1/2} (i Omega) V^{1/2} Hermitian, K^2 = -V^{1/2} Omega V Omega V^{1/2} is real
 // symmetric with eigenvalues nu_j^2, each twice.  Both symmetric eigenproblems are solved by
@@ -15,6 +16,8 @@
 #include <algorithm>
 #include <cmath>
 #include <functional>
+#include <queue>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -125,23 +128,32 @@ std::vector<double> symplectic_eigenvalues(const std::vector<double>& Vb, int m)
 std::vector<double> gaussian_bond_spectrum(const std::vector<double>& V, int M, int cut, int k) {
     std::vector<double> spec(1, 1.0);
     if (cut > 0 && cut < M) {
-        const int m = cut, n = 2 * m;
+        // a pure state's two sides share their spectrum: use the smaller block
+        const int first = 2 * cut <= M ? 0 : cut;
+        const int m = 2 * cut <= M ? cut : M - cut, n = 2 * m;
         std::vector<double> Vb((size_t)n * n);
-        auto idx = [&](int a) { return a < m ? a : M + (a - m); };
+        auto idx = [&](int a) { return a < m ? first + a : M + first + (a - m); };
         for (int a = 0; a < n; ++a)
             for (int b = 0; b < n; ++b) Vb[(size_t)a * n + b] = V[(size_t)idx(a) * 2 * M + idx(b)];
         const std::vector<double> nu = symplectic_eigenvalues(Vb, m);
         for (double v : nu) {
             const double nbar = std::max(v - 0.5, 0.0), q = nbar / (nbar + 1.0);
-            // top-k of the products: only the top k of the partial products can contribute
+            // top k of {spec[i] (1 - q) q^n}: only the top k partial products can contribute;
+            // every row i is descending in n, so a k-way merge with a heap finds them
+            using Item = std::pair<double, std::pair<int, int>>;  // (value, (i, n))
+            std::priority_queue<Item> heap;
+            for (int i = 0; i < (int)spec.size(); ++i) heap.push({spec[i] * (1.0 - q), {i, 0}});
             std::vector<double> next;
-            next.reserve(spec.size() * (size_t)k);
-            double p = 1.0 - q;
-            for (int nn = 0; nn < k && p > 0.0; ++nn, p *= q)
-                for (double x : spec) next.push_back(x * p);
-            std::sort(next.begin(), next.end(), std::greater<double>());
-            if ((int)next.size() > k) next.resize(k);
+            next.reserve((size_t)k);
+            while ((int)next.size() < k && !heap.empty()) {
+                const Item top = heap.top();
+                heap.pop();
+                if (top.first <= 0.0) break;
+                next.push_back(top.first);
+                heap.push({top.first * q, {top.second.first, top.second.second + 1}});
+            }
             spec.swap(next);
+            if (spec.empty()) spec.push_back(0.0);
         }
     }
     spec.resize(k, 0.0);
