@@ -225,3 +225,18 @@ def test_gaussian_bond_spectrum_special_cases(libvtn):
     finally:
         vtn.vtn_mpo_free(mcz)
         vtn.vtn_mpo_free(mc)
+
+
+def test_gaussian_bond_spectrum_large_blocks(libvtn):
+    """M = 40: cuts whose blocks are 10-, 40- and 60-dimensional (the library works on the
+    smaller side of each cut) against the oracle's direct block."""
+    w = inputs.workload("large", 3, M=40)
+    m = vtn.vtn_build_mpo(None, w.r, w.U, 6, 6)
+    try:
+        V = gbs.covariance(w.r, w.U)
+        for cut in (5, 20, 30):
+            got = vtn.vtn_gaussian_bond_spectrum(m, cut, 64)
+            ref = gbs.gaussian_schmidt_spectrum(V, cut, 64, n_max=64)
+            assert np.abs(got - ref).max() <= 1e-9 * ref[0]
+    finally:
+        vtn.vtn_mpo_free(m)
