@@ -157,6 +157,48 @@ def truncate(theta, direction, chi_max):
     return C, B, w, 1.0 - float(np.sum(w)) / total
 
 
+def truncate_warm(theta, direction, chi_max, Q0, q=1, p=8, seed=0, bond=0):
+    """The same split as ``truncate`` with the kept subspace found by block subspace iteration
+    on rho from a warm start instead of a full eigendecomposition (not in the paper: a
+    cheaper truncation whose energies are compared with the exact one).  Steps:
+      m = min(n, k + p) start vectors: the columns of Q0 (the current centre tensor spans the
+      previous kept subspace), then rho * Omega with Omega from the Philox TRUNC stream of
+      (seed, bond); Gram-Schmidt; q times Q <- orth(rho Q); Rayleigh-Ritz: the k largest
+      eigenpairs (w, Y) of Q^dag rho Q give U = Q Y.  rho = T T^dag ('right') or T^dag T
+      ('left') is applied as T (T^dag X), never formed.  Returns what ``truncate`` returns,
+      with the Ritz values in place of the eigenvalues."""
+    cl, d1, d2, cr = theta.shape
+    Tm = theta.reshape(cl * d1, d2 * cr)
+    nL, nR = Tm.shape
+    k = min(chi_max, nL, nR)
+    if direction == "right":
+        n = nL
+        apply = lambda X: Tm @ (Tm.conj().T @ X)
+    else:
+        n = nR
+        apply = lambda X: Tm.conj().T @ (Tm @ X)
+    m = min(n, k + p)
+    k0 = 0 if Q0 is None else min(Q0.shape[1], m)
+    S = np.empty((n, m), dtype=np.complex128)
+    if k0:
+        S[:, :k0] = Q0[:, :k0]
+    if m > k0:
+        Om = philox.complex_normals(seed, bond, n * (m - k0), stream=philox.STREAM_TRUNC)
+        S[:, k0:] = apply(Om.reshape(n, m - k0))
+    orth = lambda X: orthonormal_rows(X.conj().T).conj().T
+    Q = orth(S)
+    for _ in range(q):
+        Q = orth(apply(Q))
+    Bm = Q.conj().T @ apply(Q)
+    w, Y = np.linalg.eigh(0.5 * (Bm + Bm.conj().T))
+    w, Y = w[::-1][:k], Y[:, ::-1][:, :k]
+    U = Q @ Y
+    total = float(np.linalg.norm(Tm) ** 2)
+    if direction == "right":
+        return U.reshape(cl, d1, k), (U.conj().T @ Tm).reshape(k, d2, cr), w, 1.0 - float(np.sum(w)) / total
+    return (Tm @ U).reshape(cl, d1, k), U.conj().T.reshape(k, d2, cr), w, 1.0 - float(np.sum(w)) / total
+
+
 # ---------------------------------------------------------------- energy
 def norm2(mps):
     E = np.ones((1, 1), dtype=np.complex128)
@@ -208,9 +250,11 @@ class SweepReport:
 
 
 def dmrg(cores, d, chi_max, n_sweeps, seed, chi_schedule=(), lanczos=None,
-         e_tol=0.0, e_target=None, mps=None, max_bonds=None):
+         e_tol=0.0, e_target=None, mps=None, max_bonds=None, warm_q=None):
     """Two-site DMRG sweeps.  Returns (mps, report).  ``max_bonds`` stops after that
-    many bond optimisations (used only to time a bounded sample)."""
+    many bond optimisations (used only to time a bounded sample).  ``warm_q`` = None: exact
+    truncation; an integer: ``truncate_warm`` with that many iterations, started from the
+    current centre tensor (site i sweeping right, site i+1 sweeping left)."""
     N = len(cores)
     p = lanczos or LanczosParams()
     sched = list(chi_schedule) if chi_schedule else [chi_max]
@@ -239,7 +283,14 @@ def dmrg(cores, d, chi_max, n_sweeps, seed, chi_schedule=(), lanczos=None,
                 rep.matvecs += nmv
                 rep.not_converged += 0 if conv else 1
                 theta = x.reshape(shape)
-                left, right, _, disc = truncate(theta, direction, chi_s)
+                if warm_q is None:
+                    left, right, _, disc = truncate(theta, direction, chi_s)
+                else:
+                    if direction == "right":
+                        Q0 = mps[i].reshape(-1, mps[i].shape[2])
+                    else:
+                        Q0 = mps[i + 1].reshape(mps[i + 1].shape[0], -1).conj().T
+                    left, right, _, disc = truncate_warm(theta, direction, chi_s, Q0, q=warm_q, seed=seed, bond=i)
                 disc_max = max(disc_max, disc)
                 mps[i], mps[i + 1] = left, right
                 if direction == "right":

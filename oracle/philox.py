@@ -16,6 +16,7 @@ MASK = np.uint64(0xFFFFFFFF)
 
 STREAM_INIT = 1      # counter word 3 for initial-MPS entries
 STREAM_SAMPLE = 2    # counter word 3 for sampler uniforms
+STREAM_TRUNC = 3     # counter word 3 for the start vectors of the warm-started truncation
 
 
 def philox4x32_10(ctr, key):
@@ -58,10 +59,10 @@ def counters(index, word2: int, stream: int):
     return ctr
 
 
-def complex_normals(seed: int, site: int, count: int):
+def complex_normals(seed: int, site: int, count: int, stream: int = STREAM_INIT):
     """count complex numbers z = (g1 + i g2)/sqrt(2), g ~ N(0,1) by Box-Muller, from the
-    INIT stream of (seed, site): entry j uses counter (j, site, STREAM_INIT)."""
-    out = philox4x32_10(counters(np.arange(count, dtype=np.uint64), site, STREAM_INIT), key_of(seed))
+    given stream of (seed, site): entry j uses counter (j, site, stream)."""
+    out = philox4x32_10(counters(np.arange(count, dtype=np.uint64), site, stream), key_of(seed))
     u1 = uniform53(out[..., 0], out[..., 1])
     u2 = uniform53(out[..., 2], out[..., 3])
     rad = np.sqrt(-2.0 * np.log1p(-u1))

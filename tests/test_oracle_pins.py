@@ -538,3 +538,69 @@ def test_bond_spectrum_of_the_ground_state_is_gaussian(seed, N, d, cut):
     k = 12
     mu = gbs.gaussian_schmidt_spectrum(V, cut, k)
     assert np.sum(np.abs(lam[:k] - mu)) <= 2.0 * np.sqrt(max(e0[0], 0.0)) + 1e-12
+
+
+# ------------------------------------------------------------------ warm-started truncation
+def _theta_with_spectrum(rng, cl, d1, d2, cr, decay):
+    th = inputs.random_complex((cl, d1, d2, cr), rng)
+    Tm = th.reshape(cl * d1, d2 * cr)
+    U, s, Vh = np.linalg.svd(Tm, full_matrices=False)
+    s = decay ** np.arange(s.size)
+    return ((U * s) @ Vh).reshape(th.shape) / np.linalg.norm(s)
+
+
+def _projector(A):
+    M = A.reshape(-1, A.shape[-1])
+    return M @ M.conj().T
+
+
+@pytest.mark.parametrize("direction", ["right", "left"])
+def test_truncate_warm_full_space_and_exact_start_are_exact(direction):
+    """Rayleigh-Ritz over the whole space (k + p >= n), or started from the exact kept
+    eigenvectors with no iteration, reproduces the eigendecomposition: same eigenvalues,
+    same kept subspace, same truncated theta."""
+    rng = inputs.rng_for(41)
+    th = _theta_with_spectrum(rng, 3, 2, 2, 5, 0.7)
+    n = 6 if direction == "right" else 10
+    for chi, Q0, q, p in ((n, None, 0, 8), (4, "exact", 0, 0)):
+        l0, r0, w0, disc0 = dmrg.truncate(th, direction, chi)
+        if Q0 == "exact":
+            T = th.reshape(6, 10)
+            rho = T @ T.conj().T if direction == "right" else T.conj().T @ T
+            _, V = np.linalg.eigh(rho)
+            Q0 = V[:, ::-1][:, :chi]
+        l1, r1, w1, disc1 = dmrg.truncate_warm(th, direction, chi, Q0, q=q, p=p, seed=3, bond=1)
+        assert np.abs(w1 - w0).max() < 1e-12 and abs(disc1 - disc0) < 1e-12
+        kept0, kept1 = (l0, l1) if direction == "right" else (np.transpose(r0.conj(), (2, 1, 0)),
+                                                               np.transpose(r1.conj(), (2, 1, 0)))
+        assert np.abs(_projector(kept1) - _projector(kept0)).max() < 1e-10
+        rec0 = np.einsum("asb,btc->astc", l0, r0)
+        rec1 = np.einsum("asb,btc->astc", l1, r1)
+        assert np.abs(rec1 - rec0).max() < 1e-10
+
+
+def test_truncate_warm_ritz_values_interlace_and_converge():
+    """Ritz values from any subspace lie below the eigenvalues of the same rank (Cauchy
+    interlacing); subspace iteration drives them to the eigenvalues."""
+    rng = inputs.rng_for(42)
+    th = _theta_with_spectrum(rng, 8, 4, 4, 8, 0.85)
+    _, _, lam, _ = dmrg.truncate(th, "right", 10)
+    Q0 = inputs.random_complex((32, 10), rng)
+    for q in (0, 1, 3):
+        _, _, w, _ = dmrg.truncate_warm(th, "right", 10, Q0, q=q, p=4, seed=5, bond=2)
+        assert np.all(w <= lam + 1e-13)
+    _, _, w, _ = dmrg.truncate_warm(th, "right", 10, Q0, q=60, p=4, seed=5, bond=2)
+    assert np.abs(w - lam).max() < 1e-10
+
+
+def test_dmrg_with_warm_truncation_plain_is_exact():
+    """chi = d^2 covers the plain workload: the warm truncation works on the full space and the
+    sweep reaches the dense ground energy."""
+    w = inputs.workload("plain", 1)
+    G = gbs.hamiltonian_coefficients(w.r, w.U)
+    Hn = gbs.norm_bound(G, w.M, w.d)
+    e0 = dense.ground_state(G, w.d)[0][0]
+    cores = mpo.build_mpo(G, w.d)
+    _, rep = dmrg.dmrg(cores, w.d, 16, 4, seed=3, warm_q=1,
+                       lanczos=dmrg.LanczosParams(krylov_max=32, max_restarts=8, tol=1e-12))
+    assert abs(rep.energies[-1] - e0) <= 1e-10 * Hn
