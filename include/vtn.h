@@ -188,6 +188,9 @@ typedef struct {
     double e_target;           /* stop when E_k <= e_target (used when use_e_target != 0) */
     int use_e_target;
     uint64_t seed;             /* seed of the random initial MPS when *state == NULL      */
+    int trunc_mode;            /* 0: exact eigendecomposition (the paper's truncation);
+                                  1: warm-started subspace iteration (vtn_truncate_warm)   */
+    int trunc_q;               /* subspace iterations of trunc_mode 1 (0..64)            */
 } vtn_sweep_opts;
 
 typedef struct {
@@ -205,7 +208,7 @@ typedef struct {
 } vtn_sweep_report;
 
 /* Fill opts with the defaults: chi_max 16, 8 sweeps, FP64, lanczos_tol 1e-10,
- * krylov_max 32, 4 restarts, e_tol 0, seed 0. */
+ * krylov_max 32, 4 restarts, e_tol 0, seed 0, trunc_mode 0 (exact), trunc_q 1. */
 vtn_status vtn_sweep_opts_default(vtn_sweep_opts* opts);
 
 /* Two-site DMRG sweeps.  *state == NULL: start from vtn_mps_random(opts->chi_schedule[0]
@@ -213,8 +216,11 @@ vtn_status vtn_sweep_opts_default(vtn_sweep_opts* opts);
  * then (M-2,M-1) .. (0,1) right to left; it ends right-canonical with the centre at
  * site 0.  Each bond: Lanczos on H_eff (full re-orthogonalisation, restarts), FP64
  * eigendecomposition of the reduced density matrix, keep min(chi, chi_l d, d chi_r)
- * largest eigenpairs, environment update.  Returns VTN_ENOCONV (after finishing) if
- * some Lanczos solve missed its tolerance.  report may be NULL. */
+ * largest eigenpairs, environment update.  With opts->trunc_mode = 1 the truncation is
+ * vtn_truncate_warm with q = opts->trunc_q, p = 8, seed = opts->seed, bond = i and the
+ * current centre tensor (site i sweeping right, site i+1 sweeping left) as start vectors.
+ * Returns VTN_ENOCONV (after finishing) if some Lanczos solve missed its tolerance.  report
+ * may be NULL. */
 vtn_status vtn_sweep(vtn_ctx ctx, vtn_mpo mpo, vtn_mps* state, const vtn_sweep_opts* opts,
                      vtn_sweep_report* report);
 
@@ -346,6 +352,23 @@ vtn_status vtn_heff_ground(vtn_ctx ctx, const vtn_core* Wi, const vtn_core* Wj, 
 vtn_status vtn_truncate(vtn_ctx ctx, int chi_l, int d1, int d2, int chi_r, int direction, int k_max,
                         const double* theta, double* left, double* right, double* lam,
                         double* discarded, int* k_out);
+
+/* The same split as vtn_truncate with the kept subspace found by block subspace iteration
+ * instead of the full eigendecomposition (not the paper's truncation, which is exact: a
+ * cheaper alternative, compared with it by the energies it leads to).  With n = chi_l d1
+ * (direction 0, rho = T T^dag) or d2 chi_r (direction 1, rho = T^dag T), k = min(k_max,
+ * chi_l d1, d2 chi_r) and m = min(chi_l d1, d2 chi_r, k + p) (no more than the rank of rho):
+ *   start vectors: the k0 columns of Q0 (device complex[n*k0], row-major n x k0; in a sweep the
+ *   current centre tensor), then rho Omega for the remaining m - k0, Omega (n x (m - k0),
+ *   row-major) complex normals (g1 + i g2)/sqrt(2) of Philox4x32-10 with key seed and counter
+ *   (j, bond, 3) for entry j; Gram-Schmidt in order; q times: multiply by rho and
+ *   re-orthonormalise; Rayleigh-Ritz: the k largest eigenpairs (w, Y) of Q^dag rho Q give the
+ *   kept vectors Q Y.  rho is applied as T (T^dag X), never formed.  Outputs as vtn_truncate,
+ *   with the Ritz values w in lam and discarded = 1 - sum(w)/||T||^2.  0 <= q <= 64,
+ *   0 <= p <= 256, m <= 4096, k0 >= 0 (Q0 may be NULL when k0 = 0). */
+vtn_status vtn_truncate_warm(vtn_ctx ctx, int chi_l, int d1, int d2, int chi_r, int direction, int k_max,
+                             const double* theta, const double* Q0, int k0, int q, int p, uint64_t seed,
+                             int bond, double* left, double* right, double* lam, double* discarded, int* k_out);
 
 /* Inverse basis transformation on one site (Eq. InverseBasisTransformation):
  * out[a][n][b] = sum_m V[n][m] A[a][m][b], V device complex[D*d], A device

@@ -161,7 +161,7 @@ def truncate_warm(theta, direction, chi_max, Q0, q=1, p=8, seed=0, bond=0):
     """The same split as ``truncate`` with the kept subspace found by block subspace iteration
     on rho from a warm start instead of a full eigendecomposition (not in the paper: a
     cheaper truncation whose energies are compared with the exact one).  Steps:
-      m = min(n, k + p) start vectors: the columns of Q0 (the current centre tensor spans the
+      m = min(nL, nR, k + p) start vectors: the columns of Q0 (the current centre tensor spans the
       previous kept subspace), then rho * Omega with Omega from the Philox TRUNC stream of
       (seed, bond); Gram-Schmidt; q times Q <- orth(rho Q); Rayleigh-Ritz: the k largest
       eigenpairs (w, Y) of Q^dag rho Q give U = Q Y.  rho = T T^dag ('right') or T^dag T
@@ -177,7 +177,7 @@ def truncate_warm(theta, direction, chi_max, Q0, q=1, p=8, seed=0, bond=0):
     else:
         n = nR
         apply = lambda X: Tm.conj().T @ (Tm @ X)
-    m = min(n, k + p)
+    m = min(nL, nR, k + p)       # no more vectors than the rank of rho can hold
     k0 = 0 if Q0 is None else min(Q0.shape[1], m)
     S = np.empty((n, m), dtype=np.complex128)
     if k0:

@@ -696,6 +696,8 @@ vtn_status vtn_sweep_opts_default(vtn_sweep_opts* o) {
     o->lanczos_tol = 1e-10;
     o->krylov_max = 32;
     o->lanczos_max_restarts = 4;
+    o->trunc_mode = 0;
+    o->trunc_q = 1;
     return VTN_OK;
 }
 
@@ -708,6 +710,8 @@ vtn_status vtn_sweep(vtn_ctx ctx, vtn_mpo mpo, vtn_mps* state, const vtn_sweep_o
         VTN_REQUIRE(opts->krylov_max >= 1 && opts->krylov_max <= 64, "krylov_max must be in [1, 64]");
         VTN_REQUIRE(opts->lanczos_max_restarts >= 0, "lanczos_max_restarts must be >= 0");
         VTN_REQUIRE(opts->n_schedule == 0 || opts->chi_schedule != nullptr, "chi_schedule missing");
+        VTN_REQUIRE(opts->trunc_mode == 0 || opts->trunc_mode == 1, "trunc_mode must be 0 or 1");
+        VTN_REQUIRE(opts->trunc_mode == 0 || (opts->trunc_q >= 0 && opts->trunc_q <= 64), "trunc_q must be in [0, 64]");
         if (opts->prec != VTN_FP64 && opts->prec != VTN_BF16X3)
             throw Error{VTN_EUNSUPPORTED, "VTN_TF32X3 is not available in this build"};
         const bool split = opts->prec == VTN_BF16X3;
@@ -793,7 +797,21 @@ vtn_status vtn_sweep(vtn_ctx ctx, vtn_mpo mpo, vtn_mps* state, const vtn_sweep_o
                     rep.matvecs += lr.n_matvec;
                     rep.heff_flops += hf * lr.n_matvec;
                     if (!lr.converged) ++not_conv;
-                    TruncResult tr = truncate_dev(c, cl, d, d, cr, dir, chi_s, theta, mps->sites[i], mps->sites[i + 1]);
+                    TruncResult tr;
+                    if (opts->trunc_mode == 1) {
+                        // warm start: the current centre (site i sweeping right, i + 1 sweeping left),
+                        // as conjugated rows
+                        const double2* Sh0 = mps->sites[i + 1];  // cm x (d cr), already rows
+                        if (dir == 0) {
+                            double2* q0 = (double2*)c.workspace(WS_WARM_Q0, sizeof(double2) * (size_t)cm * cl * d);
+                            conj_transpose_dev(c, cl * d, cm, mps->sites[i], cm, q0, (long long)cl * d);
+                            Sh0 = q0;
+                        }
+                        tr = truncate_warm_dev(c, cl, d, d, cr, dir, chi_s, theta, Sh0, cm, opts->trunc_q, 8, opts->seed,
+                                               i, mps->sites[i], mps->sites[i + 1]);
+                    } else {
+                        tr = truncate_dev(c, cl, d, d, cr, dir, chi_s, theta, mps->sites[i], mps->sites[i + 1]);
+                    }
                     mps->dims[i + 1] = tr.k;
                     disc_max = std::max(disc_max, tr.discarded);
                     if (dir == 0)
@@ -1373,6 +1391,32 @@ vtn_status vtn_truncate(vtn_ctx ctx, int chi_l, int d1, int d2, int chi_r, int d
         use_device(c);
         TruncResult r = truncate_dev(c, chi_l, d1, d2, chi_r, direction, k_max, (const double2*)theta,
                                      (double2*)left, (double2*)right);
+        if (lam) std::copy(r.lam.begin(), r.lam.end(), lam);
+        if (discarded) *discarded = r.discarded;
+        if (k_out) *k_out = r.k;
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_truncate_warm(vtn_ctx ctx, int chi_l, int d1, int d2, int chi_r, int direction, int k_max,
+                             const double* theta, const double* Q0, int k0, int q, int p, uint64_t seed,
+                             int bond, double* left, double* right, double* lam, double* discarded, int* k_out) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(theta && left && right, "null device pointer");
+        VTN_REQUIRE(chi_l >= 1 && d1 >= 1 && d2 >= 1 && chi_r >= 1 && k_max >= 1, "sizes must be >= 1");
+        VTN_REQUIRE(direction == 0 || direction == 1, "direction must be 0 or 1");
+        VTN_REQUIRE(k0 >= 0 && (k0 == 0 || Q0 != nullptr), "Q0 missing");
+        Ctx& c = ctx->c;
+        use_device(c);
+        const int n = direction == 0 ? chi_l * d1 : d2 * chi_r;
+        double2* Sh0 = nullptr;
+        if (k0 > 0) {
+            Sh0 = (double2*)c.workspace(WS_WARM_Q0, sizeof(double2) * (size_t)k0 * n);
+            conj_transpose_dev(c, n, k0, (const double2*)Q0, k0, Sh0, n);
+        }
+        TruncResult r = truncate_warm_dev(c, chi_l, d1, d2, chi_r, direction, k_max, (const double2*)theta, Sh0, k0,
+                                          q, p, seed, bond, (double2*)left, (double2*)right);
         if (lam) std::copy(r.lam.begin(), r.lam.end(), lam);
         if (discarded) *discarded = r.discarded;
         if (k_out) *k_out = r.k;

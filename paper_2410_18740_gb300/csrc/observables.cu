@@ -36,10 +36,11 @@ __host__ __device__ inline double uniform53(unsigned hi, unsigned lo) {
 
 namespace {
 
-__global__ void random_normal_kernel(double2* out, long long count, unsigned k0, unsigned k1, unsigned site) {
+__global__ void random_normal_kernel(double2* out, long long count, unsigned k0, unsigned k1, unsigned site,
+                                     unsigned stream) {
     const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= count) return;
-    unsigned c[4] = {(unsigned)j, (unsigned)((unsigned long long)j >> 32), site, 1u};
+    unsigned c[4] = {(unsigned)j, (unsigned)((unsigned long long)j >> 32), site, stream};
     philox4x32_10(c, k0, k1);
     const double u1 = uniform53(c[0], c[1]);
     const double u2 = uniform53(c[2], c[3]);
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(1024) orth_rows_kernel(double2* A, int rows, i
         if (threadIdx.x == 0) {
             double t = 0.0;
             for (int w = 0; w < nw; ++w) t += nrm_sh[w];
-            nrm_sh[0] = 1.0 / sqrt(t);
+            nrm_sh[0] = t > 0.0 ? 1.0 / sqrt(t) : 0.0;  // an exactly dependent row stays zero
         }
         __syncthreads();
         const double inv = nrm_sh[0];
@@ -235,10 +236,10 @@ __global__ void __launch_bounds__(256) sample_kernel(SampleArgs a) {
 
 }  // namespace
 
-void fill_random_normal(Ctx& ctx, double2* out, long long count, uint64_t seed, int site) {
+void fill_random_normal(Ctx& ctx, double2* out, long long count, uint64_t seed, int site, unsigned stream) {
     if (count <= 0) return;
     random_normal_kernel<<<(unsigned)((count + 255) / 256), 256, 0, ctx.stream>>>(
-        out, count, (unsigned)(seed & 0xFFFFFFFFu), (unsigned)(seed >> 32), (unsigned)site);
+        out, count, (unsigned)(seed & 0xFFFFFFFFu), (unsigned)(seed >> 32), (unsigned)site, stream);
     ctx.count_launch();
     ctx.check_launch("random_normal_kernel");
 }

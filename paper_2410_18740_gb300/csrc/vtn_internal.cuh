@@ -124,7 +124,8 @@ enum WsSlot {
     WS_X = 0, WS_Y, WS_Z, WS_KRYLOV, WS_VEC_W, WS_VEC_T, WS_PARTIAL, WS_SCAL, WS_EIG_A, WS_EIG_H,
     WS_EIG_Y, WS_EIG_WORK, WS_EIG_U, WS_CORE_A, WS_CORE_B, WS_ENV_TMP, WS_MISC, WS_TC_L, WS_TC_R, WS_TC_B1,
     WS_TC_A2, WS_TC_PART, WS_GEMM_SPLIT, WS_EIG_PART, WS_TC_ENV, WS_EIG_T, WS_H2_ENV, WS_EXPAND,
-    WS_TRUNC_L, WS_TRUNC_R, WS_CENTER, WS_MLP_ACT, WS_MLP_Y, WS_MLP_G, WS_COUNT
+    WS_TRUNC_L, WS_TRUNC_R, WS_CENTER, WS_MLP_ACT, WS_MLP_Y, WS_MLP_G, WS_WARM_S, WS_WARM_Z, WS_WARM_P,
+    WS_WARM_U, WS_WARM_N, WS_WARM_Q0, WS_COUNT
 };
 
 // ------------------------------------------------------------------ cores
@@ -264,6 +265,13 @@ struct TruncResult {
     double discarded;
     std::vector<double> lam;
 };
+// Truncation by warm-started subspace iteration and Rayleigh-Ritz (trunc_warm.cu): Sh0 holds
+// k0 warm rows (conjugates of the start vectors, k0 x n, n = chi_l d1 or d2 chi_r by direction).
+TruncResult truncate_warm_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int direction, int k_max,
+                              const double2* theta, const double2* Sh0, int k0, int q, int p, uint64_t seed,
+                              int bond, double2* left, double2* right);
+// out[j][r] = conj(A[r][j]) (rows x cols A with leading dimension lda)
+void conj_transpose_dev(Ctx& ctx, int rows, int cols, const double2* A, long long lda, double2* out, long long ldo);
 // outer >= 0 limits the product formed after the eigendecomposition: direction 0 writes
 // only the first `outer` columns of right (leading dimension outer), direction 1 only the
 // first `outer` rows of left.
@@ -271,7 +279,10 @@ TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int dir
                          const double2* theta, double2* left, double2* right, int outer = -1);
 
 // ------------------------------------------------------------------ misc kernels
-void fill_random_normal(Ctx& ctx, double2* out, long long count, uint64_t seed, int site);
+// Philox counter word 3: the stream of the random numbers (initial MPS, sampler, truncation)
+constexpr unsigned PHILOX_STREAM_INIT = 1u, PHILOX_STREAM_TRUNC = 3u;
+void fill_random_normal(Ctx& ctx, double2* out, long long count, uint64_t seed, int site,
+                        unsigned stream = PHILOX_STREAM_INIT);
 void orthonormalize_rows(Ctx& ctx, double2* A, int rows, int cols);
 void lbo_rotate_dev(Ctx& ctx, int chi_l, int d, int D, int chi_r, const double2* V, const double2* A,
                     double2* out);

@@ -41,7 +41,8 @@ class vtn_sweep_opts(C.Structure):
     _fields_ = [("chi_max", C.c_int), ("chi_schedule", C.POINTER(C.c_int)), ("n_schedule", C.c_int),
                 ("n_sweeps", C.c_int), ("prec", C.c_int), ("lanczos_tol", C.c_double),
                 ("krylov_max", C.c_int), ("lanczos_max_restarts", C.c_int), ("e_tol", C.c_double),
-                ("e_target", C.c_double), ("use_e_target", C.c_int), ("seed", C.c_uint64)]
+                ("e_target", C.c_double), ("use_e_target", C.c_int), ("seed", C.c_uint64),
+                ("trunc_mode", C.c_int), ("trunc_q", C.c_int)]
 
 
 class vtn_sweep_report(C.Structure):
@@ -112,6 +113,7 @@ _SIGS = {
     "vtn_env_update": [_P, C.POINTER(vtn_core), _I, _I, _I, _P, _P, _P, _I],
     "vtn_heff_ground": [_P, C.POINTER(vtn_core), C.POINTER(vtn_core), _I, _I, _P, _P, _P, _D, _I, _I, _PD, _PI],
     "vtn_truncate": [_P, _I, _I, _I, _I, _I, _I, _P, _P, _P, _PD, _PD, _PI],
+    "vtn_truncate_warm": [_P, _I, _I, _I, _I, _I, _I, _P, _P, _I, _I, _I, C.c_uint64, _I, _P, _P, _PD, _PD, _PI],
     "vtn_lbo_rotate": [_P, _I, _I, _I, _I, _P, _P, _P],
     "vtn_heff_apply_static": [C.POINTER(vtn_core), C.POINTER(vtn_core), _I, _I, _P, _P, _P, _P, _P],
     "vtn_gemm_bf16": [_P, _I, _I, _I, _P, C.c_longlong, _P, C.c_longlong, _P, C.c_longlong, _I],
@@ -551,6 +553,20 @@ def vtn_heff_ground(ctx, Wi, Wj, chi_l, chi_r, L, R, theta, tol=1e-10, krylov_ma
                                C.byref(nmv))
     _check(ctx, st, ok=(VTN_OK, VTN_ENOCONV))
     return st, E.value, nmv.value
+
+
+def vtn_truncate_warm(ctx, chi_l, d1, d2, chi_r, direction, k_max, theta, Q0, q, p, seed, bond, left, right):
+    """Q0: device complex tensor (n x k0) or None.  Returns (k, ritz values, discarded)."""
+    kmax_eff = min(k_max, chi_l * d1, d2 * chi_r)
+    lam = np.zeros(kmax_eff)
+    disc = C.c_double()
+    k = C.c_int()
+    k0 = 0 if Q0 is None else int(Q0.shape[1])
+    _check(ctx, lib().vtn_truncate_warm(ctx, int(chi_l), int(d1), int(d2), int(chi_r), int(direction), int(k_max),
+                                        _dptr(theta), _dptr(Q0), k0, int(q), int(p), C.c_uint64(int(seed)), int(bond),
+                                        _dptr(left), _dptr(right), lam.ctypes.data_as(_PD), C.byref(disc),
+                                        C.byref(k)))
+    return k.value, lam[: k.value], disc.value
 
 
 def vtn_truncate(ctx, chi_l, d1, d2, chi_r, direction, k_max, theta, left, right):
