@@ -86,6 +86,9 @@ def parse():
     p.add_argument("--trunc-shape", type=int, nargs=2, default=None, metavar=("CHI", "D"),
                    help="trunc: theta (CHI, D, D, CHI) with k = CHI (default: the split workload's middle "
                         "bond, 128 8; the large workload's is 512 6)")
+    p.add_argument("--warm-q", type=int, default=None,
+                   help="also measure the optional warm-started truncation with this many subspace iterations "
+                        "(trunc: beside the exact one; time-to-eps: a mixed run with it)")
     p.add_argument("--ref-sweeps", type=int, default=6,
                    help="time-to-eps: sweeps of the FP64 reference run (chi schedule 16, 32, 64, 128, then 128)")
     return p.parse_args()
@@ -373,7 +376,7 @@ def run_native(args):
     e2e_elapsed = max_over_ranks(ws, sum(e2e_times))
     e2e_value = e2e_flops * ws / e2e_elapsed / 1e12
     # ---------------- time to eps: FP64 reference run and mixed run from the same random state
-    tte = None if args.no_tte else measure_tte(ctx, mpo, args.seed, args.ref_sweeps)
+    tte = None if args.no_tte else measure_tte(ctx, mpo, args.seed, args.ref_sweeps, warm_q=args.warm_q)
     # ---------------- report
     peaks, peaks_src = load_peaks()
     fpeak, fpeak_src = fp64_peak_tflops()
@@ -528,13 +531,30 @@ def run_case_trunc(args):
     torch.cuda.synchronize()
     el = (time.perf_counter() - t0) / 3
     ntri, fltri, stri = vtn.vtn_timing_read(ctx, "tridiag")
-    print(json.dumps({"case": "trunc", "n": chi * d, "k": chi, "ms": 1e3 * el,
-                      "tridiag_ms": 1e3 * stri / max(ntri, 1),
-                      "tridiag_tflops": (fltri / stri / 1e12) if stri else None}), flush=True)
+    line = {"case": "trunc", "n": chi * d, "k": chi, "ms": 1e3 * el, "tridiag_ms": 1e3 * stri / max(ntri, 1),
+            "tridiag_tflops": (fltri / stri / 1e12) if stri else None}
+    if args.warm_q is not None:
+        # the warm-started truncation from the exact kept subspace (the ideal warm start)
+        _, lam_ex, disc_ex = vtn.vtn_truncate(ctx, chi, d, d, chi, 0, chi, t, left, right)
+        q0 = left.reshape(chi * d, chi).clone()
+        lw = torch.empty_like(left)
+        rw = torch.empty_like(right)
+        for _ in range(2):
+            vtn.vtn_truncate_warm(ctx, chi, d, d, chi, 0, chi, t, q0, args.warm_q, 8, args.seed, 0, lw, rw)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            _, lam_w, disc_w = vtn.vtn_truncate_warm(ctx, chi, d, d, chi, 0, chi, t, q0, args.warm_q, 8, args.seed,
+                                                     0, lw, rw)
+        torch.cuda.synchronize()
+        line["warm"] = {"q": args.warm_q, "ms": 1e3 * (time.perf_counter() - t0) / 3,
+                        "kept_weight_rel_diff": float((np.sum(lam_ex) - np.sum(lam_w)) / np.sum(lam_ex)),
+                        "discarded_exact": disc_ex, "discarded_warm": disc_w}
+    print(json.dumps(line), flush=True)
     vtn.vtn_destroy(ctx)
 
 
-def measure_tte(ctx, mpo, seed, ref_sweeps, single_site=True):
+def measure_tte(ctx, mpo, seed, ref_sweeps, single_site=True, warm_q=None):
     """Time-to-eps on the split workload: both solvers start from the same seeded random MPS
     with the chi schedule 16, 32, 64, 128.  The FP64 solver runs ref_sweeps sweeps; E_ref is
     its last energy and eps = E_ref * 1e-8.  The mixed solver (bf16x3 H_eff psi and
@@ -548,9 +568,11 @@ def measure_tte(ctx, mpo, seed, ref_sweeps, single_site=True):
 
     sched = [16, 32, 64, CHI]
 
-    def run(prec, n_sweeps, e_target=None, one_site=False):
+    def run(prec, n_sweeps, e_target=None, one_site=False, trunc_q=None):
         kw = dict(chi_max=CHI, n_sweeps=n_sweeps, seed=seed, lanczos_tol=1e-12, krylov_max=KRYLOV,
                   lanczos_max_restarts=0, chi_schedule=sched, prec=prec)
+        if trunc_q is not None:
+            kw.update(trunc_mode=1, trunc_q=trunc_q)
         if e_target is not None:
             kw.update(e_target=e_target, use_e_target=1)
         opts = vtn.vtn_sweep_opts_default(**kw)
@@ -576,6 +598,16 @@ def measure_tte(ctx, mpo, seed, ref_sweeps, single_site=True):
     mixed, wall16 = run(vtn.VTN_BF16X3, ref_sweeps + 8, target)
     t64 = next((t for t, e in ref if e <= target), None)
     t16 = next((t for t, e in mixed if e <= target), None)
+    warm = None
+    if warm_q is not None:
+        try:
+            mw, wallw = run(vtn.VTN_BF16X3, ref_sweeps + 8, target, trunc_q=warm_q)
+            tw = next((t for t, e in mw if e <= target), None)
+            warm = {"solver": f"mixed, warm-started truncation (q = {warm_q})", "time_to_eps_s": tw,
+                    "sweeps": len(mw), "wall_s": wallw, "energies": [e for _, e in mw],
+                    "cum_seconds": [t for t, _ in mw], "speedup_vs_fp64": (t64 / tw) if (t64 and tw) else None}
+        except Exception as exc:  # reported, never fatal to the benchmark line
+            warm = {"error": repr(exc)}
     one = None
     if single_site:
         try:
@@ -597,6 +629,7 @@ def measure_tte(ctx, mpo, seed, ref_sweeps, single_site=True):
             "mixed": {"time_to_eps_s": t16, "sweeps": len(mixed), "wall_s": wall16, "energies": [e for _, e in mixed],
                       "cum_seconds": [t for t, _ in mixed]},
             "single_site_fp64": one,
+            "mixed_warm_truncation": warm,
             "speedup": (t64 / t16) if (t64 and t16) else None}
 
 
@@ -609,7 +642,7 @@ def run_case_tte(args):
     w = inputs.workload(WORKLOAD, args.seed)
     ctx = vtn.vtn_create(0)
     mpo = vtn.vtn_build_mpo(ctx, w.r, w.U, w.D, w.d)
-    line = {"case": "tte", **measure_tte(ctx, mpo, args.seed, args.ref_sweeps)}
+    line = {"case": "tte", **measure_tte(ctx, mpo, args.seed, args.ref_sweeps, warm_q=args.warm_q)}
     print(json.dumps(line), flush=True)
     vtn.vtn_mpo_free(mpo)
     vtn.vtn_destroy(ctx)
