@@ -189,6 +189,7 @@ void gemm_c64(Ctx& ctx, const GemmArgs& g, int timing_class) {
     const long long slots = 2LL * std::max(ctx.num_sms, 1);
     int S = 1;
     if (tiles < slots) S = (int)std::min<long long>({slots / tiles, steps / 16, 32LL, 65535LL / g.batch});
+    if (g.max_splits > 0) S = std::min(S, g.max_splits);
     S = std::max(S, 1);
     p.splits = S;
     p.part = nullptr;

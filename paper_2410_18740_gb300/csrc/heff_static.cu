@@ -5,9 +5,12 @@
 //
 // It runs the same kernels as vtn_heff_apply (complex GEMM, MPO-core mixing, complex GEMM)
 // but takes every intermediate from one file-scope device array instead of a context's
-// workspace, needs no context, and performs no allocation of any kind: the MPO cores'
-// index tables are built in fixed-size host arrays on the stack and copied, together with
-// the caller's operator arrays, into the front of the same device array.
+// workspace, needs no context, and performs no allocation of any kind: the GEMMs never
+// split their summation range (a split would need a partial-sum buffer), and the MPO cores'
+// index tables and operators are packed into one file-scope host buffer and copied from
+// there, in one copy, into the front of the same device array.  That host buffer is
+// ordinary pageable memory, so the copy has taken its bytes when cudaMemcpyAsync returns:
+// the caller's arrays are never read by a DMA that outlives the call.
 //
 // The array's device address is looked up once per device (cudaGetSymbolAddress with that
 // device current) by the first call on that device; make that first call before any
@@ -37,13 +40,20 @@ static __device__ __align__(256) unsigned char g_heff_scratch[kScratchBytes];
 std::mutex g_mu;
 unsigned char* g_base[kMaxDevices];  // device address of g_heff_scratch per device (0 = not looked up)
 
-// index tables of one core, grouped by output column, in fixed-size host storage
+// index tables of one core, grouped by output column, in fixed-size storage
 struct Tables {
     int col_ptr[kMaxW + 1];
     int col_src[kMaxNnz];
     int col_op[kMaxNnz];
     unsigned char ident[kMaxNnz];
 };
+
+// Host staging of both cores (guarded by g_mu from packing until the copy has returned).
+struct HostStage {
+    Tables t[2];
+    alignas(256) unsigned char blob[kCoreRegion];
+};
+HostStage g_stage;
 
 vtn_status check_core(const vtn_core* c) {
     if (!c || c->w_left < 1 || c->w_right < 1 || c->w_left > kMaxW || c->w_right > kMaxW) return VTN_EINVAL;
@@ -87,44 +97,31 @@ size_t core_bytes(const vtn_core* c) {
            round256(std::max(c->nnz, 1)) + round256(sizeof(double2) * std::max((size_t)c->nnz * c->d * c->d, size_t(1)));
 }
 
-// Copies one core into the static region at dst and fills a DevCore view of it.
-cudaError_t place_core(const vtn_core* c, const Tables& t, unsigned char* dst, cudaStream_t s, vtn::DevCore& dc) {
-    size_t off = 0;
+// Packs one core into the host blob at offset `at` (the same layout the device copy gets at
+// dev + at) and fills a DevCore view of the device copy.
+void pack_core(const vtn_core* c, const Tables& t, unsigned char* blob, unsigned char* dev, size_t at,
+               vtn::DevCore& dc) {
+    size_t off = at;
     auto put = [&](const void* src, size_t bytes) -> unsigned char* {
-        unsigned char* p = dst + off;
+        if (bytes) std::memcpy(blob + off, src, bytes);
+        unsigned char* p = dev + off;
         off += round256(std::max(bytes, size_t(1)));
         return p;
     };
-    unsigned char* p_ptr = put(nullptr, sizeof(int) * (c->w_right + 1));
-    unsigned char* p_src = put(nullptr, sizeof(int) * std::max(c->nnz, 1));
-    unsigned char* p_op = put(nullptr, sizeof(int) * std::max(c->nnz, 1));
-    unsigned char* p_id = put(nullptr, std::max(c->nnz, 1));
-    unsigned char* p_ops = put(nullptr, sizeof(double2) * std::max((size_t)c->nnz * c->d * c->d, size_t(1)));
-    // pageable-memory copies return once the source has been staged, so the stack
-    // tables may go out of scope when this function returns
-    cudaError_t e = cudaMemcpyAsync(p_ptr, t.col_ptr, sizeof(int) * (c->w_right + 1), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && c->nnz > 0) {
-        e = cudaMemcpyAsync(p_src, t.col_src, sizeof(int) * c->nnz, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(p_op, t.col_op, sizeof(int) * c->nnz, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(p_id, t.ident, c->nnz, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(p_ops, c->ops, sizeof(double2) * (size_t)c->nnz * c->d * c->d,
-                                cudaMemcpyHostToDevice, s);
-    }
+    const size_t nnz = (size_t)c->nnz;
+    dc.col_ptr = (int*)put(t.col_ptr, sizeof(int) * (c->w_right + 1));
+    dc.col_src = (int*)put(t.col_src, sizeof(int) * nnz);
+    dc.col_op = (int*)put(t.col_op, sizeof(int) * nnz);
+    dc.ident = put(t.ident, nnz);
+    dc.ops = (double2*)put(c->ops, sizeof(double2) * nnz * c->d * c->d);
     dc.wl = c->w_left;
     dc.wr = c->w_right;
     dc.d = c->d;
     dc.nnz = c->nnz;
-    dc.col_ptr = (int*)p_ptr;
-    dc.col_src = (int*)p_src;
-    dc.col_op = (int*)p_op;
-    dc.ident = p_id;
-    dc.ops = (double2*)p_ops;
     int ni = 0;
     for (int k = 0; k < c->nnz; ++k) ni += t.ident[k];
     dc.n_ident = ni;
     dc.n_dense = c->nnz - ni;
-    return e;
 }
 
 }  // namespace
@@ -159,16 +156,24 @@ extern "C" vtn_status vtn_heff_apply_static(const vtn_core* Wi, const vtn_core* 
         base = g_base[dev];
     }
     cudaStream_t stream = (cudaStream_t)cuda_stream;
-    // ---- cores into the front of the array
-    Tables ti, tj;
-    fill_tables(Wi, ti);
-    fill_tables(Wj, tj);
+    // ---- cores into the front of the array: packed on the host, one pageable copy
     vtn::DevCore ci, cj;
-    if (place_core(Wi, ti, base, stream, ci) != cudaSuccess) return VTN_ECUDA;
-    if (place_core(Wj, tj, base + core_bytes(Wi), stream, cj) != cudaSuccess) return VTN_ECUDA;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        fill_tables(Wi, g_stage.t[0]);
+        fill_tables(Wj, g_stage.t[1]);
+        const size_t bi = core_bytes(Wi);
+        pack_core(Wi, g_stage.t[0], g_stage.blob, base, 0, ci);
+        pack_core(Wj, g_stage.t[1], g_stage.blob, base, bi, cj);
+        if (cudaMemcpyAsync(base, g_stage.blob, bi + core_bytes(Wj), cudaMemcpyHostToDevice, stream) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return VTN_ECUDA;
+        }
+    }
     double2* X = (double2*)(base + kCoreRegion);
     double2* Yb = (double2*)(base + kCoreRegion + kBufBytes);
-    // ---- the product: same kernels as vtn_heff_apply, no workspace, no timing
+    // ---- the product: same kernels as vtn_heff_apply, no split-K, no workspace, no timing
     try {
         vtn::Ctx c;
         c.device = dev;
@@ -178,6 +183,7 @@ extern "C" vtn_status vtn_heff_apply_static(const vtn_core* Wi, const vtn_core* 
         g1.A = (const double2*)L; g1.lda = chi_l;
         g1.B = (const double2*)theta; g1.ldb = (long long)d * d * chi_r;
         g1.C = X; g1.ldc = (long long)d * d * chi_r;
+        g1.max_splits = 1;
         vtn::gemm_c64(c, g1);
         vtn::mix_apply(c, ci, true, chi_l, d * chi_r, X, Yb);
         vtn::mix_apply(c, cj, true, chi_l * d, chi_r, Yb, X);
@@ -186,6 +192,7 @@ extern "C" vtn_status vtn_heff_apply_static(const vtn_core* Wi, const vtn_core* 
         g2.A = X; g2.lda = chi_r; g2.sA_kb = n_theta;
         g2.B = (const double2*)R; g2.ldb = chi_r; g2.sB_kb = (long long)chi_r * chi_r;
         g2.C = (double2*)y; g2.ldc = chi_r;
+        g2.max_splits = 1;
         vtn::gemm_c64(c, g2);
     } catch (const vtn::Error& e) {
         return e.status;

@@ -146,6 +146,8 @@ struct GemmArgs {
     double2* C; long long ldc; long long sC_batch = 0;
     bool accumulate = false;  // C += result (else C = result)
     bool herm_lower = false;  // result is Hermitian: compute tiles on/below the diagonal only
+    int max_splits = 0;       // > 0: at most this many CTAs per output tile along the summation
+                              // (1 = never split, so no split-K workspace is touched); 0 = automatic
 };
 // C[i][j] = conj(C[j][i]) for j > i (n x n, leading dimension ldc)
 void mirror_lower_to_upper(Ctx& ctx, double2* C, int n, long long ldc);

@@ -61,3 +61,37 @@ def test_static_scratch_rejects_oversize_requests(libvtn):
     with pytest.raises(vtn.VtnError) as e:
         vtn.vtn_heff_apply_static(Wi, Wj, 2, 2, L, R, th, th)     # y aliases theta
     assert e.value.status == vtn.VTN_EINVAL
+
+
+def test_static_scratch_single_tile_long_sum_allocates_nothing(libvtn):
+    """The first bond of a sweep: chi_l = 1, d = 8, chi_r = 64, and a right core with 50
+    channels.  The final GEMM is then one 64 x 64 output tile summed over 50 * 64 terms, the
+    shape for which the regular entry point splits the summation over several CTAs and takes
+    a partial-sum buffer.  The static entry point must give the same result without any
+    device allocation: free device memory is unchanged across two calls in a row."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    chi_l, chi_r, d = 1, 64, 8
+    Wi, Wj, L, R, th = _case(14, chi_l, chi_r, d, (1, 6, 50))
+    ctx = vtn.vtn_create(0)
+    try:
+        y_ref = torch.empty_like(th)
+        vtn.vtn_heff_apply(ctx, Wi, Wj, chi_l, chi_r, L, R, th, y_ref)
+        ys = [torch.full_like(th, float("nan")) for _ in range(3)]
+        # a first call may load the library's device code (and with it the static array)
+        vtn.vtn_heff_apply_static(Wi, Wj, chi_l, chi_r, L, R, th, ys[0])
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        vtn.vtn_heff_apply_static(Wi, Wj, chi_l, chi_r, L, R, th, ys[1])
+        vtn.vtn_heff_apply_static(Wi, Wj, chi_l, chi_r, L, R, th, ys[2])
+        torch.cuda.synchronize()
+        free1 = torch.cuda.mem_get_info()[0]
+        assert free1 == free0, f"device memory changed by {free0 - free1} bytes"
+        b = y_ref.cpu().numpy()
+        for y in ys:
+            a = y.cpu().numpy()
+            assert np.isfinite(a).all()
+            assert np.abs(a - b).max() <= REL * np.abs(b).max()
+    finally:
+        torch.cuda.synchronize()
+        vtn.vtn_destroy(ctx)
