@@ -48,13 +48,40 @@ def orthonormal_rows(M):
     return Q.conj().T
 
 
-def initial_mps(N, d, chi0, seed):
+def initial_mps(N, d, chi0, seed, center=0):
+    """Philox normals per site; sites s >= center get their rows orthonormalised in order
+    (right-canonical), sites s < center the columns of the (chi_l d) x chi_r matrix
+    (left-canonical); the centre site is divided by sqrt(chi_center) so that <psi|psi> = 1.
+    center = 0 is the right-canonical initial state of the sweeps."""
     dims = bond_dims(N, d, chi0)
     mps = []
     for s in range(N):
         cl, cr = dims[s], dims[s + 1]
-        z = philox.complex_normals(seed, s, cl * d * cr).reshape(cl, d * cr)
-        mps.append(orthonormal_rows(z).reshape(cl, d, cr))
+        z = philox.complex_normals(seed, s, cl * d * cr)
+        if s >= center:
+            A = orthonormal_rows(z.reshape(cl, d * cr)).reshape(cl, d, cr)
+            if s == center:
+                A = A / np.sqrt(cl)
+        else:
+            A = orthonormal_rows(z.reshape(cl * d, cr).conj().T).conj().T.reshape(cl, d, cr)
+        mps.append(A)
+    return mps
+
+
+def move_center(mps, src, dst):
+    """Move the orthogonality centre of a mixed-canonical MPS from site src to site dst by exact
+    splits of theta = A_i A_i+1 (``truncate`` keeping the current bond dimension, so nothing
+    is dropped).  Returns the new list of tensors."""
+    mps = [A.copy() for A in mps]
+    c = src
+    while c < dst:
+        th = np.einsum("asb,btc->astc", mps[c], mps[c + 1], optimize=True)
+        mps[c], mps[c + 1], _, _ = truncate(th, "right", mps[c].shape[2])
+        c += 1
+    while c > dst:
+        th = np.einsum("asb,btc->astc", mps[c - 1], mps[c], optimize=True)
+        mps[c - 1], mps[c], _, _ = truncate(th, "left", mps[c].shape[0])
+        c -= 1
     return mps
 
 
@@ -80,6 +107,17 @@ def heff_apply(L, W1, W2, R, theta):
     T2 = np.einsum("abts,aisvk->bitvk", W1, T1, optimize=True)
     T3 = np.einsum("bcuv,bitvk->cituk", W2, T2, optimize=True)
     return np.einsum("cituk,ckl->itul", T3, R, optimize=True)
+
+
+def heff_apply_columns(L, W1, W2, R, theta, cols):
+    """Y[:, :, :, cols] of ``heff_apply``: the same sum with the output index l restricted to
+    ``cols``, evaluated from the right (R first, then W2, W1, L) so that a few output columns
+    of a large product cost only their share of the work (sampled checks at full size)."""
+    Rc = R[:, :, list(cols)]
+    Z = np.einsum("jsvk,ckl->jsvcl", theta, Rc, optimize=True)
+    Z = np.einsum("bcuv,jsvcl->jsbul", W2, Z, optimize=True)
+    Z = np.einsum("abts,jsbul->jatul", W1, Z, optimize=True)
+    return np.einsum("aij,jatul->itul", L, Z, optimize=True)
 
 
 # ---------------------------------------------------------------- Lanczos
@@ -249,23 +287,43 @@ class SweepReport:
     not_converged: int = 0
 
 
+def centre_energy(mps, cores, Lenv, Renv, lo):
+    """Rayleigh quotient <theta|H_eff theta>/<theta|theta> of theta = A_lo A_lo+1 under the
+    two-site effective Hamiltonian of bond (lo, lo+1): <psi|H|psi>/<psi|psi> of a state whose
+    sites < lo are left-canonical and sites > lo+1 right-canonical (Eq. MagOfSimError)."""
+    th = np.einsum("asb,btc->astc", mps[lo], mps[lo + 1], optimize=True)
+    y = heff_apply(Lenv[lo], cores[lo], cores[lo + 1], Renv[lo + 2], th)
+    return float(np.real(np.vdot(th, y))) / float(np.real(np.vdot(th, th)))
+
+
 def dmrg(cores, d, chi_max, n_sweeps, seed, chi_schedule=(), lanczos=None,
-         e_tol=0.0, e_target=None, mps=None, max_bonds=None, warm_q=None):
+         e_tol=0.0, e_target=None, mps=None, max_bonds=None, warm_q=None, window=None,
+         energy_mode="full"):
     """Two-site DMRG sweeps.  Returns (mps, report).  ``max_bonds`` stops after that
     many bond optimisations (used only to time a bounded sample).  ``warm_q`` = None: exact
     truncation; an integer: ``truncate_warm`` with that many iterations, started from the
-    current centre tensor (site i sweeping right, site i+1 sweeping left)."""
+    current centre tensor (site i sweeping right, site i+1 sweeping left).
+    ``window`` = (lo, hi): each sweep optimises bonds lo .. hi-1 left to right and back; the
+    given ``mps`` must have its centre at site lo (sites < lo left-canonical, > lo
+    right-canonical) and the sweep energy is then the centre Rayleigh quotient.
+    ``energy_mode`` = "full": the sweep energy is the full contraction; "centre": the Rayleigh
+    quotient of the final centre tensor (``centre_energy``)."""
     N = len(cores)
     p = lanczos or LanczosParams()
     sched = list(chi_schedule) if chi_schedule else [chi_max]
+    lo, hi = (0, N - 1) if window is None else window
+    if window is not None:
+        energy_mode = "centre"
     if mps is None:
-        mps = initial_mps(N, d, sched[0], seed)
+        mps = initial_mps(N, d, sched[0], seed, center=lo)
     mps = [A.copy() for A in mps]
     Lenv = [None] * (N + 1)
     Renv = [None] * (N + 1)
     Lenv[0] = np.ones((1, 1, 1), dtype=np.complex128)
     Renv[N] = np.ones((1, 1, 1), dtype=np.complex128)
-    for s in range(N - 1, 0, -1):
+    for s in range(0, lo):
+        Lenv[s + 1] = env_left(Lenv[s], mps[s], cores[s])
+    for s in range(N - 1, lo + 1, -1):
         Renv[s] = env_right(Renv[s + 1], mps[s], cores[s])
     rep = SweepReport()
     bonds_done = 0
@@ -273,7 +331,7 @@ def dmrg(cores, d, chi_max, n_sweeps, seed, chi_schedule=(), lanczos=None,
     for sweep in range(n_sweeps):
         chi_s = sched[min(sweep, len(sched) - 1)]
         disc_max = 0.0
-        for direction, bonds in (("right", range(0, N - 1)), ("left", range(N - 2, -1, -1))):
+        for direction, bonds in (("right", range(lo, hi)), ("left", range(hi - 1, lo - 1, -1))):
             for i in bonds:
                 theta = np.einsum("asb,btc->astc", mps[i], mps[i + 1], optimize=True)
                 shape = theta.shape
@@ -300,7 +358,7 @@ def dmrg(cores, d, chi_max, n_sweeps, seed, chi_schedule=(), lanczos=None,
                 bonds_done += 1
                 if max_bonds is not None and bonds_done >= max_bonds:
                     return mps, rep
-        E = energy(mps, cores)
+        E = energy(mps, cores) if energy_mode == "full" else centre_energy(mps, cores, Lenv, Renv, lo)
         rep.energies.append(E)
         rep.max_discarded.append(disc_max)
         if e_target is not None and E <= e_target:

@@ -338,6 +338,22 @@ def test_truncation_weights_and_reconstruction():
     assert abs(np.linalg.norm(th - approx) ** 2 - disc2) < 1e-12
 
 
+def test_heff_columns_match_the_full_product():
+    """The column-sampled H_eff product is the full product's columns (a different
+    association of the same sum, used for checks at the large workload's shapes)."""
+    rng = inputs.rng_for(606)
+    cl, cr, d, (wl, wm, wr) = 5, 7, 3, (4, 5, 3)
+    W1 = inputs.random_sparse_core(wl, wm, d, rng).dense()
+    W2 = inputs.random_sparse_core(wm, wr, d, rng).dense()
+    L = inputs.random_complex((wl, cl, cl), rng)
+    R = inputs.random_complex((wr, cr, cr), rng)
+    th = inputs.random_complex((cl, d, d, cr), rng)
+    Y = dmrg.heff_apply(L, W1, W2, R, th)
+    cols = [6, 0, 3]
+    Yc = dmrg.heff_apply_columns(L, W1, W2, R, th, cols)
+    assert np.abs(Yc - Y[..., cols]).max() <= 1e-13 * np.abs(Y).max()
+
+
 def test_lanczos_against_dense_eigh():
     rng = np.random.default_rng(7)
     A = inputs.random_complex((60, 60), rng)
@@ -356,6 +372,88 @@ def test_initial_mps_right_canonical():
         Am = A.reshape(A.shape[0], -1)
         assert np.abs(Am @ Am.conj().T - np.eye(A.shape[0])).max() < 1e-13
     assert abs(dmrg.norm2(mps) - 1) < 1e-12
+
+
+def _dense_vector(mps):
+    v = mps[0]
+    for A in mps[1:]:
+        v = np.einsum("...a,asb->...sb", v, A)
+    return v.reshape(-1)
+
+
+@pytest.mark.parametrize("center", [0, 2, 4])
+def test_initial_mps_mixed_canonical(center):
+    """Sites left of the centre are left isometries, sites right of it right isometries, the
+    state is normalised, and centre 0 is the right-canonical start state."""
+    mps = dmrg.initial_mps(5, 3, 7, seed=11, center=center)
+    for s, A in enumerate(mps):
+        if s < center:
+            Am = A.reshape(-1, A.shape[2])
+            assert np.abs(Am.conj().T @ Am - np.eye(A.shape[2])).max() < 1e-13
+        elif s > center:
+            Am = A.reshape(A.shape[0], -1)
+            assert np.abs(Am @ Am.conj().T - np.eye(A.shape[0])).max() < 1e-13
+    assert abs(dmrg.norm2(mps) - 1) < 1e-12
+    assert abs(np.linalg.norm(_dense_vector(mps)) - 1) < 1e-12
+    if center == 0:
+        for a, b in zip(mps, dmrg.initial_mps(5, 3, 7, seed=11)):
+            assert np.array_equal(a, b)
+
+
+def test_move_center_keeps_the_state():
+    """Exact splits only change the gauge: the dense vector is unchanged and the canonical
+    conditions hold around the new centre."""
+    mps = dmrg.initial_mps(6, 3, 9, seed=4, center=1)
+    v0 = _dense_vector(mps)
+    for dst in (4, 0, 3):
+        mps = dmrg.move_center(mps, {4: 1, 0: 4, 3: 0}[dst], dst)
+        assert np.abs(_dense_vector(mps) - v0).max() < 1e-12
+        for s, A in enumerate(mps):
+            if s < dst:
+                Am = A.reshape(-1, A.shape[2])
+                assert np.abs(Am.conj().T @ Am - np.eye(A.shape[2])).max() < 1e-12
+            elif s > dst:
+                Am = A.reshape(A.shape[0], -1)
+                assert np.abs(Am @ Am.conj().T - np.eye(A.shape[0])).max() < 1e-12
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_centre_energy_equals_full_contraction(seed):
+    """The centre Rayleigh quotient (one H_eff product) equals <psi|H|psi>/<psi|psi> from the
+    full left-to-right contraction on canonical states, so both sweep-energy modes agree."""
+    w = inputs.workload("split", seed, M=6, d=3, D=3)
+    G = gbs.hamiltonian_coefficients(w.r, w.U)
+    Hn = gbs.norm_bound(G, 6, 3)
+    cores = mpo.build_mpo(G, 3)
+    lp = dmrg.LanczosParams(krylov_max=20, max_restarts=2, tol=1e-11)
+    _, full = dmrg.dmrg(cores, 3, 6, 2, seed=seed + 5, lanczos=lp)
+    _, cen = dmrg.dmrg(cores, 3, 6, 2, seed=seed + 5, lanczos=lp, energy_mode="centre")
+    for a, b in zip(full.energies, cen.energies):
+        assert abs(a - b) <= 1e-10 * Hn
+
+
+@pytest.mark.parametrize("window", [(0, 5), (1, 4), (2, 3)])
+def test_windowed_sweep(window):
+    """A windowed sweep on a state centred at the window's first site: the full window (0, N-1)
+    repeats the full sweep; any window reports the full contraction energy of the state it
+    returns, and with a bond dimension that truncates nothing the energy never rises."""
+    lo, hi = window
+    N, d = 6, 3
+    w = inputs.workload("split", 7, M=N, d=d, D=d)
+    G = gbs.hamiltonian_coefficients(w.r, w.U)
+    Hn = gbs.norm_bound(G, N, d)
+    cores = mpo.build_mpo(G, d)
+    lp = dmrg.LanczosParams(krylov_max=24, max_restarts=3, tol=1e-11)
+    start = dmrg.initial_mps(N, d, 27, seed=3, center=lo)
+    e0 = dmrg.energy(start, cores)
+    mps, rep = dmrg.dmrg(cores, d, 27, 2, seed=3, lanczos=lp, mps=start, window=window)
+    assert abs(rep.energies[-1] - dmrg.energy(mps, cores)) <= 1e-10 * Hn
+    assert rep.energies[0] <= e0 + 1e-10 * Hn
+    assert rep.energies[1] <= rep.energies[0] + 1e-10 * Hn
+    if window == (0, N - 1):
+        _, full = dmrg.dmrg(cores, d, 27, 2, seed=3, lanczos=lp, mps=start)
+        for a, b in zip(rep.energies, full.energies):
+            assert abs(a - b) <= 1e-10 * Hn
 
 
 # ------------------------------------------------------------------ sampler
