@@ -165,6 +165,25 @@ vtn_status vtn_mps_random(vtn_ctx ctx, vtn_mpo mpo, int chi, uint64_t seed, vtn_
  * complex[dims[s]*d*dims[s+1]].  No canonical form is assumed. */
 vtn_status vtn_mps_from_host(vtn_ctx ctx, vtn_mpo mpo, const int* dims, const double* const* sites,
                              vtn_mps* out);
+/* The same draws as vtn_mps_random in mixed-canonical form with the orthogonality centre at
+ * site `center` (0 <= center < M): sites s < center get the columns of their (left bond,
+ * physical) x (right bond) matrix orthonormalised in order (left-canonical), sites s >= center
+ * the rows (right-canonical), and the centre site is then divided by sqrt(dims[center]) so
+ * that <psi|psi> = 1.  center = 0 is vtn_mps_random. */
+vtn_status vtn_mps_random_center(vtn_ctx ctx, vtn_mpo mpo, int chi, uint64_t seed, int center, vtn_mps* out);
+/* The orthogonality centre the library records for an MPS: the site whose left neighbours are
+ * all left-canonical and right neighbours all right-canonical, or -1 when unknown (an MPS
+ * from host tensors).  Sweeps and vtn_mps_move_center keep it up to date. */
+vtn_status vtn_mps_get_center(vtn_mps mps, int* center);
+/* Record the centre of an MPS whose tensors the caller built in that gauge (not checked), or
+ * forget it (center = -1).  -1 <= center < M. */
+vtn_status vtn_mps_set_center(vtn_mps mps, int center);
+/* Move the orthogonality centre to `center` (0 <= center < M) by exact splits of neighbouring
+ * sites: theta = A_i A_i+1 is split by the FP64 reduced-density-matrix eigendecomposition of
+ * vtn_truncate keeping k = the current bond dimension (no state is dropped, so psi is
+ * unchanged up to rounding and a gauge transformation).  An MPS with an unknown centre is
+ * first brought to centre 0 by splits from the right end. */
+vtn_status vtn_mps_move_center(vtn_ctx ctx, vtn_mps mps, int center);
 vtn_status vtn_mps_free(vtn_mps mps);
 vtn_status vtn_mps_info(vtn_mps mps, int* M, int* d, int* dims);
 /* Copy site s to host: complex[dims[s]*d*dims[s+1]]. */
@@ -191,6 +210,11 @@ typedef struct {
     int trunc_mode;            /* 0: exact eigendecomposition (the paper's truncation);
                                   1: warm-started subspace iteration (vtn_truncate_warm)   */
     int trunc_q;               /* subspace iterations of trunc_mode 1 (0..64)            */
+    int window_lo, window_hi;  /* window_hi > window_lo: a windowed sweep over the bonds
+                                  window_lo .. window_hi - 1 only (0 <= lo < hi <= M - 1)   */
+    int energy_mode;           /* energy reported after each sweep: 0 = full FP64 contraction
+                                  <psi|H|psi>/<psi|psi>; 1 = Rayleigh quotient of the final
+                                  centre tensor (windowed sweeps always use 1)            */
 } vtn_sweep_opts;
 
 typedef struct {
@@ -208,7 +232,8 @@ typedef struct {
 } vtn_sweep_report;
 
 /* Fill opts with the defaults: chi_max 16, 8 sweeps, FP64, lanczos_tol 1e-10,
- * krylov_max 32, 4 restarts, e_tol 0, seed 0, trunc_mode 0 (exact), trunc_q 1. */
+ * krylov_max 32, 4 restarts, e_tol 0, seed 0, trunc_mode 0 (exact), trunc_q 1, no window,
+ * energy_mode 0. */
 vtn_status vtn_sweep_opts_default(vtn_sweep_opts* opts);
 
 /* Two-site DMRG sweeps.  *state == NULL: start from vtn_mps_random(opts->chi_schedule[0]
@@ -216,7 +241,17 @@ vtn_status vtn_sweep_opts_default(vtn_sweep_opts* opts);
  * then (M-2,M-1) .. (0,1) right to left; it ends right-canonical with the centre at
  * site 0.  Each bond: Lanczos on H_eff (full re-orthogonalisation, restarts), FP64
  * eigendecomposition of the reduced density matrix, keep min(chi, chi_l d, d chi_r)
- * largest eigenpairs, environment update.  With opts->trunc_mode = 1 the truncation is
+ * largest eigenpairs, environment update.  A state whose recorded orthogonality centre is a
+ * site other than 0 is first brought back to centre 0 (vtn_mps_move_center).
+ * Windowed sweep (opts->window_hi > opts->window_lo): each sweep optimises bonds
+ * (lo,lo+1) .. (hi-1,hi) left to right, then back to (lo,lo+1), and ends with the centre at
+ * site lo; the state is first moved to centre lo if its recorded centre is elsewhere
+ * (sites < lo must be left-canonical, sites > lo right-canonical for the environments).
+ * Only the environments the window needs are built.  Its sweep energy is always the
+ * Rayleigh quotient of the final centre (energy_mode 1): <theta|H_eff theta>/<theta|theta>
+ * for theta = A_lo A_lo+1 and the H_eff of bond (lo, lo+1) in the sweep's contraction
+ * precision, FP64 sums; for a canonical state this is <psi|H|psi>/<psi|psi> (Eq.
+ * MagOfSimError) without a contraction over the whole chain.  With opts->trunc_mode = 1 the truncation is
  * vtn_truncate_warm with q = opts->trunc_q, p = 8, seed = opts->seed, bond = i and the
  * current centre tensor (site i sweeping right, site i+1 sweeping left) as start vectors.
  * Returns VTN_ENOCONV (after finishing) if some Lanczos solve missed its tolerance.  report
@@ -361,8 +396,9 @@ vtn_status vtn_truncate(vtn_ctx ctx, int chi_l, int d1, int d2, int chi_r, int d
  *   start vectors: the k0 columns of Q0 (device complex[n*k0], row-major n x k0; in a sweep the
  *   current centre tensor), then rho Omega for the remaining m - k0, Omega (n x (m - k0),
  *   row-major) complex normals (g1 + i g2)/sqrt(2) of Philox4x32-10 with key seed and counter
- *   (j, bond, 3) for entry j; Gram-Schmidt in order; q times: multiply by rho and
- *   re-orthonormalise; Rayleigh-Ritz: the k largest eigenpairs (w, Y) of Q^dag rho Q give the
+ *   (j, bond, 3) for entry j; Gram-Schmidt in order (a vector numerically dependent on the ones
+ *   before it -- residual below 1e-10 of its norm -- is replaced by an orthonormal completion);
+ *   q times: multiply by rho and re-orthonormalise; Rayleigh-Ritz: the k largest eigenpairs (w, Y) of Q^dag rho Q give the
  *   kept vectors Q Y.  rho is applied as T (T^dag X), never formed.  Outputs as vtn_truncate,
  *   with the Ritz values w in lam and discarded = 1 - sum(w)/||T||^2.  0 <= q <= 64,
  *   0 <= p <= 256, m <= 4096, k0 >= 0 (Q0 may be NULL when k0 = 0). */

@@ -268,6 +268,39 @@ struct Envs {
     }
 };
 
+// Exact split of bond (i, i+1): theta = A_i A_i+1 factored by the truncation eigensolver
+// keeping k = the current bond dimension (rank(theta) <= k, so nothing is dropped).
+// dir 0: site i left-canonical, the centre moves to i+1; dir 1: site i+1 right-canonical,
+// the centre moves to i.
+void exact_split(Ctx& c, vtn_mps mps, int i, int dir) {
+    const int d = mps->d, cl = mps->dims[i], cm = mps->dims[i + 1], cr = mps->dims[i + 2];
+    double2* theta = (double2*)c.workspace(WS_VEC_T, sizeof(double2) * (size_t)cl * d * d * cr);
+    GemmArgs g;
+    g.M = cl * d; g.N = d * cr; g.K = cm;
+    g.A = mps->sites[i]; g.lda = cm;
+    g.B = mps->sites[i + 1]; g.ldb = (long long)d * cr;
+    g.C = theta; g.ldc = (long long)d * cr;
+    gemm_c64(c, g);
+    TruncResult tr = truncate_dev(c, cl, d, d, cr, dir, cm, theta, mps->sites[i], mps->sites[i + 1]);
+    mps->dims[i + 1] = tr.k;
+}
+
+void move_center(Ctx& c, vtn_mps mps, int target) {
+    const int M = mps->M;
+    if (mps->center < 0 || mps->center >= M) {
+        for (int i = M - 2; i >= 0; --i) exact_split(c, mps, i, 1);
+        mps->center = 0;
+    }
+    while (mps->center < target) {
+        exact_split(c, mps, mps->center, 0);
+        ++mps->center;
+    }
+    while (mps->center > target) {
+        exact_split(c, mps, mps->center - 1, 1);
+        --mps->center;
+    }
+}
+
 void check_mps_matches(vtn_mpo mpo, vtn_mps mps) {
     VTN_REQUIRE(mps != nullptr, "null MPS");
     VTN_REQUIRE(mps->M == mpo->hp.M && mps->d == mpo->hp.d, "MPS does not match the MPO (M or d)");
@@ -535,28 +568,73 @@ vtn_status vtn_mpo_norm_bound(vtn_mpo mpo, double* out) {
 }
 
 // ------------------------------------------------------------------ MPS
-vtn_status vtn_mps_random(vtn_ctx ctx, vtn_mpo mpo, int chi, uint64_t seed, vtn_mps* out) {
+vtn_status vtn_mps_random_center(vtn_ctx ctx, vtn_mpo mpo, int chi, uint64_t seed, int center, vtn_mps* out) {
     if (!ctx) return VTN_EINVAL;
     return guard(ctx, [&]() -> vtn_status {
         VTN_REQUIRE(out && mpo, "null argument");
         VTN_REQUIRE(chi >= 1, "chi must be >= 1");
+        const int M = mpo->hp.M, d = mpo->hp.d;
+        VTN_REQUIRE(center >= 0 && center < M, "center must be in [0, M)");
         Ctx& c = ctx->c;
         use_device(c);
-        const int M = mpo->hp.M, d = mpo->hp.d;
         vtn_mps m = new_mps(ctx, M, d, bond_dims(M, d, chi));
         try {
             for (int s = 0; s < M; ++s) {
                 const int cl = m->dims[s], cr = m->dims[s + 1];
                 fill_random_normal(c, m->sites[s], (long long)cl * d * cr, seed, s);
-                orthonormalize_rows(c, m->sites[s], cl, d * cr);
+                if (s >= center) {
+                    orthonormalize_rows(c, m->sites[s], cl, d * cr);
+                } else {
+                    // columns of the (cl d) x cr matrix = rows of its conjugate transpose
+                    double2* t = (double2*)c.workspace(WS_ENV_TMP, sizeof(double2) * (size_t)cl * d * cr);
+                    conj_transpose_dev(c, cl * d, cr, m->sites[s], cr, t, (long long)cl * d);
+                    orthonormalize_rows(c, t, cr, cl * d);
+                    conj_transpose_dev(c, cr, cl * d, t, (long long)cl * d, m->sites[s], cr);
+                }
+            }
+            if (m->dims[center] > 1) {
+                const long long n = (long long)m->dims[center] * d * m->dims[center + 1];
+                double* nrm = (double*)c.workspace(WS_RQ_S, sizeof(double) * 64);
+                // divide by sqrt(dims[center]) = sqrt(|A_center|^2) (orthonormal rows)
+                norm2_dev(c, m->sites[center], n, nrm);
+                scale_inv_sqrt(c, m->sites[center], n, nrm);
             }
             c.sync();
         } catch (...) {
             destroy_mps(m);
             throw;
         }
-        m->center = 0;
+        m->center = center;
         *out = m;
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_mps_random(vtn_ctx ctx, vtn_mpo mpo, int chi, uint64_t seed, vtn_mps* out) {
+    return vtn_mps_random_center(ctx, mpo, chi, seed, 0, out);
+}
+
+vtn_status vtn_mps_get_center(vtn_mps mps, int* center) {
+    if (!mps || !center) return VTN_EINVAL;
+    *center = mps->center;
+    return VTN_OK;
+}
+
+vtn_status vtn_mps_set_center(vtn_mps mps, int center) {
+    if (!mps || center < -1 || center >= mps->M) return VTN_EINVAL;
+    mps->center = center;
+    return VTN_OK;
+}
+
+vtn_status vtn_mps_move_center(vtn_ctx ctx, vtn_mps mps, int center) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(mps != nullptr, "null MPS");
+        VTN_REQUIRE(center >= 0 && center < mps->M, "center must be in [0, M)");
+        Ctx& c = ctx->c;
+        use_device(c);
+        move_center(c, mps, center);
+        c.sync();
         return VTN_OK;
     });
 }
@@ -732,9 +810,17 @@ vtn_status vtn_sweep(vtn_ctx ctx, vtn_mpo mpo, vtn_mps* state, const vtn_sweep_o
         }
         vtn_mps mps = *state;
         check_mps_matches(mpo, mps);
+        // bonds lo .. hi - 1 (a windowed sweep) or the whole chain
+        const bool windowed = opts->window_hi > opts->window_lo;
+        const int lo = windowed ? opts->window_lo : 0, hi = windowed ? opts->window_hi : M - 1;
+        VTN_REQUIRE(!windowed || (lo >= 0 && hi <= M - 1), "window must satisfy 0 <= window_lo < window_hi <= M - 1");
+        VTN_REQUIRE(opts->energy_mode == 0 || opts->energy_mode == 1, "energy_mode must be 0 or 1");
+        const bool centre_energy = windowed || opts->energy_mode == 1;
         int chi_cap = opts->chi_max;
         for (int x : mps->dims) chi_cap = std::max(chi_cap, x);
         mps_reserve(c, mps, chi_cap);
+        // the environments assume sites < lo left-canonical and sites > lo right-canonical
+        if (windowed ? mps->center != lo : mps->center > 0) move_center(c, mps, lo);
         const std::vector<int> capdims = cap_dims(M, chi_cap);
         // environments sized for the largest bond dimension at each cut
         Envs env;
@@ -742,9 +828,10 @@ vtn_status vtn_sweep(vtn_ctx ctx, vtn_mpo mpo, vtn_mps* state, const vtn_sweep_o
         env.L.assign(M + 1, nullptr);
         env.R.assign(M + 1, nullptr);
         for (int s = 0; s <= M; ++s) {
+            // L[s] is read or written for s <= hi, R[s] for s >= lo + 1
             const size_t cap = (size_t)mpo->hp.w[s] * capdims[s] * capdims[s];
-            env.L[s] = (double2*)c.dalloc(sizeof(double2) * std::max(cap, size_t(1)));
-            env.R[s] = (double2*)c.dalloc(sizeof(double2) * std::max(cap, size_t(1)));
+            if (s <= hi) env.L[s] = (double2*)c.dalloc(sizeof(double2) * std::max(cap, size_t(1)));
+            if (s >= lo + 1) env.R[s] = (double2*)c.dalloc(sizeof(double2) * std::max(cap, size_t(1)));
         }
         set_scalar_one(c, env.L[0]);
         set_scalar_one(c, env.R[M]);
@@ -757,7 +844,9 @@ vtn_status vtn_sweep(vtn_ctx ctx, vtn_mpo mpo, vtn_mps* state, const vtn_sweep_o
             if (split) env_right_bf16x3(c, W, cl, cr, Rin, A, Rout);
             else env_right_dev(c, W, cl, cr, Rin, A, Rout);
         };
-        for (int s = M - 1; s >= 1; --s)
+        for (int s = 0; s < lo; ++s)
+            env_left(mpo->dcores[s], mps->dims[s], mps->dims[s + 1], env.L[s], mps->sites[s], env.L[s + 1]);
+        for (int s = M - 1; s >= lo + 2; --s)
             env_right(mpo->dcores[s], mps->dims[s], mps->dims[s + 1], env.R[s + 1], mps->sites[s], env.R[s]);
         const size_t theta_cap = (size_t)chi_cap * d * d * chi_cap;
         double2* theta = (double2*)c.workspace(WS_VEC_T, sizeof(double2) * theta_cap);
@@ -766,21 +855,25 @@ vtn_status vtn_sweep(vtn_ctx ctx, vtn_mpo mpo, vtn_mps* state, const vtn_sweep_o
         long long not_conv = 0;
         double prevE = 0.0;
         bool have_prev = false;
+        // theta = A_i A_i+1
+        auto form_theta = [&](int i) {
+            const int cl = mps->dims[i], cm = mps->dims[i + 1], cr = mps->dims[i + 2];
+            GemmArgs g;
+            g.M = cl * d; g.N = d * cr; g.K = cm;
+            g.A = mps->sites[i]; g.lda = cm;
+            g.B = mps->sites[i + 1]; g.ldb = (long long)d * cr;
+            g.C = theta; g.ldc = (long long)d * cr;
+            gemm_c64(c, g);
+        };
         for (int sw = 0; sw < opts->n_sweeps; ++sw) {
             const auto t0 = std::chrono::steady_clock::now();
             const int chi_s = sched[std::min<size_t>(sw, sched.size() - 1)];
             double disc_max = 0.0;
             for (int dir = 0; dir < 2; ++dir) {
-                for (int step = 0; step < M - 1; ++step) {
-                    const int i = dir == 0 ? step : (M - 2 - step);
+                for (int step = 0; step < hi - lo; ++step) {
+                    const int i = dir == 0 ? lo + step : (hi - 1 - step);
                     const int cl = mps->dims[i], cm = mps->dims[i + 1], cr = mps->dims[i + 2];
-                    // theta = A_i A_{i+1}
-                    GemmArgs g;
-                    g.M = cl * d; g.N = d * cr; g.K = cm;
-                    g.A = mps->sites[i]; g.lda = cm;
-                    g.B = mps->sites[i + 1]; g.ldb = (long long)d * cr;
-                    g.C = theta; g.ldc = (long long)d * cr;
-                    gemm_c64(c, g);
+                    form_theta(i);
                     const long long n = (long long)cl * d * d * cr;
                     const DevCore& Wi = mpo->dcores[i];
                     const DevCore& Wj = mpo->dcores[i + 1];
@@ -820,9 +913,33 @@ vtn_status vtn_sweep(vtn_ctx ctx, vtn_mpo mpo, vtn_mps* state, const vtn_sweep_o
                         env_right(Wj, tr.k, cr, env.R[i + 2], mps->sites[i + 1], env.R[i + 1]);
                 }
             }
-            mps->center = 0;
-            const double E = energy_dev(c, mpo, mps);
-            c.sync();
+            mps->center = lo;
+            double E;
+            if (centre_energy) {
+                // Rayleigh quotient of the final centre theta = A_lo A_lo+1 under H_eff of bond (lo, lo+1)
+                const int cl = mps->dims[lo], cr = mps->dims[lo + 2];
+                const long long n = (long long)cl * d * d * cr;
+                form_theta(lo);
+                double2* y = (double2*)c.workspace(WS_RQ_Y, sizeof(double2) * (size_t)n);
+                double* sc = (double*)c.workspace(WS_RQ_S, sizeof(double) * 64);
+                const DevCore& Wi = mpo->dcores[lo];
+                const DevCore& Wj = mpo->dcores[lo + 1];
+                if (split) {
+                    HeffPacked pk;
+                    heff_pack_envs(c, Wi, Wj, cl, cr, env.L[lo], env.R[lo + 2], pk);
+                    heff_apply_bf16x3(c, Wi, Wj, pk, theta, y);
+                } else {
+                    heff_apply_dev(c, Wi, Wj, cl, cr, env.L[lo], env.R[lo + 2], theta, y);
+                }
+                multi_dot(c, theta, n, 1, y, n, (double2*)sc);
+                norm2_dev(c, theta, n, sc + 2);
+                VTN_CUDA_TRY(cudaMemcpyAsync(c.pinned, sc, sizeof(double) * 3, cudaMemcpyDeviceToHost, c.stream));
+                c.sync();
+                E = c.pinned[0] / c.pinned[2];
+            } else {
+                E = energy_dev(c, mpo, mps);
+                c.sync();
+            }
             const auto t1 = std::chrono::steady_clock::now();
             rep.energy[sw] = E;
             rep.max_discarded[sw] = disc_max;
@@ -868,6 +985,7 @@ vtn_status vtn_sweep_single_site(vtn_ctx ctx, vtn_mpo mpo, vtn_mps* state, const
         VTN_REQUIRE(std::isfinite(alpha_decay) && alpha_decay >= 0.0, "alpha_decay must be finite and >= 0");
         VTN_REQUIRE(std::isfinite(cutoff) && cutoff >= 0.0 && cutoff < 1.0, "cutoff must be in [0, 1)");
         if (opts->prec != VTN_FP64) throw Error{VTN_EUNSUPPORTED, "the single-site solver runs in FP64 only"};
+        if (opts->window_hi > opts->window_lo) throw Error{VTN_EUNSUPPORTED, "windowed sweeps are two-site only"};
         Ctx& c = ctx->c;
         use_device(c);
         ensure_mpo_device(ctx, mpo);

@@ -24,6 +24,7 @@ struct GemmP {
     double2* C; long long ldc, sC_batch;
     int accumulate;
     int herm_lower;
+    int negate;
     int splits;          // S: CTAs per output tile along the summation range
     double2* part;       // S > 1: partial tiles [S][batch][M][N]
 };
@@ -105,6 +106,12 @@ __global__ void __launch_bounds__(NT) gemm_c64_kernel(GemmP p) {
         k0 += BK;
         if (k0 >= p.K) { k0 = 0; ++kb; }
     }
+    if (p.negate) {
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) acc[i][j] = make_double2(-acc[i][j].x, -acc[i][j].y);
+    }
     const bool to_part = p.splits > 1;
     double2* C = to_part ? p.part + ((long long)split * (gridDim.z / p.splits) + bz) * p.M * p.N : p.C + bz * p.sC_batch;
     const long long ldc = to_part ? p.N : p.ldc;
@@ -180,6 +187,7 @@ void gemm_c64(Ctx& ctx, const GemmArgs& g, int timing_class) {
     p.C = g.C; p.ldc = g.ldc; p.sC_batch = g.sC_batch;
     p.accumulate = g.accumulate ? 1 : 0;
     p.herm_lower = g.herm_lower ? 1 : 0;
+    p.negate = g.negate ? 1 : 0;
     VTN_REQUIRE(!g.herm_lower || (g.M == g.N && !g.accumulate), "Hermitian GEMM needs a square, non-accumulating C");
     const int gx = (g.N + BN - 1) / BN, gy = (g.M + BM - 1) / BM;
     VTN_REQUIRE(gy <= 65535, "gemm M too large");

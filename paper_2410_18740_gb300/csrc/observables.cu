@@ -55,51 +55,79 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// Deterministic filler in [-1, 1) for (row, column, part): splitmix64 of the three indices.
+__device__ __forceinline__ double fill_value(unsigned long long r, unsigned long long c, unsigned long long part) {
+    unsigned long long z = r * 0x9E3779B97F4A7C15ull + c * 0xD1B54A32D192ED03ull + part * 0x94D049BB133111EBull + 1ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+// sum over the CTA of |x[c]|^2 (all threads get it); sh: 32 doubles
+__device__ double block_norm2(const double2* x, int cols, double* sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double s = 0.0;
+    for (int c = threadIdx.x; c < cols; c += blockDim.x) s += x[c].x * x[c].x + x[c].y * x[c].y;
+    s = warp_sum(s);
+    __syncthreads();
+    if (lane == 0) sh[wid] = s;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += sh[w];
+    __syncthreads();
+    return t;
+}
+
 // Classical Gram-Schmidt applied twice, row by row, in one CTA (rows <= 1024).
-// coef[q] for q < r computed by warps (warp w takes q = w, w + nwarps, ...).
-__global__ void __launch_bounds__(1024) orth_rows_kernel(double2* A, int rows, int cols) {
+// coef[q] for q < r computed by warps (warp w takes q = w, w + nwarps, ...).  A row whose
+// residual after the two projections is below 1e-10 of its norm (numerically dependent on the
+// rows before it, or zero) is replaced by deterministic filler values, projected twice again
+// and normalised: the rows always end orthonormal (an orthonormal completion, as Householder QR
+// gives), so a truncation built on them keeps isometric site tensors.
+__global__ void __launch_bounds__(1024) orth_rows_kernel(double2* A, int rows, int cols, const int* pred) {
+    if (pred != nullptr && *pred == 0) return;
     extern __shared__ double2 coef[];  // rows entries
     __shared__ double nrm_sh[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int r = 0; r < rows; ++r) {
         double2* ar = A + (long long)r * cols;
-        for (int pass = 0; pass < 2; ++pass) {
-            for (int q = wid; q < r; q += nw) {
-                const double2* aq = A + (long long)q * cols;
-                double re = 0.0, im = 0.0;
-                for (int c = lane; c < cols; c += 32) {
-                    const double2 a = aq[c], b = ar[c];
-                    re += a.x * b.x + a.y * b.y;
-                    im += a.x * b.y - a.y * b.x;
+        const double t0 = block_norm2(ar, cols, nrm_sh);
+        double t = 0.0;
+        for (int attempt = 0; attempt < 2; ++attempt) {
+            for (int pass = 0; pass < 2; ++pass) {
+                for (int q = wid; q < r; q += nw) {
+                    const double2* aq = A + (long long)q * cols;
+                    double re = 0.0, im = 0.0;
+                    for (int c = lane; c < cols; c += 32) {
+                        const double2 a = aq[c], b = ar[c];
+                        re += a.x * b.x + a.y * b.y;
+                        im += a.x * b.y - a.y * b.x;
+                    }
+                    re = warp_sum(re);
+                    im = warp_sum(im);
+                    if (lane == 0) coef[q] = make_double2(re, im);
                 }
-                re = warp_sum(re);
-                im = warp_sum(im);
-                if (lane == 0) coef[q] = make_double2(re, im);
-            }
-            __syncthreads();
-            for (int c = threadIdx.x; c < cols; c += blockDim.x) {
-                double2 acc = ar[c];
-                for (int q = 0; q < r; ++q) {
-                    const double2 a = A[(long long)q * cols + c], k = coef[q];
-                    acc.x -= a.x * k.x - a.y * k.y;
-                    acc.y -= a.x * k.y + a.y * k.x;
+                __syncthreads();
+                for (int c = threadIdx.x; c < cols; c += blockDim.x) {
+                    double2 acc = ar[c];
+                    for (int q = 0; q < r; ++q) {
+                        const double2 a = A[(long long)q * cols + c], k = coef[q];
+                        acc.x -= a.x * k.x - a.y * k.y;
+                        acc.y -= a.x * k.y + a.y * k.x;
+                    }
+                    ar[c] = acc;
                 }
-                ar[c] = acc;
+                __syncthreads();
             }
+            t = block_norm2(ar, cols, nrm_sh);
+            if (attempt == 1 || (t > 1e-20 * t0 && t > 0.0)) break;
+            // numerically dependent: start this row again from filler values
+            for (int c = threadIdx.x; c < cols; c += blockDim.x)
+                ar[c] = make_double2(fill_value(r, c, 0), fill_value(r, c, 1));
             __syncthreads();
         }
-        double s = 0.0;
-        for (int c = threadIdx.x; c < cols; c += blockDim.x) s += ar[c].x * ar[c].x + ar[c].y * ar[c].y;
-        s = warp_sum(s);
-        if (lane == 0) nrm_sh[wid] = s;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int w = 0; w < nw; ++w) t += nrm_sh[w];
-            nrm_sh[0] = t > 0.0 ? 1.0 / sqrt(t) : 0.0;  // an exactly dependent row stays zero
-        }
-        __syncthreads();
-        const double inv = nrm_sh[0];
+        const double inv = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
         for (int c = threadIdx.x; c < cols; c += blockDim.x) {
             ar[c].x *= inv;
             ar[c].y *= inv;
@@ -244,13 +272,21 @@ void fill_random_normal(Ctx& ctx, double2* out, long long count, uint64_t seed, 
     ctx.check_launch("random_normal_kernel");
 }
 
-void orthonormalize_rows(Ctx& ctx, double2* A, int rows, int cols) {
+void orthonormalize_rows_small(Ctx& ctx, double2* A, int rows, int cols, const int* pred) {
     VTN_REQUIRE(rows <= 4096 && rows <= cols, "row orthonormalisation needs rows <= min(cols, 4096)");
     const size_t shm = sizeof(double2) * (size_t)std::max(rows, 1);
     set_smem_attr_once(ctx, (const void*)orth_rows_kernel, 64 * 1024);
-    orth_rows_kernel<<<1, 1024, shm, ctx.stream>>>(A, rows, cols);
+    orth_rows_kernel<<<1, 1024, shm, ctx.stream>>>(A, rows, cols, pred);
     ctx.count_launch();
     ctx.check_launch("orth_rows_kernel");
+}
+
+// Gram-Schmidt of the rows in order.  Small problems run the single-CTA kernel; from 128 rows
+// and 2^25 complex multiply-adds on, CholeskyQR2 on the GEMM (same result, all SMs).
+void orthonormalize_rows(Ctx& ctx, double2* A, int rows, int cols) {
+    VTN_REQUIRE(rows <= 4096 && rows <= cols, "row orthonormalisation needs rows <= min(cols, 4096)");
+    if (rows >= 128 && (double)rows * rows * cols >= 33554432.0) orthonormalize_rows_cholqr(ctx, A, rows, cols);
+    else orthonormalize_rows_small(ctx, A, rows, cols, nullptr);
 }
 
 void lbo_rotate_dev(Ctx& ctx, int chi_l, int d, int D, int chi_r, const double2* V, const double2* A, double2* out) {
@@ -286,8 +322,14 @@ void sample_dev(Ctx& ctx, const double2* const* AF_dev, const double2* const* ER
     a.chi_max = chi_max;
     a.out = out_dev;
     const size_t shm = sizeof(double2) * (size_t)chi_max * (1 + D) + sizeof(double) * D;
-    VTN_REQUIRE(shm <= 200 * 1024, "sampler working set exceeds shared memory (chi_max * (D + 1) too large)");
-    set_smem_attr_once(ctx, (const void*)sample_kernel, 200 * 1024);
+    // the opt-in limit per block less the kernel's static shared memory
+    int optin = 0;
+    VTN_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx.device));
+    cudaFuncAttributes fa;
+    VTN_CUDA_TRY(cudaFuncGetAttributes(&fa, (const void*)sample_kernel));
+    const size_t limit = (size_t)optin - fa.sharedSizeBytes;
+    VTN_REQUIRE(shm <= limit, "sampler working set exceeds shared memory (chi_max * (D + 1) too large)");
+    set_smem_attr_once(ctx, (const void*)sample_kernel, (int)limit);
     sample_kernel<<<n_samples, 256, shm, ctx.stream>>>(a);
     ctx.count_launch();
     ctx.check_launch("sample_kernel");

@@ -32,6 +32,8 @@ namespace vtn {
 namespace {
 
 constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+// longest run of k-blocks summed in one FP32 tensor-memory accumulator (K = 64 * this)
+constexpr int MAX_KB_PER_ACC = 512;
 constexpr int A_TILE = BM * BK * 2;   // 16 KiB
 constexpr int B_TILE = BN * BK * 2;   // 32 KiB
 constexpr int STAGE_BYTES = A_TILE + B_TILE;
@@ -297,16 +299,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     }
 }
 
-// out[m][n] = sum_z part[z][m][n] in a fixed order (deterministic split-K reduction)
+// out[m][n] = sum_z part[z][m][n] in a fixed order (deterministic split-K reduction), summed in FP64
 __global__ void splitk_reduce(const float* __restrict__ part, int splits, int M, int N, void* out, long long ldo,
                               int fp64) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)M * N) return;
     const long long m = t / N, n = t % N;
-    float acc = 0.f;
-    for (int z = 0; z < splits; ++z) acc += part[(long long)z * M * N + t];
-    if (fp64) ((double*)out)[m * ldo + n] = (double)acc;
-    else ((float*)out)[m * ldo + n] = acc;
+    double acc = 0.0;
+    for (int z = 0; z < splits; ++z) acc += (double)part[(long long)z * M * N + t];
+    if (fp64) ((double*)out)[m * ldo + n] = acc;
+    else ((float*)out)[m * ldo + n] = (float)acc;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -363,13 +365,16 @@ void tc_gemm_bf16(Ctx& ctx, const TcGemmArgs& a, int timing_class, double useful
     p.status = ctx.dstatus;
     dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, 1);
     VTN_REQUIRE((long long)grid.x * grid.y * 8 < (1LL << 31), "tensor-core GEMM too large");
-    // split K when the output tiles leave most SMs idle (fixed-order reduction afterwards)
+    // split K when the output tiles leave most SMs idle (fixed-order reduction afterwards), and
+    // whenever one accumulator would sum more than MAX_KB_PER_ACC k-blocks: the FP32 accumulation
+    // in tensor memory then covers a bounded part of the sum and the partials are added in FP64
     const int nkb = a.K / BK;
     const long long tiles = (long long)grid.x * grid.y;
     int splits = 1;
     if (tiles * 2 <= ctx.num_sms && nkb >= 8)
         splits = (int)std::min<long long>(std::max<long long>(1, ctx.num_sms / tiles), nkb / 4);
     splits = std::max(1, std::min(splits, 8));
+    splits = std::max(splits, (nkb + MAX_KB_PER_ACC - 1) / MAX_KB_PER_ACC);
     int per = (nkb + splits - 1) / splits;
     splits = (nkb + per - 1) / per;
     p.kb_per = per;

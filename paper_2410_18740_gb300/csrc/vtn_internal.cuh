@@ -125,7 +125,7 @@ enum WsSlot {
     WS_EIG_Y, WS_EIG_WORK, WS_EIG_U, WS_CORE_A, WS_CORE_B, WS_ENV_TMP, WS_MISC, WS_TC_L, WS_TC_R, WS_TC_B1,
     WS_TC_A2, WS_TC_PART, WS_GEMM_SPLIT, WS_EIG_PART, WS_TC_ENV, WS_EIG_T, WS_H2_ENV, WS_EXPAND,
     WS_TRUNC_L, WS_TRUNC_R, WS_CENTER, WS_MLP_ACT, WS_MLP_Y, WS_MLP_G, WS_WARM_S, WS_WARM_Z, WS_WARM_P,
-    WS_WARM_U, WS_WARM_N, WS_WARM_Q0, WS_COUNT
+    WS_WARM_U, WS_WARM_N, WS_WARM_Q0, WS_CQR_G, WS_CQR_T, WS_CQR_B, WS_RQ_Y, WS_RQ_S, WS_COUNT
 };
 
 // ------------------------------------------------------------------ cores
@@ -148,6 +148,7 @@ struct GemmArgs {
     bool herm_lower = false;  // result is Hermitian: compute tiles on/below the diagonal only
     int max_splits = 0;       // > 0: at most this many CTAs per output tile along the summation
                               // (1 = never split, so no split-K workspace is touched); 0 = automatic
+    bool negate = false;      // C (=|+=) -op(A) op(B)
 };
 // C[i][j] = conj(C[j][i]) for j > i (n x n, leading dimension ldc)
 void mirror_lower_to_upper(Ctx& ctx, double2* C, int n, long long ldc);
@@ -286,6 +287,11 @@ constexpr unsigned PHILOX_STREAM_INIT = 1u, PHILOX_STREAM_TRUNC = 3u;
 void fill_random_normal(Ctx& ctx, double2* out, long long count, uint64_t seed, int site,
                         unsigned stream = PHILOX_STREAM_INIT);
 void orthonormalize_rows(Ctx& ctx, double2* A, int rows, int cols);
+// The same result by CholeskyQR2 (GEMM-based; chol_qr.cu), with the row-by-row kernel as the
+// fallback when the rows are too ill-conditioned (or dependent) for it.
+void orthonormalize_rows_cholqr(Ctx& ctx, double2* A, int rows, int cols);
+// single-CTA Gram-Schmidt of the rows, skipped unless pred == nullptr or *pred != 0
+void orthonormalize_rows_small(Ctx& ctx, double2* A, int rows, int cols, const int* pred);
 void lbo_rotate_dev(Ctx& ctx, int chi_l, int d, int D, int chi_r, const double2* V, const double2* A,
                     double2* out);
 void set_scalar_one(Ctx& ctx, double2* p);

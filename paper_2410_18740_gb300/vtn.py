@@ -42,7 +42,8 @@ class vtn_sweep_opts(C.Structure):
                 ("n_sweeps", C.c_int), ("prec", C.c_int), ("lanczos_tol", C.c_double),
                 ("krylov_max", C.c_int), ("lanczos_max_restarts", C.c_int), ("e_tol", C.c_double),
                 ("e_target", C.c_double), ("use_e_target", C.c_int), ("seed", C.c_uint64),
-                ("trunc_mode", C.c_int), ("trunc_q", C.c_int)]
+                ("trunc_mode", C.c_int), ("trunc_q", C.c_int), ("window_lo", C.c_int), ("window_hi", C.c_int),
+                ("energy_mode", C.c_int)]
 
 
 class vtn_sweep_report(C.Structure):
@@ -81,6 +82,10 @@ _SIGS = {
     "vtn_mpo_norm_bound": [_P, _PD],
     "vtn_mps_random": [_P, _P, _I, C.c_uint64, C.POINTER(_P)],
     "vtn_mps_from_host": [_P, _P, _PI, C.POINTER(_PD), C.POINTER(_P)],
+    "vtn_mps_random_center": [_P, _P, _I, C.c_uint64, _I, C.POINTER(_P)],
+    "vtn_mps_get_center": [_P, _PI],
+    "vtn_mps_set_center": [_P, _I],
+    "vtn_mps_move_center": [_P, _P, _I],
     "vtn_mps_free": [_P],
     "vtn_mps_info": [_P, _PI, _PI, _PI],
     "vtn_mps_get_site": [_P, _P, _I, _PD],
@@ -312,6 +317,26 @@ def vtn_mps_random(ctx, mpo, chi, seed):
     out = C.c_void_p()
     _check(ctx, lib().vtn_mps_random(ctx, mpo, int(chi), C.c_uint64(int(seed)), C.byref(out)))
     return out
+
+
+def vtn_mps_random_center(ctx, mpo, chi, seed, center):
+    out = C.c_void_p()
+    _check(ctx, lib().vtn_mps_random_center(ctx, mpo, int(chi), C.c_uint64(int(seed)), int(center), C.byref(out)))
+    return out
+
+
+def vtn_mps_get_center(mps):
+    c = C.c_int()
+    _check(None, lib().vtn_mps_get_center(mps, C.byref(c)))
+    return c.value
+
+
+def vtn_mps_set_center(mps, center):
+    _check(None, lib().vtn_mps_set_center(mps, int(center)))
+
+
+def vtn_mps_move_center(ctx, mps, center):
+    _check(ctx, lib().vtn_mps_move_center(ctx, mps, int(center)))
 
 
 def vtn_mps_from_host(ctx, mpo, sites):

@@ -42,6 +42,23 @@ def test_initial_mps_matches_oracle(ctx):
     vtn.vtn_mpo_free(m)
 
 
+def test_initial_mps_large_bonds_matches_oracle(ctx):
+    """Bond dimension 512 at d = 6 (the large workload's shape): the site matrices of 216 x 3072
+    and 512 x 1296 are orthonormalised by CholeskyQR2 on the GEMM; the rows must be the
+    Gram-Schmidt rows of the oracle (numpy Householder QR with a positive diagonal)."""
+    w = inputs.workload("plain", 0, M=8, d=6, D=6)
+    m = vtn.vtn_build_mpo(ctx, w.r, w.U, 6, 6)
+    mps = vtn.vtn_mps_random(ctx, m, 512, seed=23)
+    osites = odmrg.initial_mps(8, 6, 512, seed=23)
+    for a, b in zip(gpu_sites(ctx, mps), osites):
+        assert a.shape == b.shape
+        assert np.abs(a - b).max() < 1e-13
+        rows = a.reshape(a.shape[0], -1)
+        assert np.abs(rows @ rows.conj().T - np.eye(rows.shape[0])).max() < 1e-13
+    vtn.vtn_mps_free(mps)
+    vtn.vtn_mpo_free(m)
+
+
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_plain_workload_energy_and_marginals(ctx, seed):
     """Plain workload (M=4, d=4, chi=16): the MPS is exact, so the GPU energy must equal

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 import torch
 
-from oracle import dmrg as odmrg, gbs
+from oracle import dense, dmrg as odmrg, gbs
 from paper_2410_18740_gb300 import inputs, vtn
 
 pytestmark = pytest.mark.gpu
@@ -98,4 +98,30 @@ def test_bf16x3_sweep_energy_matches_fp64(ctx):
     assert abs(e16[-1] - e64[-1]) <= 1e-6 * max(1.0, abs(e64[-1]))
     assert abs(e16[-1] - e64[-1]) <= 1e-8 * Hn
     assert np.abs(m16 - m64).max() < 1e-4
+    vtn.vtn_mpo_free(m)
+
+
+@pytest.mark.parametrize("M,d,chi,seed", [(6, 3, 27, 11), (8, 3, 81, 12)])
+def test_bf16x3_converges_to_the_fp64_energy(ctx, M, d, chi, seed):
+    """Converged sweeps at a bond dimension that truncates nothing (chi = d^(M/2)): the FP64 and
+    the split-precision solver both reach the ground energy of P H P, and agree with each other
+    within 1e-8 relative -- the bar set for mixed against FP64.  The energy of each sweep is the
+    full FP64 contraction; the split-precision state is only first-order wrong (~1e-5), so its
+    energy is second-order close.  Also checked against the dense ground energy (oracle)."""
+    w = inputs.workload("split", seed, M=M, d=d, D=d)
+    G = gbs.hamiltonian_coefficients(w.r, w.U)
+    Hn = gbs.norm_bound(G, M, d)
+    e0 = dense.ground_state(G, d)[0][0]
+    m = vtn.vtn_build_mpo(ctx, w.r, w.U, d, d)
+    res = {}
+    for prec in (vtn.VTN_FP64, vtn.VTN_BF16X3):
+        opts = vtn.vtn_sweep_opts_default(chi_max=chi, n_sweeps=10, seed=seed, lanczos_tol=1e-12, krylov_max=32,
+                                          lanczos_max_restarts=4, prec=prec, e_tol=1e-13 * Hn)
+        st, mps, rep = vtn.vtn_sweep(ctx, m, None, opts)
+        res[prec] = rep["energy"][-1]
+        vtn.vtn_mps_free(mps)
+    e64, e16 = res[vtn.VTN_FP64], res[vtn.VTN_BF16X3]
+    assert abs(e64 - e0) <= 1e-10 * Hn
+    assert abs(e16 - e64) <= 1e-8 * abs(e64)
+    assert abs(e16 - e0) <= 1e-8 * abs(e0)
     vtn.vtn_mpo_free(m)

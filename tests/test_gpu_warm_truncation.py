@@ -50,9 +50,67 @@ def test_truncate_warm_matches_oracle(ctx, direction, q):
     assert np.abs(iso.conj().T @ iso - np.eye(k)).max() <= 1e-10
 
 
+@pytest.mark.parametrize("direction", [0, 1])
+def test_truncate_warm_large_subspace_matches_oracle(ctx, direction):
+    """m = 258 start vectors of length 768: the subspace is orthonormalised by CholeskyQR2 on
+    the GEMM instead of the row-by-row kernel; same result as the oracle's Householder QR."""
+    rng = inputs.rng_for(8200 + direction)
+    cl, d1, d2, cr, kmax = 128, 6, 6, 128, 250
+    th = _theta(rng, cl, d1, d2, cr, 0.985)
+    n = cl * d1 if direction == 0 else d2 * cr
+    Q0 = inputs.random_complex((n, 200), rng)
+    k = kmax
+    left = torch.empty((cl, d1, k), dtype=torch.complex128, device="cuda")
+    right = torch.empty((k, d2, cr), dtype=torch.complex128, device="cuda")
+    kk, lam, disc = vtn.vtn_truncate_warm(ctx, cl, d1, d2, cr, direction, kmax, dev(th), dev(Q0), 1, 8, 91, 5,
+                                          left, right)
+    ol, orr, ow, odisc = odmrg.truncate_warm(th, "right" if direction == 0 else "left", kmax, Q0, q=1, p=8,
+                                             seed=91, bond=5)
+    assert kk == k
+    assert np.abs(lam - ow).max() <= 1e-10 * ow[0]
+    assert abs(disc - odisc) <= 1e-10
+    torch.cuda.synchronize()
+    L, R = left.cpu().numpy(), right.cpu().numpy()
+    rec = np.einsum("asb,btc->astc", L, R)
+    orec = np.einsum("asb,btc->astc", ol, orr)
+    assert np.abs(rec - orec).max() <= 1e-9 * np.abs(orec).max()
+    iso = L.reshape(-1, k) if direction == 0 else R.reshape(k, -1).conj().T
+    assert np.abs(iso.conj().T @ iso - np.eye(k)).max() <= 1e-10
+
+
+def test_truncate_warm_rank_deficient_large_subspace(ctx):
+    """rho of rank 100 with m = 258 start vectors: the rows are dependent, CholeskyQR2 cannot
+    orthonormalise them, and the row-by-row Gram-Schmidt takes over, completing the dependent
+    rows to an orthonormal set.  The split is still exact and left stays an isometry: the Ritz
+    values are rho's nonzero eigenvalues (then zeros) and left * right reproduces theta."""
+    rng = inputs.rng_for(8300)
+    cl, d1, d2, cr, kmax, rank = 128, 6, 6, 128, 250, 100
+    X = inputs.random_complex((cl * d1, rank), rng)
+    Y = inputs.random_complex((rank, d2 * cr), rng)
+    th = (X @ Y).reshape(cl, d1, d2, cr)
+    th /= np.linalg.norm(th)
+    left = torch.empty((cl, d1, kmax), dtype=torch.complex128, device="cuda")
+    right = torch.empty((kmax, d2, cr), dtype=torch.complex128, device="cuda")
+    kk, lam, disc = vtn.vtn_truncate_warm(ctx, cl, d1, d2, cr, 0, kmax, dev(th), None, 1, 8, 92, 6, left, right)
+    torch.cuda.synchronize()
+    L, R = left.cpu().numpy(), right.cpu().numpy()
+    assert np.isfinite(L).all() and np.isfinite(R).all()
+    ev = np.linalg.svd(th.reshape(cl * d1, d2 * cr), compute_uv=False) ** 2
+    assert np.abs(lam[:rank] - ev[:rank]).max() <= 1e-10 * ev[0]
+    assert np.abs(lam[rank:]).max() <= 1e-10 * ev[0]
+    assert abs(disc) <= 1e-10
+    rec = np.einsum("asb,btc->astc", L, R)
+    assert np.abs(rec - th).max() <= 1e-10 * np.abs(th).max()
+    iso = L.reshape(-1, kmax)
+    assert np.abs(iso.conj().T @ iso - np.eye(kmax)).max() <= 1e-10
+
+
 @pytest.mark.parametrize("seed,M,d,sched", [(0, 6, 3, [3, 6, 9])])
 def test_sweep_with_warm_truncation_matches_oracle(ctx, seed, M, d, sched):
-    """Same trajectory as the oracle's sweep with warm truncation.  Where start vectors are
+    """Same trajectory as the oracle's sweep with warm truncation.  The schedule grows chi between
+    sweeps (3 -> 6 -> 9), so from the second sweep on the warm block (the current bond, k0 = 3 or
+    6) is smaller than the kept subspace k and the Philox fill supplies the rest of the start
+    vectors, in both directions of the sweep.  Where start vectors are
     nearly dependent the two orthonormalisations (Gram-Schmidt on the GPU, Householder QR in
     numpy) round differently and the kept subspaces can differ at the 1e-6 level (seen at
     M = 7, d = 4), so this sweep-by-sweep comparison holds on instances without that."""

@@ -74,6 +74,34 @@ def test_optimal_local_basis_against_oracle(libvtn, seed):
         vtn.vtn_mpo_free(m)
 
 
+def test_large_workload_mpo_against_oracle(libvtn):
+    """The large workload at full size (M = 100, r ~ U(0.8, 1.2), Haar U, D = 24 -> d = 6 in the
+    optimal local basis): coefficients G' = S^T G S, every mode's isometry (up to its global
+    phase), the centre-collapsed bond dimensions 2 min(s, M - s) + 2 and the norm bound, against
+    the oracle."""
+    w = inputs.workload("large", 200)
+    assert (w.M, w.D, w.d) == (100, 24, 6)
+    m = vtn.vtn_build_mpo(None, w.r, w.U, w.D, w.d)
+    try:
+        S_list, nu, Grot = gbs.lbo_transform(w.r, w.U)
+        assert np.abs(vtn.vtn_mpo_coefficients(m) - Grot).max() < 1e-11 * np.abs(Grot).max()
+        for i in range(w.M):
+            V = vtn.vtn_mpo_isometry(m, i)
+            Vo = gbs.lbo_isometry(S_list[i], w.D, w.d)
+            ph = np.vdot(V.reshape(-1), Vo.reshape(-1))
+            ph /= abs(ph)
+            assert np.abs(V * ph - Vo).max() < 1e-12
+        M, d, D, wd = vtn.vtn_mpo_info(m)
+        assert (M, d, D) == (100, 6, 24)
+        expect = [1] + [2 * min(s, 100 - s) + 2 for s in range(1, 100)] + [1]
+        assert list(wd) == expect
+        G = gbs.hamiltonian_coefficients(w.r, w.U)
+        assert abs(vtn.vtn_mpo_norm_bound(m) - gbs.norm_bound(Grot, 100, 6)) <= 1e-12 * gbs.norm_bound(Grot, 100, 6)
+        assert np.abs(G - G.T).max() < 1e-12
+    finally:
+        vtn.vtn_mpo_free(m)
+
+
 def test_fock_isometry_is_identity(libvtn):
     w = inputs.workload("plain", 0)
     m = vtn.vtn_build_mpo(None, w.r, w.U, 4, 4)
