@@ -8,6 +8,9 @@
   inverse basis transformation on the listed modes only.  Normalised by <psi|psi>, so
   with a local basis the probabilities of n < D sum to at most one.  Computed by
   brute-force transfer contractions carrying the open photon numbers.
+* ``reduced_density``: the single-mode reduced density matrix rho_i (d x d, solver basis) of
+  the variational state -- the partial trace over every other mode -- normalised by
+  <psi|psi>; its diagonal in the Fock basis is the marginal P_i(n).
 * ``sample``: sequential conditional sampling in the Fock basis,
   p(n_i | n_<i) proportional to || l_{i-1} A^F_i[n_i] ||^2 weighted by the right
   environment, inverse-CDF pick with a Philox uniform per (sample, mode).  The paper
@@ -98,3 +101,15 @@ def sample(mps, isometries, seed, n_samples):
             out[t, s] = n
             l = cand[n] / np.sqrt(p[n])
     return out
+
+
+def reduced_density(mps, site):
+    """rho[s, s'] = <psi| (|s'><s| on ``site``) |psi> / <psi|psi>: the left transfer environment of
+    sites < site, the site tensor, the right transfer environment of sites > site."""
+    E = np.ones((1, 1), dtype=np.complex128)          # (bra, ket)
+    for A in mps[:site]:
+        E = np.einsum("isk,isl->kl", A.conj(), np.einsum("ij,jsl->isl", E, A, optimize=True), optimize=True)
+    Er = _right_envs(mps)[site + 1]                    # (ket, bra)
+    A = mps[site]
+    rho = np.einsum("ij,jsb,bc,itc->st", E, A, Er, A.conj(), optimize=True)
+    return rho / norm2_solver_basis(mps)

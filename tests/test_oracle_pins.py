@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 import scipy.stats
 
-from oracle import dense, dmrg, gbs, mpo, observables, philox
+from oracle import dense, dmrg, gbs, mpo, observables, philox, warm
 from paper_2410_18740_gb300 import inputs
 from tests.conftest import GOLDEN
 
@@ -454,6 +454,48 @@ def test_windowed_sweep(window):
         _, full = dmrg.dmrg(cores, d, 27, 2, seed=3, lanczos=lp, mps=start)
         for a, b in zip(rep.energies, full.energies):
             assert abs(a - b) <= 1e-10 * Hn
+
+
+def test_reduced_density_matches_marginals_and_product_states():
+    """rho_i is Hermitian, positive, of unit trace, its diagonal is the Fock marginal computed
+    by the marginal routine, and on a product state it is the projector on the local state."""
+    w = inputs.workload("plain", 1, M=4)
+    G = gbs.hamiltonian_coefficients(w.r, w.U)
+    cores = mpo.build_mpo(G, 4)
+    mps, _ = dmrg.dmrg(cores, 4, 16, 2, seed=3, lanczos=dmrg.LanczosParams(tol=1e-11))
+    for i in range(4):
+        rho = observables.reduced_density(mps, i)
+        assert np.abs(rho - rho.conj().T).max() < 1e-13
+        assert np.linalg.eigvalsh(rho).min() > -1e-13 and abs(np.trace(rho) - 1) < 1e-12
+        assert np.abs(np.diag(rho).real - observables.marginal(mps, None, [i])).max() < 1e-12
+    rng = inputs.rng_for(77)
+    phis = [inputs.random_complex(3, rng) for _ in range(5)]
+    prod = [(2.0 * phi).reshape(1, 3, 1) for phi in phis]
+    for i, phi in enumerate(phis):
+        u = phi / np.linalg.norm(phi)
+        assert np.abs(observables.reduced_density(prod, i) - np.outer(u, u.conj())).max() < 1e-13
+
+
+def test_warm_start_features_and_targets_closed_forms():
+    """U = I: mode i is a single-mode squeezed vacuum with V_i = diag(e^{-2r}, e^{2r}) / 2, so its
+    features are [-2r - log 2, 2r - log 2, 0, -log 2]; the ground state is a product, and each
+    mode's target is its local ground state, whose vacuum weight approaches the textbook
+    |<0|S(r)|0>|^2 = 1 / cosh r as the cutoff grows."""
+    w = inputs.workload("plain", 2, M=3, identity_U=True)
+    V = gbs.covariance(w.r, w.U)
+    f = warm.features(V)
+    for i, r in enumerate(w.r):
+        assert np.abs(f[i] - [-2 * r - np.log(2), 2 * r - np.log(2), 0.0, -np.log(2)]).max() < 1e-12
+    d = 14
+    G = gbs.hamiltonian_coefficients(w.r, w.U)
+    cores = mpo.build_mpo(G, d)
+    mps, _ = dmrg.dmrg(cores, d, 1, 2, seed=1, lanczos=dmrg.LanczosParams(tol=1e-12, krylov_max=40))
+    t = warm.targets(mps)
+    for i, r in enumerate(w.r):
+        u = t[i, 0::2] + 1j * t[i, 1::2]
+        assert abs(np.linalg.norm(u) - 1) < 1e-12 and u[0].real > 0 and abs(u[0].imag) < 1e-12
+        assert abs(abs(u[0]) ** 2 - 1 / np.cosh(r)) < 2e-3
+        assert np.abs(u[1::2]).max() < 1e-10          # squeezed vacuum: even photon numbers only
 
 
 # ------------------------------------------------------------------ sampler
