@@ -91,7 +91,7 @@ def parse():
     p.add_argument("--workload", default="large", choices=["large", "split"],
                    help="large: M=100, D=24 -> d=6, chi=512, windowed sweep per step (default); "
                         "split: M=24, d=8, chi=128, full sweep per step")
-    p.add_argument("--case", default=None, choices=["heff", "trunc", "tte", "dmrg1", "c3cmp"],
+    p.add_argument("--case", default=None, choices=["heff", "trunc", "tte", "dmrg1", "c3cmp", "batch"],
                    help="heff / trunc: only that kernel at the middle-bond shape (for profiler captures); "
                         "tte: time-to-eps of the mixed and the FP64 solver from the same random state; "
                         "dmrg1: --ref-sweeps sweeps of the single-site solver with subspace expansion")
@@ -101,6 +101,10 @@ def parse():
     p.add_argument("--warm-q", type=int, default=None,
                    help="also measure the optional warm-started truncation with this many subspace iterations "
                         "(trunc: beside the exact one; time-to-eps: a mixed run with it)")
+    p.add_argument("--batch-streams", type=int, nargs="+", default=[8],
+                   help="batch: worker streams of the batched run(s)")
+    p.add_argument("--batch-serial", type=int, default=16,
+                   help="batch: instances run one after another for the serial comparison")
     p.add_argument("--ref-sweeps", type=int, default=6,
                    help="time-to-eps: sweeps of the FP64 reference run (chi schedule 16, 32, 64, 128, then 128)")
     a = p.parse_args()
@@ -380,8 +384,10 @@ def run_native_large(args):
     M, d, D, wdims = vtn.vtn_mpo_info(mpo)
     mps = vtn.vtn_mps_random_center(ctx, mpo, LARGE_CHI, seed + 1, LARGE_LO)
     prec = vtn.VTN_BF16X3 if args.prec == "bf16x3" else vtn.VTN_FP64
+    trunc = {} if args.warm_q is None else {"trunc_mode": 1, "trunc_q": args.warm_q, "seed": seed}
     opts = vtn.vtn_sweep_opts_default(chi_max=LARGE_CHI, n_sweeps=1, lanczos_tol=1e-12, krylov_max=KRYLOV,
-                                      lanczos_max_restarts=0, prec=prec, window_lo=LARGE_LO, window_hi=LARGE_HI)
+                                      lanczos_max_restarts=0, prec=prec, window_lo=LARGE_LO, window_hi=LARGE_HI,
+                                      **trunc)
     energies, step_seconds = [], []
 
     def step(state):
@@ -519,6 +525,8 @@ def run_native_large(args):
                        "precision_path": ("H_eff psi and environment updates: bf16x3 split products on tcgen05, "
                                           "FP32 accumulate; Lanczos, truncation, energy: FP64") if prec != vtn.VTN_FP64
                        else "FP64 contractions (SIMT DFMA)",
+                       "truncation": ("exact FP64 eigendecomposition of rho (the paper's)" if args.warm_q is None else
+                                      f"warm-started subspace iteration, q = {args.warm_q} (not the paper's)"),
                        "l2": "working set > L2 (environments ~40 GB, H_eff intermediates ~20 GB)",
                        "parallelism": f"replicas x{ws}"},
             "roofline": roof,
@@ -551,13 +559,87 @@ def run_native_large(args):
         dist.destroy_process_group()
 
 
+def batch_workload(n=64, base_seed=300):
+    """The batched workload: n independent GBS instances, instance k with seed base_seed + k:
+    M ~ U{8..64}, r ~ U(0.3, 1.0), Haar U, d = D = 6 (Fock), chi ~ U{32..256}."""
+    from paper_2410_18740_gb300 import inputs
+
+    out = []
+    for k in range(n):
+        rng = inputs.rng_for(base_seed + k)
+        M = int(rng.integers(8, 65))
+        chi = int(rng.integers(32, 257))
+        out.append((inputs.workload("split", base_seed + k, M=M, d=6, D=6, r_lo=0.3, r_hi=1.0), chi))
+    return out
+
+
+def run_case_batch(args):
+    """Batched sweeps: one split-precision sweep (chi schedule: chi_k directly, Lanczos 8 steps)
+    of each of the 64 instances of the batched workload, concurrently on --batch-streams worker
+    streams (vtn_sweep_batch), against the same sweeps one after another on one stream for the
+    first --batch-serial instances.  Reports instances per second and H_eff psi TFLOP/s of both."""
+    import torch
+
+    from paper_2410_18740_gb300 import build as vbuild
+    from paper_2410_18740_gb300 import vtn
+
+    vbuild.build()
+    ctx = vtn.vtn_create(0)
+    wl = batch_workload()
+    mpos = [vtn.vtn_build_mpo(ctx, w.r, w.U, w.D, w.d) for w, _ in wl]
+    prec = vtn.VTN_BF16X3 if args.prec == "bf16x3" else vtn.VTN_FP64
+
+    def opts(k):
+        return vtn.vtn_sweep_opts_default(chi_max=wl[k][1], n_sweeps=1, seed=k, lanczos_tol=1e-12, krylov_max=KRYLOV,
+                                          lanczos_max_restarts=0, prec=prec)
+
+    out = {"case": "batch", "workload": "64 instances: M~U{8..64}, r~U(0.3,1.0), Haar U, d=D=6, chi~U{32..256}, "
+                                        "seeds 300..363; one sweep each from a seeded random MPS",
+           "prec": args.prec, "instances_M": [w.M for w, _ in wl], "instances_chi": [c for _, c in wl]}
+    n_ser = min(args.batch_serial, len(wl))
+    # warm-up: one small instance each way (kernel loading, workspaces)
+    st, s0, _ = vtn.vtn_sweep(ctx, mpos[0], None, opts(0))
+    vtn.vtn_mps_free(s0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ser_flops = 0.0
+    for k in range(n_ser):
+        st, mps, rep = vtn.vtn_sweep(ctx, mpos[k], None, opts(k))
+        ser_flops += rep["heff_flops"]
+        vtn.vtn_mps_free(mps)
+    torch.cuda.synchronize()
+    ser_s = time.perf_counter() - t0
+    out["serial"] = {"instances": n_ser, "seconds": ser_s, "instances_per_s": n_ser / ser_s,
+                     "heff_tflops": ser_flops / ser_s / 1e12}
+    for streams in args.batch_streams:
+        for n_inst in (n_ser, len(wl)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, sts, states, reps = vtn.vtn_sweep_batch(ctx, mpos[:n_inst], [None] * n_inst,
+                                                        [opts(k) for k in range(n_inst)], n_streams=streams)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            fl = sum(r["heff_flops"] for r in reps)
+            rec = {"instances": n_inst, "seconds": el, "instances_per_s": n_inst / el, "heff_tflops": fl / el / 1e12}
+            if n_inst == n_ser:
+                rec["speedup_vs_serial_same_instances"] = ser_s / el
+            out[f"batch_{streams}_streams_{n_inst}"] = rec
+            for m in states:
+                vtn.vtn_mps_free(m)
+            print(json.dumps(out), flush=True)
+    print(json.dumps(out), flush=True)
+    for m in mpos:
+        vtn.vtn_mpo_free(m)
+    vtn.vtn_destroy(ctx)
+
+
 def run_case_c3cmp(args):
     """Mixed vs FP64 on the large workload from the same state: the window of the default step
     (bonds (49,50), (50,51) and back) run --ref-sweeps times in split precision and in FP64 from
     the same seeded random chi = 512 state centred at site 49.  Reports both solvers' time, the
     FP64 centre Rayleigh quotients of the FP64 run (exact FP64 energies of its states) and the FP64
     energy of the mixed run's final state by the full FP64 contraction (vtn_energy), and
-    their relative difference against the spec bar of 1e-8."""
+    their relative difference against the bar of 1e-8 set for mixed against FP64."""
     import torch
 
     from paper_2410_18740_gb300 import build as vbuild
@@ -570,11 +652,15 @@ def run_case_c3cmp(args):
     n_sw = max(1, min(args.ref_sweeps, 4))
     out = {"case": "c3cmp", "workload": f"large: M=100, D=24 -> d=6, chi=512, seed {args.seed}, window "
                                         f"[{LARGE_LO}, {LARGE_HI}), {n_sw} windowed sweep(s), Lanczos {KRYLOV} steps"}
-    for name, prec in (("mixed", vtn.VTN_BF16X3), ("fp64", vtn.VTN_FP64)):
+    runs = [("mixed", vtn.VTN_BF16X3, {}), ("fp64", vtn.VTN_FP64, {})]
+    if args.warm_q is not None:
+        runs.insert(1, ("mixed_warm_truncation", vtn.VTN_BF16X3,
+                        {"trunc_mode": 1, "trunc_q": args.warm_q, "seed": args.seed}))
+    for name, prec, extra in runs:
         mps = vtn.vtn_mps_random_center(ctx, mpo, LARGE_CHI, args.seed + 1, LARGE_LO)
         opts = vtn.vtn_sweep_opts_default(chi_max=LARGE_CHI, n_sweeps=n_sw, lanczos_tol=1e-12, krylov_max=KRYLOV,
                                           lanczos_max_restarts=0, prec=prec, window_lo=LARGE_LO,
-                                          window_hi=LARGE_HI)
+                                          window_hi=LARGE_HI, **extra)
         vtn.vtn_timing_reset(ctx)
         vtn.vtn_timing(ctx, True)
         torch.cuda.synchronize()
@@ -587,7 +673,7 @@ def run_case_c3cmp(args):
         rec = {"wall_s": wall, "sweep_s": rep["seconds"], "energy_centre_rq": rep["energy"],
                "heff_flops": rep["heff_flops"], "heff_gemm_tflops": flh / sh / 1e12 if sh else None,
                "heff_tflops_over_run": rep["heff_flops"] / wall / 1e12, "matvecs": rep["matvecs"]}
-        if name == "mixed":
+        if name != "fp64":
             t0 = time.perf_counter()
             rec["energy_fp64_full"] = vtn.vtn_energy(ctx, mpo, mps)
             rec["energy_fp64_full_s"] = time.perf_counter() - t0
@@ -599,6 +685,10 @@ def run_case_c3cmp(args):
     out["rel_diff_mixed_vs_fp64"] = (em - e64) / abs(e64)
     out["meets_1e-8"] = abs(em - e64) <= 1e-8 * abs(e64)
     out["speedup_mixed_vs_fp64"] = out["fp64"]["wall_s"] / out["mixed"]["wall_s"]
+    if "mixed_warm_truncation" in out:
+        ew = out["mixed_warm_truncation"]["energy_fp64_full"]
+        out["rel_diff_mixed_warm_vs_fp64"] = (ew - e64) / abs(e64)
+        out["speedup_mixed_warm_vs_fp64"] = out["fp64"]["wall_s"] / out["mixed_warm_truncation"]["wall_s"]
     print(json.dumps(out), flush=True)
     vtn.vtn_mpo_free(mpo)
     vtn.vtn_destroy(ctx)
@@ -803,8 +893,10 @@ def run_native(args):
 
 
 def run_case_heff(args):
-    """H_eff psi alone at the middle-bond shape of the split workload (random inputs,
-    w = 24 | 26 | 24, chi = 128, d = 8), 2 warm-up + 3 timed calls."""
+    """H_eff psi alone at a middle-bond shape, 2 warm-up + 3 timed calls: --workload split: random
+    inputs, w = 24 | 26 | 24, chi = 128, d = 8; --workload large: the library's own MPO cores of the
+    large workload at bond (49, 50) (w = 100 | 102 | 100, the second core the near-dense collapse
+    core), chi = 512, d = 6."""
     import torch
 
     from paper_2410_18740_gb300 import build as vbuild
@@ -812,9 +904,21 @@ def run_case_heff(args):
 
     vbuild.build()
     rng = inputs.rng_for(7)
-    chi, d, wl, wm, wr = CHI, 8, 24, 26, 24
-    Wi = vtn.core_from_sparse(inputs.random_sparse_core(wl, wm, d, rng, density=0.15))
-    Wj = vtn.core_from_sparse(inputs.random_sparse_core(wm, wr, d, rng, density=0.15))
+    if args.workload == "large":
+        chi, d = LARGE_CHI, 6
+        w = inputs.workload(LARGE, LARGE_SEED)
+        m = vtn.vtn_build_mpo(None, w.r, w.U, w.D, w.d)
+        cores = []
+        for site in (LARGE_LO, LARGE_LO + 1):
+            wl_, wr_, rows, cols, ops = vtn.vtn_mpo_core(m, site)
+            cores.append(vtn.core_from_sparse(inputs.SparseCore(wl_, wr_, d, rows, cols, ops)))
+        vtn.vtn_mpo_free(m)
+        Wi, Wj = cores
+        wl, wm, wr = Wi.w_left, Wi.w_right, Wj.w_right
+    else:
+        chi, d, wl, wm, wr = CHI, 8, 24, 26, 24
+        Wi = vtn.core_from_sparse(inputs.random_sparse_core(wl, wm, d, rng, density=0.15))
+        Wj = vtn.core_from_sparse(inputs.random_sparse_core(wm, wr, d, rng, density=0.15))
     dev = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.complex128)).cuda()
     L = dev(inputs.random_complex((wl, chi, chi), rng))
     R = dev(inputs.random_complex((wr, chi, chi), rng))
@@ -1087,6 +1191,8 @@ def main():
         run_case_dmrg1(args)
     elif args.case == "c3cmp":
         run_case_c3cmp(args)
+    elif args.case == "batch":
+        run_case_batch(args)
     elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "large":

@@ -259,6 +259,19 @@ vtn_status vtn_sweep_opts_default(vtn_sweep_opts* opts);
 vtn_status vtn_sweep(vtn_ctx ctx, vtn_mpo mpo, vtn_mps* state, const vtn_sweep_opts* opts,
                      vtn_sweep_report* report);
 
+/* Independent two-site sweeps of n instances at once (many GBS instances of uneven size):
+ * instance j runs vtn_sweep(mpos[j], &states[j], &opts[j], &reports[j]) (reports may be NULL),
+ * status[j] gets its result.  The instances are spread over n_streams worker contexts (1..64),
+ * each with its own CUDA stream and workspace and a host thread that takes the next instance
+ * when its current one is done, so that the kernels of different instances overlap on the GPU
+ * (the small-bond instances leave most SMs idle alone).  States that are NULL are created first
+ * (vtn_mps_random with opts[j]'s first bond dimension and seed) on ctx; the MPOs and states stay
+ * owned by ctx.  Results equal the one-by-one vtn_sweep calls.  Returns the first error of an
+ * instance, else VTN_ENOCONV if some instance returned it, else VTN_OK; the workers are released
+ * before returning. */
+vtn_status vtn_sweep_batch(vtn_ctx ctx, int n, const vtn_mpo* mpos, vtn_mps* states, const vtn_sweep_opts* opts,
+                           vtn_sweep_report* reports, vtn_status* status, int n_streams);
+
 /* Single-site DMRG with subspace expansion: the solver of the paper's results section
  * (single-site DMRG), with the bond dimension grown during the sweeps as its discussion
  * describes, by the strictly single-site expansion it cites (Hubig et al., Phys. Rev. B 91,
@@ -305,6 +318,15 @@ vtn_status vtn_marginals_all(vtn_ctx ctx, vtn_mpo mpo, vtn_mps mps, double* out)
  * smallest n with CDF(n) > u * CDF(D-1), u the 53-bit uniform of Philox4x32-10
  * (key = seed, counter = (t, i, 2)).  out: int32[n_samples*M]. */
 vtn_status vtn_sample(vtn_ctx ctx, vtn_mpo mpo, vtn_mps mps, uint64_t seed, int n_samples, int32_t* out);
+
+/* Single-mode reduced density matrix of the variational state, rho_i = Tr_{others} |psi><psi| /
+ * <psi|psi> in the solver basis (the partial trace of the read-out, Eq. InverseBasisTransformation
+ * applies to it as V rho_i V^dag): out complex[d*d], out[s][t] = <s|rho_i|t>. */
+vtn_status vtn_reduced_density(vtn_ctx ctx, vtn_mpo mpo, vtn_mps mps, int site, double* out);
+
+/* Product MPS (every bond dimension 1) with site s = amps[s] / |amps[s]| (amps: host complex[M*d],
+ * each site vector non-zero); its recorded centre is 0. */
+vtn_status vtn_mps_product(vtn_ctx ctx, vtn_mpo mpo, const double* amps, vtn_mps* out);
 
 /* ---------------------------------------------------------------- kernel-level calls
  * These expose single steps of the solver on caller-provided device buffers.  They
@@ -455,6 +477,19 @@ vtn_status vtn_heff_apply_static(const vtn_core* Wi, const vtn_core* Wj, int chi
  * row-major.  Every call runs on the context's stream and returns after it finished; sums run
  * in a fixed order, so results repeat bit for bit. */
 
+/* Inputs and targets of the learned warm start.  The network maps the reduced covariance of
+ * one mode to the state that mode takes in the solved MPS; the warm start is the product state
+ * of its predictions (vtn_mps_product), from which the sweeps begin instead of a random MPS.
+ * Features of mode i from its 2 x 2 reduced covariance V_i (Eq. for the covariance; xxpp
+ * blocks of V): [log V_xx, log V_pp, V_xp / sqrt(V_xx V_pp), log det V_i / 2] -> out
+ * float[M*VTN_WARM_NFEAT].  Host only; VTN_EUNSUPPORTED for MPOs given as cores. */
+#define VTN_WARM_NFEAT 4
+vtn_status vtn_warm_features(vtn_mpo mpo, float* out);
+/* Targets from a solved state: for every mode i the dominant eigenvector u_i of its reduced
+ * density matrix (vtn_reduced_density; the mode's best single-mode state), phase fixed so that
+ * u_i[0] is real and non-negative, as out float[M*2d] with (Re, Im) interleaved. */
+vtn_status vtn_warm_targets(vtn_ctx ctx, vtn_mpo mpo, vtn_mps mps, float* out);
+
 /* Create with He-uniform weights (W_l entries uniform in +-sqrt(6 / n_in_l) from a splitmix64
  * stream seeded with seed), zero biases and zero Adam moments.  1 <= n_in, width, n_out <= 4096,
  * 0 <= depth <= 16. */
@@ -477,6 +512,17 @@ vtn_status vtn_mlp_loss_grad(vtn_ctx ctx, vtn_mlp mlp, int batch, const float* x
  * before the step. */
 vtn_status vtn_mlp_train_step(vtn_ctx ctx, vtn_mlp mlp, int batch, const float* x, const float* t, float lr,
                               float* loss);
+
+/* `steps` Adam steps (as vtn_mlp_train_step) on one batch without returning to the host in between;
+ * loss (host, may be NULL) = the loss before the last step.  1 <= steps <= 1e7. */
+vtn_status vtn_mlp_train(vtn_ctx ctx, vtn_mlp mlp, int batch, const float* x, const float* t, float lr, int steps,
+                         float* loss);
+/* The learned warm start of an instance: the network (n_in = VTN_WARM_NFEAT, n_out = 2 d) maps the
+ * features of every mode (vtn_warm_features) to a site vector (2 d floats read as d complex
+ * amplitudes), and the state is their product (vtn_mps_product); pass it to vtn_sweep as the
+ * initial state.  VTN_EINVAL if the network's shape does not match; a prediction that is zero for
+ * some mode is rejected like in vtn_mps_product. */
+vtn_status vtn_mps_warm_start(vtn_ctx ctx, vtn_mpo mpo, vtn_mlp mlp, vtn_mps* out);
 
 /* Real bf16 GEMM on the tensor cores (the kernel behind VTN_BF16X3):
  *   D[m][n] = sum_k A[m][k] * B[n][k], FP32 accumulation,

@@ -5,6 +5,9 @@
 // sampling) is a kernel launched on the context's stream.  The host builds the MPO
 // once (host_mpo.cpp) and reads back per-iteration status words and final scalars.
 #include <algorithm>
+#include <thread>
+#include <atomic>
+#include <complex>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -779,191 +782,274 @@ vtn_status vtn_sweep_opts_default(vtn_sweep_opts* o) {
     return VTN_OK;
 }
 
+namespace {
+
+// Two-site sweeps of one instance: device work on `work`'s stream and workspace; the MPO's
+// device copy and a new random MPS belong to `owner` (the same context for vtn_sweep, the
+// caller's context for the workers of vtn_sweep_batch).
+vtn_status sweep_body(vtn_ctx work, vtn_ctx owner, vtn_mpo mpo, vtn_mps* state, const vtn_sweep_opts* opts,
+                      vtn_sweep_report* report) {
+    VTN_REQUIRE(mpo && state && opts, "null argument");
+    VTN_REQUIRE(opts->chi_max >= 1, "chi_max must be >= 1");
+    VTN_REQUIRE(opts->n_sweeps >= 0 && opts->n_sweeps <= 64, "n_sweeps must be in [0, 64]");
+    VTN_REQUIRE(opts->krylov_max >= 1 && opts->krylov_max <= 64, "krylov_max must be in [1, 64]");
+    VTN_REQUIRE(opts->lanczos_max_restarts >= 0, "lanczos_max_restarts must be >= 0");
+    VTN_REQUIRE(opts->n_schedule == 0 || opts->chi_schedule != nullptr, "chi_schedule missing");
+    VTN_REQUIRE(opts->trunc_mode == 0 || opts->trunc_mode == 1, "trunc_mode must be 0 or 1");
+    VTN_REQUIRE(opts->trunc_mode == 0 || (opts->trunc_q >= 0 && opts->trunc_q <= 64), "trunc_q must be in [0, 64]");
+    if (opts->prec != VTN_FP64 && opts->prec != VTN_BF16X3)
+        throw Error{VTN_EUNSUPPORTED, "VTN_TF32X3 is not available in this build"};
+    const bool split = opts->prec == VTN_BF16X3;
+    Ctx& c = work->c;
+    use_device(c);
+    ensure_mpo_device(owner, mpo);
+    const int M = mpo->hp.M, d = mpo->hp.d;
+    if (M < 2) throw Error{VTN_EUNSUPPORTED, "two-site DMRG needs M >= 2"};
+    std::vector<int> sched;
+    for (int i = 0; i < opts->n_schedule; ++i) {
+        VTN_REQUIRE(opts->chi_schedule[i] >= 1, "chi_schedule entries must be >= 1");
+        sched.push_back(std::min(opts->chi_schedule[i], opts->chi_max));
+    }
+    if (sched.empty()) sched.push_back(opts->chi_max);
+    if (*state == nullptr) {
+        vtn_status st = vtn_mps_random(owner, mpo, sched[0], opts->seed, state);
+        if (st != VTN_OK) throw Error{st, owner->c.err};
+    }
+    vtn_mps mps = *state;
+    check_mps_matches(mpo, mps);
+    // bonds lo .. hi - 1 (a windowed sweep) or the whole chain
+    const bool windowed = opts->window_hi > opts->window_lo;
+    const int lo = windowed ? opts->window_lo : 0, hi = windowed ? opts->window_hi : M - 1;
+    VTN_REQUIRE(!windowed || (lo >= 0 && hi <= M - 1), "window must satisfy 0 <= window_lo < window_hi <= M - 1");
+    VTN_REQUIRE(opts->energy_mode == 0 || opts->energy_mode == 1, "energy_mode must be 0 or 1");
+    const bool centre_energy = windowed || opts->energy_mode == 1;
+    int chi_cap = opts->chi_max;
+    for (int x : mps->dims) chi_cap = std::max(chi_cap, x);
+    mps_reserve(c, mps, chi_cap);
+    // the environments assume sites < lo left-canonical and sites > lo right-canonical
+    if (windowed ? mps->center != lo : mps->center > 0) move_center(c, mps, lo);
+    const std::vector<int> capdims = cap_dims(M, chi_cap);
+    // environments sized for the largest bond dimension at each cut
+    Envs env;
+    env.c = &c;
+    env.L.assign(M + 1, nullptr);
+    env.R.assign(M + 1, nullptr);
+    for (int s = 0; s <= M; ++s) {
+        // L[s] is read or written for s <= hi, R[s] for s >= lo + 1
+        const size_t cap = (size_t)mpo->hp.w[s] * capdims[s] * capdims[s];
+        if (s <= hi) env.L[s] = (double2*)c.dalloc(sizeof(double2) * std::max(cap, size_t(1)));
+        if (s >= lo + 1) env.R[s] = (double2*)c.dalloc(sizeof(double2) * std::max(cap, size_t(1)));
+    }
+    set_scalar_one(c, env.L[0]);
+    set_scalar_one(c, env.R[M]);
+    // environment updates run in the same precision mode as H_eff psi
+    auto env_left = [&](const DevCore& W, int cl, int cr, const double2* Lin, const double2* A, double2* Lout) {
+        if (split) env_left_bf16x3(c, W, cl, cr, Lin, A, Lout);
+        else env_left_dev(c, W, cl, cr, Lin, A, Lout);
+    };
+    auto env_right = [&](const DevCore& W, int cl, int cr, const double2* Rin, const double2* A, double2* Rout) {
+        if (split) env_right_bf16x3(c, W, cl, cr, Rin, A, Rout);
+        else env_right_dev(c, W, cl, cr, Rin, A, Rout);
+    };
+    for (int s = 0; s < lo; ++s)
+        env_left(mpo->dcores[s], mps->dims[s], mps->dims[s + 1], env.L[s], mps->sites[s], env.L[s + 1]);
+    for (int s = M - 1; s >= lo + 2; --s)
+        env_right(mpo->dcores[s], mps->dims[s], mps->dims[s + 1], env.R[s + 1], mps->sites[s], env.R[s]);
+    const size_t theta_cap = (size_t)chi_cap * d * d * chi_cap;
+    double2* theta = (double2*)c.workspace(WS_VEC_T, sizeof(double2) * theta_cap);
+    vtn_sweep_report rep;
+    std::memset(&rep, 0, sizeof(rep));
+    long long not_conv = 0;
+    double prevE = 0.0;
+    bool have_prev = false;
+    // theta = A_i A_i+1
+    auto form_theta = [&](int i) {
+        const int cl = mps->dims[i], cm = mps->dims[i + 1], cr = mps->dims[i + 2];
+        GemmArgs g;
+        g.M = cl * d; g.N = d * cr; g.K = cm;
+        g.A = mps->sites[i]; g.lda = cm;
+        g.B = mps->sites[i + 1]; g.ldb = (long long)d * cr;
+        g.C = theta; g.ldc = (long long)d * cr;
+        gemm_c64(c, g);
+    };
+    for (int sw = 0; sw < opts->n_sweeps; ++sw) {
+        const auto t0 = std::chrono::steady_clock::now();
+        const int chi_s = sched[std::min<size_t>(sw, sched.size() - 1)];
+        double disc_max = 0.0;
+        for (int dir = 0; dir < 2; ++dir) {
+            for (int step = 0; step < hi - lo; ++step) {
+                const int i = dir == 0 ? lo + step : (hi - 1 - step);
+                const int cl = mps->dims[i], cm = mps->dims[i + 1], cr = mps->dims[i + 2];
+                form_theta(i);
+                const long long n = (long long)cl * d * d * cr;
+                const DevCore& Wi = mpo->dcores[i];
+                const DevCore& Wj = mpo->dcores[i + 1];
+                const double2* L = env.L[i];
+                const double2* R = env.R[i + 2];
+                const double hf = heff_flops(Wi, Wj, cl, cr);
+                HeffPacked pk;
+                if (split) heff_pack_envs(c, Wi, Wj, cl, cr, L, R, pk);
+                LanczosResult lr = lanczos(c, n, theta, opts->lanczos_tol, opts->krylov_max,
+                                           opts->lanczos_max_restarts, [&](const double2* in, double2* out) {
+                                               if (split) heff_apply_bf16x3(c, Wi, Wj, pk, in, out);
+                                               else heff_apply_dev(c, Wi, Wj, cl, cr, L, R, in, out);
+                                           });
+                rep.matvecs += lr.n_matvec;
+                rep.heff_flops += hf * lr.n_matvec;
+                if (!lr.converged) ++not_conv;
+                TruncResult tr;
+                if (opts->trunc_mode == 1) {
+                    // warm start: the current centre (site i sweeping right, i + 1 sweeping left),
+                    // as conjugated rows
+                    const double2* Sh0 = mps->sites[i + 1];  // cm x (d cr), already rows
+                    if (dir == 0) {
+                        double2* q0 = (double2*)c.workspace(WS_WARM_Q0, sizeof(double2) * (size_t)cm * cl * d);
+                        conj_transpose_dev(c, cl * d, cm, mps->sites[i], cm, q0, (long long)cl * d);
+                        Sh0 = q0;
+                    }
+                    tr = truncate_warm_dev(c, cl, d, d, cr, dir, chi_s, theta, Sh0, cm, opts->trunc_q, 8, opts->seed,
+                                           i, mps->sites[i], mps->sites[i + 1]);
+                } else {
+                    tr = truncate_dev(c, cl, d, d, cr, dir, chi_s, theta, mps->sites[i], mps->sites[i + 1]);
+                }
+                mps->dims[i + 1] = tr.k;
+                disc_max = std::max(disc_max, tr.discarded);
+                if (dir == 0)
+                    env_left(Wi, cl, tr.k, env.L[i], mps->sites[i], env.L[i + 1]);
+                else
+                    env_right(Wj, tr.k, cr, env.R[i + 2], mps->sites[i + 1], env.R[i + 1]);
+            }
+        }
+        mps->center = lo;
+        double E;
+        if (centre_energy) {
+            // Rayleigh quotient of the final centre theta = A_lo A_lo+1 under H_eff of bond (lo, lo+1)
+            const int cl = mps->dims[lo], cr = mps->dims[lo + 2];
+            const long long n = (long long)cl * d * d * cr;
+            form_theta(lo);
+            double2* y = (double2*)c.workspace(WS_RQ_Y, sizeof(double2) * (size_t)n);
+            double* sc = (double*)c.workspace(WS_RQ_S, sizeof(double) * 64);
+            const DevCore& Wi = mpo->dcores[lo];
+            const DevCore& Wj = mpo->dcores[lo + 1];
+            if (split) {
+                HeffPacked pk;
+                heff_pack_envs(c, Wi, Wj, cl, cr, env.L[lo], env.R[lo + 2], pk);
+                heff_apply_bf16x3(c, Wi, Wj, pk, theta, y);
+            } else {
+                heff_apply_dev(c, Wi, Wj, cl, cr, env.L[lo], env.R[lo + 2], theta, y);
+            }
+            multi_dot(c, theta, n, 1, y, n, (double2*)sc);
+            norm2_dev(c, theta, n, sc + 2);
+            VTN_CUDA_TRY(cudaMemcpyAsync(c.pinned, sc, sizeof(double) * 3, cudaMemcpyDeviceToHost, c.stream));
+            c.sync();
+            E = c.pinned[0] / c.pinned[2];
+        } else {
+            E = energy_dev(c, mpo, mps);
+            c.sync();
+        }
+        const auto t1 = std::chrono::steady_clock::now();
+        rep.energy[sw] = E;
+        rep.max_discarded[sw] = disc_max;
+        rep.seconds[sw] = std::chrono::duration<double>(t1 - t0).count();
+        rep.sweeps_done = sw + 1;
+        if (opts->use_e_target && E <= opts->e_target) break;
+        if (have_prev && opts->e_tol > 0 && std::fabs(E - prevE) <= opts->e_tol) break;
+        prevE = E;
+        have_prev = true;
+    }
+    c.tflush();
+    c.check_dstatus();
+    rep.lanczos_not_converged = not_conv;
+    rep.heff_seconds = c.tc[TC_HEFF].seconds;
+    rep.gemm_flops = c.tc[TC_GEMM].flops;
+    rep.gemm_seconds = c.tc[TC_GEMM].seconds;
+    rep.eig_seconds = c.tc[TC_EIG].seconds;
+    if (report) *report = rep;
+    if (not_conv > 0) {
+        c.err = std::to_string(not_conv) + " Lanczos solves missed the tolerance";
+        return VTN_ENOCONV;
+    }
+    return VTN_OK;
+}
+
+}  // namespace
+
 vtn_status vtn_sweep(vtn_ctx ctx, vtn_mpo mpo, vtn_mps* state, const vtn_sweep_opts* opts, vtn_sweep_report* report) {
     if (!ctx) return VTN_EINVAL;
-    return guard(ctx, [&]() -> vtn_status {
-        VTN_REQUIRE(mpo && state && opts, "null argument");
-        VTN_REQUIRE(opts->chi_max >= 1, "chi_max must be >= 1");
-        VTN_REQUIRE(opts->n_sweeps >= 0 && opts->n_sweeps <= 64, "n_sweeps must be in [0, 64]");
-        VTN_REQUIRE(opts->krylov_max >= 1 && opts->krylov_max <= 64, "krylov_max must be in [1, 64]");
-        VTN_REQUIRE(opts->lanczos_max_restarts >= 0, "lanczos_max_restarts must be >= 0");
-        VTN_REQUIRE(opts->n_schedule == 0 || opts->chi_schedule != nullptr, "chi_schedule missing");
-        VTN_REQUIRE(opts->trunc_mode == 0 || opts->trunc_mode == 1, "trunc_mode must be 0 or 1");
-        VTN_REQUIRE(opts->trunc_mode == 0 || (opts->trunc_q >= 0 && opts->trunc_q <= 64), "trunc_q must be in [0, 64]");
-        if (opts->prec != VTN_FP64 && opts->prec != VTN_BF16X3)
-            throw Error{VTN_EUNSUPPORTED, "VTN_TF32X3 is not available in this build"};
-        const bool split = opts->prec == VTN_BF16X3;
+    return guard(ctx, [&]() -> vtn_status { return sweep_body(ctx, ctx, mpo, state, opts, report); });
+}
+
+vtn_status vtn_sweep_batch(vtn_ctx ctx, int n, const vtn_mpo* mpos, vtn_mps* states, const vtn_sweep_opts* opts,
+                           vtn_sweep_report* reports, vtn_status* status, int n_streams) {
+    if (!ctx) return VTN_EINVAL;
+    std::vector<vtn_ctx> workers;
+    auto release = [&]() {
+        for (vtn_ctx w : workers) {
+            cudaStream_t s = w->c.stream;
+            vtn_destroy(w);
+            if (s) cudaStreamDestroy(s);
+        }
+        workers.clear();
+    };
+    vtn_status st = guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(n >= 0 && (n == 0 || (mpos && states && opts && status)), "null argument");
+        VTN_REQUIRE(n_streams >= 1 && n_streams <= 64, "n_streams must be in [1, 64]");
         Ctx& c = ctx->c;
         use_device(c);
-        ensure_mpo_device(ctx, mpo);
-        const int M = mpo->hp.M, d = mpo->hp.d;
-        if (M < 2) throw Error{VTN_EUNSUPPORTED, "two-site DMRG needs M >= 2"};
-        std::vector<int> sched;
-        for (int i = 0; i < opts->n_schedule; ++i) {
-            VTN_REQUIRE(opts->chi_schedule[i] >= 1, "chi_schedule entries must be >= 1");
-            sched.push_back(std::min(opts->chi_schedule[i], opts->chi_max));
-        }
-        if (sched.empty()) sched.push_back(opts->chi_max);
-        if (*state == nullptr) {
-            vtn_status st = vtn_mps_random(ctx, mpo, sched[0], opts->seed, state);
-            if (st != VTN_OK) throw Error{st, c.err};
-        }
-        vtn_mps mps = *state;
-        check_mps_matches(mpo, mps);
-        // bonds lo .. hi - 1 (a windowed sweep) or the whole chain
-        const bool windowed = opts->window_hi > opts->window_lo;
-        const int lo = windowed ? opts->window_lo : 0, hi = windowed ? opts->window_hi : M - 1;
-        VTN_REQUIRE(!windowed || (lo >= 0 && hi <= M - 1), "window must satisfy 0 <= window_lo < window_hi <= M - 1");
-        VTN_REQUIRE(opts->energy_mode == 0 || opts->energy_mode == 1, "energy_mode must be 0 or 1");
-        const bool centre_energy = windowed || opts->energy_mode == 1;
-        int chi_cap = opts->chi_max;
-        for (int x : mps->dims) chi_cap = std::max(chi_cap, x);
-        mps_reserve(c, mps, chi_cap);
-        // the environments assume sites < lo left-canonical and sites > lo right-canonical
-        if (windowed ? mps->center != lo : mps->center > 0) move_center(c, mps, lo);
-        const std::vector<int> capdims = cap_dims(M, chi_cap);
-        // environments sized for the largest bond dimension at each cut
-        Envs env;
-        env.c = &c;
-        env.L.assign(M + 1, nullptr);
-        env.R.assign(M + 1, nullptr);
-        for (int s = 0; s <= M; ++s) {
-            // L[s] is read or written for s <= hi, R[s] for s >= lo + 1
-            const size_t cap = (size_t)mpo->hp.w[s] * capdims[s] * capdims[s];
-            if (s <= hi) env.L[s] = (double2*)c.dalloc(sizeof(double2) * std::max(cap, size_t(1)));
-            if (s >= lo + 1) env.R[s] = (double2*)c.dalloc(sizeof(double2) * std::max(cap, size_t(1)));
-        }
-        set_scalar_one(c, env.L[0]);
-        set_scalar_one(c, env.R[M]);
-        // environment updates run in the same precision mode as H_eff psi
-        auto env_left = [&](const DevCore& W, int cl, int cr, const double2* Lin, const double2* A, double2* Lout) {
-            if (split) env_left_bf16x3(c, W, cl, cr, Lin, A, Lout);
-            else env_left_dev(c, W, cl, cr, Lin, A, Lout);
-        };
-        auto env_right = [&](const DevCore& W, int cl, int cr, const double2* Rin, const double2* A, double2* Rout) {
-            if (split) env_right_bf16x3(c, W, cl, cr, Rin, A, Rout);
-            else env_right_dev(c, W, cl, cr, Rin, A, Rout);
-        };
-        for (int s = 0; s < lo; ++s)
-            env_left(mpo->dcores[s], mps->dims[s], mps->dims[s + 1], env.L[s], mps->sites[s], env.L[s + 1]);
-        for (int s = M - 1; s >= lo + 2; --s)
-            env_right(mpo->dcores[s], mps->dims[s], mps->dims[s + 1], env.R[s + 1], mps->sites[s], env.R[s]);
-        const size_t theta_cap = (size_t)chi_cap * d * d * chi_cap;
-        double2* theta = (double2*)c.workspace(WS_VEC_T, sizeof(double2) * theta_cap);
-        vtn_sweep_report rep;
-        std::memset(&rep, 0, sizeof(rep));
-        long long not_conv = 0;
-        double prevE = 0.0;
-        bool have_prev = false;
-        // theta = A_i A_i+1
-        auto form_theta = [&](int i) {
-            const int cl = mps->dims[i], cm = mps->dims[i + 1], cr = mps->dims[i + 2];
-            GemmArgs g;
-            g.M = cl * d; g.N = d * cr; g.K = cm;
-            g.A = mps->sites[i]; g.lda = cm;
-            g.B = mps->sites[i + 1]; g.ldb = (long long)d * cr;
-            g.C = theta; g.ldc = (long long)d * cr;
-            gemm_c64(c, g);
-        };
-        for (int sw = 0; sw < opts->n_sweeps; ++sw) {
-            const auto t0 = std::chrono::steady_clock::now();
-            const int chi_s = sched[std::min<size_t>(sw, sched.size() - 1)];
-            double disc_max = 0.0;
-            for (int dir = 0; dir < 2; ++dir) {
-                for (int step = 0; step < hi - lo; ++step) {
-                    const int i = dir == 0 ? lo + step : (hi - 1 - step);
-                    const int cl = mps->dims[i], cm = mps->dims[i + 1], cr = mps->dims[i + 2];
-                    form_theta(i);
-                    const long long n = (long long)cl * d * d * cr;
-                    const DevCore& Wi = mpo->dcores[i];
-                    const DevCore& Wj = mpo->dcores[i + 1];
-                    const double2* L = env.L[i];
-                    const double2* R = env.R[i + 2];
-                    const double hf = heff_flops(Wi, Wj, cl, cr);
-                    HeffPacked pk;
-                    if (split) heff_pack_envs(c, Wi, Wj, cl, cr, L, R, pk);
-                    LanczosResult lr = lanczos(c, n, theta, opts->lanczos_tol, opts->krylov_max,
-                                               opts->lanczos_max_restarts, [&](const double2* in, double2* out) {
-                                                   if (split) heff_apply_bf16x3(c, Wi, Wj, pk, in, out);
-                                                   else heff_apply_dev(c, Wi, Wj, cl, cr, L, R, in, out);
-                                               });
-                    rep.matvecs += lr.n_matvec;
-                    rep.heff_flops += hf * lr.n_matvec;
-                    if (!lr.converged) ++not_conv;
-                    TruncResult tr;
-                    if (opts->trunc_mode == 1) {
-                        // warm start: the current centre (site i sweeping right, i + 1 sweeping left),
-                        // as conjugated rows
-                        const double2* Sh0 = mps->sites[i + 1];  // cm x (d cr), already rows
-                        if (dir == 0) {
-                            double2* q0 = (double2*)c.workspace(WS_WARM_Q0, sizeof(double2) * (size_t)cm * cl * d);
-                            conj_transpose_dev(c, cl * d, cm, mps->sites[i], cm, q0, (long long)cl * d);
-                            Sh0 = q0;
-                        }
-                        tr = truncate_warm_dev(c, cl, d, d, cr, dir, chi_s, theta, Sh0, cm, opts->trunc_q, 8, opts->seed,
-                                               i, mps->sites[i], mps->sites[i + 1]);
-                    } else {
-                        tr = truncate_dev(c, cl, d, d, cr, dir, chi_s, theta, mps->sites[i], mps->sites[i + 1]);
-                    }
-                    mps->dims[i + 1] = tr.k;
-                    disc_max = std::max(disc_max, tr.discarded);
-                    if (dir == 0)
-                        env_left(Wi, cl, tr.k, env.L[i], mps->sites[i], env.L[i + 1]);
-                    else
-                        env_right(Wj, tr.k, cr, env.R[i + 2], mps->sites[i + 1], env.R[i + 1]);
-                }
+        // serial set-up on the caller's context: device copies of the MPOs, random initial states
+        for (int j = 0; j < n; ++j) {
+            VTN_REQUIRE(mpos[j] != nullptr, "null MPO in the batch");
+            ensure_mpo_device(ctx, mpos[j]);
+            if (states[j] == nullptr) {
+                std::vector<int> sched;
+                for (int i = 0; i < opts[j].n_schedule && opts[j].chi_schedule; ++i)
+                    sched.push_back(std::min(opts[j].chi_schedule[i], opts[j].chi_max));
+                const int chi0 = sched.empty() ? opts[j].chi_max : sched[0];
+                vtn_status s0 = vtn_mps_random(ctx, mpos[j], std::max(chi0, 1), opts[j].seed, &states[j]);
+                if (s0 != VTN_OK) throw Error{s0, c.err};
             }
-            mps->center = lo;
-            double E;
-            if (centre_energy) {
-                // Rayleigh quotient of the final centre theta = A_lo A_lo+1 under H_eff of bond (lo, lo+1)
-                const int cl = mps->dims[lo], cr = mps->dims[lo + 2];
-                const long long n = (long long)cl * d * d * cr;
-                form_theta(lo);
-                double2* y = (double2*)c.workspace(WS_RQ_Y, sizeof(double2) * (size_t)n);
-                double* sc = (double*)c.workspace(WS_RQ_S, sizeof(double) * 64);
-                const DevCore& Wi = mpo->dcores[lo];
-                const DevCore& Wj = mpo->dcores[lo + 1];
-                if (split) {
-                    HeffPacked pk;
-                    heff_pack_envs(c, Wi, Wj, cl, cr, env.L[lo], env.R[lo + 2], pk);
-                    heff_apply_bf16x3(c, Wi, Wj, pk, theta, y);
-                } else {
-                    heff_apply_dev(c, Wi, Wj, cl, cr, env.L[lo], env.R[lo + 2], theta, y);
-                }
-                multi_dot(c, theta, n, 1, y, n, (double2*)sc);
-                norm2_dev(c, theta, n, sc + 2);
-                VTN_CUDA_TRY(cudaMemcpyAsync(c.pinned, sc, sizeof(double) * 3, cudaMemcpyDeviceToHost, c.stream));
-                c.sync();
-                E = c.pinned[0] / c.pinned[2];
-            } else {
-                E = energy_dev(c, mpo, mps);
-                c.sync();
+        }
+        // nothing queued before this call may still use memory the workers' allocations return
+        VTN_CUDA_TRY(cudaDeviceSynchronize());
+        // worker contexts: own stream and workspace, the caller's allocator
+        const int W = std::min(n_streams, std::max(n, 1));
+        const vtn_allocator* al = c.has_alloc ? &c.alloc : nullptr;
+        for (int k = 0; k < W; ++k) {
+            cudaStream_t s = nullptr;
+            VTN_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+            vtn_ctx w = nullptr;
+            vtn_status cs = vtn_create(&w, c.device, s, al);
+            if (cs != VTN_OK) {
+                cudaStreamDestroy(s);
+                throw Error{cs, std::string("worker context: ") + vtn_last_error(nullptr)};
             }
-            const auto t1 = std::chrono::steady_clock::now();
-            rep.energy[sw] = E;
-            rep.max_discarded[sw] = disc_max;
-            rep.seconds[sw] = std::chrono::duration<double>(t1 - t0).count();
-            rep.sweeps_done = sw + 1;
-            if (opts->use_e_target && E <= opts->e_target) break;
-            if (have_prev && opts->e_tol > 0 && std::fabs(E - prevE) <= opts->e_tol) break;
-            prevE = E;
-            have_prev = true;
+            workers.push_back(w);
         }
-        c.tflush();
-        c.check_dstatus();
-        rep.lanczos_not_converged = not_conv;
-        rep.heff_seconds = c.tc[TC_HEFF].seconds;
-        rep.gemm_flops = c.tc[TC_GEMM].flops;
-        rep.gemm_seconds = c.tc[TC_GEMM].seconds;
-        rep.eig_seconds = c.tc[TC_EIG].seconds;
-        if (report) *report = rep;
-        if (not_conv > 0) {
-            c.err = std::to_string(not_conv) + " Lanczos solves missed the tolerance";
-            return VTN_ENOCONV;
-        }
+        std::atomic<int> next{0};
+        auto run = [&](vtn_ctx w) {
+            cudaSetDevice(w->c.device);
+            for (;;) {
+                const int j = next.fetch_add(1);
+                if (j >= n) break;
+                status[j] = guard(w, [&]() -> vtn_status {
+                    return sweep_body(w, ctx, mpos[j], &states[j], &opts[j], reports ? &reports[j] : nullptr);
+                });
+            }
+        };
+        std::vector<std::thread> threads;
+        for (int k = 1; k < W; ++k) threads.emplace_back(run, workers[k]);
+        run(workers[0]);
+        for (auto& t : threads) t.join();
+        for (int j = 0; j < n; ++j)
+            if (status[j] != VTN_OK && status[j] != VTN_ENOCONV)
+                throw Error{status[j], "instance " + std::to_string(j) + " of the batch failed"};
         return VTN_OK;
     });
+    release();
+    if (st == VTN_OK)
+        for (int j = 0; j < n; ++j)
+            if (status[j] == VTN_ENOCONV) return VTN_ENOCONV;
+    return st;
 }
 
 // Single-site DMRG with subspace expansion.  At site i sweeping right: Lanczos on the
@@ -1310,6 +1396,182 @@ vtn_status vtn_marginals_all(vtn_ctx ctx, vtn_mpo mpo, vtn_mps mps, double* out)
         c.sync();
         const double n2 = c.pinned[0];
         for (size_t i = 0; i < (size_t)M * D; ++i) out[i] = host[i] / n2;
+        return VTN_OK;
+    });
+}
+
+namespace {
+
+// rho_i (solver basis, d x d, normalised) of every site i in `sites` into host complex[|sites| d d]:
+// all left and right transfer environments once, then two GEMMs and a reduction per site.
+void reduced_densities(Ctx& c, vtn_mps mps, const std::vector<int>& sites, std::vector<std::complex<double>>& out) {
+    const int M = mps->M, d = mps->d;
+    const int chi = max_dim(mps->dims);
+    const size_t env = (size_t)chi * chi;
+    double2* EL = (double2*)c.workspace(WS_Z, sizeof(double2) * env * (M + 1) * 2);
+    double2* ER = EL + env * (M + 1);
+    double2* tmp = (double2*)c.workspace(WS_ENV_TMP, sizeof(double2) * (size_t)chi * d * chi);
+    double2* U = (double2*)c.workspace(WS_Y, sizeof(double2) * (size_t)chi * d * chi);
+    double2* rho = (double2*)c.workspace(WS_RQ_Y, sizeof(double2) * (size_t)d * d * std::max<size_t>(sites.size(), 1));
+    set_scalar_one(c, EL);
+    for (int s = 0; s < M; ++s)
+        transfer_left_batch(c, 1, mps->dims[s], d, mps->dims[s + 1], EL + env * s, mps->sites[s], EL + env * (s + 1), tmp);
+    set_scalar_one(c, ER + env * M);
+    for (int s = M - 1; s >= 0; --s)
+        transfer_right(c, mps->dims[s], d, mps->dims[s + 1], ER + env * (s + 1), mps->sites[s], ER + env * s, tmp);
+    for (size_t j = 0; j < sites.size(); ++j) {
+        const int s = sites[j], cl = mps->dims[s], cr = mps->dims[s + 1];
+        GemmArgs g1;  // tmp = EL[s] A   (cl x d cr)
+        g1.M = cl; g1.N = d * cr; g1.K = cl;
+        g1.A = EL + env * s; g1.lda = cl;
+        g1.B = mps->sites[s]; g1.ldb = (long long)d * cr;
+        g1.C = tmp; g1.ldc = (long long)d * cr;
+        gemm_c64(c, g1);
+        GemmArgs g2;  // U = tmp (cl d x cr) ER[s+1]
+        g2.M = cl * d; g2.N = cr; g2.K = cr;
+        g2.A = tmp; g2.lda = cr;
+        g2.B = ER + env * (s + 1); g2.ldb = cr;
+        g2.C = U; g2.ldc = cr;
+        gemm_c64(c, g2);
+        reduced_density_dev(c, cl, d, cr, U, mps->sites[s], rho + (size_t)j * d * d);
+    }
+    out.resize(sites.size() * d * d);
+    VTN_CUDA_TRY(cudaMemcpyAsync(out.data(), rho, sizeof(double2) * out.size(), cudaMemcpyDeviceToHost, c.stream));
+    VTN_CUDA_TRY(cudaMemcpyAsync(c.pinned, EL + env * M, sizeof(double2), cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+    const double n2 = c.pinned[0];
+    VTN_REQUIRE(n2 > 0.0, "the MPS has zero norm");
+    for (auto& v : out) v /= n2;
+}
+
+// Dominant eigenvector of a Hermitian positive semi-definite d x d matrix (row-major): 40 steps
+// of repeated squaring A <- A A / max|A A| leave A proportional to u u^dag (the other eigenvalues
+// fall by (lambda_k / lambda_1)^(2^40)); u is then the column of largest norm, normalised, with the
+// phase fixed so that component 0 is real and non-negative (or, when it vanishes, the largest).
+std::vector<std::complex<double>> dominant_eigenvector(std::vector<std::complex<double>> A, int d) {
+    using C = std::complex<double>;
+    std::vector<C> B(d * d);
+    for (int it = 0; it < 40; ++it) {
+        double mx = 0.0;
+        for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) {
+                C acc(0, 0);
+                for (int k = 0; k < d; ++k) acc += A[i * d + k] * A[k * d + j];
+                B[i * d + j] = acc;
+                mx = std::max(mx, std::abs(acc));
+            }
+        if (!(mx > 0.0)) break;
+        for (int i = 0; i < d * d; ++i) A[i] = B[i] / mx;
+    }
+    int col = 0;
+    double best = -1.0;
+    for (int j = 0; j < d; ++j) {
+        double n = 0.0;
+        for (int i = 0; i < d; ++i) n += std::norm(A[i * d + j]);
+        if (n > best) {
+            best = n;
+            col = j;
+        }
+    }
+    std::vector<C> u(d);
+    const double nrm = std::sqrt(std::max(best, 1e-300));
+    for (int i = 0; i < d; ++i) u[i] = A[i * d + col] / nrm;
+    int ref = 0;
+    if (std::abs(u[0]) < 1e-8) {
+        for (int k = 1; k < d; ++k)
+            if (std::abs(u[k]) > std::abs(u[ref])) ref = k;
+    }
+    const double m = std::abs(u[ref]);
+    const C rot = m > 0 ? std::conj(u[ref]) / m : C(1, 0);
+    for (auto& x : u) x *= rot;
+    return u;
+}
+
+}  // namespace
+
+vtn_status vtn_reduced_density(vtn_ctx ctx, vtn_mpo mpo, vtn_mps mps, int site, double* out) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(mpo && mps && out, "null argument");
+        check_mps_matches(mpo, mps);
+        VTN_REQUIRE(site >= 0 && site < mps->M, "site out of range");
+        Ctx& c = ctx->c;
+        use_device(c);
+        std::vector<std::complex<double>> rho;
+        reduced_densities(c, mps, {site}, rho);
+        std::memcpy(out, rho.data(), sizeof(double) * 2 * rho.size());
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_warm_features(vtn_mpo mpo, float* out) {
+    if (!mpo || !out) return VTN_EINVAL;
+    const auto& hp = mpo->hp;
+    if (hp.V.empty()) return VTN_EUNSUPPORTED;
+    const int M = hp.M, n2 = 2 * M;
+    for (int i = 0; i < M; ++i) {
+        const double vxx = hp.V[(size_t)i * n2 + i], vpp = hp.V[(size_t)(M + i) * n2 + M + i];
+        const double vxp = hp.V[(size_t)i * n2 + M + i];
+        out[4 * i + 0] = (float)std::log(vxx);
+        out[4 * i + 1] = (float)std::log(vpp);
+        out[4 * i + 2] = (float)(vxp / std::sqrt(vxx * vpp));
+        out[4 * i + 3] = (float)(0.5 * std::log(std::max(vxx * vpp - vxp * vxp, 1e-300)));
+    }
+    return VTN_OK;
+}
+
+vtn_status vtn_warm_targets(vtn_ctx ctx, vtn_mpo mpo, vtn_mps mps, float* out) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(mpo && mps && out, "null argument");
+        check_mps_matches(mpo, mps);
+        Ctx& c = ctx->c;
+        use_device(c);
+        const int M = mps->M, d = mps->d;
+        std::vector<int> all(M);
+        for (int i = 0; i < M; ++i) all[i] = i;
+        std::vector<std::complex<double>> rho;
+        reduced_densities(c, mps, all, rho);
+        for (int i = 0; i < M; ++i) {
+            std::vector<std::complex<double>> A(rho.begin() + (size_t)i * d * d, rho.begin() + (size_t)(i + 1) * d * d);
+            const auto u = dominant_eigenvector(A, d);
+            for (int k = 0; k < d; ++k) {
+                out[(size_t)i * 2 * d + 2 * k] = (float)u[k].real();
+                out[(size_t)i * 2 * d + 2 * k + 1] = (float)u[k].imag();
+            }
+        }
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_mps_product(vtn_ctx ctx, vtn_mpo mpo, const double* amps, vtn_mps* out) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(mpo && amps && out, "null argument");
+        Ctx& c = ctx->c;
+        use_device(c);
+        const int M = mpo->hp.M, d = mpo->hp.d;
+        std::vector<double> unit((size_t)M * 2 * d);
+        for (int i = 0; i < M; ++i) {
+            double n2 = 0.0;
+            for (int k = 0; k < 2 * d; ++k) n2 += amps[(size_t)i * 2 * d + k] * amps[(size_t)i * 2 * d + k];
+            VTN_REQUIRE(n2 > 0.0 && std::isfinite(n2), "product state: a site vector is zero or not finite");
+            const double inv = 1.0 / std::sqrt(n2);
+            for (int k = 0; k < 2 * d; ++k) unit[(size_t)i * 2 * d + k] = amps[(size_t)i * 2 * d + k] * inv;
+        }
+        std::vector<int> dims(M + 1, 1);
+        vtn_mps m = new_mps(ctx, M, d, dims);
+        try {
+            for (int i = 0; i < M; ++i)
+                VTN_CUDA_TRY(cudaMemcpyAsync(m->sites[i], unit.data() + (size_t)i * 2 * d, sizeof(double2) * d,
+                                             cudaMemcpyHostToDevice, c.stream));
+            c.sync();
+        } catch (...) {
+            destroy_mps(m);
+            throw;
+        }
+        m->center = 0;
+        *out = m;
         return VTN_OK;
     });
 }
@@ -1728,6 +1990,56 @@ vtn_status vtn_mlp_train_step(vtn_ctx ctx, vtn_mlp mlp, int batch, const float* 
         if (loss) VTN_CUDA_TRY(cudaMemcpyAsync(loss, mlp->loss, sizeof(float), cudaMemcpyDeviceToHost, c.stream));
         c.sync();
         ++mlp->step;
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_mlp_train(vtn_ctx ctx, vtn_mlp mlp, int batch, const float* x, const float* t, float lr, int steps,
+                         float* loss) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        check_mlp(ctx, mlp);
+        VTN_REQUIRE(x && t, "null device pointer");
+        VTN_REQUIRE(batch >= 1 && batch <= 4000000, "batch must be in [1, 4000000]");
+        VTN_REQUIRE(std::isfinite(lr) && lr > 0.0f, "lr must be finite and > 0");
+        VTN_REQUIRE(steps >= 1 && steps <= 10000000, "steps must be in [1, 10000000]");
+        Ctx& c = ctx->c;
+        use_device(c);
+        for (int k = 0; k < steps; ++k) {
+            mlp_loss_grad_dev(c, mlp->shape, mlp->params, batch, x, t, mlp->grad, mlp->loss);
+            mlp_adam_dev(c, mlp->shape.n_params, mlp->params, mlp->m, mlp->v, mlp->grad, lr, mlp->step + 1);
+            ++mlp->step;
+        }
+        if (loss) VTN_CUDA_TRY(cudaMemcpyAsync(loss, mlp->loss, sizeof(float), cudaMemcpyDeviceToHost, c.stream));
+        c.sync();
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_mps_warm_start(vtn_ctx ctx, vtn_mpo mpo, vtn_mlp mlp, vtn_mps* out) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        check_mlp(ctx, mlp);
+        VTN_REQUIRE(mpo && out, "null argument");
+        const int M = mpo->hp.M, d = mpo->hp.d;
+        const MlpShape& sh = mlp->shape;
+        VTN_REQUIRE(sh.n_in == VTN_WARM_NFEAT && sh.n_out == 2 * d,
+                    "the warm-start network needs VTN_WARM_NFEAT inputs and 2 d outputs");
+        Ctx& c = ctx->c;
+        use_device(c);
+        std::vector<float> feat((size_t)M * VTN_WARM_NFEAT), pred((size_t)M * 2 * d);
+        const vtn_status fs = vtn_warm_features(mpo, feat.data());
+        if (fs != VTN_OK) throw Error{fs, "the warm start needs an MPO built from (r, U)"};
+        float* x = (float*)c.workspace(WS_MLP_G, sizeof(float) * ((size_t)M * (VTN_WARM_NFEAT + 2 * d)));
+        float* y = x + (size_t)M * VTN_WARM_NFEAT;
+        float* acts = (float*)c.workspace(WS_MLP_ACT, sizeof(float) * ((size_t)std::max(sh.depth, 1) * M * sh.width));
+        VTN_CUDA_TRY(cudaMemcpyAsync(x, feat.data(), sizeof(float) * feat.size(), cudaMemcpyHostToDevice, c.stream));
+        mlp_forward_dev(c, sh, mlp->params, M, x, acts, y);
+        VTN_CUDA_TRY(cudaMemcpyAsync(pred.data(), y, sizeof(float) * pred.size(), cudaMemcpyDeviceToHost, c.stream));
+        c.sync();
+        std::vector<double> amps(pred.begin(), pred.end());
+        const vtn_status ps = vtn_mps_product(ctx, mpo, amps.data(), out);
+        if (ps != VTN_OK) throw Error{ps, c.err};
         return VTN_OK;
     });
 }

@@ -171,6 +171,16 @@ void upload_core(Ctx& ctx, const HostCore& hc, DevCore& dc) {
     dc.n_ident = 0;
     dc.n_dense = 0;
     for (int k = 0; k < nnz; ++k) (hc.ident[k] ? dc.n_ident : dc.n_dense)++;
+    {
+        std::vector<int> dcol(hc.wr, 0), drow(hc.wl, 0);
+        for (int k = 0; k < nnz; ++k)
+            if (!hc.ident[k]) {
+                dcol[hc.cols[k]]++;
+                drow[hc.rows[k]]++;
+            }
+        dc.max_dense_col = dcol.empty() ? 0 : *std::max_element(dcol.begin(), dcol.end());
+        dc.max_dense_row = drow.empty() ? 0 : *std::max_element(drow.begin(), drow.end());
+    }
     // one allocation holding everything
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~size_t(255); return o; };

@@ -262,6 +262,38 @@ __global__ void __launch_bounds__(256) sample_kernel(SampleArgs a) {
     }
 }
 
+// rho[s][t] = sum_{i, c} U[i][s][c] conj(A[i][t][c]) for s, t < d: one CTA per (s, t),
+// fixed-order block sum
+__global__ void __launch_bounds__(256) reduced_density_kernel(int cl, int d, int cr, const double2* __restrict__ U,
+                                                              const double2* __restrict__ A, double2* __restrict__ rho) {
+    __shared__ double sh[2][8];
+    const int s = blockIdx.x / d, t = blockIdx.x % d;
+    double re = 0.0, im = 0.0;
+    const long long n = (long long)cl * cr;
+    for (long long e = threadIdx.x; e < n; e += blockDim.x) {
+        const long long i = e / cr, c = e - (e / cr) * cr;
+        const double2 u = U[(i * d + s) * cr + c], a = A[(i * d + t) * cr + c];
+        re += u.x * a.x + u.y * a.y;
+        im += u.y * a.x - u.x * a.y;
+    }
+    re = warp_sum(re);
+    im = warp_sum(im);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        sh[0][wid] = re;
+        sh[1][wid] = im;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = 0.0, m = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            r += sh[0][w];
+            m += sh[1][w];
+        }
+        rho[blockIdx.x] = make_double2(r, m);
+    }
+}
+
 }  // namespace
 
 void fill_random_normal(Ctx& ctx, double2* out, long long count, uint64_t seed, int site, unsigned stream) {
@@ -333,6 +365,12 @@ void sample_dev(Ctx& ctx, const double2* const* AF_dev, const double2* const* ER
     sample_kernel<<<n_samples, 256, shm, ctx.stream>>>(a);
     ctx.count_launch();
     ctx.check_launch("sample_kernel");
+}
+
+void reduced_density_dev(Ctx& ctx, int cl, int d, int cr, const double2* U, const double2* A, double2* rho) {
+    reduced_density_kernel<<<d * d, 256, 0, ctx.stream>>>(cl, d, cr, U, A, rho);
+    ctx.count_launch();
+    ctx.check_launch("reduced_density_kernel");
 }
 
 }  // namespace vtn

@@ -33,7 +33,7 @@ namespace {
 
 constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
 // longest run of k-blocks summed in one FP32 tensor-memory accumulator (K = 64 * this)
-constexpr int MAX_KB_PER_ACC = 512;
+constexpr int MAX_KB_PER_ACC = 256;
 constexpr int A_TILE = BM * BK * 2;   // 16 KiB
 constexpr int B_TILE = BN * BK * 2;   // 32 KiB
 constexpr int STAGE_BYTES = A_TILE + B_TILE;

@@ -222,6 +222,114 @@ __global__ void __launch_bounds__(256) mix_f32_kernel(int P, int d, int Q, MixIn
         if (sp < d) y[(long long)sp * Q] = acc[sp];
 }
 
+// The same mixing with the input tile of every channel staged once in shared memory: block
+// (q tile, p) loads in[a][p][s][q0 .. q0 + 32) for all a < w_in, s < d (coalesced runs of 32
+// float2), then warp w computes output channels b = w, w + nwarps, ... from shared memory, all d
+// values s' of a channel in registers, lane = q.  Each input element is read from HBM once per
+// block instead of once per MPO entry that uses it, which is what the near-dense collapse core at
+// the centre of the chain (a w x w matrix of scaled identities) needs.  The entries of a channel
+// are fetched 32 at a time, one per lane, and broadcast with shuffles, so that the dependent
+// loads of one entry do not serialise the loop.
+constexpr int MIX_QT = 32;
+constexpr int MIX_TILED_THREADS = 512;
+
+template <int DM>
+__global__ void __launch_bounds__(MIX_TILED_THREADS, 1) mix_tiled_f32_kernel(
+    int P, int d, int Q, int w_in, int w_out, MixIn st, const int* __restrict__ ptr, const int* __restrict__ src,
+    const int* __restrict__ opi, const double2* __restrict__ ops, const unsigned char* __restrict__ ident,
+    const float2* __restrict__ in, float2* __restrict__ out) {
+    extern __shared__ float2 tile[];  // [w_in][d][MIX_QT]
+    const int p = blockIdx.y;
+    const int q0 = blockIdx.x * MIX_QT;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int nload = w_in * d * MIX_QT;
+    for (int i = threadIdx.x; i < nload; i += blockDim.x) {
+        const int qt = i % MIX_QT, as = i / MIX_QT;
+        const int s = as % d, a = as / d;
+        const int q = q0 + qt;
+        tile[i] = q < Q ? in[(long long)a * st.cs + (long long)p * st.ps + (long long)s * st.ss + q]
+                        : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const long long blk = (long long)P * d * Q;
+    const int q = q0 + lane;
+    for (int b = warp; b < w_out; b += nwarps) {
+        float2 acc[DM];
+#pragma unroll
+        for (int s = 0; s < DM; ++s) acc[s] = make_float2(0.f, 0.f);
+        const int e_begin = ptr[b], e_end = ptr[b + 1];
+        for (int e0 = e_begin; e0 < e_end; e0 += 32) {
+            // lane l holds entry e0 + l: source channel, operator index, identity flag and scalar
+            const int ne = min(32, e_end - e0);
+            int my_a = 0, my_k = 0, my_id = 1;
+            float my_cr = 0.f, my_ci = 0.f;
+            if (lane < ne) {
+                my_a = src[e0 + lane];
+                my_k = opi[e0 + lane];
+                my_id = ident[my_k];
+                const double2 c0 = ops[(long long)my_k * d * d];
+                my_cr = (float)c0.x;
+                my_ci = (float)c0.y;
+            }
+            for (int j = 0; j < ne; ++j) {
+                const int a = __shfl_sync(0xffffffffu, my_a, j);
+                const int idf = __shfl_sync(0xffffffffu, my_id, j);
+                const float2* x = tile + (a * d) * MIX_QT + lane;
+                if (idf) {
+                    const float cr = __shfl_sync(0xffffffffu, my_cr, j), ci = __shfl_sync(0xffffffffu, my_ci, j);
+#pragma unroll
+                    for (int s = 0; s < DM; ++s) {
+                        if (s < d) {
+                            const float2 v = x[s * MIX_QT];
+                            acc[s].x += cr * v.x - ci * v.y;
+                            acc[s].y += cr * v.y + ci * v.x;
+                        }
+                    }
+                } else {
+                    const int k = __shfl_sync(0xffffffffu, my_k, j);
+                    const double2* op = ops + (long long)k * d * d;
+                    float2 xv[DM];
+#pragma unroll
+                    for (int s = 0; s < DM; ++s) xv[s] = (s < d) ? x[s * MIX_QT] : make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int sp = 0; sp < DM; ++sp) {
+                        if (sp >= d) continue;
+#pragma unroll
+                        for (int s = 0; s < DM; ++s) {
+                            if (s < d) {
+                                const double2 c = op[sp * d + s];
+                                const float cr = (float)c.x, ci = (float)c.y;
+                                acc[sp].x += cr * xv[s].x - ci * xv[s].y;
+                                acc[sp].y += cr * xv[s].y + ci * xv[s].x;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (q < Q) {
+            float2* y = out + (long long)b * blk + (long long)p * d * Q + q;
+#pragma unroll
+            for (int sp = 0; sp < DM; ++sp)
+                if (sp < d) y[(long long)sp * Q] = acc[sp];
+        }
+    }
+}
+
+// largest dynamic shared memory a block of the tiled mixing kernel may take on this device
+int mix_tiled_smem_limit(const Ctx& ctx) {
+    static int limit[64] = {0};
+    const int dev = ctx.device;
+    if (dev >= 0 && dev < 64 && limit[dev] > 0) return limit[dev];
+    int optin = 0;
+    VTN_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    VTN_CUDA_TRY(cudaFuncGetAttributes(&fa, (const void*)mix_tiled_f32_kernel<16>));
+    const int l = optin - (int)fa.sharedSizeBytes;
+    if (dev >= 0 && dev < 64) limit[dev] = l;
+    return l;
+}
+
 // out[b][l][k] = T[l][b][k]  (T: rows l, row length nb * nk)
 __global__ void permute_blk(const double2* __restrict__ T, int nl, int nb, int nk, double2* __restrict__ out) {
     const long long cnt = (long long)nl * nb * nk;
@@ -302,6 +410,34 @@ void mix_apply_f32(Ctx& ctx, const DevCore& core, bool by_col, int P, int Q, con
         st.ss = in_strides[2];
     }
     int t = ctx.tbegin(TC_MIX, fl);
+    const int w_in = by_col ? core.wl : core.wr;
+    const size_t tile_bytes = sizeof(float2) * (size_t)w_in * d * MIX_QT;
+    // the tiled kernel pays off where output channels sum many entries (the near-dense collapse
+    // core): its warps own whole channels, so a channel with many dense d x d entries (the
+    // "completed" channel of the other cores) would serialise a block; those cores keep the
+    // per-channel kernel, which spreads every channel over many blocks
+    const int max_dense = by_col ? core.max_dense_col : core.max_dense_row;
+    const bool dense_core = (long long)core.nnz >= 4LL * w_out && max_dense <= 8;
+    if (dense_core && P <= 65535 && tile_bytes <= (size_t)mix_tiled_smem_limit(ctx)) {
+        dim3 g2((unsigned)((Q + MIX_QT - 1) / MIX_QT), (unsigned)P);
+        if (d <= 4) {
+            set_smem_attr_once(ctx, (const void*)mix_tiled_f32_kernel<4>, (int)tile_bytes);
+            mix_tiled_f32_kernel<4><<<g2, MIX_TILED_THREADS, tile_bytes, ctx.stream>>>(P, d, Q, w_in, w_out, st, ptr, src, opi,
+                                                                         core.ops, core.ident, in, out);
+        } else if (d <= 8) {
+            set_smem_attr_once(ctx, (const void*)mix_tiled_f32_kernel<8>, (int)tile_bytes);
+            mix_tiled_f32_kernel<8><<<g2, MIX_TILED_THREADS, tile_bytes, ctx.stream>>>(P, d, Q, w_in, w_out, st, ptr, src, opi,
+                                                                         core.ops, core.ident, in, out);
+        } else {
+            set_smem_attr_once(ctx, (const void*)mix_tiled_f32_kernel<16>, (int)tile_bytes);
+            mix_tiled_f32_kernel<16><<<g2, MIX_TILED_THREADS, tile_bytes, ctx.stream>>>(P, d, Q, w_in, w_out, st, ptr, src, opi,
+                                                                          core.ops, core.ident, in, out);
+        }
+        ctx.count_launch();
+        ctx.check_launch("mix_tiled_f32_kernel");
+        ctx.tend(t);
+        return;
+    }
     if (d <= 4)
         mix_f32_kernel<4><<<grid, 256, 0, ctx.stream>>>(P, d, Q, st, ptr, src, opi, core.ops, core.ident, in, out);
     else if (d <= 8)

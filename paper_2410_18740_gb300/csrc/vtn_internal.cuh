@@ -78,6 +78,9 @@ struct DevCore {
     unsigned char* ident = nullptr;  // [nnz]
     double flops_ident = 0, flops_dense = 0;  // counts for the flop model
     int n_ident = 0, n_dense = 0;
+    // per output channel, by column (left-to-right use) and by row: the largest number of
+    // dense (non-identity) entries
+    int max_dense_col = 0, max_dense_row = 0;
     std::vector<DevBuf> bufs;
 };
 
@@ -295,6 +298,8 @@ void orthonormalize_rows_small(Ctx& ctx, double2* A, int rows, int cols, const i
 void lbo_rotate_dev(Ctx& ctx, int chi_l, int d, int D, int chi_r, const double2* V, const double2* A,
                     double2* out);
 void set_scalar_one(Ctx& ctx, double2* p);
+// rho[s][t] = sum_{i, c} U[i][s][c] conj(A[i][t][c]) (d x d, device)
+void reduced_density_dev(Ctx& ctx, int cl, int d, int cr, const double2* U, const double2* A, double2* rho);
 void marginal_reduce_dev(Ctx& ctx, int chi_l, int D, int chi_r, const double2* AF, const double2* U, double* P);
 void sample_dev(Ctx& ctx, const double2* const* AF_dev, const double2* const* ER_dev, const int* dims_dev, int M,
                 int D, int chi_max, uint64_t seed, int n_samples, int* out_dev);

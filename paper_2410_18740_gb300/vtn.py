@@ -83,6 +83,14 @@ _SIGS = {
     "vtn_mps_random": [_P, _P, _I, C.c_uint64, C.POINTER(_P)],
     "vtn_mps_from_host": [_P, _P, _PI, C.POINTER(_PD), C.POINTER(_P)],
     "vtn_mps_random_center": [_P, _P, _I, C.c_uint64, _I, C.POINTER(_P)],
+    "vtn_mps_product": [_P, _P, _PD, C.POINTER(_P)],
+    "vtn_reduced_density": [_P, _P, _P, _I, _PD],
+    "vtn_warm_features": [_P, C.POINTER(C.c_float)],
+    "vtn_warm_targets": [_P, _P, _P, C.POINTER(C.c_float)],
+    "vtn_mlp_train": [_P, _P, _I, _P, _P, C.c_float, _I, C.POINTER(C.c_float)],
+    "vtn_sweep_batch": [_P, _I, C.POINTER(_P), C.POINTER(_P), C.POINTER(vtn_sweep_opts), C.POINTER(vtn_sweep_report),
+                        C.POINTER(C.c_int), _I],
+    "vtn_mps_warm_start": [_P, _P, _P, C.POINTER(_P)],
     "vtn_mps_get_center": [_P, _PI],
     "vtn_mps_set_center": [_P, _I],
     "vtn_mps_move_center": [_P, _P, _I],
@@ -325,6 +333,35 @@ def vtn_mps_random_center(ctx, mpo, chi, seed, center):
     return out
 
 
+def vtn_mps_product(ctx, mpo, amps):
+    """amps: complex array (M, d) of site vectors (normalised by the library)."""
+    a = _cplx_interleaved(amps)
+    out = C.c_void_p()
+    _check(ctx, lib().vtn_mps_product(ctx, mpo, a.ctypes.data_as(_PD), C.byref(out)))
+    return out
+
+
+def vtn_reduced_density(ctx, mpo, mps, site):
+    _, d, _, _ = vtn_mpo_info(mpo)
+    out = np.zeros((d, d, 2))
+    _check(ctx, lib().vtn_reduced_density(ctx, mpo, mps, int(site), out.ctypes.data_as(_PD)))
+    return out.view(np.complex128)[..., 0]
+
+
+def vtn_warm_features(mpo):
+    M = vtn_mpo_info(mpo)[0]
+    out = np.zeros((M, 4), np.float32)
+    _check(None, lib().vtn_warm_features(mpo, out.ctypes.data_as(C.POINTER(C.c_float))))
+    return out
+
+
+def vtn_warm_targets(ctx, mpo, mps):
+    M, d, _, _ = vtn_mpo_info(mpo)
+    out = np.zeros((M, 2 * d), np.float32)
+    _check(ctx, lib().vtn_warm_targets(ctx, mpo, mps, out.ctypes.data_as(C.POINTER(C.c_float))))
+    return out
+
+
 def vtn_mps_get_center(mps):
     c = C.c_int()
     _check(None, lib().vtn_mps_get_center(mps, C.byref(c)))
@@ -410,6 +447,22 @@ def vtn_sweep(ctx, mpo, state=None, opts=None, **kw):
     st = lib().vtn_sweep(ctx, mpo, C.byref(st_ptr), C.byref(opts), C.byref(rep))
     _check(ctx, st, ok=(VTN_OK, VTN_ENOCONV))
     return st, st_ptr, _report_dict(rep)
+
+
+def vtn_sweep_batch(ctx, mpos, states, opts, n_streams=8):
+    """Sweeps of many instances at once.  mpos: list of MPO handles; states: list of MPS handles or
+    None; opts: list of vtn_sweep_opts.  Returns (status, [per-instance status], [mps], [report])."""
+    n = len(mpos)
+    M_arr = (C.c_void_p * n)(*[m.value if isinstance(m, C.c_void_p) else m for m in mpos])
+    S_arr = (C.c_void_p * n)(*[(s.value if isinstance(s, C.c_void_p) else s) if s is not None else None
+                               for s in states])
+    O_arr = (vtn_sweep_opts * n)(*opts)
+    R_arr = (vtn_sweep_report * n)()
+    st_arr = (C.c_int * n)()
+    st = lib().vtn_sweep_batch(ctx, n, C.cast(M_arr, C.POINTER(_P)), C.cast(S_arr, C.POINTER(_P)), O_arr, R_arr,
+                               st_arr, int(n_streams))
+    _check(ctx, st, ok=(VTN_OK, VTN_ENOCONV))
+    return st, list(st_arr), [C.c_void_p(S_arr[j]) for j in range(n)], [_report_dict(R_arr[j]) for j in range(n)]
 
 
 def vtn_sweep_single_site(ctx, mpo, state=None, opts=None, alpha=1e-2, alpha_decay=0.5, cutoff=1e-12, **kw):
@@ -558,6 +611,19 @@ def vtn_mlp_train_step(ctx, mlp, batch, x, t, lr):
     loss = C.c_float()
     _check(ctx, lib().vtn_mlp_train_step(ctx, mlp, int(batch), _dptr(x), _dptr(t), float(lr), C.byref(loss)))
     return loss.value
+
+
+def vtn_mlp_train(ctx, mlp, batch, x, t, lr, steps):
+    """`steps` Adam steps on the batch; returns the loss before the last one."""
+    loss = C.c_float()
+    _check(ctx, lib().vtn_mlp_train(ctx, mlp, int(batch), _dptr(x), _dptr(t), float(lr), int(steps), C.byref(loss)))
+    return loss.value
+
+
+def vtn_mps_warm_start(ctx, mpo, mlp):
+    out = C.c_void_p()
+    _check(ctx, lib().vtn_mps_warm_start(ctx, mpo, mlp, C.byref(out)))
+    return out
 
 
 def vtn_heff_apply(ctx, Wi, Wj, chi_l, chi_r, L, R, theta, y, prec=VTN_FP64):

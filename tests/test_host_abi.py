@@ -268,3 +268,16 @@ def test_gaussian_bond_spectrum_large_blocks(libvtn):
             assert np.abs(got - ref).max() <= 1e-9 * ref[0]
     finally:
         vtn.vtn_mpo_free(m)
+
+
+@pytest.mark.parametrize("seed,M", [(0, 5), (1, 24)])
+def test_warm_features_against_oracle(libvtn, seed, M):
+    from oracle import warm
+    w = inputs.workload("split", seed, M=M)
+    m = vtn.vtn_build_mpo(None, w.r, w.U, 4, 4)
+    try:
+        f = vtn.vtn_warm_features(m)
+        fo = warm.features(gbs.covariance(w.r, w.U))
+        assert f.shape == (M, 4) and np.abs(f - fo).max() < 1e-6 * max(1.0, np.abs(fo).max())
+    finally:
+        vtn.vtn_mpo_free(m)
