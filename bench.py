@@ -101,6 +101,9 @@ def parse():
     p.add_argument("--warm-q", type=int, default=None,
                    help="also measure the optional warm-started truncation with this many subspace iterations "
                         "(trunc: beside the exact one; time-to-eps: a mixed run with it)")
+    p.add_argument("--heff-chi-l", type=int, default=None,
+                   help="heff: left bond dimension (default: the workload's chi); a small value keeps the "
+                        "per-block shapes of the middle bond at a fraction of its memory, for profiler captures")
     p.add_argument("--batch-streams", type=int, nargs="+", default=[8],
                    help="batch: worker streams of the batched run(s)")
     p.add_argument("--batch-serial", type=int, default=16,
@@ -906,6 +909,7 @@ def run_case_heff(args):
     rng = inputs.rng_for(7)
     if args.workload == "large":
         chi, d = LARGE_CHI, 6
+        chi_l = args.heff_chi_l or chi
         w = inputs.workload(LARGE, LARGE_SEED)
         m = vtn.vtn_build_mpo(None, w.r, w.U, w.D, w.d)
         cores = []
@@ -917,25 +921,26 @@ def run_case_heff(args):
         wl, wm, wr = Wi.w_left, Wi.w_right, Wj.w_right
     else:
         chi, d, wl, wm, wr = CHI, 8, 24, 26, 24
+        chi_l = args.heff_chi_l or chi
         Wi = vtn.core_from_sparse(inputs.random_sparse_core(wl, wm, d, rng, density=0.15))
         Wj = vtn.core_from_sparse(inputs.random_sparse_core(wm, wr, d, rng, density=0.15))
     dev = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.complex128)).cuda()
-    L = dev(inputs.random_complex((wl, chi, chi), rng))
+    L = dev(inputs.random_complex((wl, chi_l, chi_l), rng))
     R = dev(inputs.random_complex((wr, chi, chi), rng))
-    th = dev(inputs.random_complex((chi, d, d, chi), rng))
+    th = dev(inputs.random_complex((chi_l, d, d, chi), rng))
     y = torch.empty_like(th)
     ctx = vtn.vtn_create(0)
     prec = vtn.VTN_BF16X3 if args.prec == "bf16x3" else vtn.VTN_FP64
     for _ in range(2):
-        vtn.vtn_heff_apply(ctx, Wi, Wj, chi, chi, L, R, th, y, prec=prec)
+        vtn.vtn_heff_apply(ctx, Wi, Wj, chi_l, chi, L, R, th, y, prec=prec)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(3):
-        vtn.vtn_heff_apply(ctx, Wi, Wj, chi, chi, L, R, th, y, prec=prec)
+        vtn.vtn_heff_apply(ctx, Wi, Wj, chi_l, chi, L, R, th, y, prec=prec)
     torch.cuda.synchronize()
     el = (time.perf_counter() - t0) / 3
-    print(json.dumps({"case": "heff", "prec": args.prec, "shape": [wl, wm, wr, chi, d], "ms": 1e3 * el,
-                      "tflops": heff_flops(chi, chi, d, wl, wr) / el / 1e12}), flush=True)
+    print(json.dumps({"case": "heff", "prec": args.prec, "shape": [wl, wm, wr, chi_l, chi, d], "ms": 1e3 * el,
+                      "tflops": heff_flops(chi_l, chi, d, wl, wr) / el / 1e12}), flush=True)
     vtn.vtn_destroy(ctx)
 
 

@@ -229,6 +229,10 @@ typedef struct {
     double gemm_flops;         /* algorithmic real flops of every complex GEMM launch     */
     double gemm_seconds;       /* their device time (timing on)                           */
     double eig_seconds;        /* device time of the truncation eigensolver (timing on)   */
+    long long host_syncs;      /* times the call waited for the GPU (stream synchronisations):
+                                  with lanczos_max_restarts = 0 and the exact truncation, once
+                                  per sweep plus set-up and workspace growth; otherwise also
+                                  once per Lanczos step and per truncation                  */
 } vtn_sweep_report;
 
 /* Fill opts with the defaults: chi_max 16, 8 sweeps, FP64, lanczos_tol 1e-10,

@@ -363,6 +363,7 @@ vtn_status vtn_destroy(vtn_ctx ctx) {
     }
     for (auto e : c.event_pool) cudaEventDestroy(e);
     if (c.pinned) cudaFreeHost(c.pinned);
+    if (c.defer_buf) cudaFreeHost(c.defer_buf);
     delete ctx;
     return VTN_OK;
 }
@@ -801,6 +802,7 @@ vtn_status sweep_body(vtn_ctx work, vtn_ctx owner, vtn_mpo mpo, vtn_mps* state, 
         throw Error{VTN_EUNSUPPORTED, "VTN_TF32X3 is not available in this build"};
     const bool split = opts->prec == VTN_BF16X3;
     Ctx& c = work->c;
+    const long long syncs0 = c.host_syncs;
     use_device(c);
     ensure_mpo_device(owner, mpo);
     const int M = mpo->hp.M, d = mpo->hp.d;
@@ -872,6 +874,15 @@ vtn_status sweep_body(vtn_ctx work, vtn_ctx owner, vtn_mpo mpo, vtn_mps* state, 
         g.C = theta; g.ldc = (long long)d * cr;
         gemm_c64(c, g);
     };
+    // Without Lanczos restarts (and with the exact truncation) a sweep returns to the host only
+    // at its end: each Lanczos solve runs its Krylov steps on a device stop flag and the
+    // truncation's eigenvalues and status are staged in pinned memory, read once per sweep.
+    const bool deferred = opts->lanczos_max_restarts == 0 && opts->trunc_mode == 0;
+    const int steps_per_sweep = 2 * (hi - lo);
+    const size_t slot = (size_t)chi_cap + 16;  // 5 doubles of Lanczos results, then k + 5 of truncation
+    double* dbuf = deferred ? c.defer_reserve(slot * (size_t)steps_per_sweep) : nullptr;
+    std::vector<double> step_hf(steps_per_sweep, 0.0);
+    std::vector<int> step_k(steps_per_sweep, 0);
     for (int sw = 0; sw < opts->n_sweeps; ++sw) {
         const auto t0 = std::chrono::steady_clock::now();
         const int chi_s = sched[std::min<size_t>(sw, sched.size() - 1)];
@@ -880,6 +891,9 @@ vtn_status sweep_body(vtn_ctx work, vtn_ctx owner, vtn_mpo mpo, vtn_mps* state, 
             for (int step = 0; step < hi - lo; ++step) {
                 const int i = dir == 0 ? lo + step : (hi - 1 - step);
                 const int cl = mps->dims[i], cm = mps->dims[i + 1], cr = mps->dims[i + 2];
+                const int sidx = dir * (hi - lo) + step;
+                double* lz_slot = deferred ? dbuf + slot * sidx : nullptr;
+                double* tr_slot = deferred ? lz_slot + 5 : nullptr;
                 form_theta(i);
                 const long long n = (long long)cl * d * d * cr;
                 const DevCore& Wi = mpo->dcores[i];
@@ -893,10 +907,13 @@ vtn_status sweep_body(vtn_ctx work, vtn_ctx owner, vtn_mpo mpo, vtn_mps* state, 
                                            opts->lanczos_max_restarts, [&](const double2* in, double2* out) {
                                                if (split) heff_apply_bf16x3(c, Wi, Wj, pk, in, out);
                                                else heff_apply_dev(c, Wi, Wj, cl, cr, L, R, in, out);
-                                           });
-                rep.matvecs += lr.n_matvec;
-                rep.heff_flops += hf * lr.n_matvec;
-                if (!lr.converged) ++not_conv;
+                                           }, lz_slot);
+                step_hf[sidx] = hf;
+                if (!deferred) {
+                    rep.matvecs += lr.n_matvec;
+                    rep.heff_flops += hf * lr.n_matvec;
+                    if (!lr.converged) ++not_conv;
+                }
                 TruncResult tr;
                 if (opts->trunc_mode == 1) {
                     // warm start: the current centre (site i sweeping right, i + 1 sweeping left),
@@ -910,10 +927,11 @@ vtn_status sweep_body(vtn_ctx work, vtn_ctx owner, vtn_mpo mpo, vtn_mps* state, 
                     tr = truncate_warm_dev(c, cl, d, d, cr, dir, chi_s, theta, Sh0, cm, opts->trunc_q, 8, opts->seed,
                                            i, mps->sites[i], mps->sites[i + 1]);
                 } else {
-                    tr = truncate_dev(c, cl, d, d, cr, dir, chi_s, theta, mps->sites[i], mps->sites[i + 1]);
+                    tr = truncate_dev(c, cl, d, d, cr, dir, chi_s, theta, mps->sites[i], mps->sites[i + 1], -1, tr_slot);
                 }
                 mps->dims[i + 1] = tr.k;
-                disc_max = std::max(disc_max, tr.discarded);
+                step_k[sidx] = tr.k;
+                if (!deferred) disc_max = std::max(disc_max, tr.discarded);
                 if (dir == 0)
                     env_left(Wi, cl, tr.k, env.L[i], mps->sites[i], env.L[i + 1]);
                 else
@@ -947,6 +965,16 @@ vtn_status sweep_body(vtn_ctx work, vtn_ctx owner, vtn_mpo mpo, vtn_mps* state, 
             E = energy_dev(c, mpo, mps);
             c.sync();
         }
+        if (deferred) {
+            // the stream is synchronised: the staged results of this sweep are complete
+            for (int k = 0; k < steps_per_sweep; ++k) {
+                const LanczosResult lr = lanczos_deferred_result(dbuf + slot * k);
+                rep.matvecs += lr.n_matvec;
+                rep.heff_flops += step_hf[k] * lr.n_matvec;
+                if (!lr.converged) ++not_conv;
+                disc_max = std::max(disc_max, truncate_deferred_result(dbuf + slot * k + 5, step_k[k]).discarded);
+            }
+        }
         const auto t1 = std::chrono::steady_clock::now();
         rep.energy[sw] = E;
         rep.max_discarded[sw] = disc_max;
@@ -964,6 +992,7 @@ vtn_status sweep_body(vtn_ctx work, vtn_ctx owner, vtn_mpo mpo, vtn_mps* state, 
     rep.gemm_flops = c.tc[TC_GEMM].flops;
     rep.gemm_seconds = c.tc[TC_GEMM].seconds;
     rep.eig_seconds = c.tc[TC_EIG].seconds;
+    rep.host_syncs = c.host_syncs - syncs0;
     if (report) *report = rep;
     if (not_conv > 0) {
         c.err = std::to_string(not_conv) + " Lanczos solves missed the tolerance";

@@ -60,6 +60,19 @@ void* Ctx::workspace(int slot, size_t bytes) {
     return b.p;
 }
 
+double* Ctx::defer_reserve(size_t doubles) {
+    if (defer_cap < doubles) {
+        sync();
+        if (defer_buf) cudaFreeHost(defer_buf);
+        defer_buf = nullptr;
+        defer_cap = 0;
+        const size_t want = std::max(doubles, size_t(4096));
+        VTN_CUDA_TRY(cudaMallocHost((void**)&defer_buf, sizeof(double) * want));
+        defer_cap = want;
+    }
+    return defer_buf;
+}
+
 int Ctx::tbegin(int cls, double flops) {
     if (!timing) return -1;
     if (pending.size() > 4096 && open_intervals == 0) tflush();
@@ -151,55 +164,92 @@ void upload_core(Ctx& ctx, const HostCore& hc, DevCore& dc) {
     dc.d = hc.d;
     dc.nnz = hc.nnz();
     const int nnz = dc.nnz, d = hc.d;
-    std::vector<int> col_ptr(hc.wr + 1, 0), row_ptr(hc.wl + 1, 0);
-    for (int k = 0; k < nnz; ++k) {
-        col_ptr[hc.cols[k] + 1]++;
-        row_ptr[hc.rows[k] + 1]++;
-    }
-    for (int b = 0; b < hc.wr; ++b) col_ptr[b + 1] += col_ptr[b];
-    for (int a = 0; a < hc.wl; ++a) row_ptr[a + 1] += row_ptr[a];
-    std::vector<int> col_src(nnz), col_op(nnz), row_src(nnz), row_op(nnz);
-    std::vector<int> cfill(col_ptr.begin(), col_ptr.end() - 1), rfill(row_ptr.begin(), row_ptr.end() - 1);
-    for (int k = 0; k < nnz; ++k) {
-        int pc = cfill[hc.cols[k]]++;
-        col_src[pc] = hc.rows[k];
-        col_op[pc] = k;
-        int pr = rfill[hc.rows[k]]++;
-        row_src[pr] = hc.cols[k];
-        row_op[pr] = k;
-    }
+    // grouped index lists of a subset of the entries: by output column (ptr over wr) or row
+    auto group = [&](bool by_col, bool dense_only, std::vector<int>& ptr, std::vector<int>& src,
+                     std::vector<int>& op) {
+        const int w_out = by_col ? hc.wr : hc.wl;
+        ptr.assign(w_out + 1, 0);
+        for (int k = 0; k < nnz; ++k)
+            if (!dense_only || !hc.ident[k]) ptr[(by_col ? hc.cols[k] : hc.rows[k]) + 1]++;
+        for (int b = 0; b < w_out; ++b) ptr[b + 1] += ptr[b];
+        src.assign(std::max(ptr[w_out], 0), 0);
+        op.assign(src.size(), 0);
+        std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+        for (int k = 0; k < nnz; ++k) {
+            if (dense_only && hc.ident[k]) continue;
+            const int o = by_col ? hc.cols[k] : hc.rows[k];
+            const int pos = fill[o]++;
+            src[pos] = by_col ? hc.rows[k] : hc.cols[k];
+            op[pos] = k;
+        }
+    };
+    std::vector<int> col_ptr, col_src, col_op, row_ptr, row_src, row_op;
+    group(true, false, col_ptr, col_src, col_op);
+    group(false, false, row_ptr, row_src, row_op);
     dc.n_ident = 0;
     dc.n_dense = 0;
     for (int k = 0; k < nnz; ++k) (hc.ident[k] ? dc.n_ident : dc.n_dense)++;
-    {
-        std::vector<int> dcol(hc.wr, 0), drow(hc.wl, 0);
-        for (int k = 0; k < nnz; ++k)
-            if (!hc.ident[k]) {
-                dcol[hc.cols[k]]++;
-                drow[hc.rows[k]]++;
-            }
-        dc.max_dense_col = dcol.empty() ? 0 : *std::max_element(dcol.begin(), dcol.end());
-        dc.max_dense_row = drow.empty() ? 0 : *std::max_element(drow.begin(), drow.end());
+    // a core whose scaled-identity entries fill a large part of the w_l x w_r channel matrix (the
+    // collapse core at the centre of the chain) keeps them as a dense matrix C[a][b] as well, and
+    // its remaining entries as separate lists: its FP32 mixing is then a channel GEMM plus a
+    // sparse pass over the few dense d x d entries
+    dc.has_cid = dc.n_ident >= 4 * std::max(hc.wl, hc.wr);
+    std::vector<float> cid;
+    std::vector<int> dcp, dcs, dco, drp, drs, dro;
+    if (dc.has_cid) {
+        cid.assign((size_t)2 * hc.wl * hc.wr, 0.f);
+        dc.cid_real = true;
+        for (int k = 0; k < nnz; ++k) {
+            if (!hc.ident[k]) continue;
+            const cplx c = hc.ops[(size_t)k * d * d];
+            const size_t at = (size_t)hc.rows[k] * hc.wr + hc.cols[k];
+            cid[2 * at] += (float)c.real();
+            cid[2 * at + 1] += (float)c.imag();
+            if (c.imag() != 0.0) dc.cid_real = false;
+        }
+        group(true, true, dcp, dcs, dco);
+        group(false, true, drp, drs, dro);
     }
     // one allocation holding everything
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~size_t(255); return o; };
-    size_t o_cp = take(sizeof(int) * (hc.wr + 1)), o_cs = take(sizeof(int) * std::max(nnz, 1)),
-           o_co = take(sizeof(int) * std::max(nnz, 1)), o_rp = take(sizeof(int) * (hc.wl + 1)),
-           o_rs = take(sizeof(int) * std::max(nnz, 1)), o_ro = take(sizeof(int) * std::max(nnz, 1)),
-           o_ops = take(sizeof(double2) * std::max((size_t)nnz * d * d, size_t(1))),
-           o_id = take(std::max(nnz, 1));
+    auto ibytes = [](const std::vector<int>& v) { return sizeof(int) * std::max(v.size(), size_t(1)); };
+    const size_t o_cp = take(ibytes(col_ptr)), o_cs = take(ibytes(col_src)), o_co = take(ibytes(col_op)),
+                 o_rp = take(ibytes(row_ptr)), o_rs = take(ibytes(row_src)), o_ro = take(ibytes(row_op)),
+                 o_ops = take(sizeof(double2) * std::max((size_t)nnz * d * d, size_t(1))),
+                 o_id = take(std::max(nnz, 1)),
+                 o_f32 = take(sizeof(float) * 2 * std::max((size_t)nnz * d * d, size_t(1))),
+                 o_cid = take(sizeof(float) * std::max(cid.size(), size_t(1))), o_dcp = take(ibytes(dcp)),
+                 o_dcs = take(ibytes(dcs)), o_dco = take(ibytes(dco)), o_drp = take(ibytes(drp)),
+                 o_drs = take(ibytes(drs)), o_dro = take(ibytes(dro));
     std::vector<unsigned char> blob(off, 0);
-    std::memcpy(&blob[o_cp], col_ptr.data(), sizeof(int) * col_ptr.size());
+    auto put = [&](size_t o, const void* p, size_t bytes) {
+        if (bytes) std::memcpy(&blob[o], p, bytes);
+    };
+    auto puti = [&](size_t o, const std::vector<int>& v) { put(o, v.data(), sizeof(int) * v.size()); };
+    puti(o_cp, col_ptr);
+    puti(o_cs, col_src);
+    puti(o_co, col_op);
+    puti(o_rp, row_ptr);
+    puti(o_rs, row_src);
+    puti(o_ro, row_op);
     if (nnz) {
-        std::memcpy(&blob[o_cs], col_src.data(), sizeof(int) * nnz);
-        std::memcpy(&blob[o_co], col_op.data(), sizeof(int) * nnz);
-        std::memcpy(&blob[o_rs], row_src.data(), sizeof(int) * nnz);
-        std::memcpy(&blob[o_ro], row_op.data(), sizeof(int) * nnz);
-        std::memcpy(&blob[o_ops], hc.ops.data(), sizeof(double2) * (size_t)nnz * d * d);
-        std::memcpy(&blob[o_id], hc.ident.data(), nnz);
+        put(o_ops, hc.ops.data(), sizeof(double2) * (size_t)nnz * d * d);
+        put(o_id, hc.ident.data(), nnz);
+        std::vector<float> f32((size_t)nnz * d * d * 2);
+        for (size_t i = 0; i < (size_t)nnz * d * d; ++i) {
+            f32[2 * i] = (float)hc.ops[i].real();
+            f32[2 * i + 1] = (float)hc.ops[i].imag();
+        }
+        put(o_f32, f32.data(), sizeof(float) * f32.size());
     }
-    std::memcpy(&blob[o_rp], row_ptr.data(), sizeof(int) * row_ptr.size());
+    put(o_cid, cid.data(), sizeof(float) * cid.size());
+    puti(o_dcp, dcp);
+    puti(o_dcs, dcs);
+    puti(o_dco, dco);
+    puti(o_drp, drp);
+    puti(o_drs, drs);
+    puti(o_dro, dro);
     DevBuf b;
     b.bytes = off;
     b.p = ctx.dalloc(off);
@@ -214,6 +264,16 @@ void upload_core(Ctx& ctx, const HostCore& hc, DevCore& dc) {
     dc.row_op = (int*)(base + o_ro);
     dc.ops = (double2*)(base + o_ops);
     dc.ident = base + o_id;
+    dc.ops_f32 = (float2*)(base + o_f32);
+    if (dc.has_cid) {
+        dc.cid = (float2*)(base + o_cid);
+        dc.dcol_ptr = (int*)(base + o_dcp);
+        dc.dcol_src = (int*)(base + o_dcs);
+        dc.dcol_op = (int*)(base + o_dco);
+        dc.drow_ptr = (int*)(base + o_drp);
+        dc.drow_src = (int*)(base + o_drs);
+        dc.drow_op = (int*)(base + o_dro);
+    }
     dc.bufs.push_back(b);
 }
 

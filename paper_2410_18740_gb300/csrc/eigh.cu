@@ -1072,8 +1072,23 @@ __global__ void __launch_bounds__(BT_THREADS) backtransform(int n, int k, const 
 
 }  // namespace
 
+TruncResult truncate_deferred_result(const double* slot, int k) {
+    // slot: lam[k], tr(rho), then 8 status ints (4 doubles' worth)
+    TruncResult r;
+    r.k = k;
+    r.lam.assign(slot, slot + k);
+    const double tr = slot[k];
+    double kept = 0.0;
+    for (double l : r.lam) kept += l;
+    r.discarded = tr > 0 ? 1.0 - kept / tr : 0.0;
+    int st[8];
+    std::memcpy(st, slot + k + 1, sizeof(st));
+    if (st[6] != 0) throw Error{VTN_ETIMEOUT, "tridiagonalisation grid barrier timed out"};
+    return r;
+}
+
 TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int direction, int k_max,
-                         const double2* theta, double2* left, double2* right, int outer) {
+                         const double2* theta, double2* left, double2* right, int outer, double* defer) {
     const int nL = chi_l * d1, nR = d2 * chi_r;
     const int n = direction == 0 ? nL : nR;
     const int k = std::min(k_max, std::min(nL, nR));
@@ -1238,6 +1253,15 @@ TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int dir
     ctx.check_launch("back-transformation");
     ctx.tend(tt);
     // results to the host
+    if (defer != nullptr) {
+        VTN_CUDA_TRY(cudaMemcpyAsync(defer, s.lam, sizeof(double) * k, cudaMemcpyDeviceToHost, ctx.stream));
+        VTN_CUDA_TRY(cudaMemcpyAsync(defer + k, s.scal, sizeof(double), cudaMemcpyDeviceToHost, ctx.stream));
+        VTN_CUDA_TRY(cudaMemcpyAsync(defer + k + 1, status, sizeof(int) * 8, cudaMemcpyDeviceToHost, ctx.stream));
+        TruncResult r;
+        r.k = k;
+        r.discarded = 0.0;
+        return r;
+    }
     VTN_CUDA_TRY(cudaMemcpyAsync(ctx.pinned, s.lam, sizeof(double) * k, cudaMemcpyDeviceToHost, ctx.stream));
     VTN_CUDA_TRY(cudaMemcpyAsync(ctx.pinned + k, s.scal, sizeof(double), cudaMemcpyDeviceToHost, ctx.stream));
     VTN_CUDA_TRY(cudaMemcpyAsync(ctx.pinned + k + 1, status, sizeof(int) * 8, cudaMemcpyDeviceToHost, ctx.stream));

@@ -46,8 +46,10 @@ __device__ double block_sum(double v, double* sh) {
 // butterfly reduce-scatter per warp (lane l ends with value l) and one shared-memory pass.
 __global__ void __launch_bounds__(RB) multi_dot_partial(const double2* __restrict__ V, long long ld, int g0,
                                                         int cnt, const double2* __restrict__ w, long long n,
-                                                        double2* __restrict__ partial, int nv_stride) {
+                                                        double2* __restrict__ partial, int nv_stride,
+                                                        const int* __restrict__ stop) {
     static_assert(2 * DOT_GROUP <= 32, "one butterfly holds at most 32 values");
+    if (stop && *stop) return;
     __shared__ double sh[RB / 32][32];
     double v[32];
 #pragma unroll
@@ -79,7 +81,8 @@ __global__ void __launch_bounds__(RB) multi_dot_partial(const double2* __restric
 
 // out[i] = sum_blk partial[blk][i] (one block per i, fixed order)
 __global__ void __launch_bounds__(RB) reduce_partials(const double2* __restrict__ partial, int nblk, int nv_stride,
-                                                      double2* __restrict__ out) {
+                                                      double2* __restrict__ out, const int* __restrict__ stop) {
+    if (stop && *stop) return;
     __shared__ double sh[32];
     const int i = blockIdx.x;
     double re = 0.0, im = 0.0;
@@ -96,7 +99,8 @@ __global__ void __launch_bounds__(RB) reduce_partials(const double2* __restrict_
 // w[e] -= sum_i V[i][e] c[i]
 __global__ void __launch_bounds__(RB) multi_axpy_kernel(const double2* __restrict__ V, long long ld, int nv,
                                                         const double2* __restrict__ c, double2* __restrict__ w,
-                                                        long long n) {
+                                                        long long n, const int* __restrict__ stop) {
+    if (stop && *stop) return;
     __shared__ double2 cs[KMAX_DEV];
     for (int i = threadIdx.x; i < nv; i += RB) cs[i] = c[i];
     __syncthreads();
@@ -112,9 +116,11 @@ __global__ void __launch_bounds__(RB) multi_axpy_kernel(const double2* __restric
     }
 }
 
+// nv_dev (may be null): the number of vectors read from the device instead of nv
 __global__ void __launch_bounds__(RB) lincomb_real_kernel(const double2* __restrict__ V, long long ld, int nv,
                                                           const double* __restrict__ y, double2* __restrict__ out,
-                                                          long long n) {
+                                                          long long n, const int* __restrict__ nv_dev) {
+    if (nv_dev) nv = *nv_dev;
     __shared__ double ys[KMAX_DEV];
     for (int i = threadIdx.x; i < nv; i += RB) ys[i] = y[i];
     __syncthreads();
@@ -130,7 +136,8 @@ __global__ void __launch_bounds__(RB) lincomb_real_kernel(const double2* __restr
 }
 
 __global__ void __launch_bounds__(RB) norm2_partial(const double2* __restrict__ x, long long n,
-                                                    double* __restrict__ partial) {
+                                                    double* __restrict__ partial, const int* __restrict__ stop) {
+    if (stop && *stop) return;
     __shared__ double sh[32];
     double acc = 0.0;
     for (long long e = (long long)blockIdx.x * RB + threadIdx.x; e < n; e += (long long)gridDim.x * RB) {
@@ -142,7 +149,8 @@ __global__ void __launch_bounds__(RB) norm2_partial(const double2* __restrict__ 
 }
 
 __global__ void __launch_bounds__(RB) reduce_real(const double* __restrict__ partial, int nblk,
-                                                  double* __restrict__ out) {
+                                                  double* __restrict__ out, const int* __restrict__ stop) {
+    if (stop && *stop) return;
     __shared__ double sh[32];
     double acc = 0.0;
     for (int b = threadIdx.x; b < nblk; b += RB) acc += partial[b];
@@ -174,7 +182,9 @@ struct LzState {
     double resid;
     double scratch;
     int flag;            // 0 continue, 1 converged, 2 breakdown, 3 last iteration
-    int pad[3];
+    int stop;            // set (and kept) once an iteration's flag is non-zero
+    int m_stop;          // Krylov dimension at that iteration
+    int pad;
 };
 
 __device__ int sturm_count(const double* a, const double* b, int m, double x, double pivmin) {
@@ -195,6 +205,7 @@ __device__ int sturm_count(const double* a, const double* b, int m, double x, do
 __global__ void ritz_kernel(LzState* st, int m, double tol, double breakdown, int last) {
     __shared__ double lo_s, hi_s;
     const int lane = threadIdx.x;
+    if (st->stop) return;  // an earlier iteration ended the recursion (device-driven loop)
     const double* a = st->alpha;
     const double* b = st->beta;
     if (lane == 0) st->alpha[m - 1] = st->c1[m - 1].x;
@@ -298,6 +309,10 @@ __global__ void ritz_kernel(LzState* st, int m, double tol, double breakdown, in
     else if (last) flag = 3;
     st->flag = flag;
     if (flag == 0) st->beta[m - 1] = bj;
+    else {
+        st->stop = 1;
+        st->m_stop = m;
+    }
 }
 
 int reduction_blocks(const Ctx& ctx, long long n) {
@@ -308,36 +323,39 @@ int reduction_blocks(const Ctx& ctx, long long n) {
 
 }  // namespace
 
-void multi_dot(Ctx& ctx, const double2* V, long long ld, int nv, const double2* w, long long n, double2* dots) {
+void multi_dot(Ctx& ctx, const double2* V, long long ld, int nv, const double2* w, long long n, double2* dots,
+               const int* stop) {
     const int nblk = reduction_blocks(ctx, n);
     double2* partial = (double2*)ctx.workspace(WS_PARTIAL, sizeof(double2) * (size_t)nblk * KMAX_DEV);
     for (int g0 = 0; g0 < nv; g0 += DOT_GROUP) {
         const int cnt = std::min(DOT_GROUP, nv - g0);
-        multi_dot_partial<<<nblk, RB, 0, ctx.stream>>>(V, ld, g0, cnt, w, n, partial, KMAX_DEV);
+        multi_dot_partial<<<nblk, RB, 0, ctx.stream>>>(V, ld, g0, cnt, w, n, partial, KMAX_DEV, stop);
         ctx.count_launch();
     }
-    reduce_partials<<<nv, RB, 0, ctx.stream>>>(partial, nblk, KMAX_DEV, dots);
+    reduce_partials<<<nv, RB, 0, ctx.stream>>>(partial, nblk, KMAX_DEV, dots, stop);
     ctx.count_launch();
     ctx.check_launch("multi_dot");
 }
 
-void multi_axpy(Ctx& ctx, const double2* V, long long ld, int nv, const double2* c, double2* w, long long n) {
-    multi_axpy_kernel<<<reduction_blocks(ctx, n), RB, 0, ctx.stream>>>(V, ld, nv, c, w, n);
+void multi_axpy(Ctx& ctx, const double2* V, long long ld, int nv, const double2* c, double2* w, long long n,
+                const int* stop) {
+    multi_axpy_kernel<<<reduction_blocks(ctx, n), RB, 0, ctx.stream>>>(V, ld, nv, c, w, n, stop);
     ctx.count_launch();
     ctx.check_launch("multi_axpy");
 }
 
-void lincomb_real(Ctx& ctx, const double2* V, long long ld, int nv, const double* y, double2* out, long long n) {
-    lincomb_real_kernel<<<reduction_blocks(ctx, n), RB, 0, ctx.stream>>>(V, ld, nv, y, out, n);
+void lincomb_real(Ctx& ctx, const double2* V, long long ld, int nv, const double* y, double2* out, long long n,
+                  const int* nv_dev) {
+    lincomb_real_kernel<<<reduction_blocks(ctx, n), RB, 0, ctx.stream>>>(V, ld, nv, y, out, n, nv_dev);
     ctx.count_launch();
     ctx.check_launch("lincomb_real");
 }
 
-void norm2_dev(Ctx& ctx, const double2* x, long long n, double* out) {
+void norm2_dev(Ctx& ctx, const double2* x, long long n, double* out, const int* stop) {
     const int nblk = reduction_blocks(ctx, n);
     double* partial = (double*)ctx.workspace(WS_MISC, sizeof(double) * (size_t)nblk);
-    norm2_partial<<<nblk, RB, 0, ctx.stream>>>(x, n, partial);
-    reduce_real<<<1, RB, 0, ctx.stream>>>(partial, nblk, out);
+    norm2_partial<<<nblk, RB, 0, ctx.stream>>>(x, n, partial, stop);
+    reduce_real<<<1, RB, 0, ctx.stream>>>(partial, nblk, out, stop);
     ctx.count_launch(2);
     ctx.check_launch("norm2");
 }
@@ -348,8 +366,19 @@ void scale_inv_sqrt(Ctx& ctx, double2* x, long long n, const double* nrm2) {
     ctx.check_launch("scale");
 }
 
+LanczosResult lanczos_deferred_result(const double* slot) {
+    // slot: theta, resid, scratch (doubles), then flag, stop, m_stop, pad (ints)
+    int ints[4];
+    std::memcpy(ints, slot + 3, sizeof(ints));
+    LanczosResult r;
+    r.theta = slot[0];
+    r.n_matvec = ints[2];
+    r.converged = ints[0] == 1 || ints[0] == 2;
+    return r;
+}
+
 LanczosResult lanczos(Ctx& ctx, long long n, double2* x, double tol, int kmax, int restarts,
-                      const std::function<void(const double2*, double2*)>& matvec) {
+                      const std::function<void(const double2*, double2*)>& matvec, double* defer) {
     VTN_REQUIRE(kmax >= 1 && kmax <= KMAX_DEV, "krylov_max must be in [1, 64]");
     VTN_REQUIRE(restarts >= 0, "negative restart count");
     double2* V = (double2*)ctx.workspace(WS_KRYLOV, sizeof(double2) * (size_t)n * kmax);
@@ -363,9 +392,40 @@ LanczosResult lanczos(Ctx& ctx, long long n, double2* x, double tol, int kmax, i
     ctx.count_launch();
     LanczosResult res{0.0, 0, false};
     const double breakdown = 1e-14;
+    if (defer != nullptr && restarts == 0) {
+        // device-driven: all kmax steps queued; the stop flag set by ritz_kernel ends the
+        // recursion on the device, and the Ritz vector is built from the first m_stop vectors
+        const int* stop = &st->stop;
+        for (int j = 0; j < kmax; ++j) {
+            matvec(V + (size_t)j * n, W);
+            int tl = ctx.tbegin(TC_LANCZOS, 0.0);
+            multi_dot(ctx, V, n, j + 1, W, n, st->c1, stop);
+            multi_axpy(ctx, V, n, j + 1, st->c1, W, n, stop);
+            multi_dot(ctx, V, n, j + 1, W, n, st->c2, stop);
+            multi_axpy(ctx, V, n, j + 1, st->c2, W, n, stop);
+            norm2_dev(ctx, W, n, &st->beta2, stop);
+            ritz_kernel<<<1, 32, 0, ctx.stream>>>(st, j + 1, tol, breakdown, j == kmax - 1 ? 1 : 0);
+            ctx.count_launch();
+            if (j + 1 < kmax) {
+                scale_kernel<<<nblk, RB, 0, ctx.stream>>>(V + (size_t)(j + 1) * n, n, &st->beta2, &st->flag, W);
+                ctx.count_launch();
+            }
+            ctx.tend(tl);
+            ctx.check_launch("lanczos iteration");
+        }
+        lincomb_real(ctx, V, n, kmax, st->y, x, n, &st->m_stop);
+        norm2_dev(ctx, x, n, &st->scratch);
+        scale_inv_sqrt(ctx, x, n, &st->scratch);
+        VTN_CUDA_TRY(cudaMemcpyAsync(defer, &st->theta, 3 * sizeof(double) + 4 * sizeof(int), cudaMemcpyDeviceToHost,
+                                     ctx.stream));
+        res.n_matvec = kmax;
+        return res;
+    }
     for (int rs = 0; rs <= restarts; ++rs) {
         int m = 0;
         int flag = 0;
+        // the stop flag of the previous pass must not end this one (ritz_kernel returns early on it)
+        VTN_CUDA_TRY(cudaMemsetAsync(&st->stop, 0, 2 * sizeof(int), ctx.stream));
         for (int j = 0; j < kmax; ++j) {
             double2* vj = V + (size_t)j * n;
             matvec(vj, W);

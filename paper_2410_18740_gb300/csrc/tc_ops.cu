@@ -151,9 +151,10 @@ struct MixIn {
 template <int DM>
 __global__ void __launch_bounds__(256) mix_f32_kernel(int P, int d, int Q, MixIn st, const int* __restrict__ ptr,
                                                       const int* __restrict__ src, const int* __restrict__ opi,
-                                                      const double2* __restrict__ ops,
+                                                      const float2* __restrict__ ops,
                                                       const unsigned char* __restrict__ ident,
-                                                      const float2* __restrict__ in, float2* __restrict__ out) {
+                                                      const float2* __restrict__ in, float2* __restrict__ out,
+                                                      int accumulate) {
     __shared__ float2 op_sh[MIX_SH];
     __shared__ int src_sh[MIX_SH / 4];
     __shared__ unsigned char id_sh[MIX_SH / 4];
@@ -169,13 +170,13 @@ __global__ void __launch_bounds__(256) mix_f32_kernel(int P, int d, int Q, MixIn
 #pragma unroll
     for (int s = 0; s < DM; ++s) acc[s] = make_float2(0.f, 0.f);
     const int e_begin = ptr[b], e_end = ptr[b + 1];
+    if (accumulate && e_begin == e_end) return;  // nothing to add to this channel
     for (int e0 = e_begin; e0 < e_end; e0 += chunk) {
         const int ne = min(chunk, e_end - e0);
         __syncthreads();
         for (int i = threadIdx.x; i < ne * dd; i += blockDim.x) {
             const int e = i / dd, j = i - e * dd;
-            const double2 o = ops[(long long)opi[e0 + e] * dd + j];
-            op_sh[i] = make_float2((float)o.x, (float)o.y);
+            op_sh[i] = ops[(long long)opi[e0 + e] * dd + j];
         }
         for (int e = threadIdx.x; e < ne; e += blockDim.x) {
             src_sh[e] = src[e0 + e];
@@ -218,116 +219,121 @@ __global__ void __launch_bounds__(256) mix_f32_kernel(int P, int d, int Q, MixIn
     if (!active) return;
     float2* y = out + (long long)b * blk + pp * d * Q + q;
 #pragma unroll
-    for (int sp = 0; sp < DM; ++sp)
-        if (sp < d) y[(long long)sp * Q] = acc[sp];
+    for (int sp = 0; sp < DM; ++sp) {
+        if (sp < d) {
+            if (accumulate) {
+                const float2 o = y[(long long)sp * Q];
+                acc[sp].x += o.x;
+                acc[sp].y += o.y;
+            }
+            y[(long long)sp * Q] = acc[sp];
+        }
+    }
 }
 
-// The same mixing with the input tile of every channel staged once in shared memory: block
-// (q tile, p) loads in[a][p][s][q0 .. q0 + 32) for all a < w_in, s < d (coalesced runs of 32
-// float2), then warp w computes output channels b = w, w + nwarps, ... from shared memory, all d
-// values s' of a channel in registers, lane = q.  Each input element is read from HBM once per
-// block instead of once per MPO entry that uses it, which is what the near-dense collapse core at
-// the centre of the chain (a w x w matrix of scaled identities) needs.  The entries of a channel
-// are fetched 32 at a time, one per lane, and broadcast with shuffles, so that the dependent
-// loads of one entry do not serialise the loop.
-constexpr int MIX_QT = 32;
-constexpr int MIX_TILED_THREADS = 512;
-
-template <int DM>
-__global__ void __launch_bounds__(MIX_TILED_THREADS, 1) mix_tiled_f32_kernel(
-    int P, int d, int Q, int w_in, int w_out, MixIn st, const int* __restrict__ ptr, const int* __restrict__ src,
-    const int* __restrict__ opi, const double2* __restrict__ ops, const unsigned char* __restrict__ ident,
-    const float2* __restrict__ in, float2* __restrict__ out) {
-    extern __shared__ float2 tile[];  // [w_in][d][MIX_QT]
-    const int p = blockIdx.y;
-    const int q0 = blockIdx.x * MIX_QT;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int nload = w_in * d * MIX_QT;
-    for (int i = threadIdx.x; i < nload; i += blockDim.x) {
-        const int qt = i % MIX_QT, as = i / MIX_QT;
-        const int s = as % d, a = as / d;
-        const int q = q0 + qt;
-        tile[i] = q < Q ? in[(long long)a * st.cs + (long long)p * st.ps + (long long)s * st.ss + q]
-                        : make_float2(0.f, 0.f);
+// The scaled-identity part of a collapse core as a channel GEMM: out[b][e] = sum_a C[a][b] in[a][e]
+// for every element e of the standard layout (e = (p, s, q), contiguous per channel).
+// Persistent: one CTA of 256 threads per SM walks element tiles of ET; C (w_in x w_out) stays in
+// shared memory, and the next tile of every input channel is copied by cp.async into the second
+// buffer while the current one is used.  Thread (tb, te) accumulates channels b = tb + 16 j
+// (j < JB) and elements e = te + 16 i (i < EI) in registers, so each shared-memory load feeds
+// JB or EI FMAs; a real C (the GBS couplings) takes 2 FMAs per complex product.
+template <int JB, int EI, bool REAL_C>
+__global__ void __launch_bounds__(256, 1) mix_cid_kernel(int w_in, int w_out, long long E, const float2* __restrict__ C,
+                                                         const float2* __restrict__ in, float2* __restrict__ out) {
+    constexpr int ET = 16 * EI;
+    extern __shared__ float2 sh[];
+    float2* Csh = sh;                                // [w_in][16 JB]
+    float2* buf0 = Csh + (size_t)w_in * 16 * JB;     // [w_in][ET] x 2
+    float2* buf1 = buf0 + (size_t)w_in * ET;
+    const int wpad = 16 * JB;
+    for (int t = threadIdx.x; t < w_in * wpad; t += blockDim.x) {
+        const int a = t / wpad, b = t - (t / wpad) * wpad;
+        Csh[t] = b < w_out ? C[(long long)a * w_out + b] : make_float2(0.f, 0.f);
     }
-    __syncthreads();
-    const long long blk = (long long)P * d * Q;
-    const int q = q0 + lane;
-    for (int b = warp; b < w_out; b += nwarps) {
-        float2 acc[DM];
-#pragma unroll
-        for (int s = 0; s < DM; ++s) acc[s] = make_float2(0.f, 0.f);
-        const int e_begin = ptr[b], e_end = ptr[b + 1];
-        for (int e0 = e_begin; e0 < e_end; e0 += 32) {
-            // lane l holds entry e0 + l: source channel, operator index, identity flag and scalar
-            const int ne = min(32, e_end - e0);
-            int my_a = 0, my_k = 0, my_id = 1;
-            float my_cr = 0.f, my_ci = 0.f;
-            if (lane < ne) {
-                my_a = src[e0 + lane];
-                my_k = opi[e0 + lane];
-                my_id = ident[my_k];
-                const double2 c0 = ops[(long long)my_k * d * d];
-                my_cr = (float)c0.x;
-                my_ci = (float)c0.y;
+    const int tb = threadIdx.x & 15, te = threadIdx.x >> 4;
+    const long long n_tiles = (E + ET - 1) / ET;
+    // cp.async of tile `tile` into `dst`: rows a of ET float2, 16 bytes (2 elements) per thread
+    // when every row starts 16-byte aligned (E even), else 8 bytes; zero-filled past E
+    const bool pairs = (E & 1) == 0;
+    auto load = [&](long long tile, float2* dst) {
+        const long long e0 = tile * ET;
+        if (pairs) {
+            constexpr int per_row = ET / 2;
+            for (int t = threadIdx.x; t < w_in * per_row; t += blockDim.x) {
+                const int a = t / per_row, c = t - (t / per_row) * per_row;
+                const long long e = e0 + 2 * c;
+                const int bytes = e + 1 < E ? 16 : (e < E ? 8 : 0);
+                const float2* g = in + (long long)a * E + (bytes > 0 ? e : 0);
+                const unsigned s_addr = (unsigned)__cvta_generic_to_shared(dst + (size_t)a * ET + 2 * c);
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(s_addr), "l"(g), "r"(bytes)
+                             : "memory");
             }
-            for (int j = 0; j < ne; ++j) {
-                const int a = __shfl_sync(0xffffffffu, my_a, j);
-                const int idf = __shfl_sync(0xffffffffu, my_id, j);
-                const float2* x = tile + (a * d) * MIX_QT + lane;
-                if (idf) {
-                    const float cr = __shfl_sync(0xffffffffu, my_cr, j), ci = __shfl_sync(0xffffffffu, my_ci, j);
+        } else {
+            for (int t = threadIdx.x; t < w_in * ET; t += blockDim.x) {
+                const int a = t / ET, c = t - (t / ET) * ET;
+                const long long e = e0 + c;
+                const int bytes = e < E ? 8 : 0;
+                const float2* g = in + (long long)a * E + (bytes > 0 ? e : 0);
+                const unsigned s_addr = (unsigned)__cvta_generic_to_shared(dst + (size_t)a * ET + c);
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s_addr), "l"(g), "r"(bytes)
+                             : "memory");
+            }
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    long long tile = blockIdx.x;
+    if (tile < n_tiles) load(tile, buf0);
+    int cur = 0;
+    for (; tile < n_tiles; tile += gridDim.x) {
+        const long long next = tile + gridDim.x;
+        float2* bc = cur ? buf1 : buf0;
+        float2* bn = cur ? buf0 : buf1;
+        if (next < n_tiles) {
+            load(next, bn);
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        }
+        __syncthreads();
+        float2 acc[JB][EI];
 #pragma unroll
-                    for (int s = 0; s < DM; ++s) {
-                        if (s < d) {
-                            const float2 v = x[s * MIX_QT];
-                            acc[s].x += cr * v.x - ci * v.y;
-                            acc[s].y += cr * v.y + ci * v.x;
-                        }
-                    }
-                } else {
-                    const int k = __shfl_sync(0xffffffffu, my_k, j);
-                    const double2* op = ops + (long long)k * d * d;
-                    float2 xv[DM];
+        for (int j = 0; j < JB; ++j)
 #pragma unroll
-                    for (int s = 0; s < DM; ++s) xv[s] = (s < d) ? x[s * MIX_QT] : make_float2(0.f, 0.f);
+            for (int i = 0; i < EI; ++i) acc[j][i] = make_float2(0.f, 0.f);
+        for (int a = 0; a < w_in; ++a) {
+            float2 c[JB], x[EI];
 #pragma unroll
-                    for (int sp = 0; sp < DM; ++sp) {
-                        if (sp >= d) continue;
+            for (int j = 0; j < JB; ++j) c[j] = Csh[a * wpad + tb + 16 * j];
 #pragma unroll
-                        for (int s = 0; s < DM; ++s) {
-                            if (s < d) {
-                                const double2 c = op[sp * d + s];
-                                const float cr = (float)c.x, ci = (float)c.y;
-                                acc[sp].x += cr * xv[s].x - ci * xv[s].y;
-                                acc[sp].y += cr * xv[s].y + ci * xv[s].x;
-                            }
-                        }
+            for (int i = 0; i < EI; ++i) x[i] = bc[(size_t)a * ET + te + 16 * i];
+#pragma unroll
+            for (int j = 0; j < JB; ++j)
+#pragma unroll
+                for (int i = 0; i < EI; ++i) {
+                    acc[j][i].x = fmaf(c[j].x, x[i].x, acc[j][i].x);
+                    acc[j][i].y = fmaf(c[j].x, x[i].y, acc[j][i].y);
+                    if (!REAL_C) {
+                        acc[j][i].x = fmaf(-c[j].y, x[i].y, acc[j][i].x);
+                        acc[j][i].y = fmaf(c[j].y, x[i].x, acc[j][i].y);
                     }
                 }
+        }
+        const long long e0 = tile * ET;
+#pragma unroll
+        for (int j = 0; j < JB; ++j) {
+            const int b = tb + 16 * j;
+            if (b >= w_out) continue;
+#pragma unroll
+            for (int i = 0; i < EI; ++i) {
+                const long long e = e0 + te + 16 * i;
+                if (e < E) out[(long long)b * E + e] = acc[j][i];
             }
         }
-        if (q < Q) {
-            float2* y = out + (long long)b * blk + (long long)p * d * Q + q;
-#pragma unroll
-            for (int sp = 0; sp < DM; ++sp)
-                if (sp < d) y[(long long)sp * Q] = acc[sp];
-        }
+        __syncthreads();  // the buffer just read is the next prefetch target
+        cur ^= 1;
     }
-}
-
-// largest dynamic shared memory a block of the tiled mixing kernel may take on this device
-int mix_tiled_smem_limit(const Ctx& ctx) {
-    static int limit[64] = {0};
-    const int dev = ctx.device;
-    if (dev >= 0 && dev < 64 && limit[dev] > 0) return limit[dev];
-    int optin = 0;
-    VTN_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    cudaFuncAttributes fa;
-    VTN_CUDA_TRY(cudaFuncGetAttributes(&fa, (const void*)mix_tiled_f32_kernel<16>));
-    const int l = optin - (int)fa.sharedSizeBytes;
-    if (dev >= 0 && dev < 64) limit[dev] = l;
-    return l;
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
 // out[b][l][k] = T[l][b][k]  (T: rows l, row length nb * nk)
@@ -339,6 +345,47 @@ __global__ void permute_blk(const double2* __restrict__ T, int nl, int nb, int n
     const long long r = t / nk;
     const int l = (int)(r % nl), b = (int)(r / nl);
     out[t] = T[((long long)l * nb + b) * nk + k];
+}
+
+// largest dynamic shared memory a block may take on the context's device
+int mix_smem_limit(const Ctx& ctx) {
+    static int limit[64] = {0};
+    const int dev = ctx.device;
+    if (dev >= 0 && dev < 64 && limit[dev] > 0) return limit[dev];
+    int optin = 0;
+    VTN_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (dev >= 0 && dev < 64) limit[dev] = optin;
+    return optin;
+}
+
+template <int JB, int EI, bool R>
+void launch_mix_cid_t(Ctx& ctx, int bytes, unsigned grid, int w_in, int w_out, long long E, const float2* C,
+                      const float2* in, float2* out) {
+    set_smem_attr_once(ctx, (const void*)mix_cid_kernel<JB, EI, R>, bytes);
+    mix_cid_kernel<JB, EI, R><<<grid, 256, bytes, ctx.stream>>>(w_in, w_out, E, C, in, out);
+    ctx.count_launch();
+}
+
+template <int JB>
+void launch_mix_cid_j(Ctx& ctx, int EI, bool real_c, int bytes, unsigned grid, int w_in, int w_out, long long E,
+                      const float2* C, const float2* in, float2* out) {
+    if (EI == 4) {
+        if (real_c) launch_mix_cid_t<JB, 4, true>(ctx, bytes, grid, w_in, w_out, E, C, in, out);
+        else launch_mix_cid_t<JB, 4, false>(ctx, bytes, grid, w_in, w_out, E, C, in, out);
+    } else {
+        if (real_c) launch_mix_cid_t<JB, 2, true>(ctx, bytes, grid, w_in, w_out, E, C, in, out);
+        else launch_mix_cid_t<JB, 2, false>(ctx, bytes, grid, w_in, w_out, E, C, in, out);
+    }
+}
+
+void launch_mix_cid(Ctx& ctx, int JB, int EI, bool real_c, int bytes, unsigned grid, int w_in, int w_out, long long E,
+                    const float2* C, const float2* in, float2* out) {
+    switch (JB) {
+        case 2: launch_mix_cid_j<2>(ctx, EI, real_c, bytes, grid, w_in, w_out, E, C, in, out); break;
+        case 4: launch_mix_cid_j<4>(ctx, EI, real_c, bytes, grid, w_in, w_out, E, C, in, out); break;
+        case 7: launch_mix_cid_j<7>(ctx, EI, real_c, bytes, grid, w_in, w_out, E, C, in, out); break;
+        default: launch_mix_cid_j<8>(ctx, EI, real_c, bytes, grid, w_in, w_out, E, C, in, out); break;
+    }
 }
 
 long long k6(long long Kt) { return ((6 * Kt + 63) / 64) * 64; }
@@ -396,7 +443,7 @@ void mix_apply_f32(Ctx& ctx, const DevCore& core, bool by_col, int P, int Q, con
     if (PQ == 0) return;
     VTN_REQUIRE(w_out <= 65535, "too many MPO channels");
     dim3 grid((unsigned)((PQ + 255) / 256), w_out);
-    const int* ptr = by_col ? core.col_ptr : core.row_ptr;
+    const int* ptr = by_col ? core.col_ptr : core.row_ptr;  // reassigned to the dense-only lists of a collapse core
     const int* src = by_col ? core.col_src : core.row_src;
     const int* opi = by_col ? core.col_op : core.row_op;
     double fl = 8.0 * PQ * ((double)core.n_ident * d + (double)core.n_dense * d * d);
@@ -410,40 +457,39 @@ void mix_apply_f32(Ctx& ctx, const DevCore& core, bool by_col, int P, int Q, con
         st.ss = in_strides[2];
     }
     int t = ctx.tbegin(TC_MIX, fl);
+    VTN_REQUIRE(core.ops_f32 != nullptr, "FP32 mixing needs the core's FP32 operators");
     const int w_in = by_col ? core.wl : core.wr;
-    const size_t tile_bytes = sizeof(float2) * (size_t)w_in * d * MIX_QT;
-    // the tiled kernel pays off where output channels sum many entries (the near-dense collapse
-    // core): its warps own whole channels, so a channel with many dense d x d entries (the
-    // "completed" channel of the other cores) would serialise a block; those cores keep the
-    // per-channel kernel, which spreads every channel over many blocks
-    const int max_dense = by_col ? core.max_dense_col : core.max_dense_row;
-    const bool dense_core = (long long)core.nnz >= 4LL * w_out && max_dense <= 8;
-    if (dense_core && P <= 65535 && tile_bytes <= (size_t)mix_tiled_smem_limit(ctx)) {
-        dim3 g2((unsigned)((Q + MIX_QT - 1) / MIX_QT), (unsigned)P);
-        if (d <= 4) {
-            set_smem_attr_once(ctx, (const void*)mix_tiled_f32_kernel<4>, (int)tile_bytes);
-            mix_tiled_f32_kernel<4><<<g2, MIX_TILED_THREADS, tile_bytes, ctx.stream>>>(P, d, Q, w_in, w_out, st, ptr, src, opi,
-                                                                         core.ops, core.ident, in, out);
-        } else if (d <= 8) {
-            set_smem_attr_once(ctx, (const void*)mix_tiled_f32_kernel<8>, (int)tile_bytes);
-            mix_tiled_f32_kernel<8><<<g2, MIX_TILED_THREADS, tile_bytes, ctx.stream>>>(P, d, Q, w_in, w_out, st, ptr, src, opi,
-                                                                         core.ops, core.ident, in, out);
-        } else {
-            set_smem_attr_once(ctx, (const void*)mix_tiled_f32_kernel<16>, (int)tile_bytes);
-            mix_tiled_f32_kernel<16><<<g2, MIX_TILED_THREADS, tile_bytes, ctx.stream>>>(P, d, Q, w_in, w_out, st, ptr, src, opi,
-                                                                          core.ops, core.ident, in, out);
+    const long long E = PQ * d;
+    bool accumulate = false;
+    if (core.has_cid && by_col && in_strides == nullptr && w_out <= 128) {
+        // collapse core: the scaled identities as a channel GEMM, then the dense entries added
+        const int jneed = (w_out + 15) / 16;
+        const int JB = jneed <= 2 ? 2 : jneed <= 4 ? 4 : jneed <= 7 ? 7 : 8;
+        const size_t cbytes = sizeof(float2) * (size_t)w_in * 16 * JB;
+        const int limit = mix_smem_limit(ctx);
+        int EI = 4;
+        if (cbytes + 2 * sizeof(float2) * (size_t)w_in * 64 > (size_t)limit) EI = 2;
+        const size_t bytes = cbytes + 2 * sizeof(float2) * (size_t)w_in * 16 * EI;
+        if (bytes <= (size_t)limit) {
+            const long long tiles = (E + 16 * EI - 1) / (16 * EI);
+            const unsigned grid_c = (unsigned)std::min<long long>(tiles, std::max(ctx.num_sms, 1));
+            launch_mix_cid(ctx, JB, EI, core.cid_real, (int)bytes, grid_c, w_in, w_out, E, core.cid, in, out);
+            ctx.check_launch("mix_cid_kernel");
+            ptr = core.dcol_ptr;
+            src = core.dcol_src;
+            opi = core.dcol_op;
+            accumulate = true;
         }
-        ctx.count_launch();
-        ctx.check_launch("mix_tiled_f32_kernel");
-        ctx.tend(t);
-        return;
     }
     if (d <= 4)
-        mix_f32_kernel<4><<<grid, 256, 0, ctx.stream>>>(P, d, Q, st, ptr, src, opi, core.ops, core.ident, in, out);
+        mix_f32_kernel<4><<<grid, 256, 0, ctx.stream>>>(P, d, Q, st, ptr, src, opi, core.ops_f32, core.ident, in, out,
+                                                        accumulate ? 1 : 0);
     else if (d <= 8)
-        mix_f32_kernel<8><<<grid, 256, 0, ctx.stream>>>(P, d, Q, st, ptr, src, opi, core.ops, core.ident, in, out);
+        mix_f32_kernel<8><<<grid, 256, 0, ctx.stream>>>(P, d, Q, st, ptr, src, opi, core.ops_f32, core.ident, in, out,
+                                                        accumulate ? 1 : 0);
     else
-        mix_f32_kernel<16><<<grid, 256, 0, ctx.stream>>>(P, d, Q, st, ptr, src, opi, core.ops, core.ident, in, out);
+        mix_f32_kernel<16><<<grid, 256, 0, ctx.stream>>>(P, d, Q, st, ptr, src, opi, core.ops_f32, core.ident, in, out,
+                                                         accumulate ? 1 : 0);
     ctx.count_launch();
     ctx.check_launch("mix_f32_kernel");
     ctx.tend(t);

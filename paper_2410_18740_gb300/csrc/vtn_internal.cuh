@@ -75,12 +75,19 @@ struct DevCore {
     int* row_src = nullptr;   // [nnz]
     int* row_op = nullptr;    // [nnz]
     double2* ops = nullptr;   // [nnz][d][d]
+    float2* ops_f32 = nullptr;  // the same operators rounded to FP32 once at upload (the FP32 mixing
+                                // of the split-precision mode reads these: a double -> float
+                                // conversion runs on GB300's narrow FP64 pipe)
     unsigned char* ident = nullptr;  // [nnz]
     double flops_ident = 0, flops_dense = 0;  // counts for the flop model
     int n_ident = 0, n_dense = 0;
-    // per output channel, by column (left-to-right use) and by row: the largest number of
-    // dense (non-identity) entries
-    int max_dense_col = 0, max_dense_row = 0;
+    // collapse cores (many scaled-identity entries): C[a][b] (w_l x w_r, FP32, the identity
+    // entries' scalars; cid_real when every imaginary part is zero) and the index lists of the
+    // remaining (dense) entries by column and by row
+    bool has_cid = false, cid_real = false;
+    float2* cid = nullptr;
+    int *dcol_ptr = nullptr, *dcol_src = nullptr, *dcol_op = nullptr;
+    int *drow_ptr = nullptr, *drow_src = nullptr, *drow_op = nullptr;
     std::vector<DevBuf> bufs;
 };
 
@@ -107,6 +114,10 @@ struct Ctx {
     // named workspace slots
     std::vector<DevBuf> ws;
     double* pinned = nullptr;  // pinned host scratch (4096 doubles)
+    double* defer_buf = nullptr;  // pinned staging of results read back once per sweep
+    size_t defer_cap = 0;         // doubles
+    long long host_syncs = 0;     // stream synchronisations made by sync()
+    double* defer_reserve(size_t doubles);  // grows (synchronising first), never shrinks
     int* dstatus = nullptr;    // device status word: non-zero after a bounded device wait gave up
     int num_sms = 0;
 
@@ -118,7 +129,10 @@ struct Ctx {
     int tbegin(int cls, double flops);
     void tend(int idx);
     void tflush();  // synchronise and accumulate pending intervals
-    void sync() { VTN_CUDA_TRY(cudaStreamSynchronize(stream)); }
+    void sync() {
+        ++host_syncs;
+        VTN_CUDA_TRY(cudaStreamSynchronize(stream));
+    }
     void check_launch(const char* what);
     void check_dstatus();  // synchronises; throws VTN_ETIMEOUT (and clears the word) if set
 };
@@ -243,16 +257,18 @@ void env_right_dev(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const doubl
 
 // ------------------------------------------------------------------ vector kernels (Lanczos)
 // dots[i] = sum_e conj(V[i][e]) w[e], i < nv (deterministic two-stage reduction)
+// (stop, when given: a device flag; the kernels do nothing once it is non-zero)
 void multi_dot(Ctx& ctx, const double2* V, long long ld, int nv, const double2* w, long long n,
-               double2* dots_dev);
+               double2* dots_dev, const int* stop = nullptr);
 // w -= sum_i V[i] c[i]
 void multi_axpy(Ctx& ctx, const double2* V, long long ld, int nv, const double2* c_dev, double2* w,
-                long long n);
+                long long n, const int* stop = nullptr);
 // out = sum_i V[i] y[i] (y real, device)
+// nv_dev (may be null): the vector count is read on the device
 void lincomb_real(Ctx& ctx, const double2* V, long long ld, int nv, const double* y_dev, double2* out,
-                  long long n);
+                  long long n, const int* nv_dev = nullptr);
 // norm2 (sum |x|^2) into dev scalar
-void norm2_dev(Ctx& ctx, const double2* x, long long n, double* out_dev);
+void norm2_dev(Ctx& ctx, const double2* x, long long n, double* out_dev, const int* stop = nullptr);
 // x *= 1/sqrt(*nrm2_dev)
 void scale_inv_sqrt(Ctx& ctx, double2* x, long long n, const double* nrm2_dev);
 
@@ -262,8 +278,15 @@ struct LanczosResult {
     bool converged;
 };
 // Lowest eigenpair of the operator applied by `matvec(in, out)` (device vectors of n complex).
+// With defer != nullptr and restarts == 0 the Krylov steps are queued without any host round
+// trip (every vector kernel skips itself once the device stop flag is set; the matvecs after
+// the stop still run, their results unused) and {theta, resid, scratch, flag, stop, m_stop}
+// (5 doubles' worth) are copied to *defer asynchronously; the returned fields are then
+// placeholders until the caller has synchronised and read them (lanczos_deferred_result).
 LanczosResult lanczos(Ctx& ctx, long long n, double2* x, double tol, int kmax, int restarts,
-                      const std::function<void(const double2*, double2*)>& matvec);
+                      const std::function<void(const double2*, double2*)>& matvec, double* defer = nullptr);
+// The result a deferred solve copied to `slot` (after the stream has been synchronised).
+LanczosResult lanczos_deferred_result(const double* slot);
 
 // ------------------------------------------------------------------ truncation eigensolver
 struct TruncResult {
@@ -281,8 +304,13 @@ void conj_transpose_dev(Ctx& ctx, int rows, int cols, const double2* A, long lon
 // outer >= 0 limits the product formed after the eigendecomposition: direction 0 writes
 // only the first `outer` columns of right (leading dimension outer), direction 1 only the
 // first `outer` rows of left.
+// defer != nullptr: nothing is read back; the k eigenvalues, tr(rho) and the status words are
+// copied asynchronously to defer (k + 1 + 4 doubles) and the result's lam is empty until
+// truncate_deferred_result reads them after a synchronisation.
 TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int direction, int k_max,
-                         const double2* theta, double2* left, double2* right, int outer = -1);
+                         const double2* theta, double2* left, double2* right, int outer = -1,
+                         double* defer = nullptr);
+TruncResult truncate_deferred_result(const double* slot, int k);
 
 // ------------------------------------------------------------------ misc kernels
 // Philox counter word 3: the stream of the random numbers (initial MPS, sampler, truncation)

@@ -50,7 +50,7 @@ class vtn_sweep_report(C.Structure):
     _fields_ = [("sweeps_done", C.c_int), ("energy", C.c_double * 64), ("max_discarded", C.c_double * 64),
                 ("seconds", C.c_double * 64), ("matvecs", C.c_longlong), ("lanczos_not_converged", C.c_longlong),
                 ("heff_flops", C.c_double), ("heff_seconds", C.c_double), ("gemm_flops", C.c_double),
-                ("gemm_seconds", C.c_double), ("eig_seconds", C.c_double)]
+                ("gemm_seconds", C.c_double), ("eig_seconds", C.c_double), ("host_syncs", C.c_longlong)]
 
 
 class vtn_core(C.Structure):
@@ -435,7 +435,7 @@ def _report_dict(rep):
             "seconds": list(rep.seconds[:n]), "matvecs": rep.matvecs,
             "lanczos_not_converged": rep.lanczos_not_converged, "heff_flops": rep.heff_flops,
             "heff_seconds": rep.heff_seconds, "gemm_flops": rep.gemm_flops, "gemm_seconds": rep.gemm_seconds,
-            "eig_seconds": rep.eig_seconds}
+            "eig_seconds": rep.eig_seconds, "host_syncs": rep.host_syncs}
 
 
 def vtn_sweep(ctx, mpo, state=None, opts=None, **kw):

@@ -55,3 +55,51 @@ def test_warm_targets_and_product_state_match_oracle(ctx):
     for s in (mps, prod):
         vtn.vtn_mps_free(s)
     vtn.vtn_mpo_free(m)
+
+
+def test_learned_warm_start_trained_on_the_gpu(ctx):
+    """The network (4 -> 256 x 3 -> 2d, FP32) is trained by the library's own kernels on pairs
+    from solved small instances (features of each mode -> the dominant eigenvector of its reduced
+    density in the solved MPS), then used on larger held-out instances.  What it gains over the
+    method without it, measured here: its product state starts the sweeps far below a random MPS
+    in energy, its per-mode states reproduce the closed-form local states (squeezed vacua of the
+    Williamson decomposition) it was never shown, and the sweeps from it reach the same energy
+    as those from random initialisation (within 1 %).  It does not reduce the number of sweeps on
+    these Haar-random instances (measured and recorded in the design notes)."""
+    d = 4
+    X, T = [], []
+    for k in range(12):
+        w = inputs.workload("split", 10000 + k, M=6, d=d, D=d)
+        m = vtn.vtn_build_mpo(ctx, w.r, w.U, d, d)
+        st, mps, _ = vtn.vtn_sweep(ctx, m, None, chi_max=16, n_sweeps=3, seed=k, lanczos_tol=1e-10)
+        X.append(vtn.vtn_warm_features(m))
+        T.append(vtn.vtn_warm_targets(ctx, m, mps))
+        vtn.vtn_mps_free(mps)
+        vtn.vtn_mpo_free(m)
+    X, T = np.concatenate(X), np.concatenate(T)
+    xd, td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    net = vtn.vtn_mlp_create(ctx, 4, 256, 3, 2 * d, seed=3)
+    first = vtn.vtn_mlp_loss_grad(ctx, net, X.shape[0], xd, td, with_grad=False)[0]
+    last = vtn.vtn_mlp_train(ctx, net, X.shape[0], xd, td, 1e-3, 3000)
+    assert last < 0.05 * first
+    for k in range(2):
+        w = inputs.workload("split", 20000 + k, M=10, d=d, D=d)
+        m = vtn.vtn_build_mpo(ctx, w.r, w.U, d, d)
+        m1 = vtn.vtn_build_mpo(ctx, w.r, w.U, d, 1, vtn.VTN_FLAG_LBO)
+        ws = vtn.vtn_mps_warm_start(ctx, m, net)
+        pred = np.stack([vtn.vtn_mps_get_site(ctx, ws, i)[0, :, 0] for i in range(10)])
+        closed = np.stack([vtn.vtn_mpo_isometry(m1, i)[:, 0] for i in range(10)])
+        fid = np.abs(np.sum(pred.conj() * closed, axis=1)) ** 2 / np.sum(np.abs(closed) ** 2, axis=1)
+        assert fid.mean() > 0.95, fid
+        rnd = vtn.vtn_mps_random(ctx, m, 8, 40 + k)
+        assert vtn.vtn_energy(ctx, m, ws) < 0.5 * vtn.vtn_energy(ctx, m, rnd)
+        opts = vtn.vtn_sweep_opts_default(chi_max=32, n_sweeps=6, seed=40 + k, lanczos_tol=1e-10,
+                                          chi_schedule=[8, 16, 32])
+        _, a, ra = vtn.vtn_sweep(ctx, m, ws, opts)
+        _, b, rb = vtn.vtn_sweep(ctx, m, rnd, opts)
+        assert abs(ra["energy"][-1] - rb["energy"][-1]) <= 0.01 * rb["energy"][-1]
+        for s in (a, b):
+            vtn.vtn_mps_free(s)
+        vtn.vtn_mpo_free(m)
+        vtn.vtn_mpo_free(m1)
+    vtn.vtn_mlp_free(net)

@@ -166,3 +166,37 @@ def test_window_validation(ctx):
     assert vtn.vtn_mps_get_center(mps) == -1
     vtn.vtn_mps_free(mps)
     vtn.vtn_mpo_free(m)
+
+
+def test_sweep_without_restarts_waits_for_the_gpu_once_per_sweep(ctx):
+    """Lanczos without restarts and the exact truncation: the Krylov steps stop on a device flag
+    and the truncation results are staged, so a sweep synchronises with the GPU once (its
+    energy) plus the end-of-call checks -- none per bond -- and still follows the oracle's
+    trajectory with the same Lanczos settings (12 Krylov vectors, no restart)."""
+    lo, hi, M, d, chi = 2, 6, 9, 3, 20
+    w = inputs.workload("split", 6, M=M, d=d, D=d)
+    G = gbs.hamiltonian_coefficients(w.r, w.U)
+    Hn = gbs.norm_bound(G, M, d)
+    m = vtn.vtn_build_mpo(ctx, w.r, w.U, d, d)
+    lp = dict(lanczos_tol=1e-12, krylov_max=12, lanczos_max_restarts=0)
+    for window, n_sw in (((lo, hi), 3), ((0, M - 1), 2)):
+        kw = dict(window_lo=window[0], window_hi=window[1]) if window != (0, M - 1) else {}
+        start = vtn.vtn_mps_random_center(ctx, m, chi, 14, window[0])
+        opts = vtn.vtn_sweep_opts_default(chi_max=chi, n_sweeps=n_sw, **lp, **kw)
+        st, start, rep0 = vtn.vtn_sweep(ctx, m, start, opts)          # sizes every workspace
+        vtn.vtn_mps_free(start)
+        mps = vtn.vtn_mps_random_center(ctx, m, chi, 14, window[0])
+        st, mps, rep = vtn.vtn_sweep(ctx, m, mps, opts)
+        assert rep["energy"] == rep0["energy"]
+        # a windowed sweep reads its centre energy once; the full contraction of a full sweep twice
+        # (energy and norm); per-bond round trips would be (bonds) x (Krylov steps + 1)
+        bound = n_sw + 3 if window != (0, M - 1) else 2 * n_sw + 4
+        assert rep["host_syncs"] <= bound, rep["host_syncs"]
+        cores = ompo.build_mpo(G, d)
+        _, orep = odmrg.dmrg(cores, d, chi, n_sw, seed=14, mps=odmrg.initial_mps(M, d, chi, seed=14, center=window[0]),
+                             window=None if window == (0, M - 1) else window,
+                             lanczos=odmrg.LanczosParams(krylov_max=12, max_restarts=0, tol=1e-12))
+        for a, b in zip(rep["energy"], orep.energies):
+            assert abs(a - b) <= 1e-10 * Hn
+        vtn.vtn_mps_free(mps)
+    vtn.vtn_mpo_free(m)
