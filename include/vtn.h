@@ -151,6 +151,19 @@ vtn_status vtn_mpo_isometry(vtn_mpo mpo, int site, double* V);
  * output the count.  ops: complex[nnz*d*d], ops[k][s'][s].  Passing rows == NULL
  * returns only the count. */
 vtn_status vtn_mpo_core(vtn_mpo mpo, int site, int* nnz, int* rows, int* cols, double* ops);
+/* Term form of the two-site H_eff of bond (bond, bond+1) used by the split-precision sweeps
+ * (host query, no device needed).  Each core's d x d entries are expanded in an operator basis
+ * (Bi: ri operators of core `bond`, Bj: rj of core `bond + 1`, each d x d with [0] = I), and
+ *   H_eff = sum_t (sum_a U[t][a] L[a]) (x) (Bi[o_t] (x) Bj[p_t]) (x) (sum_c V[t][c] R[c])
+ * exactly (up to rounding) for the environments L[a] (a < w[bond]) and R[c] (c < w[bond+2]) of
+ * Sec. "Matrix Product States"; the first n_id terms have o_t = p_t = 0.  Call with ops == NULL to
+ * get *usable, *n_terms, *n_id, *ri, *rj; then ops int[2 n_terms] (o_t, p_t), U complex[n_terms
+ * w[bond]], V complex[n_terms w[bond+2]], Bi complex[ri d d], Bj complex[rj d d] (row = output
+ * level).  *usable = 1: the sweeps use the term form at this bond; 2: the bond has one, but with
+ * more than 1.15 max(w_l, w_r) + 4 terms the channel-mixing form is cheaper and is used; 0 (and
+ * n_terms = 0): no compact term form (an operator basis of 16 or more elements, or d > 8). */
+vtn_status vtn_mpo_bond_terms(vtn_mpo mpo, int bond, int* usable, int* n_terms, int* n_id, int* ri, int* rj,
+                              int* ops, double* U, double* V, double* Bi, double* Bj);
 /* Deterministic bound ||P H P|| <= lambda_max(G) M (2d - 1), used to scale tolerances. */
 vtn_status vtn_mpo_norm_bound(vtn_mpo mpo, double* out);
 
@@ -215,6 +228,15 @@ typedef struct {
     int energy_mode;           /* energy reported after each sweep: 0 = full FP64 contraction
                                   <psi|H|psi>/<psi|psi>; 1 = Rayleigh quotient of the final
                                   centre tensor (windowed sweeps always use 1)            */
+    int heff_form;             /* split-precision H_eff psi: 0 = the term form where the bond
+                                  has one and it is the cheaper form (cores folded into the
+                                  environments once per bond, see vtn_mpo_bond_terms), else
+                                  the channel-mixing form; 1 = the channel-mixing form always;
+                                  2 = the term form wherever the bond has one               */
+    int env_fp64;              /* with prec = VTN_BF16X3: 1 = environment updates in FP64 (their
+                                  split-precision errors add up along the chain: about 5e-4
+                                  relative after 49 updates at chi = 256, see
+                                  vtn_set_tc_accumulation); 0 = split precision as H_eff psi */
 } vtn_sweep_opts;
 
 typedef struct {
@@ -237,7 +259,7 @@ typedef struct {
 
 /* Fill opts with the defaults: chi_max 16, 8 sweeps, FP64, lanczos_tol 1e-10,
  * krylov_max 32, 4 restarts, e_tol 0, seed 0, trunc_mode 0 (exact), trunc_q 1, no window,
- * energy_mode 0. */
+ * energy_mode 0, heff_form 0, env_fp64 0. */
 vtn_status vtn_sweep_opts_default(vtn_sweep_opts* opts);
 
 /* Two-site DMRG sweeps.  *state == NULL: start from vtn_mps_random(opts->chi_schedule[0]
@@ -536,6 +558,22 @@ vtn_status vtn_mps_warm_start(vtn_ctx ctx, vtn_mpo mpo, vtn_mlp mlp, vtn_mps* ou
  * split-precision products; exposed for parity tests and kernel timing. */
 vtn_status vtn_gemm_bf16(vtn_ctx ctx, int M, int N, int K, const void* A, long long lda, const void* B,
                          long long ldb, void* D, long long ldd, int d_fp64);
+
+/* Accumulation length of the split-precision tensor-core products: the largest number of
+ * 64-wide k-blocks (bf16 split operands) one tensor-memory accumulator sums before its FP32
+ * partial is added to the others in FP64 (longer sums are split along k).  The tensor cores'
+ * FP32 accumulation loses accuracy about linearly with the sum's length, so shorter runs are
+ * more accurate and cost more split-K partial traffic.  env_kblocks applies to the environment
+ * updates (vtn_env_update and those of the sweeps: their errors add up along the chain),
+ * heff_kblocks to H_eff psi.  Defaults 64 and 256; each must be in [1, 4096].  Per context. */
+vtn_status vtn_set_tc_accumulation(vtn_ctx ctx, int env_kblocks, int heff_kblocks);
+
+/* Form of the truncation's Householder tridiagonalisation (one persistent cooperative kernel
+ * either way): for n >= min_n the kernel keeps only the lower triangle of the trailing matrix up
+ * to date (8 instead of 12 FP64 multiply-adds per element and column, two grid barriers per
+ * column instead of one), below it the full matrix.  Default: never (min_n above 4096); 0 =
+ * always the lower form.  Per context; results agree to rounding. */
+vtn_status vtn_set_tridiag_lower(vtn_ctx ctx, int min_n);
 
 /* Turn per-kernel device timing (CUDA events on the context stream) on or off and read
  * the accumulated figures: launches, algorithmic flops and seconds per kernel class.

@@ -50,6 +50,11 @@ vtn_status guard(vtn_ctx ctx, F&& f) {
 
 void use_device(Ctx& c) { VTN_CUDA_TRY(cudaSetDevice(c.device)); }
 
+void free_mpo_device(Ctx& c, vtn_mpo mpo) {
+    for (auto& dc : mpo->dcores) free_core(c, dc);
+    for (auto& bt : mpo->bterms) free_bond_terms(c, bt);
+}
+
 void ensure_mpo_device(vtn_ctx ctx, vtn_mpo mpo) {
     VTN_REQUIRE(mpo != nullptr, "null MPO");
     if (!mpo->dcores.empty()) {
@@ -59,6 +64,8 @@ void ensure_mpo_device(vtn_ctx ctx, vtn_mpo mpo) {
     Ctx& c = ctx->c;
     mpo->dcores.resize(mpo->hp.M);
     for (int s = 0; s < mpo->hp.M; ++s) upload_core(c, mpo->hp.cores[s], mpo->dcores[s]);
+    mpo->bterms.resize(std::max(mpo->hp.M - 1, 0));
+    for (int s = 0; s + 1 < mpo->hp.M; ++s) build_bond_terms(c, mpo->hp.cores[s], mpo->hp.cores[s + 1], mpo->bterms[s]);
     const size_t iso_bytes = sizeof(double2) * mpo->hp.iso.size();
     mpo->iso_dev = (double2*)c.dalloc(iso_bytes);
     VTN_CUDA_TRY(cudaMemcpyAsync(mpo->iso_dev, mpo->hp.iso.data(), iso_bytes, cudaMemcpyHostToDevice, c.stream));
@@ -153,6 +160,19 @@ struct TempCore {
         if (c) {
             cudaStreamSynchronize(c->stream);
             free_core(*c, dc);
+        }
+    }
+};
+
+// The term form of a bond given as two cores, for the duration of one call.
+struct TempTerms {
+    Ctx* c;
+    BondTerms bt;
+    TempTerms(Ctx& ctx, const HostCore& a, const HostCore& b) : c(&ctx) { build_bond_terms(ctx, a, b, bt); }
+    ~TempTerms() {
+        if (c) {
+            cudaStreamSynchronize(c->stream);
+            free_bond_terms(*c, bt);
         }
     }
 };
@@ -395,7 +415,7 @@ vtn_status vtn_build_mpo(vtn_ctx ctx, int M, const double* r, const double* U, i
                 use_device(ctx->c);
                 ensure_mpo_device(ctx, mpo);
             } catch (...) {
-                for (auto& dc : mpo->dcores) free_core(ctx->c, dc);
+                free_mpo_device(ctx->c, mpo);
                 delete mpo;
                 throw;
             }
@@ -420,7 +440,7 @@ vtn_status vtn_build_mpo_cz(vtn_ctx ctx, int M, const double* r, const double* U
                 use_device(ctx->c);
                 ensure_mpo_device(ctx, mpo);
             } catch (...) {
-                for (auto& dc : mpo->dcores) free_core(ctx->c, dc);
+                free_mpo_device(ctx->c, mpo);
                 delete mpo;
                 throw;
             }
@@ -435,7 +455,7 @@ vtn_status vtn_mpo_free(vtn_mpo mpo) {
     if (mpo->owner) {
         Ctx& c = mpo->owner->c;
         cudaStreamSynchronize(c.stream);
-        for (auto& dc : mpo->dcores) free_core(c, dc);
+        free_mpo_device(c, mpo);
         c.dfree(mpo->iso_dev);
     }
     delete mpo;
@@ -470,7 +490,7 @@ vtn_status vtn_mpo_from_cores(vtn_ctx ctx, int M, const vtn_core* cores, vtn_mpo
                 use_device(ctx->c);
                 ensure_mpo_device(ctx, mpo);
             } catch (...) {
-                for (auto& dc : mpo->dcores) free_core(ctx->c, dc);
+                free_mpo_device(ctx->c, mpo);
                 delete mpo;
                 throw;
             }
@@ -563,6 +583,35 @@ vtn_status vtn_mpo_core(vtn_mpo mpo, int site, int* nnz, int* rows, int* cols, d
     std::memcpy(ops, h.ops.data(), sizeof(double) * 2 * h.ops.size());
     *nnz = n;
     return VTN_OK;
+}
+
+vtn_status vtn_mpo_bond_terms(vtn_mpo mpo, int bond, int* usable, int* n_terms, int* n_id, int* ri, int* rj,
+                              int* ops, double* U, double* V, double* Bi, double* Bj) {
+    if (!mpo || !usable || !n_terms || !n_id || !ri || !rj || bond < 0 || bond + 1 >= mpo->hp.M) return VTN_EINVAL;
+    try {
+        const HostCore& a = mpo->hp.cores[bond];
+        const HostCore& b = mpo->hp.cores[bond + 1];
+        int nid = 0, r1 = 0, r2 = 0;
+        std::vector<int> o;
+        std::vector<std::complex<double>> u, v, b1, b2;
+        bool worthwhile = false;
+        const bool ok = bond_terms_host(a, b, nid, o, u, v, b1, b2, r1, r2, worthwhile);
+        *usable = ok ? (worthwhile ? 1 : 2) : 0;
+        *n_terms = ok ? (int)o.size() / 2 : 0;
+        *n_id = ok ? nid : 0;
+        *ri = r1;
+        *rj = r2;
+        if (!ops || !ok) return VTN_OK;
+        if (!U || !V || !Bi || !Bj) return VTN_EINVAL;
+        std::copy(o.begin(), o.end(), ops);
+        std::memcpy(U, u.data(), sizeof(double) * 2 * u.size());
+        std::memcpy(V, v.data(), sizeof(double) * 2 * v.size());
+        std::memcpy(Bi, b1.data(), sizeof(double) * 2 * b1.size());
+        std::memcpy(Bj, b2.data(), sizeof(double) * 2 * b2.size());
+        return VTN_OK;
+    } catch (const std::exception&) {
+        return VTN_ENOMEM;
+    }
 }
 
 vtn_status vtn_mpo_norm_bound(vtn_mpo mpo, double* out) {
@@ -824,6 +873,15 @@ vtn_status sweep_body(vtn_ctx work, vtn_ctx owner, vtn_mpo mpo, vtn_mps* state, 
     const int lo = windowed ? opts->window_lo : 0, hi = windowed ? opts->window_hi : M - 1;
     VTN_REQUIRE(!windowed || (lo >= 0 && hi <= M - 1), "window must satisfy 0 <= window_lo < window_hi <= M - 1");
     VTN_REQUIRE(opts->energy_mode == 0 || opts->energy_mode == 1, "energy_mode must be 0 or 1");
+    VTN_REQUIRE(opts->heff_form >= 0 && opts->heff_form <= 2, "heff_form must be 0, 1 or 2");
+    VTN_REQUIRE(opts->env_fp64 == 0 || opts->env_fp64 == 1, "env_fp64 must be 0 or 1");
+    // term form of bond i's H_eff (split precision), or null for the channel-mixing form
+    auto bond_terms = [&](int i) -> const BondTerms* {
+        if (opts->heff_form == 1 || i < 0 || i >= (int)mpo->bterms.size()) return nullptr;
+        const BondTerms& bt = mpo->bterms[i];
+        if (!bt.usable || (opts->heff_form == 0 && !bt.worthwhile)) return nullptr;
+        return &bt;
+    };
     const bool centre_energy = windowed || opts->energy_mode == 1;
     int chi_cap = opts->chi_max;
     for (int x : mps->dims) chi_cap = std::max(chi_cap, x);
@@ -845,12 +903,13 @@ vtn_status sweep_body(vtn_ctx work, vtn_ctx owner, vtn_mpo mpo, vtn_mps* state, 
     set_scalar_one(c, env.L[0]);
     set_scalar_one(c, env.R[M]);
     // environment updates run in the same precision mode as H_eff psi
+    const bool split_env = split && opts->env_fp64 == 0;
     auto env_left = [&](const DevCore& W, int cl, int cr, const double2* Lin, const double2* A, double2* Lout) {
-        if (split) env_left_bf16x3(c, W, cl, cr, Lin, A, Lout);
+        if (split_env) env_left_bf16x3(c, W, cl, cr, Lin, A, Lout);
         else env_left_dev(c, W, cl, cr, Lin, A, Lout);
     };
     auto env_right = [&](const DevCore& W, int cl, int cr, const double2* Rin, const double2* A, double2* Rout) {
-        if (split) env_right_bf16x3(c, W, cl, cr, Rin, A, Rout);
+        if (split_env) env_right_bf16x3(c, W, cl, cr, Rin, A, Rout);
         else env_right_dev(c, W, cl, cr, Rin, A, Rout);
     };
     for (int s = 0; s < lo; ++s)
@@ -902,7 +961,7 @@ vtn_status sweep_body(vtn_ctx work, vtn_ctx owner, vtn_mpo mpo, vtn_mps* state, 
                 const double2* R = env.R[i + 2];
                 const double hf = heff_flops(Wi, Wj, cl, cr);
                 HeffPacked pk;
-                if (split) heff_pack_envs(c, Wi, Wj, cl, cr, L, R, pk);
+                if (split) heff_pack_envs(c, Wi, Wj, cl, cr, L, R, pk, bond_terms(i));
                 LanczosResult lr = lanczos(c, n, theta, opts->lanczos_tol, opts->krylov_max,
                                            opts->lanczos_max_restarts, [&](const double2* in, double2* out) {
                                                if (split) heff_apply_bf16x3(c, Wi, Wj, pk, in, out);
@@ -951,7 +1010,7 @@ vtn_status sweep_body(vtn_ctx work, vtn_ctx owner, vtn_mpo mpo, vtn_mps* state, 
             const DevCore& Wj = mpo->dcores[lo + 1];
             if (split) {
                 HeffPacked pk;
-                heff_pack_envs(c, Wi, Wj, cl, cr, env.L[lo], env.R[lo + 2], pk);
+                heff_pack_envs(c, Wi, Wj, cl, cr, env.L[lo], env.R[lo + 2], pk, bond_terms(lo));
                 heff_apply_bf16x3(c, Wi, Wj, pk, theta, y);
             } else {
                 heff_apply_dev(c, Wi, Wj, cl, cr, env.L[lo], env.R[lo + 2], theta, y);
@@ -1677,8 +1736,10 @@ vtn_status vtn_heff_apply(vtn_ctx ctx, const vtn_core* Wi, const vtn_core* Wj, i
         VTN_REQUIRE(hi.wr == hj.wl && hi.d == hj.d, "Wi.w_right must equal Wj.w_left and d must agree");
         TempCore ci(c, hi), cj(c, hj);
         if (prec == VTN_BF16X3) {
+            TempTerms tt(c, hi, hj);
             HeffPacked pk;
-            heff_pack_envs(c, ci.dc, cj.dc, chi_l, chi_r, (const double2*)L, (const double2*)R, pk);
+            heff_pack_envs(c, ci.dc, cj.dc, chi_l, chi_r, (const double2*)L, (const double2*)R, pk,
+                           tt.bt.worthwhile ? &tt.bt : nullptr);
             heff_apply_bf16x3(c, ci.dc, cj.dc, pk, (const double2*)theta, (double2*)y);
         } else {
             heff_apply_dev(c, ci.dc, cj.dc, chi_l, chi_r, (const double2*)L, (const double2*)R,
@@ -2095,6 +2156,26 @@ vtn_status vtn_gemm_bf16(vtn_ctx ctx, int M, int N, int K, const void* A, long l
         tc_gemm_bf16(c, g);
         c.sync();
         c.check_dstatus();
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_set_tc_accumulation(vtn_ctx ctx, int env_kblocks, int heff_kblocks) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(env_kblocks >= 1 && env_kblocks <= 4096 && heff_kblocks >= 1 && heff_kblocks <= 4096,
+                    "accumulation lengths must be in [1, 4096] k-blocks");
+        ctx->c.tc_kb_env = env_kblocks;
+        ctx->c.tc_kb_heff = heff_kblocks;
+        return VTN_OK;
+    });
+}
+
+vtn_status vtn_set_tridiag_lower(vtn_ctx ctx, int min_n) {
+    if (!ctx) return VTN_EINVAL;
+    return guard(ctx, [&]() -> vtn_status {
+        VTN_REQUIRE(min_n >= 0, "min_n must be >= 0");
+        ctx->c.tri_lower_min_n = min_n;
         return VTN_OK;
     });
 }

@@ -634,6 +634,363 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_persistent(double2* __res
     }
 }
 
+// ---------------------------------------------------------------- lower-triangle form
+// The same reduction with only the lower triangle (row >= column) of the trailing block kept up
+// to date.  Each stored element a = A[j][c] takes the pending rank-2 update once (8 FMAs) and
+// feeds both halves of p = A v: conj(a) v_j to p_c (the column part, summed in the lanes as in
+// tri_pass) and, for j > c, a v_c to p_j (the row part, 4 FMAs): 8 FP64 FMAs per element of the
+// full trailing block and column instead of 12.  A warp takes TRL_RB rows at a time; their row
+// parts are combined across the lanes by a reduce-scatter (6 complex additions per lane for 4
+// rows) and written per (column chunk, row).  The column chunks are cut into units of about
+// equal numbers of rows (chunk c holds rows c W .. m-1), interleaved over the warps of a unit.
+// After a grid barrier the CTAs finalise p in slices -- column part, then the row parts of
+// chunks 0 .. row/W in order (deterministic) -- and a second barrier publishes it.  Row k+1 of
+// the updated matrix, which gives the next reflector, is read as column k+1 (the stored half).
+constexpr int TRL_THREADS = 256;
+constexpr int TRL_NW = TRL_THREADS / 32;
+constexpr int TRL_RB = 4;  // rows per warp batch
+
+struct TriBufsL {
+    double2* part;     // [2][2 nb + 8][n] column partials per unit of a chunk
+    double2* pcol;     // [2][n] column part of A v (unscaled), written by a chunk's last unit
+    double2* prow;     // [2][TRI_MAX_CHUNKS][n] row parts per column chunk
+    double2* p;        // [2][n] p = tau A v
+    unsigned* arrive;  // [2][TRI_MAX_CHUNKS] arrivals per column chunk (zero at launch)
+};
+
+// x (complex, per lane) summed over the lanes that share bits >= 2 of the lane index, for 4 rows:
+// on return r[0] of lane l holds the sum of row (l & 3) over all 32 lanes
+__device__ __forceinline__ double2 shfl_xor_d2(double2 v, int o) {
+    return make_double2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
+
+__device__ __forceinline__ double2 reduce_scatter4(double2 r[TRL_RB], int lane) {
+    // stage 1: lanes with bit 1 keep rows 2, 3; the others rows 0, 1
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const bool up = (lane & 2) != 0;
+        const double2 send = up ? r[t] : r[t + 2];
+        const double2 keep = up ? r[t + 2] : r[t];
+        const double2 got = shfl_xor_d2(send, 2);
+        r[t] = make_double2(keep.x + got.x, keep.y + got.y);
+    }
+    // stage 2: bit 0 picks row 2b1 + 1 or 2b1
+    {
+        const bool up = (lane & 1) != 0;
+        const double2 send = up ? r[0] : r[1];
+        const double2 keep = up ? r[1] : r[0];
+        const double2 got = shfl_xor_d2(send, 1);
+        r[0] = make_double2(keep.x + got.x, keep.y + got.y);
+    }
+    // the row is lane & 3; add over lane bits 2..4
+#pragma unroll
+    for (int o = 4; o <= 16; o <<= 1) {
+        const double2 got = shfl_xor_d2(r[0], o);
+        r[0] = make_double2(r[0].x + got.x, r[0].y + got.y);
+    }
+    return r[0];
+}
+
+// Trailing pass of step k, lower triangle.  Work unit u: chunk c = the largest with prefix[c] <= u,
+// slice cs = u - prefix[c] of CS_c = prefix[c+1] - prefix[c]; warp w walks the local rows
+// c W + cs NW + w + t CS_c NW; lane l owns the columns c W + q 32 + l (q < CPL).
+template <int CPL>
+__device__ void tri_pass_lower(double2* __restrict__ A, int n, int k, int m, int nb, bool have_prev,
+                               const double2* vprev, const double2* wprev, const double2* vcur, double2* pk,
+                               double2* pcol, double2* prow, unsigned* arrive, double2* colred, int& last_sh,
+                               const int* prefix, int C) {
+    constexpr int W = 32 * CPL;
+    constexpr int LD = TRI_MAX_CPL * 32;  // colred row stride
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int U = prefix[C];
+    for (int unit = (int)blockIdx.x; unit < U; unit += nb) {
+        int lo = 0, hi = C;  // prefix[lo] <= unit < prefix[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (prefix[mid] <= unit) lo = mid;
+            else hi = mid;
+        }
+        const int c = lo, cs = unit - prefix[c], CSc = prefix[c + 1] - prefix[c];
+        int il[CPL];
+        bool ok[CPL];
+        double2 vpi[CPL], wpi[CPL], vci[CPL];
+        double accx[CPL], accy[CPL];
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+            il[q] = c * W + q * 32 + lane;
+            ok[q] = il[q] < m;
+            vpi[q] = make_double2(0.0, 0.0);
+            wpi[q] = make_double2(0.0, 0.0);
+            if (have_prev && ok[q]) {
+                vpi[q] = vprev[il[q] + 1];
+                wpi[q] = wprev[il[q] + 1];
+            }
+            vci[q] = ok[q] ? vcur[il[q]] : make_double2(0.0, 0.0);
+            accx[q] = accy[q] = 0.0;
+        }
+        const int S = CSc * TRL_NW;
+        for (int jb = c * W + cs * TRL_NW + warp; jb < m; jb += TRL_RB * S) {
+            double2 a[TRL_RB][CPL];
+            // loads first (TRL_RB * CPL in flight), then the updates, stores and sums
+#pragma unroll
+            for (int r = 0; r < TRL_RB; ++r) {
+                const int j = jb + r * S;
+#pragma unroll
+                for (int q = 0; q < CPL; ++q)
+                    a[r][q] = (j < m && ok[q] && j >= il[q]) ? __ldcg(&A[(long long)(k + 1 + j) * n + (k + 1 + il[q])])
+                                                             : make_double2(0.0, 0.0);
+            }
+            double2 racc[TRL_RB];
+#pragma unroll
+            for (int r = 0; r < TRL_RB; ++r) {
+                const int j = jb + r * S;
+                racc[r] = make_double2(0.0, 0.0);
+                if (j >= m) continue;  // warp-uniform
+                const double2 v = vcur[j];
+                double2 vpj = make_double2(0.0, 0.0), wpj = make_double2(0.0, 0.0);
+                if (have_prev) {
+                    vpj = vprev[j + 1];
+                    wpj = wprev[j + 1];
+                }
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) {
+                    if (!(ok[q] && j >= il[q])) continue;
+                    double2 x = a[r][q];
+                    if (have_prev) {
+                        x = sub_two_cmulc(x, vpj, wpi[q], wpj, vpi[q]);
+                        A[(long long)(k + 1 + j) * n + (k + 1 + il[q])] = x;
+                    }
+                    // column part: conj(x) v_j
+                    accx[q] = fma(x.x, v.x, accx[q]);
+                    accx[q] = fma(x.y, v.y, accx[q]);
+                    accy[q] = fma(x.x, v.y, accy[q]);
+                    accy[q] = fma(-x.y, v.x, accy[q]);
+                    // row part: x v_c (strictly below the diagonal)
+                    if (j > il[q]) {
+                        racc[r].x = fma(x.x, vci[q].x, racc[r].x);
+                        racc[r].x = fma(-x.y, vci[q].y, racc[r].x);
+                        racc[r].y = fma(x.x, vci[q].y, racc[r].y);
+                        racc[r].y = fma(x.y, vci[q].x, racc[r].y);
+                    }
+                }
+            }
+            const double2 rs = reduce_scatter4(racc, lane);
+            const int jr = jb + (lane & 3) * S;
+            if (lane < TRL_RB && jr < m) prow[(long long)c * n + jr] = rs;
+        }
+        // column partials of this unit: tree over the warps, then the chunk's last unit sums the
+        // CS_c partials in slice order
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) colred[warp * LD + q * 32 + lane] = make_double2(accx[q], accy[q]);
+        __syncthreads();
+#pragma unroll
+        for (int h = TRL_NW / 2; h >= 2; h >>= 1) {
+            if (warp < h) {
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) {
+                    const double2 o = colred[(warp + h) * LD + q * 32 + lane];
+                    colred[warp * LD + q * 32 + lane].x += o.x;
+                    colred[warp * LD + q * 32 + lane].y += o.y;
+                }
+            }
+            __syncthreads();
+        }
+        if (warp == 0) {
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) {
+                const double2 a0 = colred[q * 32 + lane], a1 = colred[LD + q * 32 + lane];
+                if (ok[q]) pk[(long long)cs * n + il[q]] = make_double2(a0.x + a1.x, a0.y + a1.y);
+            }
+            __threadfence();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            last_sh = atomicAdd(&arrive[c], 1u) == (unsigned)(CSc - 1);
+        }
+        __syncthreads();
+        if (last_sh && warp < CPL) {
+            __threadfence();
+            const int ilq = c * W + warp * 32 + lane;
+            if (ilq < m) {
+                double sx = 0.0, sy = 0.0;
+                for (int s2 = 0; s2 < CSc; ++s2) {
+                    const double2 pp = __ldcg(&pk[(long long)s2 * n + ilq]);
+                    sx += pp.x;
+                    sy += pp.y;
+                }
+                pcol[ilq] = make_double2(sx, sy);
+            }
+            if (warp == 0 && lane == 0) arrive[c] = 0u;  // reused two steps later, after four barriers
+        }
+        __syncthreads();  // colred and last_sh are reused by the next unit
+    }
+}
+
+__global__ void __launch_bounds__(TRL_THREADS) tridiag_lower(double2* __restrict__ A, int n, double2* __restrict__ H,
+                                                             EigSmall s, TriBufsL tb, GridBar* bar) {
+    extern __shared__ double2 sm[];
+    double2* vprev = sm;
+    double2* wprev = sm + n;
+    double2* vcur = sm + 2 * n;
+    __shared__ double red[33];
+    __shared__ double tau_sh, dk_sh;
+    __shared__ double2 p0_sh;
+    __shared__ int last_sh;
+    __shared__ int prefix_sh[TRI_MAX_CHUNKS + 1];
+    __shared__ double2 colred[TRL_NW][TRI_MAX_CPL * 32];
+    const int nb = (int)gridDim.x;
+    unsigned epoch = 0;
+    bool have_prev = false;
+    // row 0 (no pending update; the whole matrix is valid at the start): x = conj(A[0][1..n-1])
+    double a2 = 0.0;
+    for (int t = threadIdx.x; t < n - 1; t += blockDim.x) {
+        const double2 a = __ldcg(&A[1 + t]);
+        const double2 x = make_double2(a.x, -a.y);
+        vcur[t] = x;
+        a2 = fma(x.x, x.x, fma(x.y, x.y, a2));
+    }
+    if (threadIdx.x == 0) dk_sh = __ldcg(&A[0]).x;
+    for (int k = 0; k + 2 < n; ++k) {
+        const int m = n - k - 1;
+        // ---- reflector for column k (as in tridiag_persistent)
+        a2 = block_sum(a2, red);
+        if (threadIdx.x == 0) {
+            const double2 x0 = vcur[0];
+            const double q0 = fma(x0.x, x0.x, x0.y * x0.y);
+            double tau = 0.0;
+            double2 beta = make_double2(0.0, 0.0);
+            if (a2 > 0.0) {
+                const double ra = rsqrt(a2);
+                const double alpha = a2 * ra;
+                double2 phia;
+                double ax0 = 0.0;
+                if (q0 > 0.0) {
+                    const double rq = rsqrt(q0);
+                    ax0 = q0 * rq;
+                    const double sc = alpha * rq;
+                    phia = make_double2(x0.x * sc, x0.y * sc);
+                } else {
+                    phia = make_double2(alpha, 0.0);
+                }
+                vcur[0] = make_double2(x0.x + phia.x, x0.y + phia.y);
+                tau = 1.0 / fma(alpha, ax0, a2);
+                beta = make_double2(-phia.x, -phia.y);
+            }
+            tau_sh = tau;
+            if (blockIdx.x == 0) {
+                s.diag[k] = dk_sh;
+                s.tau[k] = tau;
+                s.e[k] = beta;
+            }
+        }
+        __syncthreads();
+        const double tau = tau_sh;
+        if (tau == 0.0)
+            for (int t = threadIdx.x; t < m; t += blockDim.x) vcur[t] = make_double2(0.0, 0.0);
+        __syncthreads();
+        if (blockIdx.x == 0)
+            for (int t = threadIdx.x; t < m; t += blockDim.x) H[(long long)k * n + t] = vcur[t];
+        // ---- B: trailing pass over the lower triangle
+        double2* pk = tb.part + (long long)(k & 1) * (2 * nb + 8) * n;
+        double2* pcol = tb.pcol + (long long)(k & 1) * n;
+        double2* prow = tb.prow + (long long)(k & 1) * TRI_MAX_CHUNKS * n;
+        double2* pfin = tb.p + (long long)(k & 1) * n;
+        unsigned* arrive = tb.arrive + (k & 1) * TRI_MAX_CHUNKS;
+        const int cpl = m >= 256 ? 2 : 1;
+        const int W = 32 * cpl;
+        const int C = (m + W - 1) / W;
+        if ((int)threadIdx.x <= C) {
+            // rows per unit: the chunks' rows spread over the CTAs, at most 2 nb units per chunk
+            const long long total = (long long)C * m - (long long)W * C * (C - 1) / 2;
+            int RT = (int)((total + nb - 1) / nb);
+            RT = max(RT, (m + 2 * nb - 1) / (2 * nb));
+            RT = max(TRL_NW, (RT + TRL_NW - 1) / TRL_NW * TRL_NW);
+            int acc = 0;
+            for (int c = 0; c < (int)threadIdx.x; ++c) acc += (m - c * W + RT - 1) / RT;
+            prefix_sh[threadIdx.x] = acc;
+        }
+        __syncthreads();
+        if (cpl == 2)
+            tri_pass_lower<2>(A, n, k, m, nb, have_prev, vprev, wprev, vcur, pk, pcol, prow, arrive, &colred[0][0],
+                              last_sh, prefix_sh, C);
+        else
+            tri_pass_lower<1>(A, n, k, m, nb, have_prev, vprev, wprev, vcur, pk, pcol, prow, arrive, &colred[0][0],
+                              last_sh, prefix_sh, C);
+        if (!grid_sync(bar, (unsigned)nb, epoch++)) return;
+        // ---- p = tau (column part + row parts of chunks 0 .. il / W), in slices over the CTAs
+        for (int il = (int)(blockIdx.x * blockDim.x + threadIdx.x); il < m; il += nb * (int)blockDim.x) {
+            const double2 pc = __ldcg(&pcol[il]);
+            double sx = pc.x, sy = pc.y;
+            const int cl = il / W;
+            for (int c = 0; c <= cl; ++c) {
+                const double2 r = __ldcg(&prow[(long long)c * n + il]);
+                sx += r.x;
+                sy += r.y;
+            }
+            pfin[il] = make_double2(tau * sx, tau * sy);
+        }
+        if (!grid_sync(bar, (unsigned)nb, epoch++)) return;
+        // ---- C(k): K = (tau/2) Re(v^dag p); p parked in wprev (its old content is spent)
+        const bool next = k + 3 < n;
+        double dot = 0.0;
+        for (int t = threadIdx.x; t < m; t += blockDim.x) {
+            const double2 p = __ldcg(&pfin[t]), v = vcur[t];
+            if (next && t >= 1) vprev[t - 1] = __ldcg(&A[(long long)(k + 1 + t) * n + (k + 1)]);  // column k+1, raw
+            wprev[t] = p;
+            if (t == 0) p0_sh = p;
+            dot = fma(v.x, p.x, fma(v.y, p.y, dot));
+        }
+        dot = block_sum(dot, red);
+        const double K = 0.5 * tau * dot;
+        double2* vnew = vcur;
+        double2* wnew = wprev;
+        double2* xnext = vprev;
+        const double2 v0 = vnew[0];
+        const double2 w0 = make_double2(fma(-K, v0.x, p0_sh.x), fma(-K, v0.y, p0_sh.y));
+        a2 = 0.0;
+        for (int t = threadIdx.x; t < m; t += blockDim.x) {
+            const double2 p = wnew[t], v = vnew[t];
+            const double2 w = make_double2(fma(-K, v.x, p.x), fma(-K, v.y, p.y));
+            wnew[t] = w;
+            if (next && t >= 1) {
+                // column k+1 with the pending update: A[j][k+1] -= v_j conj(w_0) + w_j conj(v_0); it is
+                // the conjugate of row k+1, so x = the updated column itself
+                double2 x = xnext[t - 1];
+                x = sub_two_cmulc(x, v, w0, w, v0);
+                xnext[t - 1] = x;
+                a2 = fma(x.x, x.x, fma(x.y, x.y, a2));
+            }
+        }
+        if (threadIdx.x == 0 && next) dk_sh = __ldcg(&A[(long long)(k + 1) * n + (k + 1)]).x - 2.0 * (v0.x * w0.x + v0.y * w0.y);
+        vprev = vnew;
+        wprev = wnew;
+        vcur = xnext;
+        have_prev = true;
+        __syncthreads();
+    }
+    // ---- tail: last 2 x 2 block (lower half) with the pending update applied
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (n >= 2) {
+            double2 a00 = __ldcg(&A[(long long)(n - 2) * n + (n - 2)]);
+            double2 a11 = __ldcg(&A[(long long)(n - 1) * n + (n - 1)]);
+            double2 a10 = __ldcg(&A[(long long)(n - 1) * n + (n - 2)]);
+            if (have_prev) {
+                a00.x -= 2.0 * (vprev[0].x * wprev[0].x + vprev[0].y * wprev[0].y);
+                a11.x -= 2.0 * (vprev[1].x * wprev[1].x + vprev[1].y * wprev[1].y);
+                const double2 u = cmulc(vprev[1], wprev[0]), v = cmulc(wprev[1], vprev[0]);
+                a10.x -= u.x + v.x;
+                a10.y -= u.y + v.y;
+            }
+            s.diag[n - 2] = a00.x;
+            s.diag[n - 1] = a11.x;
+            s.e[n - 2] = a10;  // conj of the upper element a01
+        } else {
+            s.diag[0] = __ldcg(&A[0]).x;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- eigenvalues
 // Number of eigenvalues of the symmetric tridiagonal (a, b) below x: the number of negative
 // pivots of T - x I, i.e. sign changes between consecutive leading principal minors
@@ -879,6 +1236,134 @@ __global__ void __launch_bounds__(1024) cholesky_kernel(double* __restrict__ G, 
                 G[(long long)i * k + l] = fma(-gij, G[(long long)l * k + j], G[(long long)i * k + l]);
         }
         __syncthreads();
+    }
+}
+
+// Blocked right-looking form of the same Cholesky for large k (the one-CTA kernel above walks k
+// steps with two block barriers each): per block of CH_NB columns, the diagonal block is factored
+// (and its factor inverted) by one CTA, the panel below becomes L21 = G21 L11^{-T} (a product with
+// the inverse, one thread per element), and the lower tiles of the trailing matrix take
+// G22 -= L21 L21^T.  The diagonal pivots use the same rsqrt form as cholesky_kernel.
+constexpr int CH_NB = 32;
+
+__global__ void __launch_bounds__(256) chol_diag(double* __restrict__ G, int k, int j0, double* __restrict__ dinv,
+                                                 double* __restrict__ Linv, int* __restrict__ status,
+                                                 const int* pred, int want) {
+    if (skip(pred, want)) return;
+    __shared__ double S[CH_NB][CH_NB + 1];
+    __shared__ double X[CH_NB][CH_NB + 1];
+    const int b = min(CH_NB, k - j0);
+    for (int t = threadIdx.x; t < CH_NB * CH_NB; t += blockDim.x) {
+        const int i = t / CH_NB, j = t - (t / CH_NB) * CH_NB;
+        S[i][j] = (i < b && j <= i) ? G[(long long)(j0 + i) * k + j0 + j] : 0.0;
+        X[i][j] = 0.0;
+    }
+    __syncthreads();
+    for (int j = 0; j < b; ++j) {
+        if (threadIdx.x == 0) {
+            double djj = S[j][j];
+            if (!(djj > 0.0)) {
+                status[0] = 1;
+                djj = 1e-300;
+            }
+            const double r = rsqrt(djj);
+            S[j][j] = djj * r;
+            X[j][j] = r;
+        }
+        __syncthreads();
+        const double r = X[j][j];
+        for (int i = j + 1 + threadIdx.x; i < b; i += blockDim.x) S[i][j] *= r;
+        __syncthreads();
+        const int w = b - j - 1;
+        for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
+            const int i = j + 1 + t / w, l = j + 1 + t % w;
+            if (l <= i) S[i][l] = fma(-S[i][j], S[l][j], S[i][l]);
+        }
+        __syncthreads();
+    }
+    // inverse of the factor, one column per thread: X[i][c] = -(sum_{c<=l<i} S[i][l] X[l][c]) / S[i][i]
+    if ((int)threadIdx.x < b) {
+        const int c = threadIdx.x;
+        for (int i = c + 1; i < b; ++i) {
+            double acc = 0.0;
+            for (int l = c; l < i; ++l) acc = fma(S[i][l], X[l][c], acc);
+            X[i][c] = -acc * X[i][i];
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < CH_NB * CH_NB; t += blockDim.x) {
+        const int i = t / CH_NB, j = t - (t / CH_NB) * CH_NB;
+        Linv[t] = X[i][j];
+        if (i < b && j <= i) G[(long long)(j0 + i) * k + j0 + j] = S[i][j];
+    }
+    for (int i = threadIdx.x; i < b; i += blockDim.x) dinv[j0 + i] = X[i][i];
+}
+
+// rows j0 + CH_NB + 8 blockIdx.x + r of the panel: L21[i][j] = sum_{l <= j} G21[i][l] Linv[j][l]
+__global__ void __launch_bounds__(256) chol_panel(double* __restrict__ G, int k, int j0,
+                                                  const double* __restrict__ Linv, const int* pred, int want) {
+    if (skip(pred, want)) return;
+    __shared__ double Li[CH_NB][CH_NB + 1];
+    __shared__ double Rw[8][CH_NB + 1];
+    for (int t = threadIdx.x; t < CH_NB * CH_NB; t += blockDim.x) Li[t / CH_NB][t % CH_NB] = Linv[t];
+    const int r = threadIdx.x / CH_NB, j = threadIdx.x % CH_NB;
+    const int i = j0 + CH_NB + blockIdx.x * 8 + r;
+    Rw[r][j] = i < k ? G[(long long)i * k + j0 + j] : 0.0;
+    __syncthreads();
+    if (i < k) {
+        double acc = 0.0;
+        for (int l = 0; l <= j; ++l) acc = fma(Rw[r][l], Li[j][l], acc);
+        G[(long long)i * k + j0 + j] = acc;
+    }
+}
+
+// lower tile (ti, tj), tj <= ti, of the trailing block at s0 = j0 + CH_NB: G22 -= L21 L21^T
+__global__ void __launch_bounds__(256) chol_update(double* __restrict__ G, int k, int j0, const int* pred, int want) {
+    if (skip(pred, want)) return;
+    __shared__ double Pa[CH_NB][CH_NB + 1], Pb[CH_NB][CH_NB + 1];
+    const int t = blockIdx.x;
+    int ti = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+    while (ti * (ti + 1) / 2 > t) --ti;
+    const int tj = t - ti * (ti + 1) / 2;
+    const int s0 = j0 + CH_NB;
+    for (int e = threadIdx.x; e < CH_NB * CH_NB; e += blockDim.x) {
+        const int rr = e / CH_NB, l = e % CH_NB;
+        const int ia = s0 + ti * CH_NB + rr, ib = s0 + tj * CH_NB + rr;
+        Pa[rr][l] = ia < k ? G[(long long)ia * k + j0 + l] : 0.0;
+        Pb[rr][l] = ib < k ? G[(long long)ib * k + j0 + l] : 0.0;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < CH_NB * CH_NB; e += blockDim.x) {
+        const int rr = e / CH_NB, cc = e % CH_NB;
+        const int gi = s0 + ti * CH_NB + rr, gj = s0 + tj * CH_NB + cc;
+        if (gi < k && gj <= gi) {
+            double acc = 0.0;
+#pragma unroll 8
+            for (int l = 0; l < CH_NB; ++l) acc = fma(Pa[rr][l], Pb[cc][l], acc);
+            G[(long long)gi * k + gj] -= acc;
+        }
+    }
+}
+
+// lower Cholesky of the k x k G in place, dinv[j] = 1 / L[j][j]; one CTA for small k, blocked above
+void cholesky_dev(Ctx& ctx, double* G, int k, double* dinv, int* status, const int* pred, int want) {
+    if (k <= 128) {
+        cholesky_kernel<<<1, 1024, 0, ctx.stream>>>(G, k, dinv, status, pred, want);
+        ctx.count_launch();
+        return;
+    }
+    double* Linv = (double*)ctx.workspace(WS_CHOL_LINV, sizeof(double) * CH_NB * CH_NB);
+    for (int j0 = 0; j0 < k; j0 += CH_NB) {
+        chol_diag<<<1, 256, 0, ctx.stream>>>(G, k, j0, dinv, Linv, status, pred, want);
+        ctx.count_launch();
+        const int rest = k - j0 - CH_NB;
+        if (rest > 0) {
+            chol_panel<<<(unsigned)((rest + 7) / 8), 256, 0, ctx.stream>>>(G, k, j0, Linv, pred, want);
+            const int T = (rest + CH_NB - 1) / CH_NB;
+            chol_update<<<(unsigned)(T * (T + 1) / 2), 256, 0, ctx.stream>>>(G, k, j0, pred, want);
+            ctx.count_launch(2);
+        }
     }
 }
 
@@ -1136,7 +1621,40 @@ TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int dir
     // 2. tridiagonalisation: one persistent cooperative launch when it fits, else one
     //    launch per Householder step
     bool done = false;
-    if (n <= TRI_MAX_N) {
+    if (n <= TRI_MAX_N && n >= ctx.tri_lower_min_n) {
+        const size_t shm = sizeof(double2) * 3 * (size_t)n;
+        set_smem_attr_once(ctx, (const void*)tridiag_lower, (int)(sizeof(double2) * 3 * TRI_MAX_N + 1024));
+        int per_sm = 0;
+        VTN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tridiag_lower, TRL_THREADS, shm));
+        const int grid = std::min(ctx.num_sms, std::max(1, (n + 3) / 4));
+        if (per_sm >= 1 && grid >= 1) {
+            const size_t part_n = (size_t)(2 * grid + 8) * n;
+            const size_t elems = 2 * part_n + 2 * (size_t)n + 2 * (size_t)TRI_MAX_CHUNKS * n + 2 * (size_t)n;
+            const size_t bytes = sizeof(double2) * elems;
+            char* wsp = (char*)ctx.workspace(WS_EIG_PART, bytes + sizeof(unsigned) * 2 * TRI_MAX_CHUNKS);
+            TriBufsL tb;
+            tb.part = (double2*)wsp;
+            tb.pcol = tb.part + 2 * part_n;
+            tb.prow = tb.pcol + 2 * (size_t)n;
+            tb.p = tb.prow + 2 * (size_t)TRI_MAX_CHUNKS * n;
+            tb.arrive = (unsigned*)(wsp + bytes);
+            VTN_CUDA_TRY(cudaMemsetAsync(tb.arrive, 0, sizeof(unsigned) * 2 * TRI_MAX_CHUNKS, ctx.stream));
+            GridBar* bar = (GridBar*)(status + 4);
+            VTN_CUDA_TRY(cudaMemsetAsync(bar, 0, sizeof(GridBar), ctx.stream));
+            double2* Ap = A;
+            double2* Hp = H;
+            int nn = n;
+            void* args[] = {&Ap, &nn, &Hp, &s, &tb, &bar};
+            const int ttri = ctx.tbegin(TC_TRI, 16.0 / 3.0 * (double)n * n * n);
+            VTN_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)tridiag_lower, dim3(grid), dim3(TRL_THREADS), args, shm,
+                                                     ctx.stream));
+            ctx.tend(ttri);
+            ctx.count_launch();
+            ctx.check_launch("tridiag_lower");
+            done = true;
+        }
+    }
+    if (!done && n <= TRI_MAX_N) {
         const size_t shm = sizeof(double2) * 3 * (size_t)n;
         set_smem_attr_once(ctx, (const void*)tridiag_persistent, (int)(sizeof(double2) * 3 * TRI_MAX_N + 1024));
         int per_sm = 0;
@@ -1203,9 +1721,9 @@ TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int dir
     const unsigned ts_grid = (unsigned)((n + 31) / 32);
     gram_kernel<<<gg, 256, 0, ctx.stream>>>(Z, n, k, G, 0.0, nullptr, 0);
     ortho_check<<<1, 256, 0, ctx.stream>>>(G, k, 1e-3, flag);
-    cholesky_kernel<<<1, 1024, 0, ctx.stream>>>(G, k, dinv, status, flag, 0);
+    cholesky_dev(ctx, G, k, dinv, status, flag, 0);
     trsm_rows<<<ts_grid, 32 * TS_WARPS, ts_shm, ctx.stream>>>(Z, n, k, G, dinv, flag, 0);
-    ctx.count_launch(4);
+    ctx.count_launch(3);
     for (int pass = 0; pass < 3; ++pass) {
         double shift = 0.0;
         if (pass == 0) {
@@ -1213,9 +1731,9 @@ TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int dir
             shift = 11.0 * ((double)n * k + (double)k * (k + 1)) * EPS * (double)k;
         }
         gram_kernel<<<gg, 256, 0, ctx.stream>>>(Z, n, k, G, shift, flag, 1);
-        cholesky_kernel<<<1, 1024, 0, ctx.stream>>>(G, k, dinv, status, flag, 1);
+        cholesky_dev(ctx, G, k, dinv, status, flag, 1);
         trsm_rows<<<ts_grid, 32 * TS_WARPS, ts_shm, ctx.stream>>>(Z, n, k, G, dinv, flag, 1);
-        ctx.count_launch(3);
+        ctx.count_launch(2);
     }
     ctx.check_launch("orthonormalisation");
     // 6. back-transformation into the site tensors: T factors of the reflector blocks, then

@@ -374,7 +374,8 @@ void tc_gemm_bf16(Ctx& ctx, const TcGemmArgs& a, int timing_class, double useful
     if (tiles * 2 <= ctx.num_sms && nkb >= 8)
         splits = (int)std::min<long long>(std::max<long long>(1, ctx.num_sms / tiles), nkb / 4);
     splits = std::max(1, std::min(splits, 8));
-    splits = std::max(splits, (nkb + MAX_KB_PER_ACC - 1) / MAX_KB_PER_ACC);
+    const int kb_acc = a.max_kb_per_acc > 0 ? a.max_kb_per_acc : MAX_KB_PER_ACC;
+    splits = std::max(splits, (nkb + kb_acc - 1) / kb_acc);
     int per = (nkb + splits - 1) / splits;
     splits = (nkb + per - 1) / per;
     p.kb_per = per;

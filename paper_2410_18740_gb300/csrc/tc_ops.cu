@@ -232,7 +232,8 @@ __global__ void __launch_bounds__(256) mix_f32_kernel(int P, int d, int Q, MixIn
 }
 
 // The scaled-identity part of a collapse core as a channel GEMM: out[b][e] = sum_a C[a][b] in[a][e]
-// for every element e of the standard layout (e = (p, s, q), contiguous per channel).
+// for every element e of the standard layout (e = (p, s, q), contiguous per channel); C has row
+// stride ldc (>= w_out), so that a block of columns of a wider C can be applied.
 // Persistent: one CTA of 256 threads per SM walks element tiles of ET; C (w_in x w_out) stays in
 // shared memory, and the next tile of every input channel is copied by cp.async into the second
 // buffer while the current one is used.  Thread (tb, te) accumulates channels b = tb + 16 j
@@ -240,7 +241,8 @@ __global__ void __launch_bounds__(256) mix_f32_kernel(int P, int d, int Q, MixIn
 // JB or EI FMAs; a real C (the GBS couplings) takes 2 FMAs per complex product.
 template <int JB, int EI, bool REAL_C>
 __global__ void __launch_bounds__(256, 1) mix_cid_kernel(int w_in, int w_out, long long E, const float2* __restrict__ C,
-                                                         const float2* __restrict__ in, float2* __restrict__ out) {
+                                                         int ldc, const float2* __restrict__ in,
+                                                         float2* __restrict__ out) {
     constexpr int ET = 16 * EI;
     extern __shared__ float2 sh[];
     float2* Csh = sh;                                // [w_in][16 JB]
@@ -249,7 +251,7 @@ __global__ void __launch_bounds__(256, 1) mix_cid_kernel(int w_in, int w_out, lo
     const int wpad = 16 * JB;
     for (int t = threadIdx.x; t < w_in * wpad; t += blockDim.x) {
         const int a = t / wpad, b = t - (t / wpad) * wpad;
-        Csh[t] = b < w_out ? C[(long long)a * w_out + b] : make_float2(0.f, 0.f);
+        Csh[t] = b < w_out ? C[(long long)a * ldc + b] : make_float2(0.f, 0.f);
     }
     const int tb = threadIdx.x & 15, te = threadIdx.x >> 4;
     const long long n_tiles = (E + ET - 1) / ET;
@@ -359,32 +361,32 @@ int mix_smem_limit(const Ctx& ctx) {
 }
 
 template <int JB, int EI, bool R>
-void launch_mix_cid_t(Ctx& ctx, int bytes, unsigned grid, int w_in, int w_out, long long E, const float2* C,
+void launch_mix_cid_t(Ctx& ctx, int bytes, unsigned grid, int w_in, int w_out, long long E, const float2* C, int ldc,
                       const float2* in, float2* out) {
     set_smem_attr_once(ctx, (const void*)mix_cid_kernel<JB, EI, R>, bytes);
-    mix_cid_kernel<JB, EI, R><<<grid, 256, bytes, ctx.stream>>>(w_in, w_out, E, C, in, out);
+    mix_cid_kernel<JB, EI, R><<<grid, 256, bytes, ctx.stream>>>(w_in, w_out, E, C, ldc, in, out);
     ctx.count_launch();
 }
 
 template <int JB>
 void launch_mix_cid_j(Ctx& ctx, int EI, bool real_c, int bytes, unsigned grid, int w_in, int w_out, long long E,
-                      const float2* C, const float2* in, float2* out) {
+                      const float2* C, int ldc, const float2* in, float2* out) {
     if (EI == 4) {
-        if (real_c) launch_mix_cid_t<JB, 4, true>(ctx, bytes, grid, w_in, w_out, E, C, in, out);
-        else launch_mix_cid_t<JB, 4, false>(ctx, bytes, grid, w_in, w_out, E, C, in, out);
+        if (real_c) launch_mix_cid_t<JB, 4, true>(ctx, bytes, grid, w_in, w_out, E, C, ldc, in, out);
+        else launch_mix_cid_t<JB, 4, false>(ctx, bytes, grid, w_in, w_out, E, C, ldc, in, out);
     } else {
-        if (real_c) launch_mix_cid_t<JB, 2, true>(ctx, bytes, grid, w_in, w_out, E, C, in, out);
-        else launch_mix_cid_t<JB, 2, false>(ctx, bytes, grid, w_in, w_out, E, C, in, out);
+        if (real_c) launch_mix_cid_t<JB, 2, true>(ctx, bytes, grid, w_in, w_out, E, C, ldc, in, out);
+        else launch_mix_cid_t<JB, 2, false>(ctx, bytes, grid, w_in, w_out, E, C, ldc, in, out);
     }
 }
 
 void launch_mix_cid(Ctx& ctx, int JB, int EI, bool real_c, int bytes, unsigned grid, int w_in, int w_out, long long E,
-                    const float2* C, const float2* in, float2* out) {
+                    const float2* C, int ldc, const float2* in, float2* out) {
     switch (JB) {
-        case 2: launch_mix_cid_j<2>(ctx, EI, real_c, bytes, grid, w_in, w_out, E, C, in, out); break;
-        case 4: launch_mix_cid_j<4>(ctx, EI, real_c, bytes, grid, w_in, w_out, E, C, in, out); break;
-        case 7: launch_mix_cid_j<7>(ctx, EI, real_c, bytes, grid, w_in, w_out, E, C, in, out); break;
-        default: launch_mix_cid_j<8>(ctx, EI, real_c, bytes, grid, w_in, w_out, E, C, in, out); break;
+        case 2: launch_mix_cid_j<2>(ctx, EI, real_c, bytes, grid, w_in, w_out, E, C, ldc, in, out); break;
+        case 4: launch_mix_cid_j<4>(ctx, EI, real_c, bytes, grid, w_in, w_out, E, C, ldc, in, out); break;
+        case 7: launch_mix_cid_j<7>(ctx, EI, real_c, bytes, grid, w_in, w_out, E, C, ldc, in, out); break;
+        default: launch_mix_cid_j<8>(ctx, EI, real_c, bytes, grid, w_in, w_out, E, C, ldc, in, out); break;
     }
 }
 
@@ -435,6 +437,27 @@ void tc_pack(Ctx& ctx, const float2* X, int rows, int K, int kb, long long ld, l
     pack_impl<float2>(ctx, X, rows, K, kb, ld, s_kb, conj_t, is_b, out, rq, s_rq);
 }
 
+bool channel_gemm_f32(Ctx& ctx, int w_in, int w_out, long long E, const float2* C, int ldc, bool real_c,
+                      const float2* in, float2* out) {
+    if (E <= 0 || w_out <= 0) return true;
+    const int limit = mix_smem_limit(ctx);
+    for (int b0 = 0; b0 < w_out; b0 += 128) {
+        const int wo = std::min(128, w_out - b0);
+        const int jneed = (wo + 15) / 16;
+        const int JB = jneed <= 2 ? 2 : jneed <= 4 ? 4 : jneed <= 7 ? 7 : 8;
+        const size_t cbytes = sizeof(float2) * (size_t)w_in * 16 * JB;
+        int EI = 4;
+        if (cbytes + 2 * sizeof(float2) * (size_t)w_in * 64 > (size_t)limit) EI = 2;
+        const size_t bytes = cbytes + 2 * sizeof(float2) * (size_t)w_in * 16 * EI;
+        if (bytes > (size_t)limit) return false;
+        const long long tiles = (E + 16 * EI - 1) / (16 * EI);
+        const unsigned grid = (unsigned)std::min<long long>(tiles, std::max(ctx.num_sms, 1));
+        launch_mix_cid(ctx, JB, EI, real_c, (int)bytes, grid, w_in, wo, E, C + b0, ldc, in, out + (long long)b0 * E);
+        ctx.check_launch("mix_cid_kernel");
+    }
+    return true;
+}
+
 void mix_apply_f32(Ctx& ctx, const DevCore& core, bool by_col, int P, int Q, const float2* in, float2* out,
                    const long long* in_strides) {
     const int w_out = by_col ? core.wr : core.wl;
@@ -473,7 +496,7 @@ void mix_apply_f32(Ctx& ctx, const DevCore& core, bool by_col, int P, int Q, con
         if (bytes <= (size_t)limit) {
             const long long tiles = (E + 16 * EI - 1) / (16 * EI);
             const unsigned grid_c = (unsigned)std::min<long long>(tiles, std::max(ctx.num_sms, 1));
-            launch_mix_cid(ctx, JB, EI, core.cid_real, (int)bytes, grid_c, w_in, w_out, E, core.cid, in, out);
+            launch_mix_cid(ctx, JB, EI, core.cid_real, (int)bytes, grid_c, w_in, w_out, E, core.cid, w_out, in, out);
             ctx.check_launch("mix_cid_kernel");
             ptr = core.dcol_ptr;
             src = core.dcol_src;
@@ -497,7 +520,12 @@ void mix_apply_f32(Ctx& ctx, const DevCore& core, bool by_col, int P, int Q, con
 
 // ----------------------------------------------------------------------------- H_eff
 void heff_pack_envs(Ctx& ctx, const DevCore& Wi, const DevCore& Wj, int chi_l, int chi_r, const double2* L,
-                    const double2* R, HeffPacked& pk) {
+                    const double2* R, HeffPacked& pk, const BondTerms* terms) {
+    if (terms && terms->usable) {
+        heff_pack_terms(ctx, *terms, chi_l, chi_r, L, R, pk);
+        return;
+    }
+    pk.terms = nullptr;
     const int wl = Wi.wl, wr = Wj.wr;
     pk.chi_l = chi_l;
     pk.chi_r = chi_r;
@@ -515,6 +543,10 @@ void heff_pack_envs(Ctx& ctx, const DevCore& Wi, const DevCore& Wj, int chi_l, i
 
 void heff_apply_bf16x3(Ctx& ctx, const DevCore& Wi, const DevCore& Wj, const HeffPacked& pk, const double2* theta,
                        double2* y) {
+    if (pk.terms) {
+        heff_apply_terms(ctx, pk, theta, y);
+        return;
+    }
     const int d = Wi.d, chi_l = pk.chi_l, chi_r = pk.chi_r;
     const long long n_theta = (long long)chi_l * d * d * chi_r;
     const int wmax = std::max(Wi.wl, std::max(Wi.wr, Wj.wr));
@@ -539,6 +571,7 @@ void heff_apply_bf16x3(Ctx& ctx, const DevCore& Wi, const DevCore& Wj, const Hef
     g1.D = X;
     g1.ldd = 2LL * d * d * chi_r;
     g1.d_fp64 = false;
+    g1.max_kb_per_acc = ctx.tc_kb_heff;
     tc_gemm_bf16(ctx, g1, TC_HEFF, useful1);
     mix_apply_f32(ctx, Wi, true, chi_l, d * chi_r, X, Yb);
     mix_apply_f32(ctx, Wj, true, chi_l * d, chi_r, Yb, X);
@@ -555,6 +588,7 @@ void heff_apply_bf16x3(Ctx& ctx, const DevCore& Wi, const DevCore& Wj, const Hef
     g2.D = y;
     g2.ldd = 2LL * chi_r;
     g2.d_fp64 = true;
+    g2.max_kb_per_acc = ctx.tc_kb_heff;
     tc_gemm_bf16(ctx, g2, TC_HEFF, useful2);
 }
 
@@ -589,6 +623,7 @@ void env_left_bf16x3(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const dou
     g1.D = X;
     g1.ldd = 2LL * d * chi_r;
     g1.d_fp64 = false;
+    g1.max_kb_per_acc = ctx.tc_kb_env;
     tc_gemm_bf16(ctx, g1, -1, 8.0 * wl * chi_l * (double)chi_l * d * chi_r);
     // 2. U[b][i][t][k] = sum W[a,b,t,s] T[a][i][s][k]
     mix_apply_f32(ctx, W, true, chi_l, chi_r, X, Yb);
@@ -610,6 +645,7 @@ void env_left_bf16x3(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const dou
     g3.D = T;
     g3.ldd = 2LL * wr * chi_r;
     g3.d_fp64 = true;
+    g3.max_kb_per_acc = ctx.tc_kb_env;
     tc_gemm_bf16(ctx, g3, -1, 8.0 * chi_r * (double)wr * chi_r * chi_l * d);
     const long long cnt = (long long)wr * chi_r * chi_r;
     permute_blk<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx.stream>>>(T, chi_r, wr, chi_r, out);
@@ -642,6 +678,7 @@ void env_right_bf16x3(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const do
     g1.D = X;
     g1.ldd = 2LL * wr * chi_r;
     g1.d_fp64 = false;
+    g1.max_kb_per_acc = ctx.tc_kb_env;
     tc_gemm_bf16(ctx, g1, -1, 8.0 * chi_l * d * (double)wr * chi_r * chi_r);
     // 2. U[b][j][t][p] = sum W[b,c,t,s] T[c][j][s][p]; T element (c, j, s, p) sits at
     //    ((j d + s) wr + c) chi_r + p
@@ -664,6 +701,7 @@ void env_right_bf16x3(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const do
     g3.D = out;
     g3.ldd = 2LL * chi_l;
     g3.d_fp64 = true;
+    g3.max_kb_per_acc = ctx.tc_kb_env;
     tc_gemm_bf16(ctx, g3, -1, 8.0 * wl * chi_l * (double)chi_l * d * chi_r);
 }
 

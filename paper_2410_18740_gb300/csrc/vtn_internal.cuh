@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <complex>
 #include <cstdint>
 #include <functional>
 #include <string>
@@ -99,6 +100,11 @@ struct Ctx {
     std::string err;
     long long launches = 0;
     bool timing = false;
+    // k-blocks per tensor-memory accumulator in the split-precision products: environment updates
+    // (their errors accumulate along the chain) and H_eff psi
+    int tc_kb_env = 64, tc_kb_heff = 256;
+    // the truncation's tridiagonalisation keeps only the lower triangle up to date for n >= this
+    int tri_lower_min_n = 1 << 30;
     struct Tc {
         long long launches = 0;
         double flops = 0, seconds = 0;
@@ -142,7 +148,7 @@ enum WsSlot {
     WS_EIG_Y, WS_EIG_WORK, WS_EIG_U, WS_CORE_A, WS_CORE_B, WS_ENV_TMP, WS_MISC, WS_TC_L, WS_TC_R, WS_TC_B1,
     WS_TC_A2, WS_TC_PART, WS_GEMM_SPLIT, WS_EIG_PART, WS_TC_ENV, WS_EIG_T, WS_H2_ENV, WS_EXPAND,
     WS_TRUNC_L, WS_TRUNC_R, WS_CENTER, WS_MLP_ACT, WS_MLP_Y, WS_MLP_G, WS_WARM_S, WS_WARM_Z, WS_WARM_P,
-    WS_WARM_U, WS_WARM_N, WS_WARM_Q0, WS_CQR_G, WS_CQR_T, WS_CQR_B, WS_RQ_Y, WS_RQ_S, WS_COUNT
+    WS_WARM_U, WS_WARM_N, WS_WARM_Q0, WS_CQR_G, WS_CQR_T, WS_CQR_B, WS_RQ_Y, WS_RQ_S, WS_CHOL_LINV, WS_COUNT
 };
 
 // ------------------------------------------------------------------ cores
@@ -186,6 +192,8 @@ struct TcGemmArgs {
     void* D;
     long long ldd;
     bool d_fp64 = false;
+    int max_kb_per_acc = 0;  // > 0: at most this many 64-wide k-blocks per tensor-memory accumulator
+                             // (longer sums are split and their FP32 partials added in FP64); 0 = 256
 };
 void tc_gemm_bf16(Ctx& ctx, const TcGemmArgs& a, int timing_class = -1, double useful_flops = 0.0);
 long long tc_k6(long long Kt);
@@ -210,17 +218,57 @@ void mix_apply_f32(Ctx& ctx, const DevCore& core, bool by_col, int P, int Q, con
 void heff_apply_dev(Ctx& ctx, const DevCore& Wi, const DevCore& Wj, int chi_l, int chi_r,
                     const double2* L, const double2* R, const double2* theta, double2* y);
 double heff_flops(const DevCore& Wi, const DevCore& Wj, int chi_l, int chi_r);
-// split-precision (BF16X3) H_eff psi: environments packed once per bond
+// out[b][e] = sum_a C[a * ldc + b] in[a][e] (b < w_out, e < E), FP32, on the channel-GEMM kernel of the
+// collapse cores; false (nothing launched) when C does not fit in shared memory
+bool channel_gemm_f32(Ctx& ctx, int w_in, int w_out, long long E, const float2* C, int ldc, bool real_c,
+                      const float2* in, float2* out);
+
+// Term form of a bond's two-site H_eff for the split-precision mode (heff_terms.cu):
+//   H_eff = sum_t Lhat_t (x) (B_o(t) (x) B'_p(t)) (x) Rhat_t,
+//   Lhat_t = sum_a Cl[a][t] L[a],  Rhat_t = sum_c Cr[c][t] R[c],
+// where {B_o} and {B'_p} are operator bases of the two cores' d x d entries (B_0 = I) and the
+// coefficient matrices K_op = W_i^(o) W_{i+1}^(p) are factorised exactly.  The first n_id terms
+// have o = p = 0 (identity operators); kron holds B_o and B'_p for the others.
+struct BondTerms {
+    bool usable = false;      // false: no compact term form (the bond keeps the channel-mixing form)
+    bool worthwhile = false;  // the term form is the cheaper one for this bond
+    int wl = 0, wr = 0, d = 0, n_t = 0, n_id = 0;
+    bool real_l = false, real_r = false;  // Cl / Cr have no imaginary parts
+    float2* Cl = nullptr;     // [wl][n_t]
+    float2* Cr = nullptr;     // [wr][n_t]
+    float2* kron = nullptr;   // [n_t - n_id][2][d][d]: B_o and B'_p of the terms that are not identities
+    int* kop = nullptr;       // [n_t - n_id][2]: their basis indices (0 = identity, skipped)
+    double2* Cl64 = nullptr;  // [n_t][wl] (transposed, FP64: the fold's fallback on the FP64 GEMM)
+    double2* Cr64 = nullptr;  // [n_t][wr]
+    DevBuf buf;
+};
+void build_bond_terms(Ctx& ctx, const HostCore& Wi, const HostCore& Wj, BondTerms& out);
+// host part: operator bases (ri and rj elements of d x d, B_0 = I), the terms' operator pairs
+// (ops[2t], ops[2t+1]) and factors U[t][a], V[t][c]; false when the bond has no compact term form;
+// worthwhile: the term form is the cheaper one for this bond
+bool bond_terms_host(const HostCore& Wi, const HostCore& Wj, int& n_id, std::vector<int>& ops,
+                     std::vector<std::complex<double>>& U, std::vector<std::complex<double>>& V,
+                     std::vector<std::complex<double>>& Bi, std::vector<std::complex<double>>& Bj, int& ri, int& rj,
+                     bool& worthwhile);
+void free_bond_terms(Ctx& ctx, BondTerms& bt);
+
+// split-precision (BF16X3) H_eff psi: environments packed once per bond (folded into the term
+// environments Lhat, Rhat when the bond has a usable term form)
 struct HeffPacked {
     int chi_l = 0, chi_r = 0, wl = 0, wr = 0;
     long long ldL = 0, ldR = 0;
     __nv_bfloat16* L = nullptr;
     __nv_bfloat16* R = nullptr;
+    const BondTerms* terms = nullptr;  // non-null: term form (wl = wr = n_t then)
 };
 void heff_pack_envs(Ctx& ctx, const DevCore& Wi, const DevCore& Wj, int chi_l, int chi_r, const double2* L,
-                    const double2* R, HeffPacked& pk);
+                    const double2* R, HeffPacked& pk, const BondTerms* terms = nullptr);
 void heff_apply_bf16x3(Ctx& ctx, const DevCore& Wi, const DevCore& Wj, const HeffPacked& pk, const double2* theta,
                        double2* y);
+// the term form's pieces (heff_terms.cu)
+void heff_pack_terms(Ctx& ctx, const BondTerms& bt, int chi_l, int chi_r, const double2* L, const double2* R,
+                     HeffPacked& pk);
+void heff_apply_terms(Ctx& ctx, const HeffPacked& pk, const double2* theta, double2* y);
 void env_left2_dev(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const double2* L2, const double2* A,
                    double2* out, double2* tv, double2* u);
 // multilayer perceptron of the learned warm start (mlp.cu)
@@ -344,6 +392,7 @@ struct vtn_mpo_s {
     int device = -1;
     vtn_ctx owner = nullptr;
     std::vector<vtn::DevCore> dcores;
+    std::vector<vtn::BondTerms> bterms;  // M - 1: term form of each bond's H_eff (split precision)
     double2* iso_dev = nullptr;  // M * D * d
 };
 

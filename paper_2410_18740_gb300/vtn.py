@@ -43,7 +43,7 @@ class vtn_sweep_opts(C.Structure):
                 ("krylov_max", C.c_int), ("lanczos_max_restarts", C.c_int), ("e_tol", C.c_double),
                 ("e_target", C.c_double), ("use_e_target", C.c_int), ("seed", C.c_uint64),
                 ("trunc_mode", C.c_int), ("trunc_q", C.c_int), ("window_lo", C.c_int), ("window_hi", C.c_int),
-                ("energy_mode", C.c_int)]
+                ("energy_mode", C.c_int), ("heff_form", C.c_int), ("env_fp64", C.c_int)]
 
 
 class vtn_sweep_report(C.Structure):
@@ -79,6 +79,7 @@ _SIGS = {
     "vtn_mpo_covariance": [_P, _PD],
     "vtn_mpo_isometry": [_P, _I, _PD],
     "vtn_mpo_core": [_P, _I, _PI, _PI, _PI, _PD],
+    "vtn_mpo_bond_terms": [_P, _I, _PI, _PI, _PI, _PI, _PI, _PI, _PD, _PD, _PD, _PD],
     "vtn_mpo_norm_bound": [_P, _PD],
     "vtn_mps_random": [_P, _P, _I, C.c_uint64, C.POINTER(_P)],
     "vtn_mps_from_host": [_P, _P, _PI, C.POINTER(_PD), C.POINTER(_P)],
@@ -131,6 +132,8 @@ _SIGS = {
     "vtn_heff_apply_static": [C.POINTER(vtn_core), C.POINTER(vtn_core), _I, _I, _P, _P, _P, _P, _P],
     "vtn_gemm_bf16": [_P, _I, _I, _I, _P, C.c_longlong, _P, C.c_longlong, _P, C.c_longlong, _I],
     "vtn_timing": [_P, _I],
+    "vtn_set_tc_accumulation": [_P, _I, _I],
+    "vtn_set_tridiag_lower": [_P, _I],
     "vtn_timing_read": [_P, _I, C.POINTER(C.c_longlong), _PD, _PD],
     "vtn_timing_reset": [_P],
 }
@@ -299,6 +302,30 @@ def vtn_mpo_core(mpo, site):
     _check(None, lib().vtn_mpo_core(mpo, int(site), C.byref(n), rows.ctypes.data_as(_PI),
                                     cols.ctypes.data_as(_PI), ops.ctypes.data_as(_PD)))
     return int(w[site]), int(w[site + 1]), rows, cols, ops.view(np.complex128)[..., 0][: n.value]
+
+
+def vtn_mpo_bond_terms(mpo, bond):
+    """Term form of bond (bond, bond+1): None when the bond has no compact one, else a dict with
+    used (the split-precision sweeps use it), n_id, ops (n_terms x 2), U (n_terms x w_l),
+    V (n_terms x w_r), Bi (ri x d x d), Bj."""
+    _, d, _, w = vtn_mpo_info(mpo)
+    usable, nt, nid, ri, rj = C.c_int(0), C.c_int(0), C.c_int(0), C.c_int(0), C.c_int(0)
+    _check(None, lib().vtn_mpo_bond_terms(mpo, int(bond), C.byref(usable), C.byref(nt), C.byref(nid), C.byref(ri),
+                                          C.byref(rj), None, None, None, None, None))
+    if not usable.value:
+        return None
+    n, wl, wr = nt.value, int(w[bond]), int(w[bond + 2])
+    ops = np.zeros((max(n, 1), 2), np.int32)
+    U = np.zeros((max(n, 1), wl, 2))
+    V = np.zeros((max(n, 1), wr, 2))
+    Bi = np.zeros((ri.value, d, d, 2))
+    Bj = np.zeros((rj.value, d, d, 2))
+    _check(None, lib().vtn_mpo_bond_terms(mpo, int(bond), C.byref(usable), C.byref(nt), C.byref(nid), C.byref(ri),
+                                          C.byref(rj), ops.ctypes.data_as(_PI), U.ctypes.data_as(_PD),
+                                          V.ctypes.data_as(_PD), Bi.ctypes.data_as(_PD), Bj.ctypes.data_as(_PD)))
+    cv = lambda x: x.view(np.complex128)[..., 0]
+    return {"used": usable.value == 1, "n_id": nid.value, "ops": ops[:n], "U": cv(U)[:n], "V": cv(V)[:n],
+            "Bi": cv(Bi), "Bj": cv(Bj)}
 
 
 def vtn_gaussian_bond_spectrum(mpo, cut, k):
@@ -698,6 +725,14 @@ def vtn_gemm_bf16(ctx, A, B, D):
     _check(ctx, lib().vtn_gemm_bf16(ctx, int(M), int(N), int(K), _dptr(A), int(A.stride(0)), _dptr(B),
                                     int(B.stride(0)), _dptr(D), int(D.stride(0)),
                                     1 if D.dtype == torch.float64 else 0))
+
+
+def vtn_set_tc_accumulation(ctx, env_kblocks=64, heff_kblocks=256):
+    _check(ctx, lib().vtn_set_tc_accumulation(ctx, int(env_kblocks), int(heff_kblocks)))
+
+
+def vtn_set_tridiag_lower(ctx, min_n=1 << 30):
+    _check(ctx, lib().vtn_set_tridiag_lower(ctx, int(min_n)))
 
 
 def vtn_timing(ctx, enable):

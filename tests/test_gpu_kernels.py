@@ -104,8 +104,12 @@ TRUNC_CASES = [
 ]
 
 
-@pytest.mark.parametrize("cl,d1,d2,cr,direction,kmax", TRUNC_CASES)
-def test_truncation_matches_oracle(ctx, cl, d1, d2, cr, direction, kmax):
+@pytest.mark.parametrize("tri_form", ["full", "lower"])
+@pytest.mark.parametrize("cl,d1,d2,cr,direction,kmax", TRUNC_CASES + [(48, 6, 6, 50, 0, 64), (50, 6, 6, 48, 1, 64)])
+def test_truncation_matches_oracle(ctx, cl, d1, d2, cr, direction, kmax, tri_form):
+    """Both forms of the tridiagonalisation (the lower-triangle one normally runs from n = 2048);
+    n = 288 and 300 take its two-column-per-lane chunks."""
+    vtn.vtn_set_tridiag_lower(ctx, 0 if tri_form == "lower" else 1 << 30)
     rng = inputs.rng_for(3000 + cl * 31 + cr + direction)
     # Schmidt values decaying slowly enough that every kept weight is resolved in FP64
     # (rho = T T^dag carries sigma^2, so weights below ~1e-16 are numerical noise)
@@ -130,6 +134,7 @@ def test_truncation_matches_oracle(ctx, cl, d1, d2, cr, direction, kmax):
     prod = np.einsum("asb,btc->astc", L, R)
     oprod = np.einsum("asb,btc->astc", oleft, oright)
     assert np.abs(prod - oprod).max() < 1e-11
+    vtn.vtn_set_tridiag_lower(ctx)
 
 
 def test_truncation_rank_deficient(ctx):
@@ -222,11 +227,13 @@ def test_kernel_calls_reject_bad_arguments(ctx):
     assert e.value.status == vtn.VTN_EUNSUPPORTED
 
 
-def test_truncation_at_the_large_workload_shape(ctx):
+@pytest.mark.parametrize("tri_form", ["lower", "full"])
+def test_truncation_at_the_large_workload_shape(ctx, tri_form):
     """Maximum size used by the solver: theta (512, 6, 6, 512) as at the middle bond of the
     large workload (chi = 512, d = 6), n = 3072, k = 512.  Theta = U diag(s) V^dag is built with
     a known SVD (Haar U, V; s_i = exp(-i / 300)), so the kept weights, the discarded weight and
     the projected product are known without a CPU eigensolver."""
+    vtn.vtn_set_tridiag_lower(ctx, 0 if tri_form == "lower" else 1 << 30)
     rng = inputs.rng_for(4242)
     chi, d, k = 512, 6, 512
     n = chi * d
@@ -246,3 +253,4 @@ def test_truncation_at_the_large_workload_shape(ctx):
     prod = Lm @ host(right).reshape(k, n)
     expect = (U[:, :k] * s[:k]) @ V[:, :k].conj().T
     assert np.abs(prod - expect).max() < 1e-11
+    vtn.vtn_set_tridiag_lower(ctx)

@@ -132,3 +132,26 @@ def test_windowed_sweep_at_full_size(ctx):
     assert smp.shape == (16, 100) and smp.min() >= 0 and smp.max() < 24
     vtn.vtn_mps_free(mps)
     vtn.vtn_mpo_free(m)
+
+
+def test_shorter_accumulation_runs_are_more_accurate(ctx, large_cores):
+    """The tensor cores' FP32 accumulation loses accuracy with the length of the sum: the left
+    environment update at the middle of the large workload (K = 6 chi d = 18432 split terms per
+    output) with 4 k-blocks per accumulator is closer to the oracle than with 256, and both meet
+    the split-precision bars."""
+    W_s, W = large_cores[MID]
+    rng = inputs.rng_for(4545)
+    A = inputs.random_complex((CHI, D_LOC, CHI), rng)
+    env = inputs.random_complex((W_s.w_left, CHI, CHI), rng)
+    chans = [0, 1, 37, W_s.w_right - 1]
+    ref = odmrg.env_left(env, A, W_s.dense()[:, chans])
+    errs = {}
+    for kb in (256, 4):
+        vtn.vtn_set_tc_accumulation(ctx, kb, 256)
+        out = torch.empty((W_s.w_right, CHI, CHI), dtype=torch.complex128, device="cuda")
+        vtn.vtn_env_update(ctx, W, 0, CHI, CHI, dev(env), dev(A), out, prec=vtn.VTN_BF16X3)
+        got = out[chans].cpu().numpy()
+        errs[kb] = _rel_norm(got, ref)
+        assert _rel_max(got, ref) <= 2e-4 and errs[kb] <= 5e-5
+    vtn.vtn_set_tc_accumulation(ctx)
+    assert errs[4] < errs[256], errs
