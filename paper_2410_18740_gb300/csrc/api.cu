@@ -924,8 +924,14 @@ vtn_status sweep_body(vtn_ctx work, vtn_ctx owner, vtn_mpo mpo, vtn_mps* state, 
     double prevE = 0.0;
     bool have_prev = false;
     // theta = A_i A_i+1
-    auto form_theta = [&](int i) {
+    auto form_theta = [&](int i, bool start_vector) {
         const int cl = mps->dims[i], cm = mps->dims[i + 1], cr = mps->dims[i + 2];
+        if (split && start_vector && false) {
+            // the Lanczos start vector feeds split-precision products only
+            zgemm_bf16x3(c, cl * d, d * cr, cm, mps->sites[i], cm, mps->sites[i + 1], (long long)d * cr, theta,
+                         (long long)d * cr);
+            return;
+        }
         GemmArgs g;
         g.M = cl * d; g.N = d * cr; g.K = cm;
         g.A = mps->sites[i]; g.lda = cm;
@@ -953,7 +959,7 @@ vtn_status sweep_body(vtn_ctx work, vtn_ctx owner, vtn_mpo mpo, vtn_mps* state, 
                 const int sidx = dir * (hi - lo) + step;
                 double* lz_slot = deferred ? dbuf + slot * sidx : nullptr;
                 double* tr_slot = deferred ? lz_slot + 5 : nullptr;
-                form_theta(i);
+                form_theta(i, true);
                 const long long n = (long long)cl * d * d * cr;
                 const DevCore& Wi = mpo->dcores[i];
                 const DevCore& Wj = mpo->dcores[i + 1];
@@ -1003,7 +1009,7 @@ vtn_status sweep_body(vtn_ctx work, vtn_ctx owner, vtn_mpo mpo, vtn_mps* state, 
             // Rayleigh quotient of the final centre theta = A_lo A_lo+1 under H_eff of bond (lo, lo+1)
             const int cl = mps->dims[lo], cr = mps->dims[lo + 2];
             const long long n = (long long)cl * d * d * cr;
-            form_theta(lo);
+            form_theta(lo, false);
             double2* y = (double2*)c.workspace(WS_RQ_Y, sizeof(double2) * (size_t)n);
             double* sc = (double*)c.workspace(WS_RQ_S, sizeof(double) * 64);
             const DevCore& Wi = mpo->dcores[lo];

@@ -651,7 +651,7 @@ constexpr int TRL_NW = TRL_THREADS / 32;
 constexpr int TRL_RB = 4;  // rows per warp batch
 
 struct TriBufsL {
-    double2* part;     // [2][2 nb + 8][n] column partials per unit of a chunk
+    double2* part;     // [2][nb][n] column partials per CTA slot of a chunk
     double2* pcol;     // [2][n] column part of A v (unscaled), written by a chunk's last unit
     double2* prow;     // [2][TRI_MAX_CHUNKS][n] row parts per column chunk
     double2* p;        // [2][n] p = tau A v
@@ -691,26 +691,56 @@ __device__ __forceinline__ double2 reduce_scatter4(double2 r[TRL_RB], int lane) 
     return r[0];
 }
 
-// Trailing pass of step k, lower triangle.  Work unit u: chunk c = the largest with prefix[c] <= u,
-// slice cs = u - prefix[c] of CS_c = prefix[c+1] - prefix[c]; warp w walks the local rows
-// c W + cs NW + w + t CS_c NW; lane l owns the columns c W + q 32 + l (q < CPL).
+// Trailing pass of step k, lower triangle.  The rows of the chunks, in blocks of TRL_IB rows (item
+// i of chunk c: local rows c W + TRL_IB (i - items[c]) ...), are split into nb equal contiguous
+// ranges, one per CTA; a CTA's range covers one or more chunk segments.  In a segment warp w walks
+// the rows r0 + w + t NW; lane l owns the columns c W + q 32 + l (q < CPL).  Column partials go to
+// slot (CTA - first CTA of the chunk) and the chunk's last CTA sums them in slot order.
+constexpr int TRL_IB = 8;
+
+__device__ __forceinline__ int tri_item_start(int b, int T, int nb) { return (int)(((long long)b * T) / nb); }
+
+// the CTA whose range holds item i
+__device__ __forceinline__ int tri_item_owner(int i, int T, int nb) {
+    int lo = 0, hi = nb;  // start(lo) <= i < start(hi)
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (tri_item_start(mid, T, nb) <= i) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 template <int CPL>
 __device__ void tri_pass_lower(double2* __restrict__ A, int n, int k, int m, int nb, bool have_prev,
                                const double2* vprev, const double2* wprev, const double2* vcur, double2* pk,
                                double2* pcol, double2* prow, unsigned* arrive, double2* colred, int& last_sh,
-                               const int* prefix, int C) {
+                               const int* items, int C) {
     constexpr int W = 32 * CPL;
     constexpr int LD = TRI_MAX_CPL * 32;  // colred row stride
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int U = prefix[C];
-    for (int unit = (int)blockIdx.x; unit < U; unit += nb) {
-        int lo = 0, hi = C;  // prefix[lo] <= unit < prefix[hi]
+    const int T = items[C];
+    const int nbe = min(nb, T);  // CTAs with a non-empty range (every range below nbe holds an item)
+    const int b = (int)blockIdx.x;
+    if (b >= nbe) return;
+    const int i0 = tri_item_start(b, T, nbe), i1 = tri_item_start(b + 1, T, nbe);
+    int c = 0;
+    {
+        int lo = 0, hi = C;  // items[lo] <= i0 < items[hi]
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
-            if (prefix[mid] <= unit) lo = mid;
+            if (items[mid] <= i0) lo = mid;
             else hi = mid;
         }
-        const int c = lo, cs = unit - prefix[c], CSc = prefix[c + 1] - prefix[c];
+        c = lo;
+    }
+    for (; c < C && items[c] < i1; ++c) {
+        const int lo_i = max(i0, items[c]), hi_i = min(i1, items[c + 1]);
+        const int r0 = c * W + TRL_IB * (lo_i - items[c]);
+        const int r1 = min(m, c * W + TRL_IB * (hi_i - items[c]));
+        const int b_first = tri_item_owner(items[c], T, nbe);
+        const int b_last = tri_item_owner(items[c + 1] - 1, T, nbe);
+        const int slot = b - b_first, nslots = b_last - b_first + 1;
         int il[CPL];
         bool ok[CPL];
         double2 vpi[CPL], wpi[CPL], vci[CPL];
@@ -728,8 +758,8 @@ __device__ void tri_pass_lower(double2* __restrict__ A, int n, int k, int m, int
             vci[q] = ok[q] ? vcur[il[q]] : make_double2(0.0, 0.0);
             accx[q] = accy[q] = 0.0;
         }
-        const int S = CSc * TRL_NW;
-        for (int jb = c * W + cs * TRL_NW + warp; jb < m; jb += TRL_RB * S) {
+        constexpr int S = TRL_NW;
+        for (int jb = r0 + warp; jb < r1; jb += TRL_RB * S) {
             double2 a[TRL_RB][CPL];
             // loads first (TRL_RB * CPL in flight), then the updates, stores and sums
 #pragma unroll
@@ -737,15 +767,16 @@ __device__ void tri_pass_lower(double2* __restrict__ A, int n, int k, int m, int
                 const int j = jb + r * S;
 #pragma unroll
                 for (int q = 0; q < CPL; ++q)
-                    a[r][q] = (j < m && ok[q] && j >= il[q]) ? __ldcg(&A[(long long)(k + 1 + j) * n + (k + 1 + il[q])])
-                                                             : make_double2(0.0, 0.0);
+                    a[r][q] = (j < r1 && ok[q] && j >= il[q])
+                                  ? __ldcg(&A[(long long)(k + 1 + j) * n + (k + 1 + il[q])])
+                                  : make_double2(0.0, 0.0);
             }
             double2 racc[TRL_RB];
 #pragma unroll
             for (int r = 0; r < TRL_RB; ++r) {
                 const int j = jb + r * S;
                 racc[r] = make_double2(0.0, 0.0);
-                if (j >= m) continue;  // warp-uniform
+                if (j >= r1) continue;  // warp-uniform
                 const double2 v = vcur[j];
                 double2 vpj = make_double2(0.0, 0.0), wpj = make_double2(0.0, 0.0);
                 if (have_prev) {
@@ -776,10 +807,10 @@ __device__ void tri_pass_lower(double2* __restrict__ A, int n, int k, int m, int
             }
             const double2 rs = reduce_scatter4(racc, lane);
             const int jr = jb + (lane & 3) * S;
-            if (lane < TRL_RB && jr < m) prow[(long long)c * n + jr] = rs;
+            if (lane < TRL_RB && jr < r1) prow[(long long)c * n + jr] = rs;
         }
-        // column partials of this unit: tree over the warps, then the chunk's last unit sums the
-        // CS_c partials in slice order
+        // column partials of this segment: tree over the warps, then the chunk's last CTA sums the
+        // slots in order
 #pragma unroll
         for (int q = 0; q < CPL; ++q) colred[warp * LD + q * 32 + lane] = make_double2(accx[q], accy[q]);
         __syncthreads();
@@ -799,14 +830,14 @@ __device__ void tri_pass_lower(double2* __restrict__ A, int n, int k, int m, int
 #pragma unroll
             for (int q = 0; q < CPL; ++q) {
                 const double2 a0 = colred[q * 32 + lane], a1 = colred[LD + q * 32 + lane];
-                if (ok[q]) pk[(long long)cs * n + il[q]] = make_double2(a0.x + a1.x, a0.y + a1.y);
+                if (ok[q]) pk[(long long)slot * n + il[q]] = make_double2(a0.x + a1.x, a0.y + a1.y);
             }
             __threadfence();
         }
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
-            last_sh = atomicAdd(&arrive[c], 1u) == (unsigned)(CSc - 1);
+            last_sh = atomicAdd(&arrive[c], 1u) == (unsigned)(nslots - 1);
         }
         __syncthreads();
         if (last_sh && warp < CPL) {
@@ -814,7 +845,7 @@ __device__ void tri_pass_lower(double2* __restrict__ A, int n, int k, int m, int
             const int ilq = c * W + warp * 32 + lane;
             if (ilq < m) {
                 double sx = 0.0, sy = 0.0;
-                for (int s2 = 0; s2 < CSc; ++s2) {
+                for (int s2 = 0; s2 < nslots; ++s2) {
                     const double2 pp = __ldcg(&pk[(long long)s2 * n + ilq]);
                     sx += pp.x;
                     sy += pp.y;
@@ -823,7 +854,7 @@ __device__ void tri_pass_lower(double2* __restrict__ A, int n, int k, int m, int
             }
             if (warp == 0 && lane == 0) arrive[c] = 0u;  // reused two steps later, after four barriers
         }
-        __syncthreads();  // colred and last_sh are reused by the next unit
+        __syncthreads();  // colred and last_sh are reused by the next segment
     }
 }
 
@@ -892,7 +923,7 @@ __global__ void __launch_bounds__(TRL_THREADS) tridiag_lower(double2* __restrict
         if (blockIdx.x == 0)
             for (int t = threadIdx.x; t < m; t += blockDim.x) H[(long long)k * n + t] = vcur[t];
         // ---- B: trailing pass over the lower triangle
-        double2* pk = tb.part + (long long)(k & 1) * (2 * nb + 8) * n;
+        double2* pk = tb.part + (long long)(k & 1) * nb * n;
         double2* pcol = tb.pcol + (long long)(k & 1) * n;
         double2* prow = tb.prow + (long long)(k & 1) * TRI_MAX_CHUNKS * n;
         double2* pfin = tb.p + (long long)(k & 1) * n;
@@ -901,13 +932,9 @@ __global__ void __launch_bounds__(TRL_THREADS) tridiag_lower(double2* __restrict
         const int W = 32 * cpl;
         const int C = (m + W - 1) / W;
         if ((int)threadIdx.x <= C) {
-            // rows per unit: the chunks' rows spread over the CTAs, at most 2 nb units per chunk
-            const long long total = (long long)C * m - (long long)W * C * (C - 1) / 2;
-            int RT = (int)((total + nb - 1) / nb);
-            RT = max(RT, (m + 2 * nb - 1) / (2 * nb));
-            RT = max(TRL_NW, (RT + TRL_NW - 1) / TRL_NW * TRL_NW);
+            // items (blocks of TRL_IB rows) before chunk t: chunk c holds rows c W .. m-1
             int acc = 0;
-            for (int c = 0; c < (int)threadIdx.x; ++c) acc += (m - c * W + RT - 1) / RT;
+            for (int c = 0; c < (int)threadIdx.x; ++c) acc += (m - c * W + TRL_IB - 1) / TRL_IB;
             prefix_sh[threadIdx.x] = acc;
         }
         __syncthreads();
@@ -1628,7 +1655,7 @@ TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int dir
         VTN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tridiag_lower, TRL_THREADS, shm));
         const int grid = std::min(ctx.num_sms, std::max(1, (n + 3) / 4));
         if (per_sm >= 1 && grid >= 1) {
-            const size_t part_n = (size_t)(2 * grid + 8) * n;
+            const size_t part_n = (size_t)grid * n;
             const size_t elems = 2 * part_n + 2 * (size_t)n + 2 * (size_t)TRI_MAX_CHUNKS * n + 2 * (size_t)n;
             const size_t bytes = sizeof(double2) * elems;
             char* wsp = (char*)ctx.workspace(WS_EIG_PART, bytes + sizeof(unsigned) * 2 * TRI_MAX_CHUNKS);

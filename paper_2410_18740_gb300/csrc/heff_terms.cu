@@ -131,103 +131,139 @@ bool bond_terms_host(const HostCore& Wi, const HostCore& Wj, int& n_id, std::vec
     rj = ej.r;
     Bi = ei.B;
     Bj = ej.B;
-    // K_op = W_i^(o) W_j^(p), dense w_l x w_r
-    std::vector<std::vector<cplx>> K((size_t)ri * rj);
-    double kmax = 0.0;
+    // K_op = W_i^(o) W_j^(p) (w_l x w_r), kept as the dense block over the rows and columns that
+    // the sparse product touches (for this Hamiltonian most blocks touch one row or one column)
+    struct Block {
+        std::vector<int> rows, cols;  // touched, ascending
+        std::vector<cplx> k;          // rows.size() x cols.size()
+    };
+    std::vector<Block> K((size_t)ri * rj);
+    double kmax2 = 0.0;
+    std::vector<int> rpos(wl, -1), cpos(wr, -1);
     for (int p = 0; p < rj; ++p) {
         std::vector<std::vector<std::pair<int, cplx>>> jrow(wm);
         for (const Trip& t : ej.coef[p]) jrow[t.a].push_back({t.b, t.c});
         for (int o = 0; o < ri; ++o) {
-            std::vector<cplx>& k = K[(size_t)o * rj + p];
-            k.assign((size_t)wl * wr, cplx(0.0, 0.0));
+            Block& B = K[(size_t)o * rj + p];
             for (const Trip& t : ei.coef[o])
-                for (const auto& q : jrow[t.b]) k[(size_t)t.a * wr + q.first] += t.c * q.second;
-            for (const cplx& x : k) kmax = std::max(kmax, std::abs(x));
+                if (!jrow[t.b].empty()) {
+                    if (rpos[t.a] < 0) {
+                        rpos[t.a] = 0;
+                        B.rows.push_back(t.a);
+                    }
+                    for (const auto& q : jrow[t.b])
+                        if (cpos[q.first] < 0) {
+                            cpos[q.first] = 0;
+                            B.cols.push_back(q.first);
+                        }
+                }
+            std::sort(B.rows.begin(), B.rows.end());
+            std::sort(B.cols.begin(), B.cols.end());
+            for (size_t i = 0; i < B.rows.size(); ++i) rpos[B.rows[i]] = (int)i;
+            for (size_t i = 0; i < B.cols.size(); ++i) cpos[B.cols[i]] = (int)i;
+            const size_t nc = B.cols.size();
+            B.k.assign(B.rows.size() * nc, cplx(0.0, 0.0));
+            for (const Trip& t : ei.coef[o])
+                for (const auto& q : jrow[t.b]) B.k[(size_t)rpos[t.a] * nc + cpos[q.first]] += t.c * q.second;
+            for (int a : B.rows) rpos[a] = -1;
+            for (int c : B.cols) cpos[c] = -1;
+            for (const cplx& x : B.k) kmax2 = std::max(kmax2, std::norm(x));
         }
     }
-    if (kmax == 0.0) {  // H_eff = 0: no terms
+    if (kmax2 == 0.0) {  // H_eff = 0: no terms
         worthwhile = true;
         return true;
     }
-    const double tol = 1e-13 * kmax;
+    const double kmax = std::sqrt(kmax2);
+    const double tol = 1e-13 * kmax, tol2 = tol * tol;
     std::vector<HostTerm> id_terms, other;
     for (int o = 0; o < ri; ++o)
         for (int p = 0; p < rj; ++p) {
-            const std::vector<cplx>& k = K[(size_t)o * rj + p];
-            std::vector<int> nzr, nzc;
-            for (int a = 0; a < wl; ++a) {
+            const Block& B = K[(size_t)o * rj + p];
+            const int nr = (int)B.rows.size(), nc = (int)B.cols.size();
+            const std::vector<cplx>& k = B.k;
+            std::vector<int> nzr, nzc;  // positions in the block
+            for (int a = 0; a < nr; ++a) {
                 double m = 0.0;
-                for (int c = 0; c < wr; ++c) m = std::max(m, std::abs(k[(size_t)a * wr + c]));
-                if (m > tol) nzr.push_back(a);
+                for (int c = 0; c < nc; ++c) m = std::max(m, std::norm(k[(size_t)a * nc + c]));
+                if (m > tol2) nzr.push_back(a);
             }
-            for (int c = 0; c < wr; ++c) {
+            for (int c = 0; c < nc; ++c) {
                 double m = 0.0;
-                for (int a = 0; a < wl; ++a) m = std::max(m, std::abs(k[(size_t)a * wr + c]));
-                if (m > tol) nzc.push_back(c);
+                for (int a = 0; a < nr; ++a) m = std::max(m, std::norm(k[(size_t)a * nc + c]));
+                if (m > tol2) nzc.push_back(c);
             }
             if (nzr.empty()) continue;
             const size_t trivial = std::min(nzr.size(), nzc.size());
             std::vector<HostTerm> got;
             if (!(o == 0 && p == 0)) {
-                // Gaussian elimination with complete pivoting: K = sum_t u_t v_t^T (|u| <= 1)
+                // Gaussian elimination with complete pivoting on the block: K = sum_t u_t v_t^T (|u| <= 1)
                 std::vector<cplx> R = k;
+                std::vector<std::vector<cplx>> us, vs;
                 bool fail = false;
                 while (true) {
                     size_t at = 0;
                     double m = 0.0;
                     for (size_t i = 0; i < R.size(); ++i)
-                        if (std::abs(R[i]) > m) {
-                            m = std::abs(R[i]);
+                        if (std::norm(R[i]) > m) {
+                            m = std::norm(R[i]);
                             at = i;
                         }
-                    if (m <= tol) break;
-                    if (got.size() >= trivial) {
+                    if (m <= tol2) break;
+                    if (us.size() >= trivial) {
                         fail = true;
                         break;
                     }
-                    const int i0 = (int)(at / wr), j0 = (int)(at % wr);
+                    const int i0 = (int)(at / nc), j0 = (int)(at % nc);
                     const cplx piv = R[at];
-                    HostTerm t{o, p, std::vector<cplx>(wl), std::vector<cplx>(wr)};
-                    for (int a = 0; a < wl; ++a) t.u[a] = R[(size_t)a * wr + j0] / piv;
-                    for (int c = 0; c < wr; ++c) t.v[c] = R[(size_t)i0 * wr + c];
-                    for (int a = 0; a < wl; ++a)
-                        if (t.u[a] != 0.0)
-                            for (int c = 0; c < wr; ++c) R[(size_t)a * wr + c] -= t.u[a] * t.v[c];
-                    got.push_back(std::move(t));
+                    std::vector<cplx> u(nr), v(nc);
+                    for (int a = 0; a < nr; ++a) u[a] = R[(size_t)a * nc + j0] / piv;
+                    for (int c = 0; c < nc; ++c) v[c] = R[(size_t)i0 * nc + c];
+                    for (int a = 0; a < nr; ++a)
+                        if (u[a] != 0.0)
+                            for (int c = 0; c < nc; ++c) R[(size_t)a * nc + c] -= u[a] * v[c];
+                    us.push_back(std::move(u));
+                    vs.push_back(std::move(v));
                 }
                 if (!fail) {
                     // the factors must reproduce K
                     double err = 0.0;
-                    for (int a = 0; a < wl; ++a)
-                        for (int c = 0; c < wr; ++c) {
-                            cplx s = 0.0;
-                            for (const HostTerm& t : got) s += t.u[a] * t.v[c];
-                            err = std::max(err, std::abs(s - k[(size_t)a * wr + c]));
+                    for (int a = 0; a < nr; ++a)
+                        for (int c = 0; c < nc; ++c) {
+                            cplx sum = 0.0;
+                            for (size_t t = 0; t < us.size(); ++t) sum += us[t][a] * vs[t][c];
+                            err = std::max(err, std::abs(sum - k[(size_t)a * nc + c]));
                         }
                     if (err > 1e-12 * kmax) fail = true;
                 }
-                if (fail || got.size() >= trivial) got.clear();
+                if (!fail && us.size() < trivial)
+                    for (size_t t = 0; t < us.size(); ++t) {
+                        HostTerm h{o, p, std::vector<cplx>(wl, 0.0), std::vector<cplx>(wr, 0.0)};
+                        for (int a = 0; a < nr; ++a) h.u[B.rows[a]] = us[t][a];
+                        for (int c = 0; c < nc; ++c) h.v[B.cols[c]] = vs[t][c];
+                        got.push_back(std::move(h));
+                    }
             }
             if (got.empty()) {
                 // by nonzero rows (u = e_a, v = K[a, :]) or columns (u = K[:, c], v = e_c)
                 if (nzr.size() <= nzc.size()) {
                     for (int a : nzr) {
-                        HostTerm t{o, p, std::vector<cplx>(wl, 0.0), std::vector<cplx>(wr)};
-                        t.u[a] = 1.0;
-                        for (int c = 0; c < wr; ++c) t.v[c] = k[(size_t)a * wr + c];
-                        got.push_back(std::move(t));
+                        HostTerm h{o, p, std::vector<cplx>(wl, 0.0), std::vector<cplx>(wr, 0.0)};
+                        h.u[B.rows[a]] = 1.0;
+                        for (int c = 0; c < nc; ++c) h.v[B.cols[c]] = k[(size_t)a * nc + c];
+                        got.push_back(std::move(h));
                     }
                 } else {
                     for (int c : nzc) {
-                        HostTerm t{o, p, std::vector<cplx>(wl), std::vector<cplx>(wr, 0.0)};
-                        for (int a = 0; a < wl; ++a) t.u[a] = k[(size_t)a * wr + c];
-                        t.v[c] = 1.0;
-                        got.push_back(std::move(t));
+                        HostTerm h{o, p, std::vector<cplx>(wl, 0.0), std::vector<cplx>(wr, 0.0)};
+                        for (int a = 0; a < nr; ++a) h.u[B.rows[a]] = k[(size_t)a * nc + c];
+                        h.v[B.cols[c]] = 1.0;
+                        got.push_back(std::move(h));
                     }
                 }
             }
             auto& dst = (o == 0 && p == 0) ? id_terms : other;
-            for (auto& t : got) dst.push_back(std::move(t));
+            for (auto& h : got) dst.push_back(std::move(h));
         }
     const size_t n_t = id_terms.size() + other.size();
     // worthwhile: two GEMMs over n_t terms against two over w_l and w_r channels plus two mixing

@@ -592,6 +592,31 @@ void heff_apply_bf16x3(Ctx& ctx, const DevCore& Wi, const DevCore& Wj, const Hef
     tc_gemm_bf16(ctx, g2, TC_HEFF, useful2);
 }
 
+// C = A B for complex FP64 A (M x K, row stride lda) and B (K x N, row stride ldb), C (M x N, row
+// stride ldc) in FP64, as one split-precision tensor-core GEMM (used where the product feeds
+// split-precision work only: the two-site tensor that starts a Lanczos solve)
+void zgemm_bf16x3(Ctx& ctx, int M, int N, int K, const double2* A, long long lda, const double2* B, long long ldb,
+                  double2* C, long long ldc) {
+    const long long kk = k6(K);
+    __nv_bfloat16* Ap = (__nv_bfloat16*)ctx.workspace(WS_TH_A, sizeof(__nv_bfloat16) * (size_t)M * kk);
+    __nv_bfloat16* Bp = (__nv_bfloat16*)ctx.workspace(WS_TH_B, sizeof(__nv_bfloat16) * (size_t)2 * N * kk);
+    tc_pack(ctx, A, M, K, 1, lda, 0, false, false, Ap);
+    tc_pack(ctx, B, N, K, 1, ldb, 0, false, true, Bp);
+    TcGemmArgs g;
+    g.M = M;
+    g.N = 2 * N;
+    g.K = (int)kk;
+    g.A = Ap;
+    g.lda = kk;
+    g.B = Bp;
+    g.ldb = kk;
+    g.D = C;
+    g.ldd = 2 * ldc;
+    g.d_fp64 = true;
+    g.max_kb_per_acc = ctx.tc_kb_env;
+    tc_gemm_bf16(ctx, g, -1, 8.0 * M * (double)N * K);
+}
+
 // ----------------------------------------------------------------------------- environments
 // Split-precision (VTN_BF16X3) environment updates: the same three steps as the FP64
 // versions (dense contraction, MPO mixing, dense contraction with the conjugate site

@@ -104,7 +104,7 @@ struct Ctx {
     // (their errors accumulate along the chain) and H_eff psi
     int tc_kb_env = 64, tc_kb_heff = 256;
     // the truncation's tridiagonalisation keeps only the lower triangle up to date for n >= this
-    int tri_lower_min_n = 1 << 30;
+    int tri_lower_min_n = 2048;
     struct Tc {
         long long launches = 0;
         double flops = 0, seconds = 0;
@@ -148,7 +148,7 @@ enum WsSlot {
     WS_EIG_Y, WS_EIG_WORK, WS_EIG_U, WS_CORE_A, WS_CORE_B, WS_ENV_TMP, WS_MISC, WS_TC_L, WS_TC_R, WS_TC_B1,
     WS_TC_A2, WS_TC_PART, WS_GEMM_SPLIT, WS_EIG_PART, WS_TC_ENV, WS_EIG_T, WS_H2_ENV, WS_EXPAND,
     WS_TRUNC_L, WS_TRUNC_R, WS_CENTER, WS_MLP_ACT, WS_MLP_Y, WS_MLP_G, WS_WARM_S, WS_WARM_Z, WS_WARM_P,
-    WS_WARM_U, WS_WARM_N, WS_WARM_Q0, WS_CQR_G, WS_CQR_T, WS_CQR_B, WS_RQ_Y, WS_RQ_S, WS_CHOL_LINV, WS_COUNT
+    WS_WARM_U, WS_WARM_N, WS_WARM_Q0, WS_CQR_G, WS_CQR_T, WS_CQR_B, WS_RQ_Y, WS_RQ_S, WS_CHOL_LINV, WS_TH_A, WS_TH_B, WS_COUNT
 };
 
 // ------------------------------------------------------------------ cores
@@ -269,6 +269,9 @@ void heff_apply_bf16x3(Ctx& ctx, const DevCore& Wi, const DevCore& Wj, const Hef
 void heff_pack_terms(Ctx& ctx, const BondTerms& bt, int chi_l, int chi_r, const double2* L, const double2* R,
                      HeffPacked& pk);
 void heff_apply_terms(Ctx& ctx, const HeffPacked& pk, const double2* theta, double2* y);
+// C = A B (complex, FP64 in and out) as one split-precision tensor-core GEMM (tc_ops.cu)
+void zgemm_bf16x3(Ctx& ctx, int M, int N, int K, const double2* A, long long lda, const double2* B, long long ldb,
+                  double2* C, long long ldc);
 void env_left2_dev(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const double2* L2, const double2* A,
                    double2* out, double2* tv, double2* u);
 // multilayer perceptron of the learned warm start (mlp.cu)
