@@ -926,7 +926,7 @@ vtn_status sweep_body(vtn_ctx work, vtn_ctx owner, vtn_mpo mpo, vtn_mps* state, 
     // theta = A_i A_i+1
     auto form_theta = [&](int i, bool start_vector) {
         const int cl = mps->dims[i], cm = mps->dims[i + 1], cr = mps->dims[i + 2];
-        if (split && start_vector && false) {
+        if (split && start_vector) {
             // the Lanczos start vector feeds split-precision products only
             zgemm_bf16x3(c, cl * d, d * cr, cm, mps->sites[i], cm, mps->sites[i + 1], (long long)d * cr, theta,
                          (long long)d * cr);
