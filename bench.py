@@ -553,6 +553,10 @@ def run_native_large(args):
             "detail": {"heff_tflops_over_step": value / ws,
                        "heff_useful_tflops_in_gemms": fl_heff / s_heff / 1e12 if s_heff else None,
                        "energies_centre_rq": energies[-args.steps:],
+                       "energies_centre_rq_note": ("the sweep's own Rayleigh quotient, with split-precision "
+                                                   "environments: about 1e-3 relative below the FP64 energy of "
+                                                   "the same state at this size (--case c3cmp)")
+                       if prec != vtn.VTN_FP64 else "FP64",
                        "seconds_per_step": {"heff_gemms": s_heff / K, "truncation": tm["eig"][2] / K,
                                             "tridiag": s_tri / K, "tc_gemm": s_tc / K, "fp64_gemm": s_gemm / K,
                                             "mix": tm["mix"][2] / K, "lanczos_vectors": tm["lanczos"][2] / K},

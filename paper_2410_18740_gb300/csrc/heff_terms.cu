@@ -479,8 +479,8 @@ void heff_pack_terms(Ctx& ctx, const BondTerms& bt, int chi_l, int chi_r, const 
     pk.chi_l = chi_l;
     pk.chi_r = chi_r;
     pk.wl = pk.wr = n_t;
-    pk.ldL = tc_k6(chi_l);
-    pk.ldR = tc_k6((long long)n_t * chi_r);
+    pk.ldL = tc_ksplit(chi_l);
+    pk.ldR = tc_ksplit((long long)n_t * chi_r);
     if (n_t == 0) return;
     pk.L = (__nv_bfloat16*)ctx.workspace(WS_TC_L, sizeof(__nv_bfloat16) * (size_t)n_t * chi_l * pk.ldL);
     pk.R = (__nv_bfloat16*)ctx.workspace(WS_TC_R, sizeof(__nv_bfloat16) * (size_t)2 * chi_r * pk.ldR);
@@ -504,7 +504,7 @@ void heff_apply_terms(Ctx& ctx, const HeffPacked& pk, const double2* theta, doub
         VTN_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double2) * (size_t)n_theta, ctx.stream));
         return;
     }
-    const long long ldB1 = tc_k6(chi_l);
+    const long long ldB1 = tc_ksplit(chi_l);
     const long long ldA2 = pk.ldR;
     __nv_bfloat16* B1 = (__nv_bfloat16*)ctx.workspace(WS_TC_B1, sizeof(__nv_bfloat16) * (size_t)2 * dd * chi_r * ldB1);
     float2* X = (float2*)ctx.workspace(WS_X, sizeof(float2) * (size_t)n_t * n_theta);
@@ -524,6 +524,7 @@ void heff_apply_terms(Ctx& ctx, const HeffPacked& pk, const double2* theta, doub
     g1.D = X;
     g1.ldd = 2LL * dd * chi_r;
     g1.d_fp64 = false;
+    g1.split3 = true;
     g1.max_kb_per_acc = ctx.tc_kb_heff;
     tc_gemm_bf16(ctx, g1, TC_HEFF, useful1);
     const int n_k = n_t - bt.n_id;
@@ -551,6 +552,7 @@ void heff_apply_terms(Ctx& ctx, const HeffPacked& pk, const double2* theta, doub
     g2.D = y;
     g2.ldd = 2LL * chi_r;
     g2.d_fp64 = true;
+    g2.split3 = true;
     g2.max_kb_per_acc = ctx.tc_kb_heff;
     tc_gemm_bf16(ctx, g2, TC_HEFF, useful2);
 }

@@ -39,6 +39,12 @@ constexpr int B_TILE = BN * BK * 2;   // 32 KiB
 constexpr int STAGE_BYTES = A_TILE + B_TILE;
 constexpr int TMEM_COLS = 256;
 constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + 256;  // + barriers and the TMEM slot
+// Split operands (hi | lo halves, see tc_ops.cu): one stage holds the hi and lo tiles of A and B
+// for one k-block (twice the bytes, half the stages in the same shared memory) and feeds three
+// products hi*hi, hi*lo, lo*hi into the accumulator, so each operand tile is loaded once for the
+// two products that use it
+constexpr int S3_STAGES = STAGES / 2;
+constexpr int S3_STAGE_BYTES = 2 * STAGE_BYTES;
 
 struct TcParams {
     int M, N, K;
@@ -49,6 +55,8 @@ struct TcParams {
     int kb_per;           // k-blocks per split
     int splits;           // work item t covers split t / (m tiles * n tiles)
     long long d_split;    // element stride between the per-split outputs (split-K partials)
+    int s3;               // split operands: K = 2 * half, hi half then lo half, three products per k-block
+    int half;             // columns of one half (multiple of BK)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -165,7 +173,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles_n = (p.N + BN - 1) / BN, tiles_m = (p.M + BM - 1) / BM;
     const int items = tiles_n * tiles_m * p.splits;
-    const int nkb_total = p.K / BK;
+    const int nkb_total = (p.s3 ? p.half : p.K) / BK;
+    const int nst = p.s3 ? S3_STAGES : STAGES;
+    const int sbytes = p.s3 ? S3_STAGE_BYTES : STAGE_BYTES;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -197,13 +207,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                 const int nt = t % tiles_n, mt = (t / tiles_n) % tiles_m, z = t / (tiles_n * tiles_m);
                 const int kb0 = z * p.kb_per, nkb = min(nkb_total - kb0, p.kb_per);
                 for (int kb = 0; kb < nkb; ++kb, ++g) {
-                    const int s = g % STAGES;
-                    const uint32_t round = g / STAGES;
-                    if (g >= STAGES && !(ok = mbar_wait(&empty[s], (round & 1) ^ 1, p.status))) break;
-                    uint8_t* a_dst = smem + (size_t)s * STAGE_BYTES;
-                    mbar_expect_tx(&full[s], STAGE_BYTES);
-                    tma_load_2d(a_dst, &tmA, &full[s], (kb0 + kb) * BK, mt * BM);
-                    tma_load_2d(a_dst + A_TILE, &tmB, &full[s], (kb0 + kb) * BK, nt * BN);
+                    const int s = g % nst;
+                    const uint32_t round = g / nst;
+                    if (g >= (uint32_t)nst && !(ok = mbar_wait(&empty[s], (round & 1) ^ 1, p.status))) break;
+                    uint8_t* a_dst = smem + (size_t)s * sbytes;
+                    mbar_expect_tx(&full[s], sbytes);
+                    const int x = (kb0 + kb) * BK;
+                    if (!p.s3) {
+                        tma_load_2d(a_dst, &tmA, &full[s], x, mt * BM);
+                        tma_load_2d(a_dst + A_TILE, &tmB, &full[s], x, nt * BN);
+                    } else {
+                        // A hi, A lo, B hi, B lo
+                        tma_load_2d(a_dst, &tmA, &full[s], x, mt * BM);
+                        tma_load_2d(a_dst + A_TILE, &tmA, &full[s], p.half + x, mt * BM);
+                        tma_load_2d(a_dst + 2 * A_TILE, &tmB, &full[s], x, nt * BN);
+                        tma_load_2d(a_dst + 2 * A_TILE + B_TILE, &tmB, &full[s], p.half + x, nt * BN);
+                    }
                 }
             }
         }
@@ -221,16 +240,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                 fence_after();
                 const uint32_t d_tmem = tmem + (uint32_t)(acc * TMEM_COLS);
                 for (int kb = 0; kb < nkb; ++kb, ++g) {
-                    const int s = g % STAGES;
-                    const uint32_t round = g / STAGES;
+                    const int s = g % nst;
+                    const uint32_t round = g / nst;
                     if (!(ok = mbar_wait(&full[s], round & 1, p.status))) break;
                     fence_after();
-                    const uint32_t a_addr = smem_u32(smem + (size_t)s * STAGE_BYTES);
-                    const uint32_t b_addr = a_addr + A_TILE;
+                    const uint32_t a_addr = smem_u32(smem + (size_t)s * sbytes);
+                    if (!p.s3) {
+                        const uint32_t b_addr = a_addr + A_TILE;
 #pragma unroll
-                    for (int k = 0; k < BK / 16; ++k)
-                        mma_bf16(d_tmem, smem_desc(a_addr + 32 * k), smem_desc(b_addr + 32 * k),
-                                 (kb | k) != 0 ? 1u : 0u);
+                        for (int k = 0; k < BK / 16; ++k)
+                            mma_bf16(d_tmem, smem_desc(a_addr + 32 * k), smem_desc(b_addr + 32 * k),
+                                     (kb | k) != 0 ? 1u : 0u);
+                    } else {
+                        const uint32_t al = a_addr + A_TILE, bh = a_addr + 2 * A_TILE, bl = bh + B_TILE;
+#pragma unroll
+                        for (int k = 0; k < BK / 16; ++k) {
+                            mma_bf16(d_tmem, smem_desc(a_addr + 32 * k), smem_desc(bh + 32 * k), (kb | k) != 0 ? 1u : 0u);
+                            mma_bf16(d_tmem, smem_desc(a_addr + 32 * k), smem_desc(bl + 32 * k), 1u);
+                            mma_bf16(d_tmem, smem_desc(al + 32 * k), smem_desc(bh + 32 * k), 1u);
+                        }
+                    }
                     mma_commit(&empty[s]);
                 }
                 if (!ok) break;
@@ -368,13 +397,19 @@ void tc_gemm_bf16(Ctx& ctx, const TcGemmArgs& a, int timing_class, double useful
     // split K when the output tiles leave most SMs idle (fixed-order reduction afterwards), and
     // whenever one accumulator would sum more than MAX_KB_PER_ACC k-blocks: the FP32 accumulation
     // in tensor memory then covers a bounded part of the sum and the partials are added in FP64
-    const int nkb = a.K / BK;
+    if (a.split3) VTN_REQUIRE(a.K % (2 * BK) == 0, "split operands need two halves of whole k-blocks");
+    p.s3 = a.split3 ? 1 : 0;
+    p.half = a.split3 ? a.K / 2 : 0;
+    // k-blocks of the loop; a split k-block carries three products, so an accumulator run of
+    // kb_acc k-blocks of split terms is kb_acc / 3 of them
+    const int nkb = (a.split3 ? a.K / 2 : a.K) / BK;
     const long long tiles = (long long)grid.x * grid.y;
     int splits = 1;
     if (tiles * 2 <= ctx.num_sms && nkb >= 8)
         splits = (int)std::min<long long>(std::max<long long>(1, ctx.num_sms / tiles), nkb / 4);
     splits = std::max(1, std::min(splits, 8));
-    const int kb_acc = a.max_kb_per_acc > 0 ? a.max_kb_per_acc : MAX_KB_PER_ACC;
+    int kb_acc = a.max_kb_per_acc > 0 ? a.max_kb_per_acc : MAX_KB_PER_ACC;
+    if (a.split3) kb_acc = std::max(1, kb_acc / 3);
     splits = std::max(splits, (nkb + kb_acc - 1) / kb_acc);
     int per = (nkb + splits - 1) / splits;
     splits = (nkb + per - 1) / per;
@@ -395,7 +430,7 @@ void tc_gemm_bf16(Ctx& ctx, const TcGemmArgs& a, int timing_class, double useful
     p.splits = splits;
     const long long items = tiles * splits;
     const unsigned n_cta = (unsigned)std::min<long long>(items, std::max(ctx.num_sms, 1));
-    const double flops = 2.0 * a.M * (double)a.N * a.K;
+    const double flops = 2.0 * a.M * (double)a.N * (a.split3 ? 3.0 * (a.K / 2) : (double)a.K);
     int t0 = ctx.tbegin(TC_TC, flops);
     int t1 = timing_class >= 0 ? ctx.tbegin(timing_class, useful_flops) : -1;
     tc_gemm_kernel<<<n_cta, TC_THREADS, SMEM_BYTES, ctx.stream>>>(ma, mb, p);

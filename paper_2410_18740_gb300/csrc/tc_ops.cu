@@ -7,12 +7,13 @@
 //                            rows 2n, 2n+1 of B^ = [Re b(:,n), -Im b(:,n)], [Im b(:,n), Re b(:,n)]
 //                            so that (A^ B^T)[m][2n] = Re C, [m][2n+1] = Im C (interleaved output)
 //   split precision          x = hi + lo with hi = bf16(x), lo = bf16(x - hi)
-//   three products           A~ = [A^_hi | A^_hi | A^_lo], B~ = [B^_hi | B^_lo | B^_hi] along K,
-//                            A~ B~^T = A_hi B_hi + A_hi B_lo + A_lo B_hi   (FP32 accumulation)
+//   three products           A_hi B_hi + A_hi B_lo + A_lo B_hi   (FP32 accumulation)
 //
-// K~ = 6 Kt rounded up to a multiple of 64 (zero padded).  The packers read FP64 or FP32
-// complex data through 32 x 32 shared-memory tiles so that both the read and the write side
-// are coalesced whatever the operand's transposition.
+// Each split operand is stored as two halves along K, [X^_hi | X^_lo], each 2 Kt wide and
+// zero padded to a multiple of 64; the GEMM loads the hi and lo tiles of A and B for a k-block
+// once and issues the three products from them.  The packers read FP64 or FP32 complex data
+// through 32 x 32 shared-memory tiles so that both the read and the write side are coalesced
+// whatever the operand's transposition.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -49,6 +50,7 @@ struct PackP {
     long long s_rq;
     __nv_bfloat16* out;
     long long ldo;
+    long long half;    // columns of one half (ldo = 2 half)
 };
 
 // value of the operand element (r, kk) of op(X) as seen by the product:
@@ -100,32 +102,27 @@ __global__ void __launch_bounds__(256) pack_kernel(const T* __restrict__ X, Pack
         __nv_bfloat16 rh, rl, ih, il;
         CplxTraits<T>::split(v.x, rh, rl);
         CplxTraits<T>::split(v.y, ih, il);
+        const long long H = p.half;
         if (!p.is_b) {
+            // row m: [Re a, Im a] hi | lo
             __nv_bfloat16* o = p.out + (long long)r * p.ldo;
             o[kk] = rh;
             o[Kt + kk] = ih;
-            o[2 * Kt + kk] = rh;
-            o[3 * Kt + kk] = ih;
-            o[4 * Kt + kk] = rl;
-            o[5 * Kt + kk] = il;
+            o[H + kk] = rl;
+            o[H + Kt + kk] = il;
         } else {
             __nv_bfloat16* o0 = p.out + (long long)(2 * r) * p.ldo;
             __nv_bfloat16* o1 = o0 + p.ldo;
-            const __nv_bfloat16 nih = __hneg(ih), nil = __hneg(il);
-            // row 2n: [Re b, -Im b] in segments hi | lo | hi
+            // row 2n: [Re b, -Im b] hi | lo
             o0[kk] = rh;
-            o0[Kt + kk] = nih;
-            o0[2 * Kt + kk] = rl;
-            o0[3 * Kt + kk] = nil;
-            o0[4 * Kt + kk] = rh;
-            o0[5 * Kt + kk] = nih;
-            // row 2n+1: [Im b, Re b]
+            o0[Kt + kk] = __hneg(ih);
+            o0[H + kk] = rl;
+            o0[H + Kt + kk] = __hneg(il);
+            // row 2n+1: [Im b, Re b] hi | lo
             o1[kk] = ih;
             o1[Kt + kk] = rh;
-            o1[2 * Kt + kk] = il;
-            o1[3 * Kt + kk] = rl;
-            o1[4 * Kt + kk] = ih;
-            o1[5 * Kt + kk] = rh;
+            o1[H + kk] = il;
+            o1[H + Kt + kk] = rl;
         }
     }
 }
@@ -390,13 +387,14 @@ void launch_mix_cid(Ctx& ctx, int JB, int EI, bool real_c, int bytes, unsigned g
     }
 }
 
-long long k6(long long Kt) { return ((6 * Kt + 63) / 64) * 64; }
+// row width of a split operand: two halves of 2 Kt columns, each padded to a multiple of 64
+long long ksplit(long long Kt) { return 2 * (((2 * Kt + 63) / 64) * 64); }
 
 template <typename T>
 void pack_impl(Ctx& ctx, const T* X, int rows, int K, int kb, long long ld, long long s_kb, bool conj_t, bool is_b,
                __nv_bfloat16* out, int rq, long long s_rq) {
     const long long Kt = (long long)K * kb;
-    const long long ldo = k6(Kt);
+    const long long ldo = ksplit(Kt);
     PackP p;
     p.rows = rows;
     p.K = K;
@@ -409,15 +407,18 @@ void pack_impl(Ctx& ctx, const T* X, int rows, int K, int kb, long long ld, long
     p.s_rq = s_rq;
     p.out = out;
     p.ldo = ldo;
+    p.half = ldo / 2;
     dim3 grid((unsigned)((Kt + 31) / 32), (unsigned)((rows + 31) / 32));
     VTN_REQUIRE(grid.y <= 65535, "pack: too many rows");
     pack_kernel<T><<<grid, dim3(32, 8), 0, ctx.stream>>>(X, p);
     const int orows = is_b ? 2 * rows : rows;
-    const int from = (int)(6 * Kt), to = (int)ldo;
+    const int from = (int)(2 * Kt), to = (int)(ldo / 2);
     if (to > from) {
+        // the padding of both halves
         const long long cnt = (long long)orows * (to - from);
         zero_pad_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx.stream>>>(out, ldo, orows, from, to);
-        ctx.count_launch();
+        zero_pad_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx.stream>>>(out, ldo, orows, to + from, 2 * to);
+        ctx.count_launch(2);
     }
     ctx.count_launch();
     ctx.check_launch("pack_kernel");
@@ -425,7 +426,7 @@ void pack_impl(Ctx& ctx, const T* X, int rows, int K, int kb, long long ld, long
 
 }  // namespace
 
-long long tc_k6(long long Kt) { return k6(Kt); }
+long long tc_ksplit(long long Kt) { return ksplit(Kt); }
 
 void tc_pack(Ctx& ctx, const double2* X, int rows, int K, int kb, long long ld, long long s_kb, bool conj_t, bool is_b,
              __nv_bfloat16* out, int rq, long long s_rq) {
@@ -531,8 +532,8 @@ void heff_pack_envs(Ctx& ctx, const DevCore& Wi, const DevCore& Wj, int chi_l, i
     pk.chi_r = chi_r;
     pk.wl = wl;
     pk.wr = wr;
-    pk.ldL = k6(chi_l);
-    pk.ldR = k6((long long)wr * chi_r);
+    pk.ldL = ksplit(chi_l);
+    pk.ldR = ksplit((long long)wr * chi_r);
     pk.L = (__nv_bfloat16*)ctx.workspace(WS_TC_L, sizeof(__nv_bfloat16) * (size_t)wl * chi_l * pk.ldL);
     pk.R = (__nv_bfloat16*)ctx.workspace(WS_TC_R, sizeof(__nv_bfloat16) * (size_t)2 * chi_r * pk.ldR);
     // A operand of T1 = L theta: rows (a, i), inner index j
@@ -550,8 +551,8 @@ void heff_apply_bf16x3(Ctx& ctx, const DevCore& Wi, const DevCore& Wj, const Hef
     const int d = Wi.d, chi_l = pk.chi_l, chi_r = pk.chi_r;
     const long long n_theta = (long long)chi_l * d * d * chi_r;
     const int wmax = std::max(Wi.wl, std::max(Wi.wr, Wj.wr));
-    const long long ldB1 = k6(chi_l);
-    const long long ldA2 = k6((long long)Wj.wr * chi_r);
+    const long long ldB1 = ksplit(chi_l);
+    const long long ldA2 = ksplit((long long)Wj.wr * chi_r);
     __nv_bfloat16* B1 = (__nv_bfloat16*)ctx.workspace(WS_TC_B1, sizeof(__nv_bfloat16) * (size_t)2 * d * d * chi_r * ldB1);
     float2* X = (float2*)ctx.workspace(WS_X, sizeof(float2) * (size_t)wmax * n_theta);
     float2* Yb = (float2*)ctx.workspace(WS_Y, sizeof(float2) * (size_t)wmax * n_theta);
@@ -571,6 +572,7 @@ void heff_apply_bf16x3(Ctx& ctx, const DevCore& Wi, const DevCore& Wj, const Hef
     g1.D = X;
     g1.ldd = 2LL * d * d * chi_r;
     g1.d_fp64 = false;
+    g1.split3 = true;
     g1.max_kb_per_acc = ctx.tc_kb_heff;
     tc_gemm_bf16(ctx, g1, TC_HEFF, useful1);
     mix_apply_f32(ctx, Wi, true, chi_l, d * chi_r, X, Yb);
@@ -588,6 +590,7 @@ void heff_apply_bf16x3(Ctx& ctx, const DevCore& Wi, const DevCore& Wj, const Hef
     g2.D = y;
     g2.ldd = 2LL * chi_r;
     g2.d_fp64 = true;
+    g2.split3 = true;
     g2.max_kb_per_acc = ctx.tc_kb_heff;
     tc_gemm_bf16(ctx, g2, TC_HEFF, useful2);
 }
@@ -597,7 +600,7 @@ void heff_apply_bf16x3(Ctx& ctx, const DevCore& Wi, const DevCore& Wj, const Hef
 // split-precision work only: the two-site tensor that starts a Lanczos solve)
 void zgemm_bf16x3(Ctx& ctx, int M, int N, int K, const double2* A, long long lda, const double2* B, long long ldb,
                   double2* C, long long ldc) {
-    const long long kk = k6(K);
+    const long long kk = ksplit(K);
     __nv_bfloat16* Ap = (__nv_bfloat16*)ctx.workspace(WS_TH_A, sizeof(__nv_bfloat16) * (size_t)M * kk);
     __nv_bfloat16* Bp = (__nv_bfloat16*)ctx.workspace(WS_TH_B, sizeof(__nv_bfloat16) * (size_t)2 * N * kk);
     tc_pack(ctx, A, M, K, 1, lda, 0, false, false, Ap);
@@ -613,6 +616,7 @@ void zgemm_bf16x3(Ctx& ctx, int M, int N, int K, const double2* A, long long lda
     g.D = C;
     g.ldd = 2 * ldc;
     g.d_fp64 = true;
+    g.split3 = true;
     g.max_kb_per_acc = ctx.tc_kb_env;
     tc_gemm_bf16(ctx, g, -1, 8.0 * M * (double)N * K);
 }
@@ -630,7 +634,7 @@ void env_left_bf16x3(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const dou
     const long long nA = (long long)chi_l * d * chi_r;
     const int wmax = std::max(wl, wr);
     // 1. T[(a,i)][(s,k)] = sum_j L[a][i][j] A[j][(s,k)]
-    const long long ld1 = k6(chi_l);
+    const long long ld1 = ksplit(chi_l);
     __nv_bfloat16* PA = (__nv_bfloat16*)ctx.workspace(WS_TC_L, sizeof(__nv_bfloat16) * (size_t)wl * chi_l * ld1);
     __nv_bfloat16* PB = (__nv_bfloat16*)ctx.workspace(WS_TC_B1, sizeof(__nv_bfloat16) * (size_t)2 * d * chi_r * ld1);
     float2* X = (float2*)ctx.workspace(WS_X, sizeof(float2) * (size_t)wmax * nA);
@@ -648,12 +652,13 @@ void env_left_bf16x3(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const dou
     g1.D = X;
     g1.ldd = 2LL * d * chi_r;
     g1.d_fp64 = false;
+    g1.split3 = true;
     g1.max_kb_per_acc = ctx.tc_kb_env;
     tc_gemm_bf16(ctx, g1, -1, 8.0 * wl * chi_l * (double)chi_l * d * chi_r);
     // 2. U[b][i][t][k] = sum W[a,b,t,s] T[a][i][s][k]
     mix_apply_f32(ctx, W, true, chi_l, chi_r, X, Yb);
     // 3. D[l][(b,k)] = sum_{(i,t)} conj(A[(i,t)][l]) U[b][(i,t)][k], then out[b][l][k] = D[l][b][k]
-    const long long ld3 = k6((long long)chi_l * d);
+    const long long ld3 = ksplit((long long)chi_l * d);
     __nv_bfloat16* PA3 = (__nv_bfloat16*)ctx.workspace(WS_TC_A2, sizeof(__nv_bfloat16) * (size_t)chi_r * ld3);
     __nv_bfloat16* PB3 = (__nv_bfloat16*)ctx.workspace(WS_TC_R, sizeof(__nv_bfloat16) * (size_t)2 * wr * chi_r * ld3);
     double2* T = (double2*)ctx.workspace(WS_TC_ENV, sizeof(double2) * (size_t)chi_r * wr * chi_r);
@@ -670,6 +675,7 @@ void env_left_bf16x3(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const dou
     g3.D = T;
     g3.ldd = 2LL * wr * chi_r;
     g3.d_fp64 = true;
+    g3.split3 = true;
     g3.max_kb_per_acc = ctx.tc_kb_env;
     tc_gemm_bf16(ctx, g3, -1, 8.0 * chi_r * (double)wr * chi_r * chi_l * d);
     const long long cnt = (long long)wr * chi_r * chi_r;
@@ -685,7 +691,7 @@ void env_right_bf16x3(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const do
     const long long nA = (long long)chi_l * d * chi_r;
     const int wmax = std::max(wl, wr);
     // 1. T[(j,s)][(c,p)] = sum_g A[(j,s)][g] R[c][g][p]
-    const long long ld1 = k6(chi_r);
+    const long long ld1 = ksplit(chi_r);
     __nv_bfloat16* PA = (__nv_bfloat16*)ctx.workspace(WS_TC_L, sizeof(__nv_bfloat16) * (size_t)chi_l * d * ld1);
     __nv_bfloat16* PB = (__nv_bfloat16*)ctx.workspace(WS_TC_R, sizeof(__nv_bfloat16) * (size_t)2 * wr * chi_r * ld1);
     float2* X = (float2*)ctx.workspace(WS_X, sizeof(float2) * (size_t)wmax * nA);
@@ -703,6 +709,7 @@ void env_right_bf16x3(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const do
     g1.D = X;
     g1.ldd = 2LL * wr * chi_r;
     g1.d_fp64 = false;
+    g1.split3 = true;
     g1.max_kb_per_acc = ctx.tc_kb_env;
     tc_gemm_bf16(ctx, g1, -1, 8.0 * chi_l * d * (double)wr * chi_r * chi_r);
     // 2. U[b][j][t][p] = sum W[b,c,t,s] T[c][j][s][p]; T element (c, j, s, p) sits at
@@ -710,7 +717,7 @@ void env_right_bf16x3(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const do
     const long long st[3] = {chi_r, (long long)d * wr * chi_r, (long long)wr * chi_r};
     mix_apply_f32(ctx, W, false, chi_l, chi_r, X, Yb, st);
     // 3. out[(b,j)][i] = sum_{(t,p)} U[(b,j)][(t,p)] conj(A[i][(t,p)])
-    const long long ld3 = k6((long long)d * chi_r);
+    const long long ld3 = ksplit((long long)d * chi_r);
     __nv_bfloat16* PA3 = (__nv_bfloat16*)ctx.workspace(WS_TC_A2, sizeof(__nv_bfloat16) * (size_t)wl * chi_l * ld3);
     __nv_bfloat16* PB3 = (__nv_bfloat16*)ctx.workspace(WS_TC_B1, sizeof(__nv_bfloat16) * (size_t)2 * chi_l * ld3);
     tc_pack(ctx, (const float2*)Yb, wl * chi_l, d * chi_r, 1, (long long)d * chi_r, 0, false, false, PA3);
@@ -726,6 +733,7 @@ void env_right_bf16x3(Ctx& ctx, const DevCore& W, int chi_l, int chi_r, const do
     g3.D = out;
     g3.ldd = 2LL * chi_l;
     g3.d_fp64 = true;
+    g3.split3 = true;
     g3.max_kb_per_acc = ctx.tc_kb_env;
     tc_gemm_bf16(ctx, g3, -1, 8.0 * wl * chi_l * (double)chi_l * d * chi_r);
 }

@@ -192,11 +192,13 @@ struct TcGemmArgs {
     void* D;
     long long ldd;
     bool d_fp64 = false;
+    bool split3 = false;     // A and B are split operands in hi | lo halves (tc_pack): three products
+                             // (hi hi, hi lo, lo hi) per k-block of the hi half; K = both halves
     int max_kb_per_acc = 0;  // > 0: at most this many 64-wide k-blocks per tensor-memory accumulator
                              // (longer sums are split and their FP32 partials added in FP64); 0 = 256
 };
 void tc_gemm_bf16(Ctx& ctx, const TcGemmArgs& a, int timing_class = -1, double useful_flops = 0.0);
-long long tc_k6(long long Kt);
+long long tc_ksplit(long long Kt);
 // split-precision operand packing (see tc_ops.cu)
 // rq > 0: operand rows come in blocks of rq, block b starting s_rq elements after block b-1
 void tc_pack(Ctx& ctx, const double2* X, int rows, int K, int kb, long long ld, long long s_kb, bool conj_t, bool is_b,
