@@ -64,6 +64,12 @@ N_SAMPLES = 256
 TC_GEMM_TRAFFIC = 0.5 * ((32.512000 + 145.623040) + (311.471872 + 3.002112)) * 1e6
 # DRAM bytes (read + write) of one tridiag_persistent launch at n = 1024 (ncu).
 TRI_TRAFFIC = (16.843264 + 3.543040) * 1e6
+# DRAM bytes (read + write) of one tridiag_lower launch at n = 3072, the large workload's truncation
+# shape (ncu, --set full capture of bench.py --case trunc --trunc-shape 512 6).
+TRI_LOWER_TRAFFIC = (1.117808 + 19.664044) * 1e9
+# DRAM bytes (read + write) per launch of the term-form H_eff GEMM pair at the large workload's centre
+# bond (ncu, bench.py --case heff --workload large): 15.51 + 8.58 GB and 10.90 + 1.64 GB; their mean.
+TC_GEMM_TRAFFIC_LARGE = 0.5 * ((15.508355 + 8.579924) + (10.900055 + 1.643347)) * 1e9
 # DRAM bytes (read + write) per launch of the FP64 complex GEMM pair of H_eff psi at the middle
 # bond of the split workload (ncu), mean of the two launches.
 GEMM_F64_TRAFFIC = 0.5 * ((30.710272 + 345.032960) + (416.077056 + 13.165824)) * 1e6
@@ -494,17 +500,20 @@ def run_native_large(args):
     K = args.steps
     cands = {
         "tridiag": (s_tri, _roof("alu", fl_tri / s_tri / 1e12 if s_tri else None, fpeak, fpeak_src,
-                                 "tridiag_persistent (FP64 Householder tridiagonalisation of rho, one cooperative "
-                                 "launch per truncation, n = 3072)", "16/3 n^3 real flops per launch",
-                                 n_tri, s_tri, K)),
+                                 "tridiag_lower (FP64 Householder tridiagonalisation of rho keeping the lower "
+                                 "triangle, one cooperative launch per truncation, n = 3072)",
+                                 "16/3 n^3 real flops per launch", n_tri, s_tri, K, TRI_LOWER_TRAFFIC,
+                                 "ncu dram read+write of one launch at n = 3072 (the same kernel and shape)")),
         "tc_gemm": (s_tc, _roof("tensor", fl_tc / s_tc / 1e12 if s_tc else None, tc_peak,
                                 f"{peaks_src} bf16 dense, sustained (kernel timed inside a long step)",
                                 "tc_gemm_kernel (persistent tcgen05 bf16 GEMM, TMEM accumulators, TMA tiles) in "
                                 "H_eff psi and the environment updates",
                                 "2 M N K executed bf16 flops per launch (3 split products per useful product)",
-                                n_tc, s_tc, K)),
+                                n_tc, s_tc, K, TC_GEMM_TRAFFIC_LARGE,
+                                "ncu dram read+write per launch, mean of the centre-bond H_eff GEMM pair of the "
+                                "term form (the step's launches also include smaller environment GEMMs)")),
         "fp64_gemm": (s_gemm, _roof("alu", fl_gemm / s_gemm / 1e12 if s_gemm else None, fpeak, fpeak_src,
-                                    "gemm_c64_kernel (complex FP64 GEMM: rho, theta, the truncation's products, "
+                                    "gemm_c64_kernel (complex FP64 GEMM: rho, the truncation's products, "
                                     "the Rayleigh quotient)", "8 M N K (Hermitian rho: half) real flops per launch",
                                     n_gemm, s_gemm, K)),
     }
