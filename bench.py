@@ -17,7 +17,7 @@ Lanczos, the truncation and the energy stay FP64.
 
 value     = whole-step H_eff psi throughput: algorithmic flops of every H_eff psi product
             in the step / step time (TFLOP/s).
-e2e       = the same metric through the C ABI from host buffers: every step builds the MPO
+e2e       = the same metric through the C ABI from pinned host buffers: every step builds the MPO
             from (r, U), uploads the MPS from host memory, runs the window and reads the MPS
             back.
 roofline  = the kernel with the largest share of the timed steps, timed with CUDA events on
@@ -458,8 +458,17 @@ def run_native_large(args):
         readout["mean_photons_sampled"] = float(smp.sum(1).mean())
     except Exception as exc:  # reported, never fatal to the benchmark line
         readout["error"] = repr(exc)
-    # ---------------- end-to-end through the C ABI with host buffers
-    sites_host = [vtn.vtn_mps_get_site(ctx, mps, s) for s in range(M)]
+    # ---------------- end-to-end through the C ABI with host buffers (pinned host memory)
+    def pinned_like(shape):
+        return torch.empty(shape, dtype=torch.complex128, pin_memory=True).numpy()
+
+    sites_host = []
+    for s in range(M):
+        a = vtn.vtn_mps_get_site(ctx, mps, s)
+        b = pinned_like(a.shape)
+        b[...] = a
+        sites_host.append(b)
+    out_sites = [pinned_like(a.shape) for a in sites_host]
     e2e_times, e2e_flops, h2d, d2h = [], 0.0, 0, 0
     for _ in range(2):
         torch.cuda.synchronize()
@@ -468,7 +477,8 @@ def run_native_large(args):
         s2 = vtn.vtn_mps_from_host(ctx, m2, sites_host)
         vtn.vtn_mps_set_center(s2, LARGE_LO)
         st, s2, rep2 = vtn.vtn_sweep(ctx, m2, s2, opts)
-        out_sites = [vtn.vtn_mps_get_site(ctx, s2, s) for s in range(M)]
+        for s in range(M):
+            vtn.vtn_mps_get_site(ctx, s2, s, out=out_sites[s])
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
         e2e_flops += rep2["heff_flops"]
@@ -507,7 +517,8 @@ def run_native_large(args):
         "tc_gemm": (s_tc, _roof("tensor", fl_tc / s_tc / 1e12 if s_tc else None, tc_peak,
                                 f"{peaks_src} bf16 dense, sustained (kernel timed inside a long step)",
                                 "tc_gemm_kernel (persistent tcgen05 bf16 GEMM, TMEM accumulators, TMA tiles) in "
-                                "H_eff psi and the environment updates",
+                                "H_eff psi and the environment updates; each launch timed with its split-K sum "
+                                "where it has one",
                                 "2 M N K executed bf16 flops per launch (3 split products per useful product)",
                                 n_tc, s_tc, K, TC_GEMM_TRAFFIC_LARGE,
                                 "ncu dram read+write per launch, mean of the centre-bond H_eff GEMM pair of the "
@@ -816,7 +827,12 @@ def run_native(args):
     elapsed_max = max_over_ranks(ws, elapsed)
     value = whole_job_rate(ws, flops, elapsed) / 1e12   # every replica does the same work per step
     # ---------------- end-to-end through the C ABI with host buffers
-    sites_host = [vtn.vtn_mps_get_site(ctx, mps, s) for s in range(M)]
+    sites_host = []
+    for s in range(M):
+        a = vtn.vtn_mps_get_site(ctx, mps, s)
+        b = torch.empty(a.shape, dtype=torch.complex128, pin_memory=True).numpy()
+        b[...] = a
+        sites_host.append(b)
     e2e_times, e2e_flops, h2d, d2h = [], 0.0, 0, 0
     for _ in range(max(1, min(args.steps, 2))):
         torch.cuda.synchronize()
@@ -826,7 +842,7 @@ def run_native(args):
         st, s2, rep2 = vtn.vtn_sweep(ctx, m2, s2, opts)
         marg = vtn.vtn_marginals_all(ctx, m2, s2)
         smp = vtn.vtn_sample(ctx, m2, s2, 7, N_SAMPLES)
-        out_sites = [vtn.vtn_mps_get_site(ctx, s2, s) for s in range(M)]
+        out_sites = [vtn.vtn_mps_get_site(ctx, s2, s) for s in range(M)]  # sizes vary per sweep
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
         e2e_flops += rep2["heff_flops"]
@@ -848,7 +864,7 @@ def run_native(args):
                "traffic_note": "ncu dram read+write per launch, mean of the middle-bond H_eff GEMM pair "
                                "(algorithmic: 2 x 201 MB FP32 out + 302 MB packed operand in)",
                "kernel": "tc_gemm_kernel (persistent tcgen05 bf16 GEMM, TMEM accumulators, TMA tiles) in H_eff psi "
-                         "and the environment updates",
+                         "and the environment updates; each launch timed with its split-K sum where it has one",
                "launches": n_tc, "seconds_per_step": s_tc / args.steps,
                "peak_source": f"{peaks_src} bf16 dense, sustained (kernel timed inside a long step)",
                "useful_complex_tflops": fl_heff / s_heff / 1e12 if s_heff else None,

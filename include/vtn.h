@@ -561,7 +561,7 @@ vtn_status vtn_gemm_bf16(vtn_ctx ctx, int M, int N, int K, const void* A, long l
 
 /* Accumulation length of the split-precision tensor-core products: the largest number of
  * 64-wide k-blocks (bf16 split operands) one tensor-memory accumulator sums before its FP32
- * partial is added to the others in FP64 (longer sums are split along k).  The tensor cores'
+ * partial is added to the others by compensated FP32 summation (longer sums are split along k).  The tensor cores'
  * FP32 accumulation loses accuracy about linearly with the sum's length, so shorter runs are
  * more accurate and cost more split-K partial traffic.  env_kblocks applies to the environment
  * updates (vtn_env_update and those of the sweeps: their errors add up along the chain),

@@ -328,16 +328,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     }
 }
 
-// out[m][n] = sum_z part[z][m][n] in a fixed order (deterministic split-K reduction), summed in FP64
+// out[m][n] = sum_z part[z][m][n] in a fixed order (deterministic split-K reduction), compensated FP32
 __global__ void splitk_reduce(const float* __restrict__ part, int splits, int M, int N, void* out, long long ldo,
                               int fp64) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)M * N) return;
     const long long m = t / N, n = t % N;
-    double acc = 0.0;
-    for (int z = 0; z < splits; ++z) acc += (double)part[(long long)z * M * N + t];
-    if (fp64) ((double*)out)[m * ldo + n] = acc;
-    else ((float*)out)[m * ldo + n] = (float)acc;
+    // compensated (Kahan) FP32 sum: its error is about one FP32 rounding of the result, far below
+    // each partial's own accumulation error, and the additions stay off GB300's narrow FP64 pipe
+    float sum = 0.f, comp = 0.f;
+    const long long MN = (long long)M * N;
+#pragma unroll 4
+    for (int z = 0; z < splits; ++z) {
+        const float y = __ldg(&part[(long long)z * MN + t]) - comp;
+        const float u = sum + y;
+        comp = (u - sum) - y;
+        sum = u;
+    }
+    if (fp64) ((double*)out)[m * ldo + n] = (double)sum - (double)comp;
+    else ((float*)out)[m * ldo + n] = sum;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -396,7 +405,8 @@ void tc_gemm_bf16(Ctx& ctx, const TcGemmArgs& a, int timing_class, double useful
     VTN_REQUIRE((long long)grid.x * grid.y * 8 < (1LL << 31), "tensor-core GEMM too large");
     // split K when the output tiles leave most SMs idle (fixed-order reduction afterwards), and
     // whenever one accumulator would sum more than MAX_KB_PER_ACC k-blocks: the FP32 accumulation
-    // in tensor memory then covers a bounded part of the sum and the partials are added in FP64
+    // in tensor memory then covers a bounded part of the sum and the partials are added with
+    // compensated FP32 summation
     if (a.split3) VTN_REQUIRE(a.K % (2 * BK) == 0, "split operands need two halves of whole k-blocks");
     p.s3 = a.split3 ? 1 : 0;
     p.half = a.split3 ? a.K / 2 : 0;

@@ -195,7 +195,7 @@ struct TcGemmArgs {
     bool split3 = false;     // A and B are split operands in hi | lo halves (tc_pack): three products
                              // (hi hi, hi lo, lo hi) per k-block of the hi half; K = both halves
     int max_kb_per_acc = 0;  // > 0: at most this many 64-wide k-blocks per tensor-memory accumulator
-                             // (longer sums are split and their FP32 partials added in FP64); 0 = 256
+                             // (longer sums are split; FP32 partials added by compensated summation); 0 = 256
 };
 void tc_gemm_bf16(Ctx& ctx, const TcGemmArgs& a, int timing_class = -1, double useful_flops = 0.0);
 long long tc_ksplit(long long Kt);

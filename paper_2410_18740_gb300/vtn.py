@@ -424,11 +424,19 @@ def vtn_mps_info(mps):
     return M.value, d.value, dims
 
 
-def vtn_mps_get_site(ctx, mps, site):
+def vtn_mps_get_site(ctx, mps, site, out=None):
+    """Site tensor (chi_l, d, chi_r) on the host; out: optional C-contiguous complex128 array of that
+    shape to write into (e.g. a view of pinned memory)."""
     _, d, dims = vtn_mps_info(mps)
-    out = np.zeros((dims[site], d, dims[site + 1], 2))
-    _check(ctx, lib().vtn_mps_get_site(ctx, mps, int(site), out.ctypes.data_as(_PD)))
-    return out.view(np.complex128)[..., 0]
+    shape = (int(dims[site]), d, int(dims[site + 1]))
+    if out is None:
+        buf = np.zeros(shape + (2,))
+        _check(ctx, lib().vtn_mps_get_site(ctx, mps, int(site), buf.ctypes.data_as(_PD)))
+        return buf.view(np.complex128)[..., 0]
+    if out.shape != shape or out.dtype != np.complex128 or not out.flags.c_contiguous:
+        raise ValueError("out must be a C-contiguous complex128 array of the site's shape")
+    _check(ctx, lib().vtn_mps_get_site(ctx, mps, int(site), out.view(np.float64).ctypes.data_as(_PD)))
+    return out
 
 
 def vtn_mps_save(ctx, mps, path):
