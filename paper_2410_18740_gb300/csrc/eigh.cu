@@ -643,9 +643,16 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_persistent(double2* __res
 // parts are combined across the lanes by a reduce-scatter (6 complex additions per lane for 4
 // rows) and written per (column chunk, row).  The column chunks are cut into units of about
 // equal numbers of rows (chunk c holds rows c W .. m-1), interleaved over the warps of a unit.
-// After a grid barrier the CTAs finalise p in slices -- column part, then the row parts of
-// chunks 0 .. row/W in order (deterministic) -- and a second barrier publishes it.  Row k+1 of
-// the updated matrix, which gives the next reflector, is read as column k+1 (the stored half).
+// The pass also accumulates v^dag A v: with (A v)_j = (column part)_j + (row part)_j it is the
+// real part of sum_j conj(v_j) (row part)_j, added per row after the reduce-scatter, plus
+// sum_c conj(v_c) (column part)_c, added per 32-column group by the chunk's last CTA; the
+// per-CTA and per-group partials go to global memory.  After a grid barrier every CTA sums them
+// in one fixed order, so K = (tau/2) v^dag p = (tau^2/2) v^dag A v is the same in every CTA, and
+// the CTAs finalise their slices of p (column part plus the row parts of chunks 0 .. row/W,
+// summed by warps over interleaved chunks and then over the warps in order: deterministic),
+// w = p - K v and the next reflector's column k+1 (read as the stored half) with step k's
+// update, with partial sums of its squared norm.  After a second barrier every CTA only loads
+// w and that column: no per-element arithmetic is repeated in every CTA.
 constexpr int TRL_THREADS = 256;
 constexpr int TRL_NW = TRL_THREADS / 32;
 constexpr int TRL_RB = 4;  // rows per warp batch
@@ -654,7 +661,11 @@ struct TriBufsL {
     double2* part;     // [2][nb][n] column partials per CTA slot of a chunk
     double2* pcol;     // [2][n] column part of A v (unscaled), written by a chunk's last unit
     double2* prow;     // [2][TRI_MAX_CHUNKS][n] row parts per column chunk
-    double2* p;        // [2][n] p = tau A v
+    double2* w;        // [2][n] w = p - K v, p = tau A v
+    double2* x;        // [n] next column below its diagonal, with step k's update
+    double* dot;       // [nb] per-CTA partials of Re sum_j conj(v_j) (row part)_j
+    double* cdot;      // [TRI_MAX_CHUNKS][TRI_MAX_CPL] per 32-column group: Re sum_c conj(v_c) (column part)_c
+    double* a2;        // [nb] per-CTA partials of |x|^2
     unsigned* arrive;  // [2][TRI_MAX_CHUNKS] arrivals per column chunk (zero at launch)
 };
 
@@ -695,7 +706,8 @@ __device__ __forceinline__ double2 reduce_scatter4(double2 r[TRL_RB], int lane) 
 // i of chunk c: local rows c W + TRL_IB (i - items[c]) ...), are split into nb equal contiguous
 // ranges, one per CTA; a CTA's range covers one or more chunk segments.  In a segment warp w walks
 // the rows r0 + w + t NW; lane l owns the columns c W + q 32 + l (q < CPL).  Column partials go to
-// slot (CTA - first CTA of the chunk) and the chunk's last CTA sums them in slot order.
+// slot (CTA - first CTA of the chunk) and the chunk's last CTA sums them in slot order.  dacc
+// (per thread) collects this CTA's share of the row-part term of v^dag A v.
 constexpr int TRL_IB = 8;
 
 __device__ __forceinline__ int tri_item_start(int b, int T, int nb) { return (int)(((long long)b * T) / nb); }
@@ -715,7 +727,7 @@ template <int CPL>
 __device__ void tri_pass_lower(double2* __restrict__ A, int n, int k, int m, int nb, bool have_prev,
                                const double2* vprev, const double2* wprev, const double2* vcur, double2* pk,
                                double2* pcol, double2* prow, unsigned* arrive, double2* colred, int& last_sh,
-                               const int* items, int C) {
+                               const int* items, int C, double& dacc, double* cdot) {
     constexpr int W = 32 * CPL;
     constexpr int LD = TRI_MAX_CPL * 32;  // colred row stride
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -807,7 +819,11 @@ __device__ void tri_pass_lower(double2* __restrict__ A, int n, int k, int m, int
             }
             const double2 rs = reduce_scatter4(racc, lane);
             const int jr = jb + (lane & 3) * S;
-            if (lane < TRL_RB && jr < r1) prow[(long long)c * n + jr] = rs;
+            if (lane < TRL_RB && jr < r1) {
+                prow[(long long)c * n + jr] = rs;
+                const double2 vj = vcur[jr];
+                dacc = fma(vj.x, rs.x, fma(vj.y, rs.y, dacc));  // Re(conj(v_j) rs)
+            }
         }
         // column partials of this segment: tree over the warps, then the chunk's last CTA sums the
         // slots in order
@@ -843,6 +859,7 @@ __device__ void tri_pass_lower(double2* __restrict__ A, int n, int k, int m, int
         if (last_sh && warp < CPL) {
             __threadfence();
             const int ilq = c * W + warp * 32 + lane;
+            double cd = 0.0;
             if (ilq < m) {
                 double sx = 0.0, sy = 0.0;
                 for (int s2 = 0; s2 < nslots; ++s2) {
@@ -851,7 +868,11 @@ __device__ void tri_pass_lower(double2* __restrict__ A, int n, int k, int m, int
                     sy += pp.y;
                 }
                 pcol[ilq] = make_double2(sx, sy);
+                const double2 vq = vcur[ilq];
+                cd = fma(vq.x, sx, vq.y * sy);  // Re(conj(v_c) (column part)_c)
             }
+            cd = warp_sum(cd);
+            if (lane == 0) cdot[c * TRI_MAX_CPL + warp] = cd;
             if (warp == 0 && lane == 0) arrive[c] = 0u;  // reused two steps later, after four barriers
         }
         __syncthreads();  // colred and last_sh are reused by the next segment
@@ -865,12 +886,14 @@ __global__ void __launch_bounds__(TRL_THREADS) tridiag_lower(double2* __restrict
     double2* wprev = sm + n;
     double2* vcur = sm + 2 * n;
     __shared__ double red[33];
-    __shared__ double tau_sh, dk_sh;
-    __shared__ double2 p0_sh;
+    __shared__ double tau_sh, dk_sh, K_sh, a2_sh;
+    __shared__ double2 w0_sh;
     __shared__ int last_sh;
     __shared__ int prefix_sh[TRI_MAX_CHUNKS + 1];
     __shared__ double2 colred[TRL_NW][TRI_MAX_CPL * 32];
     const int nb = (int)gridDim.x;
+    const int b = (int)blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned epoch = 0;
     bool have_prev = false;
     // row 0 (no pending update; the whole matrix is valid at the start): x = conj(A[0][1..n-1])
@@ -881,11 +904,11 @@ __global__ void __launch_bounds__(TRL_THREADS) tridiag_lower(double2* __restrict
         vcur[t] = x;
         a2 = fma(x.x, x.x, fma(x.y, x.y, a2));
     }
+    a2 = block_sum(a2, red);  // |x|^2, the same in every thread
     if (threadIdx.x == 0) dk_sh = __ldcg(&A[0]).x;
     for (int k = 0; k + 2 < n; ++k) {
         const int m = n - k - 1;
         // ---- reflector for column k (as in tridiag_persistent)
-        a2 = block_sum(a2, red);
         if (threadIdx.x == 0) {
             const double2 x0 = vcur[0];
             const double q0 = fma(x0.x, x0.x, x0.y * x0.y);
@@ -909,7 +932,7 @@ __global__ void __launch_bounds__(TRL_THREADS) tridiag_lower(double2* __restrict
                 beta = make_double2(-phia.x, -phia.y);
             }
             tau_sh = tau;
-            if (blockIdx.x == 0) {
+            if (b == 0) {
                 s.diag[k] = dk_sh;
                 s.tau[k] = tau;
                 s.e[k] = beta;
@@ -920,13 +943,13 @@ __global__ void __launch_bounds__(TRL_THREADS) tridiag_lower(double2* __restrict
         if (tau == 0.0)
             for (int t = threadIdx.x; t < m; t += blockDim.x) vcur[t] = make_double2(0.0, 0.0);
         __syncthreads();
-        if (blockIdx.x == 0)
+        if (b == 0)
             for (int t = threadIdx.x; t < m; t += blockDim.x) H[(long long)k * n + t] = vcur[t];
-        // ---- B: trailing pass over the lower triangle
+        // ---- B: trailing pass over the lower triangle, with this CTA's share of v^dag A v
         double2* pk = tb.part + (long long)(k & 1) * nb * n;
         double2* pcol = tb.pcol + (long long)(k & 1) * n;
         double2* prow = tb.prow + (long long)(k & 1) * TRI_MAX_CHUNKS * n;
-        double2* pfin = tb.p + (long long)(k & 1) * n;
+        double2* wfin = tb.w + (long long)(k & 1) * n;
         unsigned* arrive = tb.arrive + (k & 1) * TRI_MAX_CHUNKS;
         const int cpl = m >= 256 ? 2 : 1;
         const int W = 32 * cpl;
@@ -938,63 +961,102 @@ __global__ void __launch_bounds__(TRL_THREADS) tridiag_lower(double2* __restrict
             prefix_sh[threadIdx.x] = acc;
         }
         __syncthreads();
+        double dacc = 0.0;
         if (cpl == 2)
             tri_pass_lower<2>(A, n, k, m, nb, have_prev, vprev, wprev, vcur, pk, pcol, prow, arrive, &colred[0][0],
-                              last_sh, prefix_sh, C);
+                              last_sh, prefix_sh, C, dacc, tb.cdot);
         else
             tri_pass_lower<1>(A, n, k, m, nb, have_prev, vprev, wprev, vcur, pk, pcol, prow, arrive, &colred[0][0],
-                              last_sh, prefix_sh, C);
+                              last_sh, prefix_sh, C, dacc, tb.cdot);
+        dacc = block_sum(dacc, red);
+        if (threadIdx.x == 0) tb.dot[b] = dacc;
         if (!grid_sync(bar, (unsigned)nb, epoch++)) return;
-        // ---- p = tau (column part + row parts of chunks 0 .. il / W), in slices over the CTAs
-        for (int il = (int)(blockIdx.x * blockDim.x + threadIdx.x); il < m; il += nb * (int)blockDim.x) {
-            const double2 pc = __ldcg(&pcol[il]);
-            double sx = pc.x, sy = pc.y;
-            const int cl = il / W;
-            for (int c = 0; c <= cl; ++c) {
-                const double2 r = __ldcg(&prow[(long long)c * n + il]);
-                sx += r.x;
-                sy += r.y;
-            }
-            pfin[il] = make_double2(tau * sx, tau * sy);
-        }
-        if (!grid_sync(bar, (unsigned)nb, epoch++)) return;
-        // ---- C(k): K = (tau/2) Re(v^dag p); p parked in wprev (its old content is spent)
+        // ---- K = (tau^2/2) v^dag A v from the partials (one fixed order, the same in every CTA),
+        //      w_0 = p_0 - K v_0 and the next diagonal element; the last warp does this while the
+        //      others start on their slices
         const bool next = k + 3 < n;
-        double dot = 0.0;
-        for (int t = threadIdx.x; t < m; t += blockDim.x) {
-            const double2 p = __ldcg(&pfin[t]), v = vcur[t];
-            if (next && t >= 1) vprev[t - 1] = __ldcg(&A[(long long)(k + 1 + t) * n + (k + 1)]);  // column k+1, raw
-            wprev[t] = p;
-            if (t == 0) p0_sh = p;
-            dot = fma(v.x, p.x, fma(v.y, p.y, dot));
-        }
-        dot = block_sum(dot, red);
-        const double K = 0.5 * tau * dot;
-        double2* vnew = vcur;
-        double2* wnew = wprev;
-        double2* xnext = vprev;
-        const double2 v0 = vnew[0];
-        const double2 w0 = make_double2(fma(-K, v0.x, p0_sh.x), fma(-K, v0.y, p0_sh.y));
-        a2 = 0.0;
-        for (int t = threadIdx.x; t < m; t += blockDim.x) {
-            const double2 p = wnew[t], v = vnew[t];
-            const double2 w = make_double2(fma(-K, v.x, p.x), fma(-K, v.y, p.y));
-            wnew[t] = w;
-            if (next && t >= 1) {
-                // column k+1 with the pending update: A[j][k+1] -= v_j conj(w_0) + w_j conj(v_0); it is
-                // the conjugate of row k+1, so x = the updated column itself
-                double2 x = xnext[t - 1];
-                x = sub_two_cmulc(x, v, w0, w, v0);
-                xnext[t - 1] = x;
-                a2 = fma(x.x, x.x, fma(x.y, x.y, a2));
+        const double2 v0 = vcur[0];
+        if (warp == TRL_NW - 1) {
+            double sdot = 0.0;
+            for (int i = lane; i < nb; i += 32) sdot += __ldcg(&tb.dot[i]);
+            for (int i = lane; i < C * TRI_MAX_CPL; i += 32)
+                if (i % TRI_MAX_CPL < cpl) sdot += __ldcg(&tb.cdot[i]);
+            sdot = warp_sum(sdot);
+            if (lane == 0) {
+                const double K = 0.5 * tau * tau * sdot;
+                const double2 pc = __ldcg(&pcol[0]), pr = __ldcg(&prow[0]);
+                const double2 p0 = make_double2(tau * (pc.x + pr.x), tau * (pc.y + pr.y));
+                const double2 w0 = make_double2(fma(-K, v0.x, p0.x), fma(-K, v0.y, p0.y));
+                K_sh = K;
+                w0_sh = w0;
+                if (next)
+                    dk_sh = __ldcg(&A[(long long)(k + 1) * n + (k + 1)]).x - 2.0 * (v0.x * w0.x + v0.y * w0.y);
             }
         }
-        if (threadIdx.x == 0 && next) dk_sh = __ldcg(&A[(long long)(k + 1) * n + (k + 1)]).x - 2.0 * (v0.x * w0.x + v0.y * w0.y);
+        // ---- slices of 32 rows over the CTAs: p = tau (column part + row parts of chunks
+        //      0 .. row/W), warp u summing chunks u, u + NW, ..., then the warps in order; w = p - K v;
+        //      column k+1 with step k's update (A[j][k+1] -= v_j conj(w_0) + w_j conj(v_0): the
+        //      conjugate of row k+1, i.e. the next reflector's x) and its partial squared norm
+        double a2p = 0.0;
+        for (int blk = b; blk * 32 < m; blk += nb) {
+            const int il = blk * 32 + lane;
+            const int cl = (blk * 32) / W;  // the same for the 32 rows (W is a multiple of 32)
+            double sx = 0.0, sy = 0.0;
+            if (il < m)
+                for (int c = warp; c <= cl; c += TRL_NW) {
+                    const double2 r = __ldcg(&prow[(long long)c * n + il]);
+                    sx += r.x;
+                    sy += r.y;
+                }
+            colred[warp][lane] = make_double2(sx, sy);
+            __syncthreads();
+            if (warp == 0 && il < m) {
+                const double2 pc = __ldcg(&pcol[il]);
+                double tx = pc.x, ty = pc.y;
+#pragma unroll
+                for (int u = 0; u < TRL_NW; ++u) {
+                    tx += colred[u][lane].x;
+                    ty += colred[u][lane].y;
+                }
+                const double K = K_sh;
+                const double2 w0 = w0_sh;
+                const double2 v = vcur[il];
+                const double2 w = make_double2(fma(-K, v.x, tau * tx), fma(-K, v.y, tau * ty));
+                wfin[il] = w;
+                if (next && il >= 1) {
+                    double2 x = __ldcg(&A[(long long)(k + 1 + il) * n + (k + 1)]);
+                    x = sub_two_cmulc(x, v, w0, w, v0);
+                    tb.x[il - 1] = x;
+                    a2p = fma(x.x, x.x, fma(x.y, x.y, a2p));
+                }
+            }
+            __syncthreads();
+        }
+        if (warp == 0) {
+            a2p = warp_sum(a2p);
+            if (lane == 0) tb.a2[b] = a2p;
+        }
+        if (!grid_sync(bar, (unsigned)nb, epoch++)) return;
+        // ---- C(k): every CTA loads w (the pending update) and the next column; |x|^2 from the partials
+        double2* vnew = vcur;
+        double2* wnew = wprev;  // the old pending update is spent
+        double2* xnext = vprev;
+        for (int t = threadIdx.x; t < m; t += blockDim.x) {
+            wnew[t] = __ldcg(&wfin[t]);
+            if (next && t >= 1) xnext[t - 1] = __ldcg(&tb.x[t - 1]);
+        }
+        if (warp == 0) {
+            double sa = 0.0;
+            for (int i = lane; i < nb; i += 32) sa += __ldcg(&tb.a2[i]);
+            sa = warp_sum(sa);
+            if (lane == 0) a2_sh = sa;
+        }
+        __syncthreads();
+        a2 = a2_sh;
         vprev = vnew;
         wprev = wnew;
         vcur = xnext;
         have_prev = true;
-        __syncthreads();
     }
     // ---- tail: last 2 x 2 block (lower half) with the pending update applied
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1656,15 +1718,21 @@ TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int dir
         const int grid = std::min(ctx.num_sms, std::max(1, (n + 3) / 4));
         if (per_sm >= 1 && grid >= 1) {
             const size_t part_n = (size_t)grid * n;
-            const size_t elems = 2 * part_n + 2 * (size_t)n + 2 * (size_t)TRI_MAX_CHUNKS * n + 2 * (size_t)n;
+            const size_t elems = 2 * part_n + 2 * (size_t)n + 2 * (size_t)TRI_MAX_CHUNKS * n + 3 * (size_t)n;
             const size_t bytes = sizeof(double2) * elems;
-            char* wsp = (char*)ctx.workspace(WS_EIG_PART, bytes + sizeof(unsigned) * 2 * TRI_MAX_CHUNKS);
+            const size_t dbl = 2 * (size_t)grid + (size_t)TRI_MAX_CHUNKS * TRI_MAX_CPL;
+            char* wsp = (char*)ctx.workspace(WS_EIG_PART,
+                                             bytes + sizeof(double) * dbl + sizeof(unsigned) * 2 * TRI_MAX_CHUNKS);
             TriBufsL tb;
             tb.part = (double2*)wsp;
             tb.pcol = tb.part + 2 * part_n;
             tb.prow = tb.pcol + 2 * (size_t)n;
-            tb.p = tb.prow + 2 * (size_t)TRI_MAX_CHUNKS * n;
-            tb.arrive = (unsigned*)(wsp + bytes);
+            tb.w = tb.prow + 2 * (size_t)TRI_MAX_CHUNKS * n;
+            tb.x = tb.w + 2 * (size_t)n;
+            tb.dot = (double*)(wsp + bytes);
+            tb.a2 = tb.dot + grid;
+            tb.cdot = tb.a2 + grid;
+            tb.arrive = (unsigned*)(wsp + bytes + sizeof(double) * dbl);
             VTN_CUDA_TRY(cudaMemsetAsync(tb.arrive, 0, sizeof(unsigned) * 2 * TRI_MAX_CHUNKS, ctx.stream));
             GridBar* bar = (GridBar*)(status + 4);
             VTN_CUDA_TRY(cudaMemsetAsync(bar, 0, sizeof(GridBar), ctx.stream));

@@ -137,9 +137,12 @@ def test_truncation_matches_oracle(ctx, cl, d1, d2, cr, direction, kmax, tri_for
     vtn.vtn_set_tridiag_lower(ctx)
 
 
-def test_truncation_rank_deficient(ctx):
-    """Product state: rho has one non-zero eigenvalue and a degenerate null space; the kept
-    factor must still be an isometry and reproduce theta."""
+@pytest.mark.parametrize("tri_form", ["full", "lower"])
+def test_truncation_rank_deficient(ctx, tri_form):
+    """Product state: rho has one non-zero eigenvalue and a degenerate null space (reflectors
+    with tau = 0 once the trailing block vanishes); the kept factor must still be an isometry
+    and reproduce theta."""
+    vtn.vtn_set_tridiag_lower(ctx, 0 if tri_form == "lower" else 1 << 30)
     rng = inputs.rng_for(77)
     a = inputs.random_complex((2, 3), rng)
     b = inputs.random_complex((3, 4), rng)
@@ -160,6 +163,7 @@ def test_truncation_rank_deficient(ctx):
             Rm = R.reshape(6, 12)
             assert np.abs(Rm @ Rm.conj().T - np.eye(6)).max() < 1e-10
         assert np.abs(np.einsum("asb,btc->astc", L, R) - th).max() < 1e-12
+    vtn.vtn_set_tridiag_lower(ctx)
 
 
 @pytest.mark.parametrize("chi_l,chi_r,d,ws", [(3, 4, 3, (2, 3, 2)), (8, 8, 4, (4, 5, 4))])
