@@ -66,7 +66,7 @@ TC_GEMM_TRAFFIC = 0.5 * ((32.512000 + 145.623040) + (311.471872 + 3.002112)) * 1
 TRI_TRAFFIC = (16.843264 + 3.543040) * 1e6
 # DRAM bytes (read + write) of one tridiag_lower launch at n = 3072, the large workload's truncation
 # shape (ncu, --set full capture of bench.py --case trunc --trunc-shape 512 6).
-TRI_LOWER_TRAFFIC = (1.168024 + 19.770892) * 1e9
+TRI_LOWER_TRAFFIC = (1.152237 + 19.671560) * 1e9
 # DRAM bytes (read + write) per launch of the term-form H_eff GEMM pair at the large workload's centre
 # bond (ncu, bench.py --case heff --workload large): 15.51 + 8.58 GB and 10.90 + 1.64 GB; their mean.
 TC_GEMM_TRAFFIC_LARGE = 0.5 * ((15.508355 + 8.579924) + (10.900055 + 1.643347)) * 1e9

@@ -641,32 +641,28 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_persistent(double2* __res
 // tri_pass) and, for j > c, a v_c to p_j (the row part, 4 FMAs): 8 FP64 FMAs per element of the
 // full trailing block and column instead of 12.  A warp takes TRL_RB rows at a time; their row
 // parts are combined across the lanes by a reduce-scatter (6 complex additions per lane for 4
-// rows) and written per (column chunk, row).  The column chunks are cut into units of about
-// equal numbers of rows (chunk c holds rows c W .. m-1), interleaved over the warps of a unit.
-// The pass also accumulates v^dag A v: with (A v)_j = (column part)_j + (row part)_j it is the
-// real part of sum_j conj(v_j) (row part)_j, added per row after the reduce-scatter, plus
-// sum_c conj(v_c) (column part)_c, added per 32-column group by the chunk's last CTA; the
-// per-CTA and per-group partials go to global memory.  After a grid barrier every CTA sums them
-// in one fixed order, so K = (tau/2) v^dag p = (tau^2/2) v^dag A v is the same in every CTA, and
-// the CTAs finalise their slices of p (column part plus the row parts of chunks 0 .. row/W,
-// summed by warps over interleaved chunks and then over the warps in order: deterministic),
-// w = p - K v and the next reflector's column k+1 (read as the stored half) with step k's
-// update, with partial sums of its squared norm.  After a second barrier every CTA only loads
-// w and that column: no per-element arithmetic is repeated in every CTA.
+// rows) and written per (column chunk, row); the column parts of a CTA's rows of a chunk are
+// written per (CTA slot of the chunk, column).  The pass also accumulates v^dag A v: with
+// (A v)_j = (column part)_j + (row part)_j it is the real part of sum_j conj(v_j) (row part)_j
+// plus sum_c conj(v_c) (column part)_c, and both sums split over the CTAs' rows and slots, so
+// each CTA adds its own share and writes one partial.  After a grid barrier every CTA sums the
+// partials in one fixed order, so K = (tau/2) v^dag p = (tau^2/2) v^dag A v is the same in every
+// CTA, and the CTAs finalise their slices of 32 rows: p (the slots of the row's chunk plus the
+// row parts of chunks 0 .. row/W, summed by warps over interleaved terms and then over the warps
+// in order: deterministic), w = p - K v and the next reflector's column k+1 (read as the stored
+// half) with step k's update, with partial sums of its squared norm.  After a second barrier
+// every CTA only loads w and that column: no per-element arithmetic is repeated in every CTA.
 constexpr int TRL_THREADS = 256;
 constexpr int TRL_NW = TRL_THREADS / 32;
 constexpr int TRL_RB = 4;  // rows per warp batch
 
 struct TriBufsL {
-    double2* part;     // [2][nb][n] column partials per CTA slot of a chunk
-    double2* pcol;     // [2][n] column part of A v (unscaled), written by a chunk's last unit
-    double2* prow;     // [2][TRI_MAX_CHUNKS][n] row parts per column chunk
-    double2* w;        // [2][n] w = p - K v, p = tau A v
-    double2* x;        // [n] next column below its diagonal, with step k's update
-    double* dot;       // [nb] per-CTA partials of Re sum_j conj(v_j) (row part)_j
-    double* cdot;      // [TRI_MAX_CHUNKS][TRI_MAX_CPL] per 32-column group: Re sum_c conj(v_c) (column part)_c
-    double* a2;        // [nb] per-CTA partials of |x|^2
-    unsigned* arrive;  // [2][TRI_MAX_CHUNKS] arrivals per column chunk (zero at launch)
+    double2* part;  // [2][nb][n] column parts per CTA slot of a chunk
+    double2* prow;  // [2][TRI_MAX_CHUNKS][n] row parts per column chunk
+    double2* w;     // [2][n] w = p - K v, p = tau A v
+    double2* x;     // [n] next column below its diagonal, with step k's update
+    double* dot;    // [nb] per-CTA partials of v^dag A v
+    double* a2;     // [nb] per-CTA partials of |x|^2
 };
 
 // x (complex, per lane) summed over the lanes that share bits >= 2 of the lane index, for 4 rows:
@@ -705,29 +701,24 @@ __device__ __forceinline__ double2 reduce_scatter4(double2 r[TRL_RB], int lane) 
 // Trailing pass of step k, lower triangle.  The rows of the chunks, in blocks of TRL_IB rows (item
 // i of chunk c: local rows c W + TRL_IB (i - items[c]) ...), are split into nb equal contiguous
 // ranges, one per CTA; a CTA's range covers one or more chunk segments.  In a segment warp w walks
-// the rows r0 + w + t NW; lane l owns the columns c W + q 32 + l (q < CPL).  Column partials go to
-// slot (CTA - first CTA of the chunk) and the chunk's last CTA sums them in slot order.  dacc
-// (per thread) collects this CTA's share of the row-part term of v^dag A v.
+// the rows r0 + w + t NW; lane l owns the columns c W + q 32 + l (q < CPL).  The segment's column
+// parts are summed over the warps and written to slot (CTA - first CTA of the chunk).  dacc (per
+// thread) collects this CTA's share of v^dag A v.
 constexpr int TRL_IB = 8;
 
-__device__ __forceinline__ int tri_item_start(int b, int T, int nb) { return (int)(((long long)b * T) / nb); }
-
-// the CTA whose range holds item i
+// first item of CTA b's range, and the CTA whose range holds item i (the largest b with
+// start(b) <= i); b T and (i + 1) nb stay below 2^32 for n <= TRI_MAX_N and nb <= 1024
+__device__ __forceinline__ int tri_item_start(int b, int T, int nb) {
+    return (int)(((unsigned)b * (unsigned)T) / (unsigned)nb);
+}
 __device__ __forceinline__ int tri_item_owner(int i, int T, int nb) {
-    int lo = 0, hi = nb;  // start(lo) <= i < start(hi)
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (tri_item_start(mid, T, nb) <= i) lo = mid;
-        else hi = mid;
-    }
-    return lo;
+    return (int)(((unsigned)(i + 1) * (unsigned)nb - 1u) / (unsigned)T);
 }
 
 template <int CPL>
 __device__ void tri_pass_lower(double2* __restrict__ A, int n, int k, int m, int nb, bool have_prev,
                                const double2* vprev, const double2* wprev, const double2* vcur, double2* pk,
-                               double2* pcol, double2* prow, unsigned* arrive, double2* colred, int& last_sh,
-                               const int* items, int C, double& dacc, double* cdot) {
+                               double2* prow, double2* colred, const int* items, int C, double& dacc) {
     constexpr int W = 32 * CPL;
     constexpr int LD = TRI_MAX_CPL * 32;  // colred row stride
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -750,9 +741,7 @@ __device__ void tri_pass_lower(double2* __restrict__ A, int n, int k, int m, int
         const int lo_i = max(i0, items[c]), hi_i = min(i1, items[c + 1]);
         const int r0 = c * W + TRL_IB * (lo_i - items[c]);
         const int r1 = min(m, c * W + TRL_IB * (hi_i - items[c]));
-        const int b_first = tri_item_owner(items[c], T, nbe);
-        const int b_last = tri_item_owner(items[c + 1] - 1, T, nbe);
-        const int slot = b - b_first, nslots = b_last - b_first + 1;
+        const int slot = b - tri_item_owner(items[c], T, nbe);
         int il[CPL];
         bool ok[CPL];
         double2 vpi[CPL], wpi[CPL], vci[CPL];
@@ -825,8 +814,8 @@ __device__ void tri_pass_lower(double2* __restrict__ A, int n, int k, int m, int
                 dacc = fma(vj.x, rs.x, fma(vj.y, rs.y, dacc));  // Re(conj(v_j) rs)
             }
         }
-        // column partials of this segment: tree over the warps, then the chunk's last CTA sums the
-        // slots in order
+        // column parts of this segment: tree over the warps; warp 0 writes the slot and adds
+        // Re(conj(v_c) s_c) to this CTA's share of v^dag A v
 #pragma unroll
         for (int q = 0; q < CPL; ++q) colred[warp * LD + q * 32 + lane] = make_double2(accx[q], accy[q]);
         __syncthreads();
@@ -846,36 +835,14 @@ __device__ void tri_pass_lower(double2* __restrict__ A, int n, int k, int m, int
 #pragma unroll
             for (int q = 0; q < CPL; ++q) {
                 const double2 a0 = colred[q * 32 + lane], a1 = colred[LD + q * 32 + lane];
-                if (ok[q]) pk[(long long)slot * n + il[q]] = make_double2(a0.x + a1.x, a0.y + a1.y);
-            }
-            __threadfence();
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            last_sh = atomicAdd(&arrive[c], 1u) == (unsigned)(nslots - 1);
-        }
-        __syncthreads();
-        if (last_sh && warp < CPL) {
-            __threadfence();
-            const int ilq = c * W + warp * 32 + lane;
-            double cd = 0.0;
-            if (ilq < m) {
-                double sx = 0.0, sy = 0.0;
-                for (int s2 = 0; s2 < nslots; ++s2) {
-                    const double2 pp = __ldcg(&pk[(long long)s2 * n + ilq]);
-                    sx += pp.x;
-                    sy += pp.y;
+                const double2 sq = make_double2(a0.x + a1.x, a0.y + a1.y);
+                if (ok[q]) {
+                    pk[(long long)slot * n + il[q]] = sq;
+                    dacc = fma(vci[q].x, sq.x, fma(vci[q].y, sq.y, dacc));  // Re(conj(v_c) s_c)
                 }
-                pcol[ilq] = make_double2(sx, sy);
-                const double2 vq = vcur[ilq];
-                cd = fma(vq.x, sx, vq.y * sy);  // Re(conj(v_c) (column part)_c)
             }
-            cd = warp_sum(cd);
-            if (lane == 0) cdot[c * TRI_MAX_CPL + warp] = cd;
-            if (warp == 0 && lane == 0) arrive[c] = 0u;  // reused two steps later, after four barriers
         }
-        __syncthreads();  // colred and last_sh are reused by the next segment
+        __syncthreads();  // colred is reused by the next segment
     }
 }
 
@@ -888,7 +855,6 @@ __global__ void __launch_bounds__(TRL_THREADS) tridiag_lower(double2* __restrict
     __shared__ double red[33];
     __shared__ double tau_sh, dk_sh, K_sh, a2_sh;
     __shared__ double2 w0_sh;
-    __shared__ int last_sh;
     __shared__ int prefix_sh[TRI_MAX_CHUNKS + 1];
     __shared__ double2 colred[TRL_NW][TRI_MAX_CPL * 32];
     const int nb = (int)gridDim.x;
@@ -947,10 +913,8 @@ __global__ void __launch_bounds__(TRL_THREADS) tridiag_lower(double2* __restrict
             for (int t = threadIdx.x; t < m; t += blockDim.x) H[(long long)k * n + t] = vcur[t];
         // ---- B: trailing pass over the lower triangle, with this CTA's share of v^dag A v
         double2* pk = tb.part + (long long)(k & 1) * nb * n;
-        double2* pcol = tb.pcol + (long long)(k & 1) * n;
         double2* prow = tb.prow + (long long)(k & 1) * TRI_MAX_CHUNKS * n;
         double2* wfin = tb.w + (long long)(k & 1) * n;
-        unsigned* arrive = tb.arrive + (k & 1) * TRI_MAX_CHUNKS;
         const int cpl = m >= 256 ? 2 : 1;
         const int W = 32 * cpl;
         const int C = (m + W - 1) / W;
@@ -963,56 +927,71 @@ __global__ void __launch_bounds__(TRL_THREADS) tridiag_lower(double2* __restrict
         __syncthreads();
         double dacc = 0.0;
         if (cpl == 2)
-            tri_pass_lower<2>(A, n, k, m, nb, have_prev, vprev, wprev, vcur, pk, pcol, prow, arrive, &colred[0][0],
-                              last_sh, prefix_sh, C, dacc, tb.cdot);
+            tri_pass_lower<2>(A, n, k, m, nb, have_prev, vprev, wprev, vcur, pk, prow, &colred[0][0], prefix_sh, C,
+                              dacc);
         else
-            tri_pass_lower<1>(A, n, k, m, nb, have_prev, vprev, wprev, vcur, pk, pcol, prow, arrive, &colred[0][0],
-                              last_sh, prefix_sh, C, dacc, tb.cdot);
+            tri_pass_lower<1>(A, n, k, m, nb, have_prev, vprev, wprev, vcur, pk, prow, &colred[0][0], prefix_sh, C,
+                              dacc);
         dacc = block_sum(dacc, red);
         if (threadIdx.x == 0) tb.dot[b] = dacc;
         if (!grid_sync(bar, (unsigned)nb, epoch++)) return;
-        // ---- K = (tau^2/2) v^dag A v from the partials (one fixed order, the same in every CTA),
-        //      w_0 = p_0 - K v_0 and the next diagonal element; the last warp does this while the
-        //      others start on their slices
+        // ---- K = (tau^2/2) v^dag A v from the CTA partials (one fixed order, the same in every
+        //      CTA), w_0 = p_0 - K v_0 and the next diagonal element; the last warp does this while
+        //      the others start on their slices.  p_0 has no row part and chunk 0's slots in order.
         const bool next = k + 3 < n;
         const double2 v0 = vcur[0];
+        const int T = prefix_sh[C];
+        const int nbe = min(nb, T);
         if (warp == TRL_NW - 1) {
             double sdot = 0.0;
             for (int i = lane; i < nb; i += 32) sdot += __ldcg(&tb.dot[i]);
-            for (int i = lane; i < C * TRI_MAX_CPL; i += 32)
-                if (i % TRI_MAX_CPL < cpl) sdot += __ldcg(&tb.cdot[i]);
             sdot = warp_sum(sdot);
             if (lane == 0) {
                 const double K = 0.5 * tau * tau * sdot;
-                const double2 pc = __ldcg(&pcol[0]), pr = __ldcg(&prow[0]);
-                const double2 p0 = make_double2(tau * (pc.x + pr.x), tau * (pc.y + pr.y));
-                const double2 w0 = make_double2(fma(-K, v0.x, p0.x), fma(-K, v0.y, p0.y));
+                const int ns0 = tri_item_owner(prefix_sh[1] - 1, T, nbe) + 1;  // slots of chunk 0
+                double px = 0.0, py = 0.0;
+                for (int s2 = 0; s2 < ns0; ++s2) {
+                    const double2 q = __ldcg(&pk[(long long)s2 * n]);
+                    px += q.x;
+                    py += q.y;
+                }
+                const double2 w0 = make_double2(fma(-K, v0.x, tau * px), fma(-K, v0.y, tau * py));
                 K_sh = K;
                 w0_sh = w0;
                 if (next)
                     dk_sh = __ldcg(&A[(long long)(k + 1) * n + (k + 1)]).x - 2.0 * (v0.x * w0.x + v0.y * w0.y);
             }
         }
-        // ---- slices of 32 rows over the CTAs: p = tau (column part + row parts of chunks
-        //      0 .. row/W), warp u summing chunks u, u + NW, ..., then the warps in order; w = p - K v;
-        //      column k+1 with step k's update (A[j][k+1] -= v_j conj(w_0) + w_j conj(v_0): the
-        //      conjugate of row k+1, i.e. the next reflector's x) and its partial squared norm
+        // ---- slices of 32 rows over the CTAs: p = tau (column parts of the CTA slots of the row's
+        //      chunk + row parts of chunks 0 .. row/W); warp u sums slots and chunks u, u + NW, ...,
+        //      then warp 0 adds the warps in order; w = p - K v; column k+1 with step k's update
+        //      (A[j][k+1] -= v_j conj(w_0) + w_j conj(v_0): the conjugate of row k+1, i.e. the next
+        //      reflector's x) and its partial squared norm
         double a2p = 0.0;
         for (int blk = b; blk * 32 < m; blk += nb) {
             const int il = blk * 32 + lane;
             const int cl = (blk * 32) / W;  // the same for the 32 rows (W is a multiple of 32)
+            const int s_first = tri_item_owner(prefix_sh[cl], T, nbe);
+            const int nsl = tri_item_owner(prefix_sh[cl + 1] - 1, T, nbe) - s_first + 1;
+            double2 xa = make_double2(0.0, 0.0);
+            if (warp == 0 && next && il >= 1 && il < m) xa = __ldcg(&A[(long long)(k + 1 + il) * n + (k + 1)]);
             double sx = 0.0, sy = 0.0;
-            if (il < m)
+            if (il < m) {
+                for (int s2 = warp; s2 < nsl; s2 += TRL_NW) {
+                    const double2 r = __ldcg(&pk[(long long)s2 * n + il]);
+                    sx += r.x;
+                    sy += r.y;
+                }
                 for (int c = warp; c <= cl; c += TRL_NW) {
                     const double2 r = __ldcg(&prow[(long long)c * n + il]);
                     sx += r.x;
                     sy += r.y;
                 }
+            }
             colred[warp][lane] = make_double2(sx, sy);
             __syncthreads();
             if (warp == 0 && il < m) {
-                const double2 pc = __ldcg(&pcol[il]);
-                double tx = pc.x, ty = pc.y;
+                double tx = 0.0, ty = 0.0;
 #pragma unroll
                 for (int u = 0; u < TRL_NW; ++u) {
                     tx += colred[u][lane].x;
@@ -1024,8 +1003,7 @@ __global__ void __launch_bounds__(TRL_THREADS) tridiag_lower(double2* __restrict
                 const double2 w = make_double2(fma(-K, v.x, tau * tx), fma(-K, v.y, tau * ty));
                 wfin[il] = w;
                 if (next && il >= 1) {
-                    double2 x = __ldcg(&A[(long long)(k + 1 + il) * n + (k + 1)]);
-                    x = sub_two_cmulc(x, v, w0, w, v0);
+                    const double2 x = sub_two_cmulc(xa, v, w0, w, v0);
                     tb.x[il - 1] = x;
                     a2p = fma(x.x, x.x, fma(x.y, x.y, a2p));
                 }
@@ -1718,22 +1696,16 @@ TruncResult truncate_dev(Ctx& ctx, int chi_l, int d1, int d2, int chi_r, int dir
         const int grid = std::min(ctx.num_sms, std::max(1, (n + 3) / 4));
         if (per_sm >= 1 && grid >= 1) {
             const size_t part_n = (size_t)grid * n;
-            const size_t elems = 2 * part_n + 2 * (size_t)n + 2 * (size_t)TRI_MAX_CHUNKS * n + 3 * (size_t)n;
+            const size_t elems = 2 * part_n + 2 * (size_t)TRI_MAX_CHUNKS * n + 3 * (size_t)n;
             const size_t bytes = sizeof(double2) * elems;
-            const size_t dbl = 2 * (size_t)grid + (size_t)TRI_MAX_CHUNKS * TRI_MAX_CPL;
-            char* wsp = (char*)ctx.workspace(WS_EIG_PART,
-                                             bytes + sizeof(double) * dbl + sizeof(unsigned) * 2 * TRI_MAX_CHUNKS);
+            char* wsp = (char*)ctx.workspace(WS_EIG_PART, bytes + sizeof(double) * 2 * (size_t)grid);
             TriBufsL tb;
             tb.part = (double2*)wsp;
-            tb.pcol = tb.part + 2 * part_n;
-            tb.prow = tb.pcol + 2 * (size_t)n;
+            tb.prow = tb.part + 2 * part_n;
             tb.w = tb.prow + 2 * (size_t)TRI_MAX_CHUNKS * n;
             tb.x = tb.w + 2 * (size_t)n;
             tb.dot = (double*)(wsp + bytes);
             tb.a2 = tb.dot + grid;
-            tb.cdot = tb.a2 + grid;
-            tb.arrive = (unsigned*)(wsp + bytes + sizeof(double) * dbl);
-            VTN_CUDA_TRY(cudaMemsetAsync(tb.arrive, 0, sizeof(unsigned) * 2 * TRI_MAX_CHUNKS, ctx.stream));
             GridBar* bar = (GridBar*)(status + 4);
             VTN_CUDA_TRY(cudaMemsetAsync(bar, 0, sizeof(GridBar), ctx.stream));
             double2* Ap = A;
