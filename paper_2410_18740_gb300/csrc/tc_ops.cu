@@ -127,6 +127,59 @@ __global__ void __launch_bounds__(256) pack_kernel(const T* __restrict__ X, Pack
     }
 }
 
+// The A operand when the source rows run along kk (not conjugated, rows not blocked): row r of
+// chunk c is K contiguous elements at X + c s_kb + r ld.  Each thread packs four consecutive kk
+// of one row (blockIdx.y) with 16-byte loads and writes each of the four output streams as one
+// 8-byte store; the values are those of pack_kernel.  Needs K % 4 == 0, even ld and s_kb, and a
+// 16-byte aligned X.
+template <typename T>
+__device__ __forceinline__ void load4(const T* src, T v[4]);
+template <>
+__device__ __forceinline__ void load4<float2>(const float2* src, float2 v[4]) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(src));
+    const float4 b = __ldg(reinterpret_cast<const float4*>(src) + 1);
+    v[0] = make_float2(a.x, a.y);
+    v[1] = make_float2(a.z, a.w);
+    v[2] = make_float2(b.x, b.y);
+    v[3] = make_float2(b.z, b.w);
+}
+template <>
+__device__ __forceinline__ void load4<double2>(const double2* src, double2 v[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = __ldg(src + i);
+}
+
+__device__ __forceinline__ uint2 bf16x4(__nv_bfloat16 a, __nv_bfloat16 b, __nv_bfloat16 c, __nv_bfloat16 d) {
+    uint2 u;
+    u.x = (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+    u.y = (uint32_t)__bfloat16_as_ushort(c) | ((uint32_t)__bfloat16_as_ushort(d) << 16);
+    return u;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) pack_rows4_kernel(const T* __restrict__ X, PackP p) {
+    const int Kt = p.K * p.kb;
+    const int kk = (int)(blockIdx.x * 256 + threadIdx.x) * 4;
+    const int r = (int)blockIdx.y;
+    if (kk >= Kt) return;
+    const int c = kk / p.K, k = kk - c * p.K;
+    T v[4];
+    load4<T>(X + (long long)c * p.s_kb + (long long)r * p.ld + k, v);
+    __nv_bfloat16 rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        CplxTraits<T>::split(v[i].x, rh[i], rl[i]);
+        CplxTraits<T>::split(v[i].y, ih[i], il[i]);
+    }
+    // row m: [Re a, Im a] hi | lo
+    __nv_bfloat16* o = p.out + (long long)r * p.ldo;
+    const long long H = p.half;
+    *reinterpret_cast<uint2*>(o + kk) = bf16x4(rh[0], rh[1], rh[2], rh[3]);
+    *reinterpret_cast<uint2*>(o + Kt + kk) = bf16x4(ih[0], ih[1], ih[2], ih[3]);
+    *reinterpret_cast<uint2*>(o + H + kk) = bf16x4(rl[0], rl[1], rl[2], rl[3]);
+    *reinterpret_cast<uint2*>(o + H + Kt + kk) = bf16x4(il[0], il[1], il[2], il[3]);
+}
+
 __global__ void zero_pad_kernel(__nv_bfloat16* out, long long ldo, int rows, int from, int to) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int w = to - from;
@@ -408,9 +461,16 @@ void pack_impl(Ctx& ctx, const T* X, int rows, int K, int kb, long long ld, long
     p.out = out;
     p.ldo = ldo;
     p.half = ldo / 2;
-    dim3 grid((unsigned)((Kt + 31) / 32), (unsigned)((rows + 31) / 32));
-    VTN_REQUIRE(grid.y <= 65535, "pack: too many rows");
-    pack_kernel<T><<<grid, dim3(32, 8), 0, ctx.stream>>>(X, p);
+    const bool rows4 = !is_b && !conj_t && rq == 0 && K % 4 == 0 && ld % 2 == 0 && s_kb % 2 == 0 && rows <= 65535 &&
+                       Kt <= (1LL << 30) && ((uintptr_t)X & 15) == 0 && ((uintptr_t)out & 7) == 0;
+    if (rows4) {
+        dim3 grid((unsigned)((Kt / 4 + 255) / 256), (unsigned)rows);
+        pack_rows4_kernel<T><<<grid, 256, 0, ctx.stream>>>(X, p);
+    } else {
+        dim3 grid((unsigned)((Kt + 31) / 32), (unsigned)((rows + 31) / 32));
+        VTN_REQUIRE(grid.y <= 65535, "pack: too many rows");
+        pack_kernel<T><<<grid, dim3(32, 8), 0, ctx.stream>>>(X, p);
+    }
     const int orows = is_b ? 2 * rows : rows;
     const int from = (int)(2 * Kt), to = (int)(ldo / 2);
     if (to > from) {
@@ -421,7 +481,7 @@ void pack_impl(Ctx& ctx, const T* X, int rows, int K, int kb, long long ld, long
         ctx.count_launch(2);
     }
     ctx.count_launch();
-    ctx.check_launch("pack_kernel");
+    ctx.check_launch(rows4 ? "pack_rows4_kernel" : "pack_kernel");
 }
 
 }  // namespace
