@@ -108,7 +108,7 @@ def parse():
                    help="also measure the optional warm-started truncation with this many subspace iterations "
                         "(trunc: beside the exact one; time-to-eps: a mixed run with it)")
     p.add_argument("--tri-min-n", type=int, default=None,
-                   help="trunc case: the lower-triangle tridiagonalisation from this n on (default 2048)")
+                   help="trunc case: the lower-triangle tridiagonalisation from this n on (default 1200)")
     p.add_argument("--heff-form", type=int, default=0, choices=[0, 1, 2],
                    help="split-precision H_eff psi: 0 = term form where it is the cheaper form (default), "
                         "1 = channel-mixing form, 2 = term form wherever the bond has one")

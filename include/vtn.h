@@ -571,9 +571,10 @@ vtn_status vtn_set_tc_accumulation(vtn_ctx ctx, int env_kblocks, int heff_kblock
 /* Form of the truncation's Householder tridiagonalisation (one persistent cooperative kernel
  * either way): for n >= min_n the kernel keeps only the lower triangle of the trailing matrix up
  * to date (8 instead of 12 FP64 multiply-adds per element and column, two grid barriers per
- * column instead of one), below it the full matrix.  Default 2048 (measured: 230 against 270 ms
- * at n = 3072, equal at 2048, 27 against 22 ms at 1024); 0 = always the lower form, above 4096 =
- * never.  Per context; results agree to rounding. */
+ * column instead of one), below it the full matrix.  Default 1200 (measured, lower against full:
+ * 207 against 270 ms at n = 3072, 81 against 94 at 2048, 46 against 49 at 1536, 23.6 against
+ * 22.0 at 1024); 0 = always the lower form, above 4096 = never.  Per context; results agree to
+ * rounding. */
 vtn_status vtn_set_tridiag_lower(vtn_ctx ctx, int min_n);
 
 /* Turn per-kernel device timing (CUDA events on the context stream) on or off and read

@@ -104,7 +104,7 @@ struct Ctx {
     // (their errors accumulate along the chain) and H_eff psi
     int tc_kb_env = 64, tc_kb_heff = 256;
     // the truncation's tridiagonalisation keeps only the lower triangle up to date for n >= this
-    int tri_lower_min_n = 2048;
+    int tri_lower_min_n = 1200;
     struct Tc {
         long long launches = 0;
         double flops = 0, seconds = 0;

@@ -739,7 +739,7 @@ def vtn_set_tc_accumulation(ctx, env_kblocks=64, heff_kblocks=256):
     _check(ctx, lib().vtn_set_tc_accumulation(ctx, int(env_kblocks), int(heff_kblocks)))
 
 
-def vtn_set_tridiag_lower(ctx, min_n=2048):
+def vtn_set_tridiag_lower(ctx, min_n=1200):
     _check(ctx, lib().vtn_set_tridiag_lower(ctx, int(min_n)))
 
 

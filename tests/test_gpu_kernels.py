@@ -107,7 +107,7 @@ TRUNC_CASES = [
 @pytest.mark.parametrize("tri_form", ["full", "lower"])
 @pytest.mark.parametrize("cl,d1,d2,cr,direction,kmax", TRUNC_CASES + [(48, 6, 6, 50, 0, 64), (50, 6, 6, 48, 1, 64)])
 def test_truncation_matches_oracle(ctx, cl, d1, d2, cr, direction, kmax, tri_form):
-    """Both forms of the tridiagonalisation (the lower-triangle one normally runs from n = 2048);
+    """Both forms of the tridiagonalisation (the lower-triangle one normally runs from n = 1200);
     n = 288 and 300 take its two-column-per-lane chunks."""
     vtn.vtn_set_tridiag_lower(ctx, 0 if tri_form == "lower" else 1 << 30)
     rng = inputs.rng_for(3000 + cl * 31 + cr + direction)
