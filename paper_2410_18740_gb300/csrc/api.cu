@@ -55,6 +55,18 @@ void free_mpo_device(Ctx& c, vtn_mpo mpo) {
     for (auto& bt : mpo->bterms) free_bond_terms(c, bt);
 }
 
+// Device term form of bond s, built on its first use: the host factorisation and upload take a
+// couple of milliseconds a bond, so a windowed sweep pays only for the bonds it visits.  Not
+// thread-safe: callers that share an MPO between threads build every bond first.
+const BondTerms& mpo_bond_terms(Ctx& c, vtn_mpo mpo, int s) {
+    BondTerms& bt = mpo->bterms[s];
+    if (!bt.built) {
+        build_bond_terms(c, mpo->hp.cores[s], mpo->hp.cores[s + 1], bt);
+        bt.built = true;
+    }
+    return bt;
+}
+
 void ensure_mpo_device(vtn_ctx ctx, vtn_mpo mpo) {
     VTN_REQUIRE(mpo != nullptr, "null MPO");
     if (!mpo->dcores.empty()) {
@@ -64,8 +76,7 @@ void ensure_mpo_device(vtn_ctx ctx, vtn_mpo mpo) {
     Ctx& c = ctx->c;
     mpo->dcores.resize(mpo->hp.M);
     for (int s = 0; s < mpo->hp.M; ++s) upload_core(c, mpo->hp.cores[s], mpo->dcores[s]);
-    mpo->bterms.resize(std::max(mpo->hp.M - 1, 0));
-    for (int s = 0; s + 1 < mpo->hp.M; ++s) build_bond_terms(c, mpo->hp.cores[s], mpo->hp.cores[s + 1], mpo->bterms[s]);
+    mpo->bterms.resize(std::max(mpo->hp.M - 1, 0));  // built on first use (mpo_bond_terms)
     const size_t iso_bytes = sizeof(double2) * mpo->hp.iso.size();
     mpo->iso_dev = (double2*)c.dalloc(iso_bytes);
     VTN_CUDA_TRY(cudaMemcpyAsync(mpo->iso_dev, mpo->hp.iso.data(), iso_bytes, cudaMemcpyHostToDevice, c.stream));
@@ -878,7 +889,7 @@ vtn_status sweep_body(vtn_ctx work, vtn_ctx owner, vtn_mpo mpo, vtn_mps* state, 
     // term form of bond i's H_eff (split precision), or null for the channel-mixing form
     auto bond_terms = [&](int i) -> const BondTerms* {
         if (opts->heff_form == 1 || i < 0 || i >= (int)mpo->bterms.size()) return nullptr;
-        const BondTerms& bt = mpo->bterms[i];
+        const BondTerms& bt = mpo_bond_terms(c, mpo, i);
         if (!bt.usable || (opts->heff_form == 0 && !bt.worthwhile)) return nullptr;
         return &bt;
     };
@@ -1094,6 +1105,8 @@ vtn_status vtn_sweep_batch(vtn_ctx ctx, int n, const vtn_mpo* mpos, vtn_mps* sta
         for (int j = 0; j < n; ++j) {
             VTN_REQUIRE(mpos[j] != nullptr, "null MPO in the batch");
             ensure_mpo_device(ctx, mpos[j]);
+            // the workers may share an MPO: its bonds' term forms are built here, not on first use
+            for (int s = 0; s + 1 < mpos[j]->hp.M; ++s) mpo_bond_terms(c, mpos[j], s);
             if (states[j] == nullptr) {
                 std::vector<int> sched;
                 for (int i = 0; i < opts[j].n_schedule && opts[j].chi_schedule; ++i)

@@ -232,6 +232,7 @@ bool channel_gemm_f32(Ctx& ctx, int w_in, int w_out, long long E, const float2* 
 // coefficient matrices K_op = W_i^(o) W_{i+1}^(p) are factorised exactly.  The first n_id terms
 // have o = p = 0 (identity operators); kron holds B_o and B'_p for the others.
 struct BondTerms {
+    bool built = false;       // set by the owner once build_bond_terms has run for the bond
     bool usable = false;      // false: no compact term form (the bond keeps the channel-mixing form)
     bool worthwhile = false;  // the term form is the cheaper one for this bond
     int wl = 0, wr = 0, d = 0, n_t = 0, n_id = 0;
