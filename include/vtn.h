@@ -161,7 +161,9 @@ vtn_status vtn_mpo_core(vtn_mpo mpo, int site, int* nnz, int* rows, int* cols, d
  * w[bond]], V complex[n_terms w[bond+2]], Bi complex[ri d d], Bj complex[rj d d] (row = output
  * level).  *usable = 1: the sweeps use the term form at this bond; 2: the bond has one, but with
  * more than 1.15 max(w_l, w_r) + 4 terms the channel-mixing form is cheaper and is used; 0 (and
- * n_terms = 0): no compact term form (an operator basis of 16 or more elements, or d > 8). */
+ * n_terms = 0): no compact term form (an operator basis of 16 or more elements, or d > 8).  A
+ * sweep factorises and uploads a bond's term form on the bond's first split-precision use (a few
+ * milliseconds of host work a bond); vtn_sweep_batch does so for every bond before it starts. */
 vtn_status vtn_mpo_bond_terms(vtn_mpo mpo, int bond, int* usable, int* n_terms, int* n_id, int* ri, int* rj,
                               int* ops, double* U, double* V, double* Bi, double* Bj);
 /* Deterministic bound ||P H P|| <= lambda_max(G) M (2d - 1), used to scale tolerances. */
